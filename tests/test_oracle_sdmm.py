@@ -1,0 +1,209 @@
+"""Pins for the oracle's prox operators, projections, CG and SDMM (CPU only).
+
+The closed forms are checked against their defining variational properties;
+CG against a dense direct solve; SDMM's converged point against the
+Karush-Kuhn-Tucker conditions and Fenchel duality of problem (3) (Sec. 1,
+Eq. 3), and against an independent Chambolle-Pock solve.
+"""
+import numpy as np
+import pytest
+import scipy.stats
+
+from oracle import nufft as nf
+from oracle import primal_dual, sdmm, wavelets
+from paper_1502_05037_gb300 import synth
+
+
+# ------------------------------------------------------------ prox / proj
+def test_soft_threshold_closed_form_and_tie():
+    v = np.array([-3.0, -1.0, -0.5, 0.0, 0.5, 1.0, 2.5])
+    s = sdmm.soft_threshold(v, 1.0)
+    assert np.array_equal(s, [-2.0, 0.0, 0.0, 0.0, 0.0, 0.0, 1.5])
+
+
+def test_soft_threshold_is_prox_of_weighted_l1():
+    # s minimises 0.5 (s - v)^2 + t |s| elementwise: check against a fine scan
+    g = np.random.default_rng(0)
+    v = g.standard_normal(50) * 2
+    t = np.abs(g.standard_normal(50))
+    s = sdmm.soft_threshold(v, t)
+    grid = np.linspace(-8, 8, 160001)
+    for vi, ti, si in zip(v, t, s):
+        obj = 0.5 * (grid - vi) ** 2 + ti * np.abs(grid)
+        assert abs(grid[np.argmin(obj)] - si) <= 2e-4
+
+
+def test_moreau_decomposition():
+    # v = prox_{t|.|}(v) + t * proj_{[-1,1]}(v / t)
+    g = np.random.default_rng(1)
+    v = g.standard_normal(1000) * 3
+    t = 0.7
+    assert np.allclose(sdmm.soft_threshold(v, t) + t * np.clip(v / t, -1, 1), v, atol=1e-14)
+
+
+def test_projection_properties():
+    g = np.random.default_rng(2)
+    c = g.standard_normal(40) + 1j * g.standard_normal(40)
+    eps = 1.5
+    inside = c + 0.1 * (g.standard_normal(40) + 1j * g.standard_normal(40)) / 10
+    assert np.array_equal(sdmm.proj_l2_ball(inside, c, eps), inside)
+    out = c + 5 * (g.standard_normal(40) + 1j * g.standard_normal(40))
+    p = sdmm.proj_l2_ball(out, c, eps)
+    assert abs(np.linalg.norm(p - c) - eps) < 1e-12
+    assert np.allclose(sdmm.proj_l2_ball(p, c, eps), p, atol=1e-14)
+    # variational inequality Re <out - p, s - p> <= 0 for points s in the ball
+    for _ in range(50):
+        d = g.standard_normal(40) + 1j * g.standard_normal(40)
+        s = c + d / np.linalg.norm(d) * eps * g.uniform()
+        assert np.real(np.vdot(out - p, s - p)) <= 1e-10
+    assert np.array_equal(sdmm.proj_l2_ball(c, c, 0.0), c)
+
+
+def test_positive_projection():
+    v = np.array([-1.0, 0.0, 2.0])
+    assert np.array_equal(sdmm.proj_positive(v), [0.0, 0.0, 2.0])
+
+
+def test_epsilon_is_chi2_mean_plus_two_std():
+    # (2/sigma^2) eps^2 = 2M + 4 sqrt(M): the chi^2_{2M} mean plus two std
+    sigma = 0.3
+    for M in (10, 1000, 100000):
+        e = sdmm.epsilon_chi2(sigma, np.array([M]))[0]
+        k = 2 * M
+        assert abs(2 * e * e / sigma ** 2 - (scipy.stats.chi2.mean(k) + 2 * scipy.stats.chi2.std(k))) < 1e-6 * k
+
+
+def test_epsilon_bounds_noise_norm_usually():
+    sigma = 0.2
+    sizes = np.array([500] * 200)
+    eps = sdmm.epsilon_chi2(sigma, sizes)
+    hits = 0
+    for i in range(200):
+        n = sigma * synth.unit_noise(500, 10 + i)
+        hits += np.linalg.norm(n) <= eps[i]
+    assert hits >= 180  # ~97.7% expected
+
+
+# -------------------------------------------------------------------- CG
+def _tiny_problem(n=8, M=80, R=2, J=4, levels=2, mask=0b111, seed=3):
+    x = synth.sky(n, n, seed, n_points=4, n_blobs=1)
+    u, v = synth.uv_coverage(M, seed + 1, sigma=1.2)
+    p = nf.NufftPlan(n, n, u, v, J)
+    y0 = nf.phi(p, x)
+    s = sdmm.noise_sigma(y0, 30.0)
+    offs = synth.block_offsets(synth.block_sizes(M, R, seed + 2))
+    y = y0 + s * synth.unit_noise(M, seed + 3)
+    eps = sdmm.epsilon_chi2(s, np.diff(offs))
+    return sdmm.Problem(p, levels, y, offs, eps, mask=mask), x
+
+
+def test_cg_matches_dense_solve():
+    n = 16
+    u, v = synth.uv_coverage(300, 11, sigma=1.0)
+    p = nf.NufftPlan(n, n, u, v, 4)
+    A = nf.phi_matrix(p)
+    nu2 = nf.power_norm_sq(p, iters=200)
+    Ad = 2 * np.eye(n * n) + np.real(A.conj().T @ A) / nu2
+    b = np.random.default_rng(12).standard_normal(n * n)
+    want = np.linalg.solve(Ad, b)
+    apply = lambda x: (Ad @ x.ravel()).reshape(x.shape)
+    got, done, res = sdmm.cg(apply, b.reshape(n, n), np.zeros((n, n)), 200, 1e-14)
+    assert np.linalg.norm(got.ravel() - want) <= 1e-12 * np.linalg.norm(want)
+    # the operator form the solver uses is the same matrix
+    prob_A = lambda x: 2 * x + np.real(nf.phi_adj(p, nf.phi(p, x))) / nu2
+    xr = np.random.default_rng(13).standard_normal((n, n))
+    assert np.allclose(prob_A(xr).ravel(), Ad @ xr.ravel(), atol=1e-10)
+
+
+def test_cg_fixed_iterations_and_zero_residual():
+    apply = lambda x: 3.0 * x
+    b = np.ones(5)
+    x, done, res = sdmm.cg(apply, b, b / 3.0, 10)
+    assert done == 0 and res == 0.0
+    x, done, res = sdmm.cg(apply, b, np.zeros(5), 1)
+    assert done == 1 and np.allclose(x, b / 3.0)
+
+
+# ------------------------------------------------------------------ SDMM
+def _dual_certificate(prob, st):
+    """Fenchel dual value and feasibility residual from SDMM's multipliers
+    u_j = z_j / gamma (problem (3) in its normalised form)."""
+    g = prob.gamma
+    u1, u2, u3 = st.z1 / g, st.z2 / g, st.z3 / g
+    yn = prob.y / prob.nu
+    dual = 0.0
+    for i in range(prob.R):
+        a, b = prob.offsets[i], prob.offsets[i + 1]
+        dual -= np.real(np.vdot(u2[a:b], yn[a:b])) + prob.eps[i] / prob.nu * np.linalg.norm(u2[a:b])
+    feas = prob.psi(u1) + prob.phi_n_adj_re(u2) + u3
+    return dual, u1, u3, np.linalg.norm(feas) / np.linalg.norm(prob.psi(u1))
+
+
+@pytest.fixture(scope="module")
+def converged():
+    prob, x_true = _tiny_problem()
+    prob.gamma *= 10.0   # any gamma > 0 converges; this one converges fast here
+    st = sdmm.sdmm_solve(prob, np.zeros((8, 8)), 700, 30, 1e-12)
+    return prob, st, x_true
+
+
+def test_sdmm_kkt_and_duality_gap(converged):
+    prob, st, _ = converged
+    primal = sdmm.objective(prob, st.x)
+    dual, u1, u3, feas = _dual_certificate(prob, st)
+    assert np.all(np.abs(u1) <= 1 + 1e-9)            # u1 in the subdifferential box
+    assert np.all(u3 <= 1e-12)                         # normal cone of R_+
+    assert np.all(np.abs(u3[st.x > 1e-8]) <= 1e-6 * np.abs(u3).max() + 1e-12)
+    assert feas <= 1e-7                                # sum_j L_j^T u_j = 0
+    assert abs(primal - dual) <= 1e-9 * primal         # strong duality
+    ratios = sdmm.residual_ratios(prob, st.x)
+    assert np.all(ratios <= 1 + 1e-8)                  # constraints of Eq. 3
+    assert st.x.min() >= -1e-8                         # positive orthant
+
+
+def test_sdmm_objective_matches_chambolle_pock(converged):
+    prob, st, _ = converged
+    xc = primal_dual.chambolle_pock(prob, 6000, tau=0.05, sigma=9.8)
+    oc, os_ = sdmm.objective(prob, xc), sdmm.objective(prob, st.x)
+    assert abs(oc - os_) <= 1e-5 * os_
+    assert np.all(sdmm.residual_ratios(prob, xc) <= 1 + 1e-3)
+    assert np.linalg.norm(xc - st.x) <= 1e-2 * np.linalg.norm(st.x)
+
+
+def test_sdmm_first_iteration_from_zero_by_hand():
+    # from x = 0, z = 0: s1 = 0, s3 = 0 and s2 = projection of 0 onto each
+    # ball, z2 = -s2, so the CG right-hand side is Re Phi^H (s2 - z2) / nu
+    # = 2 Re Phi^H s2 / nu
+    prob, _ = _tiny_problem(R=1)
+    st = sdmm.init_state(prob, np.zeros((8, 8)))
+    sdmm.sdmm_iteration(prob, st, 50, 1e-14)
+    yn = prob.y / prob.nu
+    en = prob.eps[0] / prob.nu
+    s2 = yn - yn * (en / np.linalg.norm(yn))        # centre + r eps/||r||, r = -yn
+    b = prob.phi_n_adj_re(2.0 * s2)
+    want, _, _ = sdmm.cg(prob.apply_A, b, np.zeros((8, 8)), 200, 1e-14)
+    assert np.allclose(st.x, want, atol=1e-10 * np.abs(want).max())
+    assert np.allclose(st.z2, -s2, atol=1e-14)
+
+
+def test_reweight_formula():
+    prob, x = _tiny_problem()
+    c = prob.psi_adj(x)
+    w = sdmm.reweight(prob, x, 0.1)
+    assert w.shape == c.shape
+    assert np.all(w > 0) and np.all(w <= 1)
+    assert np.allclose(w * (0.1 + np.abs(c)), 0.1)
+
+
+def test_sara_reweighting_keeps_feasibility():
+    prob, x_true = _tiny_problem(seed=21)
+    x, rhos = sdmm.sara(prob, np.zeros((8, 8)), 300, passes=2, cg_iters=20)
+    assert len(rhos) == 2 and rhos[1] == rhos[0] / 2
+    assert np.all(sdmm.residual_ratios(prob, x) <= 1.01)
+    assert x.min() >= -1e-6
+
+
+def test_block_offsets_partition():
+    for M, R, seed in ((100, 7, 1), (655360, 8, 4001), (50, 50, 2)):
+        s = synth.block_sizes(M, R, seed)
+        assert s.sum() == M and s.min() >= 1 and s.size == R
