@@ -1,0 +1,192 @@
+/*
+ * purify.h - C ABI of the GB300 SARA/SDMM imaging library.
+ *
+ * The library computes the hot path of "Why CLEAN when you can PURIFY?"
+ * (Carrillo, McEwen, Wiaux; arXiv:1502.05037): the measurement operator of
+ * the discretised measurement equation y = Phi x + n (Sec. 1), the SARA
+ * dictionary Psi = [Psi_1, ..., Psi_q] and its adjoint (Sec. 1), and the SDMM
+ * solve of the block-constrained weighted-l1 problem (3) with SARA
+ * reweighting (Sec. 1, Eqs. 1-3).
+ *
+ * Conventions for every call:
+ *  - Array arguments are caller-owned and may live on the device (any CUDA
+ *    device pointer) or, where stated, on the host; the library detects which.
+ *    The plan owns only its internal tables and workspaces.
+ *  - Real arrays hold `dtype` values (float or double). "Complex" arrays hold
+ *    interleaved (re, im) pairs of `dtype`.
+ *  - Images are [ny][nx] row-major; pixel (i, j) sits at centred coordinates
+ *    (j - nx/2, i - ny/2); u pairs with the column index, v with the row index.
+ *  - Coefficient arrays are [q][ny][nx]: plane 0 is the Dirac basis, the next
+ *    planes are db_p wavelets in increasing p among those selected by the
+ *    basis mask, each in Mallat packing (coarsest low-pass band top-left).
+ *  - Visibility arrays are in the caller's order; blocks are the contiguous
+ *    ranges [block_offsets[i], block_offsets[i+1]) of Eq. 2.
+ *  - Calls are asynchronous on the plan's stream unless stated otherwise.
+ *    No exception crosses the ABI: every call returns a purify_status and, on
+ *    failure, leaves a message for purify_last_error() (thread-local).
+ *  - A plan is not thread-safe; use one plan per host thread and stream.
+ */
+#ifndef PURIFY_H
+#define PURIFY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct purify_plan purify_plan;
+
+typedef enum {
+    PURIFY_OK = 0,
+    PURIFY_EINVAL = 1,    /* bad argument; detected before any launch */
+    PURIFY_ENOMEM = 2,    /* device or host allocation failed */
+    PURIFY_ECUDA = 3,     /* a CUDA runtime call failed */
+    PURIFY_ETIMEOUT = 4,  /* a bounded device-side wait gave up */
+    PURIFY_ENOTCONV = 5,  /* tolerance not reached within the iteration cap */
+    PURIFY_ENAN = 6       /* non-finite value met in the data or iterates */
+} purify_status;
+
+typedef enum { PURIFY_F32 = 0, PURIFY_F64 = 1 } purify_dtype;
+
+/* Plan description. Sec. 1 leaves the discretisation of Phi open; the plan
+ * realises Phi = G F Z S (Kaiser-Bessel gridding): S the gridding correction,
+ * Z zero-padding to the K = oversample * n grid, F the unnormalised 2-D DFT,
+ * G interpolation with a J-tap separable Kaiser-Bessel kernel
+ * g(t) = I0(beta sqrt(1 - (2t/J)^2)), kappa = u K / (2 pi), taps
+ * k_a = floor(kappa - J/2) + 1 + a. */
+typedef struct {
+    int32_t nx, ny;                /* image size: powers of two, 8..4096, >= 2^levels */
+    int64_t M;                     /* number of visibilities, 1 <= M < 2^31 */
+    const void *u, *v;             /* M coordinates each (dtype), radians/pixel in
+                                      [-pi, pi); host or device; copied at create */
+    int32_t R;                     /* number of blocks (Eq. 2), 1 <= R <= M */
+    const int64_t *block_offsets;  /* HOST array of R + 1 offsets, 0 = first < ... < last = M;
+                                      NULL with R = 1 means one block */
+    int32_t kb_width;              /* J, 2..8 */
+    double oversample;             /* alpha; 0 => 2. Must make alpha*n a power of two */
+    double kb_beta;                /* 0 => 2.34 J */
+    int32_t levels;                /* wavelet levels L, 1..8 */
+    uint32_t basis_mask;           /* bit 0 Dirac, bit p db_p (p = 1..8); 0 => 0x1FF (q = 9) */
+    purify_dtype dtype;            /* operator precision */
+    void *stream;                  /* cudaStream_t; NULL = legacy default stream */
+    int32_t tile;                  /* gridding tile edge (power of two, 8..64); 0 => autotune */
+} purify_plan_desc;
+
+/* Build a plan: validates the description, computes the correction, kernel,
+ * twiddle and Daubechies filter tables on the host, sorts the visibilities
+ * by block then grid tile, and allocates workspaces. Synchronous.
+ * Errors: EINVAL (description), ENOMEM, ECUDA. */
+purify_status purify_plan_create(const purify_plan_desc *desc, purify_plan **out);
+
+/* Release a plan and everything it owns (synchronises its stream). NULL is a no-op. */
+purify_status purify_plan_destroy(purify_plan *plan);
+
+/* Change the stream later calls are issued on. */
+purify_status purify_plan_set_stream(purify_plan *plan, void *stream);
+
+/* Sizes of the plan: K (grid edge per axis), q, D = q nx ny, and the gridding tile. */
+typedef struct {
+    int32_t Kx, Ky, q, tile;
+    int64_t N, D, M;
+    int32_t R, J, levels;
+    double beta;
+    int64_t workspace_bytes;
+} purify_plan_info;
+purify_status purify_plan_get_info(const purify_plan *plan, purify_plan_info *info);
+
+/* y = Phi x (Sec. 1, measurement equation without noise): x real [ny][nx],
+ * y complex [M] in caller order. */
+purify_status purify_phi(purify_plan *plan, const void *x, void *y);
+
+/* x = Phi^dagger y = S Z^T F^H G^H y, the adjoint of purify_phi on complex
+ * images: y complex [M] caller order, x complex [ny][nx]. */
+purify_status purify_phi_adj(purify_plan *plan, const void *y, void *x);
+
+/* F of Phi = G F Z S alone: in-place unnormalised 2-D DFT of a complex
+ * [Ky][Kx] grid; inverse != 0 applies F^H (the +i sign, no 1/K^2 factor). */
+purify_status purify_fft2(purify_plan *plan, void *grid, int32_t inverse);
+
+/* x = Psi c = sum_j Psi_j c_j / sqrt(q) (Sec. 1, SARA dictionary):
+ * c real [q][ny][nx], x real [ny][nx]. */
+purify_status purify_psi(purify_plan *plan, const void *c, void *x);
+
+/* c = Psi^dagger x = [Psi_1^T x; ...; Psi_q^T x] / sqrt(q) (Sec. 1, the
+ * analysis operator of the average-sparsity prior): x real, c real [q][ny][nx]. */
+purify_status purify_psi_adj(purify_plan *plan, const void *x, void *c);
+
+/* ||Phi||_2^2 for real images (largest eigenvalue of Re Phi^H Phi) by
+ * `iters` power iterations from a fixed seeded start. Synchronous. */
+purify_status purify_op_norm_sq(purify_plan *plan, int32_t iters, double *norm_sq);
+
+/* SDMM solver parameters for problem (3). */
+typedef struct {
+    int32_t max_iter;     /* outer SDMM iterations (exact count when rel_obj_tol == 0) */
+    int32_t cg_iters;     /* conjugate-gradient iterations per x-update (cap) */
+    double cg_tol;        /* 0 => exactly cg_iters CG steps (fewer only if the residual is 0);
+                             > 0 => stop when ||r|| <= cg_tol ||b|| */
+    double gamma;         /* SDMM step; <= 0 => 1e-3 max|Psi^dagger Re Phi^H y| / nu^2 */
+    double nu;            /* data-term scale ||Phi||_2; <= 0 => 100 power iterations */
+    double rel_obj_tol;   /* > 0: stop once the relative objective change < rel_obj_tol
+                             and every ||y_i - Phi_i x|| / eps_i <= 1 + eps_tol */
+    double eps_tol;
+    int32_t check_every;  /* stopping test interval (iterations), 0 => 10 */
+    int32_t resume;       /* 1: continue the previous solve on this plan (same y, eps, w,
+                             gamma, nu); x is then output only */
+} purify_sdmm_params;
+
+/* Statistics of a solve, evaluated at the returned x. */
+typedef struct {
+    int32_t iters;
+    int32_t cg_iters_total;
+    double objective;          /* ||W Psi^dagger x||_1 */
+    double max_resid_over_eps; /* max_i ||y_i - Phi_i x|| / eps_i */
+    double rel_change;         /* ||x_t - x_{t-1}|| / ||x_t|| of the last iteration */
+    double gamma, nu;          /* constants used */
+    int32_t status;            /* purify_status of the solve */
+} purify_sdmm_stats;
+
+/* Solve problem (3) (Sec. 1) by SDMM: min ||W Psi^dagger x||_1 subject to
+ * ||y_i - Phi_i x||_2 <= eps_i for every block and x >= 0.
+ *   y      complex [M], caller order (host or device)
+ *   eps    HOST double [R]; each > 0
+ *   w      real [q][ny][nx] weights (host or device), NULL => W = I
+ *   x      real [ny][nx] (host or device): in = starting point, out = solution
+ *   stats  HOST, may be NULL
+ * Iteration order (from the current x, multipliers z_j starting at 0):
+ *   s1 = soft(Psi^dagger x + z1, gamma w), z1 += Psi^dagger x - s1;
+ *   s2_i = proj onto the ball B(y_i/nu, eps_i/nu) of Phi_i x/nu + z2_i, z2 += Phi x/nu - s2;
+ *   s3 = max(x + z3, 0), z3 += x - s3;
+ *   x = CG solution of (2 I + Re Phi^H Phi/nu^2) x = Psi(s1 - z1) + Re Phi^H(s2 - z2)/nu + s3 - z3.
+ * Synchronous at the end (stats). Errors: EINVAL, ENAN, ENOTCONV, ECUDA. */
+purify_status purify_sdmm_solve(purify_plan *plan, const void *y, const double *eps,
+                                const void *w, void *x, const purify_sdmm_params *params,
+                                purify_sdmm_stats *stats);
+
+/* SARA weights (Sec. 1, reweighted l1): w = rho / (rho + |Psi^dagger x|),
+ * x real [ny][nx], w real [q][ny][nx]; rho > 0. */
+purify_status purify_reweight(purify_plan *plan, const void *x, double rho, void *w);
+
+/* Standard deviation of Psi^dagger x over all D coefficients (FP64 reduction),
+ * the first SARA reweighting scale. Synchronous. */
+purify_status purify_coef_std(purify_plan *plan, const void *x, double *std_out);
+
+/* Per-kernel device timing for profiling: when enabled, every kernel launch
+ * of the plan is bracketed by CUDA events on the plan's stream. */
+purify_status purify_timing_enable(purify_plan *plan, int32_t enable);
+/* Fill up to `cap` entries (name, launches, total milliseconds) accumulated
+ * since the last reset; returns the number of kernel kinds. Synchronous. */
+typedef struct { char name[32]; int64_t launches; double total_ms; } purify_kernel_time;
+int32_t purify_timing_read(purify_plan *plan, purify_kernel_time *out, int32_t cap, int32_t reset);
+
+/* Number of kernels this library launched on any plan since load. */
+int64_t purify_launch_count(void);
+
+/* Thread-local message of the last failed call ("" if none). */
+const char *purify_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PURIFY_H */

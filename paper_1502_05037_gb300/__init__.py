@@ -1,0 +1,167 @@
+"""GB300 SARA/SDMM radio-interferometric imaging (arXiv:1502.05037).
+
+Thin Python layer over the C ABI of libpurify.so: the functions below carry
+the C names and only marshal arguments. Arrays are torch tensors (device or
+host) or NumPy arrays (host) of the plan's dtype; complex arrays are
+torch.complex64/complex128 (or interleaved real pairs).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import (PURIFY_F32, PURIFY_F64, PurifyError, check, load, purify_kernel_time, purify_plan_desc,
+                   purify_plan_info, purify_sdmm_params, purify_sdmm_stats)
+
+__all__ = [
+    "Plan", "purify_plan_create", "purify_plan_destroy", "purify_phi", "purify_phi_adj", "purify_fft2",
+    "purify_psi", "purify_psi_adj", "purify_op_norm_sq", "purify_sdmm_solve", "purify_reweight",
+    "purify_coef_std", "purify_launch_count", "PurifyError", "PURIFY_F32", "PURIFY_F64",
+]
+
+
+def _ptr(a) -> int | None:
+    """Raw data pointer of a torch tensor or NumPy array (must be contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Plan:
+    """Owns a purify_plan handle; see purify_plan_create for the fields."""
+
+    def __init__(self, nx, ny, u, v, kb_width=6, levels=4, block_offsets=None, oversample=2.0, kb_beta=0.0,
+                 basis_mask=0, dtype=PURIFY_F32, stream=None, tile=0):
+        lib = load()
+        M = int(u.numel() if hasattr(u, "numel") else np.asarray(u).size)
+        self._keep = [u, v]
+        offs = None
+        R = 1
+        if block_offsets is not None:
+            offs_np = np.ascontiguousarray(np.asarray(block_offsets, dtype=np.int64))
+            self._keep.append(offs_np)
+            R = offs_np.size - 1
+            offs = offs_np.ctypes.data_as(C.POINTER(C.c_int64))
+        d = purify_plan_desc(nx=nx, ny=ny, M=M, u=_ptr(u), v=_ptr(v), R=R, block_offsets=offs,
+                             kb_width=kb_width, oversample=oversample, kb_beta=kb_beta, levels=levels,
+                             basis_mask=basis_mask, dtype=dtype, stream=_stream_ptr(stream), tile=tile)
+        h = C.c_void_p()
+        check(lib.purify_plan_create(C.byref(d), C.byref(h)))
+        self.handle = h
+        self._keep = None
+        self.dtype = dtype
+        info = purify_plan_info()
+        check(lib.purify_plan_get_info(h, C.byref(info)))
+        self.info = info
+
+    def close(self):
+        if getattr(self, "handle", None):
+            check(load().purify_plan_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        check(load().purify_plan_set_stream(self.handle, _stream_ptr(stream)))
+
+
+# ------------------------------------------------- C-named thin wrappers
+def purify_plan_create(**kw) -> Plan:
+    return Plan(**kw)
+
+
+def purify_plan_destroy(plan: Plan):
+    plan.close()
+
+
+def purify_phi(plan: Plan, x, y):
+    check(load().purify_phi(plan.handle, _ptr(x), _ptr(y)))
+
+
+def purify_phi_adj(plan: Plan, y, x):
+    check(load().purify_phi_adj(plan.handle, _ptr(y), _ptr(x)))
+
+
+def purify_fft2(plan: Plan, grid, inverse: bool = False):
+    check(load().purify_fft2(plan.handle, _ptr(grid), int(bool(inverse))))
+
+
+def purify_psi(plan: Plan, c, x):
+    check(load().purify_psi(plan.handle, _ptr(c), _ptr(x)))
+
+
+def purify_psi_adj(plan: Plan, x, c):
+    check(load().purify_psi_adj(plan.handle, _ptr(x), _ptr(c)))
+
+
+def purify_op_norm_sq(plan: Plan, iters: int = 100) -> float:
+    out = C.c_double()
+    check(load().purify_op_norm_sq(plan.handle, iters, C.byref(out)))
+    return out.value
+
+
+def purify_sdmm_solve(plan: Plan, y, eps, x, w=None, max_iter=200, cg_iters=10, cg_tol=0.0, gamma=0.0, nu=0.0,
+                      rel_obj_tol=0.0, eps_tol=0.0, check_every=0, resume=False, raise_on_error=True):
+    """Solve problem (3); x is updated in place. Returns purify_sdmm_stats."""
+    eps_np = None
+    eps_ptr = None
+    if eps is not None:
+        eps_np = np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
+        eps_ptr = eps_np.ctypes.data_as(C.POINTER(C.c_double))
+    prm = purify_sdmm_params(max_iter=max_iter, cg_iters=cg_iters, cg_tol=cg_tol, gamma=gamma, nu=nu,
+                             rel_obj_tol=rel_obj_tol, eps_tol=eps_tol, check_every=check_every,
+                             resume=int(bool(resume)))
+    st = purify_sdmm_stats()
+    status = load().purify_sdmm_solve(plan.handle, _ptr(y), eps_ptr, _ptr(w), _ptr(x), C.byref(prm), C.byref(st))
+    if raise_on_error:
+        check(status)
+    return st
+
+
+def purify_reweight(plan: Plan, x, rho: float, w):
+    check(load().purify_reweight(plan.handle, _ptr(x), float(rho), _ptr(w)))
+
+
+def purify_coef_std(plan: Plan, x) -> float:
+    out = C.c_double()
+    check(load().purify_coef_std(plan.handle, _ptr(x), C.byref(out)))
+    return out.value
+
+
+def purify_timing_enable(plan: Plan, enable: bool = True):
+    check(load().purify_timing_enable(plan.handle, int(bool(enable))))
+
+
+def purify_timing_read(plan: Plan, reset: bool = True) -> dict:
+    lib = load()
+    buf = (purify_kernel_time * 64)()
+    n = lib.purify_timing_read(plan.handle, buf, 64, int(bool(reset)))
+    if n < 0:
+        check(1)
+    return {buf[i].name.decode(): (buf[i].launches, buf[i].total_ms) for i in range(min(n, 64))}
+
+
+def purify_launch_count() -> int:
+    return int(load().purify_launch_count())

@@ -1,0 +1,295 @@
+// C ABI of the imaging library (include/purify.h): argument checks, host
+// pointer staging, error translation, launch accounting and timing.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "launch.h"
+
+namespace purify {
+
+static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches{0};
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+struct KernelTimer {
+    bool enabled = false;
+    struct Pending { std::string name; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
+    std::map<std::string, std::pair<int64_t, double>> acc;
+    cudaEvent_t get() {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e;
+        PURIFY_CUDA(cudaEventCreate(&e));
+        return e;
+    }
+    void drain() {
+        for (auto& q : pending) {
+            float ms = 0.f;
+            PURIFY_CUDA(cudaEventSynchronize(q.b));
+            PURIFY_CUDA(cudaEventElapsedTime(&ms, q.a, q.b));
+            auto& a = acc[q.name];
+            a.first += 1;
+            a.second += ms;
+            pool.push_back(q.a);
+            pool.push_back(q.b);
+        }
+        pending.clear();
+    }
+    ~KernelTimer() {
+        for (auto& q : pending) { cudaEventDestroy(q.a); cudaEventDestroy(q.b); }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+Launch::Launch(purify_plan* plan, const char* kname) : p(plan), name(kname) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (p->timer && p->timer->enabled) {
+        e0 = p->timer->get();
+        PURIFY_CUDA(cudaEventRecord(e0, p->stream));
+    }
+}
+
+void Launch::done() {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw Error{PURIFY_ECUDA, std::string("launch of ") + name + ": " + cudaGetErrorString(e)};
+    if (e0) {
+        cudaEvent_t e1 = p->timer->get();
+        PURIFY_CUDA(cudaEventRecord(e1, p->stream));
+        p->timer->pending.push_back({name, e0, e1});
+        if (p->timer->pending.size() > 4096) p->timer->drain();
+        e0 = nullptr;
+    }
+}
+
+// Device view of a caller array: the pointer itself, or a staged copy.
+struct Staged {
+    void* dev = nullptr;
+    bool host = false;
+};
+
+static Staged stage_in(purify_plan* p, const void* ptr, size_t bytes, DevBuf& buf) {
+    Staged s;
+    if (!is_host_pointer(ptr)) { s.dev = const_cast<void*>(ptr); return s; }
+    if (buf.bytes < bytes) buf.alloc(bytes);
+    PURIFY_CUDA(cudaMemcpyAsync(buf.p, ptr, bytes, cudaMemcpyHostToDevice, p->stream));
+    s.dev = buf.p;
+    s.host = true;
+    return s;
+}
+
+static Staged stage_out(purify_plan* p, void* ptr, size_t bytes, DevBuf& buf) {
+    Staged s;
+    if (!is_host_pointer(ptr)) { s.dev = ptr; return s; }
+    if (buf.bytes < bytes) buf.alloc(bytes);
+    s.dev = buf.p;
+    s.host = true;
+    return s;
+}
+
+static void finish_out(purify_plan* p, const Staged& s, void* ptr, size_t bytes) {
+    if (!s.host) return;
+    PURIFY_CUDA(cudaMemcpyAsync(ptr, s.dev, bytes, cudaMemcpyDeviceToHost, p->stream));
+    PURIFY_CUDA(cudaStreamSynchronize(p->stream));
+}
+
+static size_t real_bytes(const purify_plan* p) { return p->dtype == PURIFY_F32 ? 4 : 8; }
+
+template <typename F> static purify_status guarded(F&& f) {
+    try {
+        f();
+        return PURIFY_OK;
+    } catch (const Error& e) {
+        set_error(e.msg);
+        return e.status;
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        return PURIFY_ENOMEM;
+    } catch (...) {
+        set_error("unexpected internal error");
+        return PURIFY_ECUDA;
+    }
+}
+
+}  // namespace purify
+
+using namespace purify;
+
+extern "C" {
+
+purify_status purify_plan_create(const purify_plan_desc* desc, purify_plan** out) {
+    return guarded([&] {
+        PURIFY_REQUIRE(out != nullptr, "null output pointer");
+        *out = nullptr;
+        *out = create_plan(desc);
+    });
+}
+
+purify_status purify_plan_destroy(purify_plan* plan) {
+    return guarded([&] {
+        if (!plan) return;
+        cudaStreamSynchronize(plan->stream);
+        delete plan->timer;
+        delete plan;
+    });
+}
+
+purify_status purify_plan_set_stream(purify_plan* plan, void* stream) {
+    return guarded([&] {
+        PURIFY_REQUIRE(plan != nullptr, "null plan");
+        plan->stream = (cudaStream_t)stream;
+    });
+}
+
+purify_status purify_plan_get_info(const purify_plan* plan, purify_plan_info* info) {
+    return guarded([&] {
+        PURIFY_REQUIRE(plan && info, "null argument");
+        info->Kx = plan->Kx;
+        info->Ky = plan->Ky;
+        info->q = plan->q;
+        info->tile = plan->work.tile;
+        info->N = plan->N;
+        info->D = plan->D;
+        info->M = plan->M;
+        info->R = plan->R;
+        info->J = plan->J;
+        info->levels = plan->levels;
+        info->beta = plan->beta;
+        info->workspace_bytes = plan->workspace_bytes;
+    });
+}
+
+purify_status purify_phi(purify_plan* p, const void* x, void* y) {
+    return guarded([&] {
+        PURIFY_REQUIRE(p && x && y, "null argument");
+        const size_t rb = real_bytes(p);
+        Staged xs = stage_in(p, x, rb * p->N, p->stage_in);
+        Staged ys = stage_out(p, y, 2 * rb * p->M, p->stage_out);
+        launch_phi(p, xs.dev, ys.dev, true, 1.0);
+        finish_out(p, ys, y, 2 * rb * p->M);
+    });
+}
+
+purify_status purify_phi_adj(purify_plan* p, const void* y, void* x) {
+    return guarded([&] {
+        PURIFY_REQUIRE(p && x && y, "null argument");
+        const size_t rb = real_bytes(p);
+        Staged ys = stage_in(p, y, 2 * rb * p->M, p->stage_in);
+        Staged xs = stage_out(p, x, 2 * rb * p->N, p->stage_out);
+        launch_phi_adj(p, ys.dev, xs.dev, true, 1.0, 0, nullptr);
+        finish_out(p, xs, x, 2 * rb * p->N);
+    });
+}
+
+purify_status purify_fft2(purify_plan* p, void* grid, int32_t inverse) {
+    return guarded([&] {
+        PURIFY_REQUIRE(p && grid, "null argument");
+        const size_t bytes = 2 * real_bytes(p) * (size_t)p->Kx * p->Ky;
+        Staged gs = stage_in(p, grid, bytes, p->stage_in);
+        launch_fft2(p, gs.dev, inverse != 0);
+        finish_out(p, gs, grid, bytes);
+    });
+}
+
+purify_status purify_psi(purify_plan* p, const void* c, void* x) {
+    return guarded([&] {
+        PURIFY_REQUIRE(p && c && x, "null argument");
+        const size_t rb = real_bytes(p);
+        Staged cs = stage_in(p, c, rb * p->D, p->stage_in);
+        Staged xs = stage_out(p, x, rb * p->N, p->stage_out);
+        launch_psi(p, cs.dev, xs.dev);
+        finish_out(p, xs, x, rb * p->N);
+    });
+}
+
+purify_status purify_psi_adj(purify_plan* p, const void* x, void* c) {
+    return guarded([&] {
+        PURIFY_REQUIRE(p && c && x, "null argument");
+        const size_t rb = real_bytes(p);
+        Staged xs = stage_in(p, x, rb * p->N, p->stage_in);
+        Staged cs = stage_out(p, c, rb * p->D, p->stage_out);
+        launch_psi_adj(p, xs.dev, cs.dev);
+        finish_out(p, cs, c, rb * p->D);
+    });
+}
+
+purify_status purify_op_norm_sq(purify_plan* p, int32_t iters, double* norm_sq) {
+    return guarded([&] {
+        PURIFY_REQUIRE(p && norm_sq && iters > 0, "bad argument");
+        *norm_sq = op_norm_sq(p, iters);
+    });
+}
+
+purify_status purify_sdmm_solve(purify_plan* p, const void* y, const double* eps, const void* w, void* x,
+                                const purify_sdmm_params* params, purify_sdmm_stats* stats) {
+    return guarded([&] {
+        PURIFY_REQUIRE(p && params && x, "null argument");
+        PURIFY_REQUIRE(params->max_iter >= 0 && params->cg_iters >= 0, "negative iteration count");
+        PURIFY_REQUIRE(params->resume || (y && eps), "y and eps are required unless resuming");
+        PURIFY_REQUIRE(!params->resume || p->sd.started, "resume without a previous solve on this plan");
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        sdmm_solve(p, y, eps, w, x, *params, stats);
+    });
+}
+
+purify_status purify_reweight(purify_plan* p, const void* x, double rho, void* w) {
+    return guarded([&] {
+        PURIFY_REQUIRE(p && x && w && rho > 0, "bad argument");
+        const size_t rb = real_bytes(p);
+        Staged xs = stage_in(p, x, rb * p->N, p->stage_in);
+        Staged ws = stage_out(p, w, rb * p->D, p->stage_out);
+        reweight(p, xs.dev, rho, ws.dev);
+        finish_out(p, ws, w, rb * p->D);
+    });
+}
+
+purify_status purify_coef_std(purify_plan* p, const void* x, double* std_out) {
+    return guarded([&] {
+        PURIFY_REQUIRE(p && x && std_out, "null argument");
+        const size_t rb = real_bytes(p);
+        Staged xs = stage_in(p, x, rb * p->N, p->stage_in);
+        *std_out = coef_std(p, xs.dev);
+    });
+}
+
+purify_status purify_timing_enable(purify_plan* p, int32_t enable) {
+    return guarded([&] {
+        PURIFY_REQUIRE(p != nullptr, "null plan");
+        if (!p->timer) p->timer = new KernelTimer();
+        p->timer->enabled = enable != 0;
+    });
+}
+
+int32_t purify_timing_read(purify_plan* p, purify_kernel_time* out, int32_t cap, int32_t reset) {
+    int32_t n = -1;
+    purify_status st = guarded([&] {
+        PURIFY_REQUIRE(p != nullptr, "null plan");
+        if (!p->timer) { n = 0; return; }
+        p->timer->drain();
+        n = 0;
+        for (auto& kv : p->timer->acc) {
+            if (out && n < cap) {
+                std::memset(out[n].name, 0, sizeof(out[n].name));
+                std::strncpy(out[n].name, kv.first.c_str(), sizeof(out[n].name) - 1);
+                out[n].launches = kv.second.first;
+                out[n].total_ms = kv.second.second;
+            }
+            ++n;
+        }
+        if (reset) p->timer->acc.clear();
+    });
+    return st == PURIFY_OK ? n : -1;
+}
+
+int64_t purify_launch_count(void) { return g_launches.load(); }
+
+const char* purify_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,163 @@
+// Internal plan structure and kernel-launch entry points of the imaging
+// library. Everything here is private to the shared library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/purify.h"
+#include "common.cuh"
+
+namespace purify {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+struct Error {
+    purify_status status;
+    std::string msg;
+};
+#define PURIFY_CUDA(call)                                                           \
+    do {                                                                            \
+        cudaError_t _e = (call);                                                    \
+        if (_e != cudaSuccess)                                                      \
+            throw ::purify::Error{PURIFY_ECUDA, std::string(#call) + ": " +         \
+                                                    cudaGetErrorString(_e)};        \
+    } while (0)
+#define PURIFY_REQUIRE(cond, msg)                                                   \
+    do {                                                                            \
+        if (!(cond)) throw ::purify::Error{PURIFY_EINVAL, (msg)};                   \
+    } while (0)
+
+// --------------------------------------------------------- launch timing
+struct KernelTimer;
+void note_launch(const char* name, cudaStream_t s, KernelTimer* t, bool begin);
+
+// ------------------------------------------------------- device buffers
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    void alloc(size_t b);
+    void release();
+    template <typename T> T* as() const { return static_cast<T*>(p); }
+    ~DevBuf() { release(); }
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+};
+
+// Wavelet filter table: for basis p (1..8) the low-pass h and high-pass g,
+// each padded to 16 taps, in the plan dtype.
+#define PURIFY_MAX_TAPS 16
+template <typename T> struct FilterBank {
+    T h[9][PURIFY_MAX_TAPS];
+    T g[9][PURIFY_MAX_TAPS];
+    int len[9];
+};
+
+// Gridding work list: subproblem s covers grid tile sub_bin[s] and the
+// visibility pieces piece_off[s] .. piece_off[s+1]-1; piece k is the internal
+// index range [piece_start[k], piece_start[k] + piece_len[k]).
+struct GridWork {
+    int nsub = 0, npieces = 0, tile = 32, tiles_x = 0, tiles_y = 0;
+    DevBuf sub_bin, piece_off, piece_start, piece_len;
+};
+
+// SDMM device state (allocated on first solve).
+struct SdmmState {
+    bool ready = false;
+    bool have_w = false;
+    DevBuf x, z1, z2, z3;         // iterate and multipliers
+    DevBuf ybar;                  // y / nu in internal order
+    DevBuf w;                     // weights [D]
+    DevBuf eps;                   // eps_i / nu, double [R]
+    DevBuf c1;                    // [D] analysis coefficients / prox output
+    DevBuf v2;                    // [M] Phi x / nu then fused residual term
+    DevBuf addend;                // [N] image-space terms of the CG residual
+    DevBuf r, p, Ap, xprev;       // CG vectors [N]
+    DevBuf scal;                  // double scalars (see sdmm.cu)
+    DevBuf part;                  // double partial sums
+    DevBuf counters;              // unsigned ints for last-block reductions, then int flags
+    DevBuf chunk_first;           // int [R + 1]: first visibility chunk of each block
+    bool started = false;
+    double gamma = 0, nu = 0;
+    std::vector<double> eps_host;
+    int64_t iters_done = 0;
+    int64_t cg_total = 0;
+};
+
+}  // namespace purify
+
+struct purify_plan {
+    purify_plan_desc desc;
+    int dtype;  // PURIFY_F32 / PURIFY_F64
+    int nx, ny, Kx, Ky, J, levels, q, R;
+    int64_t N, D, M;
+    uint32_t mask;
+    double beta, i0beta;
+    cudaStream_t stream;
+    std::vector<int64_t> offsets;     // host, R + 1
+    std::vector<int> bases;           // basis ids in dictionary order (0 = Dirac)
+    purify::AxisConst ax, ay;
+    purify::KbPoly kbp;
+    purify::DevBuf sx, sy;            // per-axis correction (dtype)
+    purify::DevBuf twx, twy;          // twiddles (complex dtype)
+    purify::DevBuf wmeta;             // int[16]: wavelet db index and plane per basis
+    purify::DevBuf us, vs;            // sorted coordinates (dtype)
+    purify::DevBuf perm;              // int32 internal -> caller
+    purify::DevBuf d_offsets;         // int64 [R + 1]
+    purify::DevBuf chunk_blk, chunk_beg, chunk_end;  // visibility chunks, each inside one block
+    int nchunks = 0;
+    purify::GridWork work;
+    // workspaces
+    purify::DevBuf grid;              // Ky * Kx complex
+    purify::DevBuf rows;              // ny * Kx complex
+    purify::DevBuf ll0, ll1;          // wavelet low-pass scratch (dtype, 8 * N / 4 each)
+    purify::DevBuf stage_in, stage_out;  // host-pointer staging
+    purify::DevBuf tmp_img, tmp_vis, tmp_coef;
+    purify::SdmmState sd;
+    purify::KernelTimer* timer = nullptr;
+    int64_t workspace_bytes = 0;
+};
+
+namespace purify {
+
+// ----------------------------------------------------------- operator steps
+// Phi: x real [ny][nx] (internal pointer) -> y complex [M]. If perm != null
+// the output is written in caller order through perm. `scale` multiplies S.
+void launch_phi(purify_plan* p, const void* x, void* y, bool caller_order, double scale);
+// Phi^H: y complex [M] (caller order if caller_order) -> image.
+//   out_mode 0: complex [ny][nx];  1: real part, out = scale * Re(.) + add (add may be null)
+void launch_phi_adj(purify_plan* p, const void* y, void* out, bool caller_order, double scale,
+                    int out_mode, const void* add);
+void launch_fft2(purify_plan* p, void* grid, bool inverse);
+// Phi stages used by the solver's fused forms
+void launch_scale_pad_rows(purify_plan* p, const void* x, double scale, void* pdir, const void* rvec,
+                           const double* beta_dev, const int* skip_flag);
+void launch_cols_fwd(purify_plan* p, const int* skip_flag);
+void launch_degrid(purify_plan* p, void* y, bool caller_order, const int* skip_flag);
+void launch_grid(purify_plan* p, const void* y, bool caller_order, const int* skip_flag);
+void launch_cols_inv(purify_plan* p, const int* skip_flag);
+void launch_rows_inv_crop(purify_plan* p, void* out, double scale, int out_mode, const void* add,
+                          double add_coef, const int* skip_flag);
+
+// Psi / Psi^dagger
+void launch_psi_adj(purify_plan* p, const void* x, void* c);
+void launch_psi(purify_plan* p, const void* c, void* x);
+void init_filter_banks();
+
+// solver
+void sdmm_solve(purify_plan* p, const void* y, const double* eps, const void* w, void* x,
+                const purify_sdmm_params& prm, purify_sdmm_stats* st);
+double op_norm_sq(purify_plan* p, int iters);
+void reweight(purify_plan* p, const void* x, double rho, void* w);
+double coef_std(purify_plan* p, const void* x);
+
+// plan-side helpers
+void build_gridwork(purify_plan* p, const std::vector<int>& bin_sorted, int tile);
+purify_plan* create_plan(const purify_plan_desc* d);
+bool is_host_pointer(const void* ptr);
+
+}  // namespace purify

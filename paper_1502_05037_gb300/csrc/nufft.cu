@@ -1,0 +1,564 @@
+// Measurement operator Phi = G F Z S and its adjoint S Z^T F^H G^H.
+//
+// The paper (Sec. 1) writes the measurement equation as y = Phi x + n and
+// leaves the discretisation open; the plan realises Phi with Kaiser-Bessel
+// gridding on a K = alpha n oversampled grid:
+//   rows_fwd  : S, Z and the row pass of F over the ny image rows only (the
+//               other K - ny grid rows are zero and never stored);
+//   cols_fwd  : column pass of F, treating the missing rows as zeros;
+//   degrid    : G, J x J separable Kaiser-Bessel interpolation per visibility;
+//   grid      : G^H, per-tile shared-memory accumulation of the footprints;
+//   cols_inv  : column pass of F^H producing only the ny rows kept by Z^T;
+//   rows_inv  : row pass of F^H fused with Z^T (crop) and S.
+// FFTs are radix-4 Stockham passes (one radix-2 pass first for odd log2 K)
+// in shared memory on several rows or columns per thread block.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "internal.h"
+#include "launch.h"
+
+namespace purify {
+
+// --------------------------------------------------------------- FFT core
+// `nb` independent length-n FFTs held in shared memory; element k of FFT f
+// lives at f*fs + k*ks. Returns the buffer holding the result.
+template <typename C, bool INV>
+__device__ C* fft_smem(C* src, C* dst, int n, int logn, int nb, int fs, int ks, const C* __restrict__ tw) {
+    const int tid = threadIdx.x, T = blockDim.x;
+    int Ns = 1;
+    if (logn & 1) {
+        const int half = n >> 1;
+        for (int t = tid; t < nb * half; t += T) {
+            int f = t % nb, j = t / nb;
+            C v0 = src[f * fs + j * ks];
+            C v1 = src[f * fs + (j + half) * ks];
+            dst[f * fs + (2 * j) * ks] = cadd(v0, v1);
+            dst[f * fs + (2 * j + 1) * ks] = csub(v0, v1);
+        }
+        __syncthreads();
+        C* s = src; src = dst; dst = s;
+        Ns = 2;
+    }
+    const int quarter = n >> 2;
+    while (Ns < n) {
+        const int tstride = n / (4 * Ns);
+        for (int t = tid; t < nb * quarter; t += T) {
+            int f = t % nb, j = t / nb;
+            int k = j & (Ns - 1);
+            C v0 = src[f * fs + j * ks];
+            C v1 = src[f * fs + (j + quarter) * ks];
+            C v2 = src[f * fs + (j + 2 * quarter) * ks];
+            C v3 = src[f * fs + (j + 3 * quarter) * ks];
+            if (Ns > 1) {
+                C w1 = tw[k * tstride], w2 = tw[2 * k * tstride], w3 = tw[3 * k * tstride];
+                if (INV) { v1 = cmulconj(v1, w1); v2 = cmulconj(v2, w2); v3 = cmulconj(v3, w3); }
+                else { v1 = cmul(v1, w1); v2 = cmul(v2, w2); v3 = cmul(v3, w3); }
+            }
+            C a0 = cadd(v0, v2), a1 = csub(v0, v2), a2 = cadd(v1, v3), a3 = csub(v1, v3);
+            // -i * a3 for the forward transform, +i * a3 for the inverse
+            C ia3 = INV ? cmake<C>(-a3.y, a3.x) : cmake<C>(a3.y, -a3.x);
+            int o = (j - k) * 4 + k;
+            dst[f * fs + o * ks] = cadd(a0, a2);
+            dst[f * fs + (o + Ns) * ks] = cadd(a1, ia3);
+            dst[f * fs + (o + 2 * Ns) * ks] = csub(a0, a2);
+            dst[f * fs + (o + 3 * Ns) * ks] = csub(a1, ia3);
+        }
+        __syncthreads();
+        C* s = src; src = dst; dst = s;
+        Ns <<= 2;
+    }
+    return src;
+}
+
+__host__ __device__ inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
+
+// ------------------------------------------------------------ row passes
+// S Z and the forward row FFT: rows [i0, i0+rb) of the image to rows[i][0..Kx).
+// When pdir != null the kernel first forms p = r + beta p in place (CG
+// direction update) and transforms the new p.
+template <typename T>
+__global__ void k_rows_fwd(const T* __restrict__ x, typename cplx_of<T>::type* __restrict__ rows,
+                           const T* __restrict__ sx, const T* __restrict__ sy,
+                           const typename cplx_of<T>::type* __restrict__ tw, int nx, int ny, int Kx,
+                           int rb, T scale, T* pdir, const T* __restrict__ rvec,
+                           const double* __restrict__ beta_dev, const int* __restrict__ skip) {
+    using C = typename cplx_of<T>::type;
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* b0 = reinterpret_cast<C*>(smem_raw);
+    C* b1 = b0 + rb * Kx;
+    const int i0 = blockIdx.x * rb;
+    const int tot = rb * Kx;
+    const T beta = beta_dev ? (T)(*beta_dev) : T(0);
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+        int f = t / Kx, p1 = t - f * Kx;
+        int i = i0 + f;
+        // pixel column j with (j - nx/2) mod Kx == p1
+        int n1 = p1 < Kx / 2 ? p1 : p1 - Kx;
+        int j = n1 + nx / 2;
+        T val = T(0);
+        if (j >= 0 && j < nx) {
+            size_t idx = (size_t)i * nx + j;
+            T xv;
+            if (pdir) {
+                xv = rvec[idx] + beta * pdir[idx];
+                pdir[idx] = xv;
+            } else {
+                xv = x[idx];
+            }
+            val = xv * sx[j] * sy[i] * scale;
+        }
+        b0[t] = cmake<C>(val, T(0));
+    }
+    __syncthreads();
+    C* res = fft_smem<C, false>(b0, b1, Kx, ilog2(Kx), rb, Kx, 1, tw);
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+        int f = t / Kx, k = t - f * Kx;
+        rows[(size_t)(i0 + f) * Kx + k] = res[t];
+    }
+}
+
+// Forward column FFT over columns [c0, c0+cb): the only non-zero grid rows
+// are p2 = (i - ny/2) mod Ky for image rows i.
+template <typename T>
+__global__ void k_cols_fwd(const typename cplx_of<T>::type* __restrict__ rows,
+                           typename cplx_of<T>::type* __restrict__ grid,
+                           const typename cplx_of<T>::type* __restrict__ tw, int ny, int Kx, int Ky,
+                           int cb, const int* __restrict__ skip) {
+    using C = typename cplx_of<T>::type;
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* b0 = reinterpret_cast<C*>(smem_raw);
+    C* b1 = b0 + cb * Ky;
+    const int c0 = blockIdx.x * cb;
+    const int tot = cb * Ky;
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+        int k = t / cb, f = t - k * cb;
+        int n2 = k < Ky / 2 ? k : k - Ky;
+        int i = n2 + ny / 2;
+        C v = cmake<C>(T(0), T(0));
+        if (i >= 0 && i < ny) v = rows[(size_t)i * Kx + c0 + f];
+        b0[t] = v;
+    }
+    __syncthreads();
+    C* res = fft_smem<C, false>(b0, b1, Ky, ilog2(Ky), cb, 1, cb, tw);
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+        int k = t / cb, f = t - k * cb;
+        grid[(size_t)k * Kx + c0 + f] = res[t];
+    }
+}
+
+// Inverse column FFT over columns [c0, c0+cb), keeping only the image rows.
+template <typename T>
+__global__ void k_cols_inv(const typename cplx_of<T>::type* __restrict__ grid,
+                           typename cplx_of<T>::type* __restrict__ rows,
+                           const typename cplx_of<T>::type* __restrict__ tw, int ny, int Kx, int Ky,
+                           int cb, const int* __restrict__ skip) {
+    using C = typename cplx_of<T>::type;
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* b0 = reinterpret_cast<C*>(smem_raw);
+    C* b1 = b0 + cb * Ky;
+    const int c0 = blockIdx.x * cb;
+    const int tot = cb * Ky;
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+        int k = t / cb, f = t - k * cb;
+        b0[t] = grid[(size_t)k * Kx + c0 + f];
+    }
+    __syncthreads();
+    C* res = fft_smem<C, true>(b0, b1, Ky, ilog2(Ky), cb, 1, cb, tw);
+    for (int t = threadIdx.x; t < ny * cb; t += blockDim.x) {
+        int i = t / cb, f = t - i * cb;
+        int p2 = (i - ny / 2) & (Ky - 1);
+        rows[(size_t)i * Kx + c0 + f] = res[p2 * cb + f];
+    }
+}
+
+// Inverse row FFT of image rows [i0, i0+rb), then Z^T and S:
+//   out_mode 0: complex out[i][j] = scale * s * v
+//   out_mode 1: real    out[i][j] = scale * s * Re v + (add ? add[i][j] : 0)
+template <typename T>
+__global__ void k_rows_inv(const typename cplx_of<T>::type* __restrict__ rows, void* out,
+                           const T* __restrict__ sx, const T* __restrict__ sy,
+                           const typename cplx_of<T>::type* __restrict__ tw, int nx, int ny, int Kx,
+                           int rb, T scale, int out_mode, const T* __restrict__ add, T add_coef,
+                           const int* __restrict__ skip) {
+    using C = typename cplx_of<T>::type;
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* b0 = reinterpret_cast<C*>(smem_raw);
+    C* b1 = b0 + rb * Kx;
+    const int i0 = blockIdx.x * rb;
+    const int tot = rb * Kx;
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+        int f = t / Kx, k = t - f * Kx;
+        b0[t] = rows[(size_t)(i0 + f) * Kx + k];
+    }
+    __syncthreads();
+    C* res = fft_smem<C, true>(b0, b1, Kx, ilog2(Kx), rb, Kx, 1, tw);
+    for (int t = threadIdx.x; t < rb * nx; t += blockDim.x) {
+        int f = t / nx, j = t - f * nx;
+        int i = i0 + f;
+        int p1 = (j - nx / 2) & (Kx - 1);
+        C v = res[f * Kx + p1];
+        T s = sx[j] * sy[i] * scale;
+        size_t idx = (size_t)i * nx + j;
+        if (out_mode == 0) {
+            reinterpret_cast<C*>(out)[idx] = cscale(v, s);
+        } else {
+            T r = v.x * s;
+            if (add) r += add_coef * add[idx];
+            reinterpret_cast<T*>(out)[idx] = r;
+        }
+    }
+}
+
+// Plain in-place 2-D FFT pieces (purify_fft2): full row pass / column pass.
+template <typename T, bool INV>
+__global__ void k_rows_full(typename cplx_of<T>::type* grid, const typename cplx_of<T>::type* __restrict__ tw,
+                            int Kx, int rb) {
+    using C = typename cplx_of<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* b0 = reinterpret_cast<C*>(smem_raw);
+    C* b1 = b0 + rb * Kx;
+    const size_t base = (size_t)blockIdx.x * rb * Kx;
+    for (int t = threadIdx.x; t < rb * Kx; t += blockDim.x) b0[t] = grid[base + t];
+    __syncthreads();
+    C* res = fft_smem<C, INV>(b0, b1, Kx, ilog2(Kx), rb, Kx, 1, tw);
+    for (int t = threadIdx.x; t < rb * Kx; t += blockDim.x) grid[base + t] = res[t];
+}
+
+template <typename T, bool INV>
+__global__ void k_cols_full(typename cplx_of<T>::type* grid, const typename cplx_of<T>::type* __restrict__ tw,
+                            int Kx, int Ky, int cb) {
+    using C = typename cplx_of<T>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* b0 = reinterpret_cast<C*>(smem_raw);
+    C* b1 = b0 + cb * Ky;
+    const int c0 = blockIdx.x * cb;
+    for (int t = threadIdx.x; t < cb * Ky; t += blockDim.x) {
+        int k = t / cb, f = t - k * cb;
+        b0[t] = grid[(size_t)k * Kx + c0 + f];
+    }
+    __syncthreads();
+    C* res = fft_smem<C, INV>(b0, b1, Ky, ilog2(Ky), cb, 1, cb, tw);
+    for (int t = threadIdx.x; t < cb * Ky; t += blockDim.x) {
+        int k = t / cb, f = t - k * cb;
+        grid[(size_t)k * Kx + c0 + f] = res[t];
+    }
+}
+
+// ------------------------------------------------------------- degridding
+// G: one thread per visibility (internal order). Output in caller order
+// through perm when perm != null.
+template <typename T, int J>
+__global__ void k_degrid(const typename cplx_of<T>::type* __restrict__ grid, const T* __restrict__ us,
+                         const T* __restrict__ vs, int M, AxisConst ax, AxisConst ay, KbPoly kp,
+                         double beta, double inv_i0beta, const int* __restrict__ perm,
+                         typename cplx_of<T>::type* __restrict__ y, const int* __restrict__ skip) {
+    using C = typename cplx_of<T>::type;
+    if (skip && *skip) return;
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    int kx0, ky0;
+    T phx, phy;
+    split_coord(us[m], ax, J, kx0, phx);
+    split_coord(vs[m], ay, J, ky0, phy);
+    T wx[J], wy[J];
+    if constexpr (sizeof(T) == 4) {
+        kb_weights<J>(kp, phx, wx);
+        kb_weights<J>(kp, phy, wy);
+    } else {
+        kb_weights<J>(beta, inv_i0beta, phx, wx);
+        kb_weights<J>(beta, inv_i0beta, phy, wy);
+    }
+    const int Kx = ax.K, Ky = ay.K;
+    T accx = 0, accy = 0;
+#pragma unroll
+    for (int b = 0; b < J; ++b) {
+        const C* row = grid + (size_t)((ky0 + b) & (Ky - 1)) * Kx;
+        T rx = 0, ry = 0;
+#pragma unroll
+        for (int a = 0; a < J; ++a) {
+            C g = row[(kx0 + a) & (Kx - 1)];
+            rx += wx[a] * g.x;
+            ry += wx[a] * g.y;
+        }
+        accx += wy[b] * rx;
+        accy += wy[b] * ry;
+    }
+    y[perm ? perm[m] : m] = cmake<C>(accx, accy);
+}
+
+// ---------------------------------------------------------------- gridding
+// G^H: one block per subproblem (a grid tile and a list of visibility
+// pieces). Footprints accumulate in a shared-memory copy of the tile plus a
+// (J-1) halo, then the touched part of that copy is added to the grid.
+__device__ __forceinline__ void atomic_add_c(float2* a, float2 v) { atomicAdd(a, v); }
+__device__ __forceinline__ void atomic_add_c(double2* a, double2 v) {
+    atomicAdd(&a->x, v.x);
+    atomicAdd(&a->y, v.y);
+}
+
+template <typename T, int J>
+__global__ void k_grid(const typename cplx_of<T>::type* __restrict__ yin, const T* __restrict__ us,
+                       const T* __restrict__ vs, AxisConst ax, AxisConst ay, KbPoly kp, double beta,
+                       double inv_i0beta, const int* __restrict__ perm, const int* __restrict__ sub_bin,
+                       const int* __restrict__ piece_off, const int* __restrict__ piece_start,
+                       const int* __restrict__ piece_len, int tile, int tiles_x,
+                       typename cplx_of<T>::type* __restrict__ grid, const int* __restrict__ skip) {
+    using C = typename cplx_of<T>::type;
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int PT = tile + J - 1;
+    T* tre = reinterpret_cast<T*>(smem_raw);
+    T* tim = tre + PT * PT;
+    int* bbox = reinterpret_cast<int*>(tim + PT * PT);  // min row, max row, min col, max col
+    const int s = blockIdx.x;
+    const int bin = sub_bin[s];
+    const int oy = (bin / tiles_x) * tile, ox = (bin % tiles_x) * tile;
+    const int Kx = ax.K, Ky = ay.K;
+    for (int t = threadIdx.x; t < PT * PT; t += blockDim.x) { tre[t] = T(0); tim[t] = T(0); }
+    if (threadIdx.x == 0) { bbox[0] = PT; bbox[1] = -1; bbox[2] = PT; bbox[3] = -1; }
+    __syncthreads();
+    int lymin = PT, lymax = -1, lxmin = PT, lxmax = -1;
+    const int p0 = piece_off[s], p1 = piece_off[s + 1];
+    for (int pc = p0; pc < p1; ++pc) {
+        const int st = piece_start[pc], len = piece_len[pc];
+        for (int q = threadIdx.x; q < len; q += blockDim.x) {
+            const int m = st + q;
+            int kx0, ky0;
+            T phx, phy;
+            split_coord(us[m], ax, J, kx0, phx);
+            split_coord(vs[m], ay, J, ky0, phy);
+            T wx[J], wy[J];
+            if constexpr (sizeof(T) == 4) {
+                kb_weights<J>(kp, phx, wx);
+                kb_weights<J>(kp, phy, wy);
+            } else {
+                kb_weights<J>(beta, inv_i0beta, phx, wx);
+                kb_weights<J>(beta, inv_i0beta, phy, wy);
+            }
+            C yv = yin[perm ? perm[m] : m];
+            int lx = ((kx0 & (Kx - 1)) - ox), ly = ((ky0 & (Ky - 1)) - oy);
+            if (lx >= 0 && lx < tile && ly >= 0 && ly < tile) {
+                lxmin = min(lxmin, lx); lxmax = max(lxmax, lx + J - 1);
+                lymin = min(lymin, ly); lymax = max(lymax, ly + J - 1);
+#pragma unroll
+                for (int b = 0; b < J; ++b) {
+                    T wb = wy[b];
+                    T yb_re = wb * yv.x, yb_im = wb * yv.y;
+                    T* rre = tre + (ly + b) * PT + lx;
+                    T* rim = tim + (ly + b) * PT + lx;
+#pragma unroll
+                    for (int a = 0; a < J; ++a) {
+                        atomicAdd(rre + a, wx[a] * yb_re);
+                        atomicAdd(rim + a, wx[a] * yb_im);
+                    }
+                }
+            } else {
+                // coordinate outside this tile (never expected: the plan bins
+                // with the same split); add straight to the grid
+#pragma unroll
+                for (int b = 0; b < J; ++b)
+#pragma unroll
+                    for (int a = 0; a < J; ++a) {
+                        T w = wy[b] * wx[a];
+                        atomic_add_c(grid + (size_t)((ky0 + b) & (Ky - 1)) * Kx + ((kx0 + a) & (Kx - 1)),
+                                     cmake<C>(w * yv.x, w * yv.y));
+                    }
+            }
+        }
+    }
+    if (lymax >= 0) {
+        atomicMin(&bbox[0], lymin); atomicMax(&bbox[1], lymax);
+        atomicMin(&bbox[2], lxmin); atomicMax(&bbox[3], lxmax);
+    }
+    __syncthreads();
+    const int r0 = bbox[0], r1 = bbox[1], q0 = bbox[2], q1 = bbox[3];
+    if (r1 < 0) return;
+    const int w = q1 - q0 + 1;
+    const int cells = (r1 - r0 + 1) * w;
+    for (int t = threadIdx.x; t < cells; t += blockDim.x) {
+        int r = r0 + t / w, c = q0 + t % w;
+        T re = tre[r * PT + c], im = tim[r * PT + c];
+        if (re != T(0) || im != T(0))
+            atomic_add_c(grid + (size_t)((oy + r) & (Ky - 1)) * Kx + ((ox + c) & (Kx - 1)), cmake<C>(re, im));
+    }
+}
+
+// ------------------------------------------------------------- launchers
+static int rows_per_block(int K) { return std::max(1, std::min(8, 1024 / K)); }
+
+template <typename T> static int cols_per_block(int Ky, int Kx) {
+    size_t cbytes = sizeof(typename cplx_of<T>::type);
+    int cb = 8;
+    while (cb > 1 && (2 * (size_t)cb * Ky * cbytes > 160 * 1024 || Kx % cb)) cb >>= 1;
+    return cb;
+}
+
+template <typename K> static void set_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024) PURIFY_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+template <typename T>
+static void rows_fwd_t(purify_plan* p, const void* x, double scale, void* pdir, const void* rvec,
+                       const double* beta_dev, const int* skip) {
+    using C = typename cplx_of<T>::type;
+    int rb = rows_per_block(p->Kx);
+    while (p->ny % rb) rb >>= 1;
+    size_t sm = 2 * (size_t)rb * p->Kx * sizeof(C);
+    set_smem(k_rows_fwd<T>, sm);
+    Launch L(p, "fft_rows_fwd");
+    k_rows_fwd<T><<<p->ny / rb, 256, sm, p->stream>>>(
+        (const T*)x, p->rows.as<C>(), p->sx.as<T>(), p->sy.as<T>(), p->twx.as<C>(), p->nx, p->ny, p->Kx,
+        rb, (T)scale, (T*)pdir, (const T*)rvec, beta_dev, skip);
+    L.done();
+}
+
+template <typename T> static void cols_fwd_t(purify_plan* p, const int* skip) {
+    using C = typename cplx_of<T>::type;
+    int cb = cols_per_block<T>(p->Ky, p->Kx);
+    size_t sm = 2 * (size_t)cb * p->Ky * sizeof(C);
+    set_smem(k_cols_fwd<T>, sm);
+    Launch L(p, "fft_cols_fwd");
+    k_cols_fwd<T><<<p->Kx / cb, 256, sm, p->stream>>>(p->rows.as<C>(), p->grid.as<C>(), p->twy.as<C>(),
+                                                      p->ny, p->Kx, p->Ky, cb, skip);
+    L.done();
+}
+
+template <typename T> static void cols_inv_t(purify_plan* p, const int* skip) {
+    using C = typename cplx_of<T>::type;
+    int cb = cols_per_block<T>(p->Ky, p->Kx);
+    size_t sm = 2 * (size_t)cb * p->Ky * sizeof(C);
+    set_smem(k_cols_inv<T>, sm);
+    Launch L(p, "fft_cols_inv");
+    k_cols_inv<T><<<p->Kx / cb, 256, sm, p->stream>>>(p->grid.as<C>(), p->rows.as<C>(), p->twy.as<C>(),
+                                                      p->ny, p->Kx, p->Ky, cb, skip);
+    L.done();
+}
+
+template <typename T>
+static void rows_inv_t(purify_plan* p, void* out, double scale, int out_mode, const void* add, double add_coef,
+                       const int* skip) {
+    using C = typename cplx_of<T>::type;
+    int rb = rows_per_block(p->Kx);
+    while (p->ny % rb) rb >>= 1;
+    size_t sm = 2 * (size_t)rb * p->Kx * sizeof(C);
+    set_smem(k_rows_inv<T>, sm);
+    Launch L(p, "fft_rows_inv");
+    k_rows_inv<T><<<p->ny / rb, 256, sm, p->stream>>>(p->rows.as<C>(), out, p->sx.as<T>(), p->sy.as<T>(),
+                                                      p->twx.as<C>(), p->nx, p->ny, p->Kx, rb, (T)scale,
+                                                      out_mode, (const T*)add, (T)add_coef, skip);
+    L.done();
+}
+
+template <typename T, int J> static void degrid_tj(purify_plan* p, void* y, bool caller_order, const int* skip) {
+    using C = typename cplx_of<T>::type;
+    int M = (int)p->M;
+    Launch L(p, "degrid");
+    k_degrid<T, J><<<(M + 255) / 256, 256, 0, p->stream>>>(
+        p->grid.as<C>(), p->us.as<T>(), p->vs.as<T>(), M, p->ax, p->ay, p->kbp, p->beta, 1.0 / p->i0beta,
+        caller_order ? p->perm.as<int>() : nullptr, (C*)y, skip);
+    L.done();
+}
+
+template <typename T, int J>
+static void grid_tj(purify_plan* p, const void* y, bool caller_order, const int* skip) {
+    using C = typename cplx_of<T>::type;
+    PURIFY_CUDA(cudaMemsetAsync(p->grid.p, 0, p->grid.bytes, p->stream));
+    if (p->work.nsub == 0) return;
+    int PT = p->work.tile + J - 1;
+    size_t sm = 2 * (size_t)PT * PT * sizeof(T) + 4 * sizeof(int);
+    set_smem(k_grid<T, J>, sm);
+    Launch L(p, "grid");
+    k_grid<T, J><<<p->work.nsub, 256, sm, p->stream>>>(
+        (const C*)y, p->us.as<T>(), p->vs.as<T>(), p->ax, p->ay, p->kbp, p->beta, 1.0 / p->i0beta,
+        caller_order ? p->perm.as<int>() : nullptr, p->work.sub_bin.as<int>(), p->work.piece_off.as<int>(),
+        p->work.piece_start.as<int>(), p->work.piece_len.as<int>(), p->work.tile, p->work.tiles_x, p->grid.as<C>(),
+        skip);
+    L.done();
+}
+
+#define PURIFY_J_DISPATCH(J, FN, ...)                                     \
+    switch (J) {                                                          \
+        case 2: FN<2>(__VA_ARGS__); break;                                \
+        case 3: FN<3>(__VA_ARGS__); break;                                \
+        case 4: FN<4>(__VA_ARGS__); break;                                \
+        case 5: FN<5>(__VA_ARGS__); break;                                \
+        case 6: FN<6>(__VA_ARGS__); break;                                \
+        case 7: FN<7>(__VA_ARGS__); break;                                \
+        case 8: FN<8>(__VA_ARGS__); break;                                \
+        default: throw Error{PURIFY_EINVAL, "kb_width out of range"};     \
+    }
+
+template <int J> static void degrid_f(purify_plan* p, void* y, bool c, const int* s) { degrid_tj<float, J>(p, y, c, s); }
+template <int J> static void degrid_d(purify_plan* p, void* y, bool c, const int* s) { degrid_tj<double, J>(p, y, c, s); }
+template <int J> static void grid_f(purify_plan* p, const void* y, bool c, const int* s) { grid_tj<float, J>(p, y, c, s); }
+template <int J> static void grid_d(purify_plan* p, const void* y, bool c, const int* s) { grid_tj<double, J>(p, y, c, s); }
+
+void launch_scale_pad_rows(purify_plan* p, const void* x, double scale, void* pdir, const void* rvec,
+                           const double* beta_dev, const int* skip) {
+    if (p->dtype == PURIFY_F32) rows_fwd_t<float>(p, x, scale, pdir, rvec, beta_dev, skip);
+    else rows_fwd_t<double>(p, x, scale, pdir, rvec, beta_dev, skip);
+}
+void launch_cols_fwd(purify_plan* p, const int* skip) {
+    if (p->dtype == PURIFY_F32) cols_fwd_t<float>(p, skip); else cols_fwd_t<double>(p, skip);
+}
+void launch_cols_inv(purify_plan* p, const int* skip) {
+    if (p->dtype == PURIFY_F32) cols_inv_t<float>(p, skip); else cols_inv_t<double>(p, skip);
+}
+void launch_rows_inv_crop(purify_plan* p, void* out, double scale, int out_mode, const void* add, double add_coef,
+                          const int* skip) {
+    if (p->dtype == PURIFY_F32) rows_inv_t<float>(p, out, scale, out_mode, add, add_coef, skip);
+    else rows_inv_t<double>(p, out, scale, out_mode, add, add_coef, skip);
+}
+void launch_degrid(purify_plan* p, void* y, bool caller_order, const int* skip) {
+    if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, degrid_f, p, y, caller_order, skip); }
+    else { PURIFY_J_DISPATCH(p->J, degrid_d, p, y, caller_order, skip); }
+}
+void launch_grid(purify_plan* p, const void* y, bool caller_order, const int* skip) {
+    if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, grid_f, p, y, caller_order, skip); }
+    else { PURIFY_J_DISPATCH(p->J, grid_d, p, y, caller_order, skip); }
+}
+
+void launch_phi(purify_plan* p, const void* x, void* y, bool caller_order, double scale) {
+    launch_scale_pad_rows(p, x, scale, nullptr, nullptr, nullptr, nullptr);
+    launch_cols_fwd(p, nullptr);
+    launch_degrid(p, y, caller_order, nullptr);
+}
+
+void launch_phi_adj(purify_plan* p, const void* y, void* out, bool caller_order, double scale, int out_mode,
+                    const void* add) {
+    launch_grid(p, y, caller_order, nullptr);
+    launch_cols_inv(p, nullptr);
+    launch_rows_inv_crop(p, out, scale, out_mode, add, 1.0, nullptr);
+}
+
+template <typename T> static void fft2_t(purify_plan* p, void* grid, bool inverse) {
+    using C = typename cplx_of<T>::type;
+    int rb = rows_per_block(p->Kx);
+    while (p->Ky % rb) rb >>= 1;
+    size_t smr = 2 * (size_t)rb * p->Kx * sizeof(C);
+    int cb = cols_per_block<T>(p->Ky, p->Kx);
+    size_t smc = 2 * (size_t)cb * p->Ky * sizeof(C);
+    if (inverse) {
+        set_smem(k_rows_full<T, true>, smr);
+        set_smem(k_cols_full<T, true>, smc);
+        { Launch L(p, "fft_full_rows"); k_rows_full<T, true><<<p->Ky / rb, 256, smr, p->stream>>>((C*)grid, p->twx.as<C>(), p->Kx, rb); L.done(); }
+        { Launch L(p, "fft_full_cols"); k_cols_full<T, true><<<p->Kx / cb, 256, smc, p->stream>>>((C*)grid, p->twy.as<C>(), p->Kx, p->Ky, cb); L.done(); }
+    } else {
+        set_smem(k_rows_full<T, false>, smr);
+        set_smem(k_cols_full<T, false>, smc);
+        { Launch L(p, "fft_full_rows"); k_rows_full<T, false><<<p->Ky / rb, 256, smr, p->stream>>>((C*)grid, p->twx.as<C>(), p->Kx, rb); L.done(); }
+        { Launch L(p, "fft_full_cols"); k_cols_full<T, false><<<p->Kx / cb, 256, smc, p->stream>>>((C*)grid, p->twy.as<C>(), p->Kx, p->Ky, cb); L.done(); }
+    }
+}
+
+void launch_fft2(purify_plan* p, void* grid, bool inverse) {
+    if (p->dtype == PURIFY_F32) fft2_t<float>(p, grid, inverse); else fft2_t<double>(p, grid, inverse);
+}
+
+}  // namespace purify

@@ -1,0 +1,718 @@
+// SDMM solve of problem (3) (Sec. 1, Eqs. 1-3) and SARA reweighting.
+//
+// Functions and linear maps (Combettes & Pesquet's SDMM): f1 = ||W .||_1
+// with L1 = Psi^dagger, f2 = indicator of the R l2 balls of Eq. 3 with
+// L2 = Phi / nu, f3 = indicator of R_+^N with L3 = I. One iteration from the
+// current x (multipliers start at zero):
+//   s1 = soft(Psi^dagger x + z1, gamma w);        z1 += Psi^dagger x - s1
+//   s2_i = proj_{B(ybar_i, eps_i / nu)}(Phi_i x / nu + z2_i); z2 += Phi x / nu - s2
+//   s3 = max(x + z3, 0);                           z3 += x - s3
+//   x  = CG solution of (2 I + Re Phi^H Phi / nu^2) x = b,
+//        b = Psi(s1 - z1) + Re Phi^H (s2 - z2) / nu + (s3 - z3), warm start.
+// The CG residual b - A x is formed with a single adjoint: Phi x / nu is
+// already at hand from the projection step, so
+//   b - A x = Psi(s1 - z1) + (s3 - z3) - 2 x + Re Phi^H (s2 - z2 - Phi x / nu) / nu.
+// Reductions (norms, dot products, objective) are FP64 with a fixed order:
+// per-block partials, summed in index order by the last block to finish.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+#include "launch.h"
+
+namespace purify {
+
+// ----------------------------------------------------------- scalar slots
+enum Slot {
+    S_RS = 0,        // r.r
+    S_RS0 = 1,       // r0.r0 of the current x-update
+    S_BETA = 2,
+    S_ALPHA = 3,
+    S_PAP = 4,
+    S_OBJ = 5,       // ||W Psi^dagger x||_1 at the iterate entering the iteration
+    S_OBJ_PREV = 6,
+    S_CGCOUNT = 7,   // CG steps done (running total)
+    S_XN2 = 8,       // ||x_new||^2
+    S_DXN2 = 9,      // ||x_new - x_old||^2
+    S_TOL2 = 10,     // cg_tol^2
+    S_GMAX = 11,     // max |.| reduction result
+    S_NORM2 = 12,    // generic norm^2 result
+    S_SUM = 13,      // generic sum result
+    S_BLOCKS = 32    // then R entries of ||r_i||^2, then R of ||Phi_i x/nu - ybar_i||^2
+};
+enum Counter { C_PROX = 0, C_PROJ, C_CGI, C_ALPHA, C_UPD, C_REL, C_GEN, C_COUNT };
+enum Flag { F_CGDONE = 0, F_NAN = 1, F_COUNT = 4 };
+
+static const int RB = 256;                 // threads per reduction block
+static int red_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + RB * 4 - 1) / (RB * 4), 152 * 8)); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the thread block (result valid in thread 0).
+__device__ double block_sum(double v) {
+    __shared__ double sh[32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        v = warp_sum(v);
+    }
+    return v;
+}
+
+// True in every thread of the last block to arrive; partials written before
+// the call by other blocks are then visible.
+__device__ bool arrive_last(unsigned* counter) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// Ordered sum of part[0..n) by the calling block (result in thread 0).
+__device__ double ordered_sum(const double* part, int n) {
+    double v = 0.0;
+    // each thread sums a strided subsequence, then the block combines them
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += __ldcg(part + i);
+    return block_sum(v);
+}
+
+// ------------------------------------------------------------ kernels
+// prox of gamma ||W .||_1 with the multiplier update; c holds Psi^dagger x on
+// entry and s1 - z1 on exit. Objective partial sum |w v|.
+template <typename T>
+__global__ void k_prox_l1(T* __restrict__ c, T* __restrict__ z1, const T* __restrict__ w, int64_t D, double gamma,
+                          double* part, unsigned* counters, double* scal, int eval_only) {
+    double obj = 0.0;
+    for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < D; d += (int64_t)gridDim.x * blockDim.x) {
+        T v = c[d];
+        T wd = w ? w[d] : T(1);
+        obj += fabs((double)wd * (double)v);
+        if (eval_only) continue;
+        T zz = z1[d];
+        T t = v + zz;
+        T thr = (T)gamma * wd;
+        T mag = fabs(t) - thr;
+        T s = mag > T(0) ? copysign(mag, t) : T(0);
+        T zn = zz + v - s;
+        z1[d] = zn;
+        c[d] = s - zn;
+    }
+    double b = block_sum(obj);
+    if (threadIdx.x == 0) part[blockIdx.x] = b;
+    if (arrive_last(counters + C_PROX)) {
+        double tot = ordered_sum(part, gridDim.x);
+        if (threadIdx.x == 0) {
+            scal[S_OBJ_PREV] = scal[S_OBJ];
+            scal[S_OBJ] = tot;
+            counters[C_PROX] = 0;
+        }
+    }
+}
+
+// Per-block norms over visibility chunks: ||v2 + z2 - ybar||^2 (z2 may be
+// null) and ||v2 - ybar||^2.
+template <typename T>
+__global__ void k_proj_norms(const typename cplx_of<T>::type* __restrict__ v2,
+                             const typename cplx_of<T>::type* __restrict__ z2,
+                             const typename cplx_of<T>::type* __restrict__ ybar, const int* __restrict__ cblk,
+                             const int* __restrict__ cbeg, const int* __restrict__ cend, int nchunks, int R,
+                             const int* __restrict__ chunk_first, double* part, unsigned* counters, double* scal) {
+    using C = typename cplx_of<T>::type;
+    const int ch = blockIdx.x;
+    double a = 0.0, e = 0.0;
+    for (int m = cbeg[ch] + threadIdx.x; m < cend[ch]; m += blockDim.x) {
+        C v = v2[m], y = ybar[m];
+        double rx = (double)v.x - (double)y.x, ry = (double)v.y - (double)y.y;
+        e += rx * rx + ry * ry;
+        if (z2) {
+            C z = z2[m];
+            double tx = (double)(v.x + z.x - y.x), ty = (double)(v.y + z.y - y.y);
+            a += tx * tx + ty * ty;
+        }
+    }
+    double sa = block_sum(a);
+    double se = block_sum(e);
+    if (threadIdx.x == 0) { part[2 * ch] = sa; part[2 * ch + 1] = se; }
+    if (arrive_last(counters + C_PROJ)) {
+        // chunk_first[r] .. chunk_first[r+1] are block r's chunks
+        for (int r = threadIdx.x; r < R; r += blockDim.x) {
+            double sa2 = 0.0, se2 = 0.0;
+            for (int k = chunk_first[r]; k < chunk_first[r + 1]; ++k) {
+                sa2 += __ldcg(part + 2 * k);
+                se2 += __ldcg(part + 2 * k + 1);
+            }
+            if (z2) scal[S_BLOCKS + r] = sa2;
+            scal[S_BLOCKS + R + r] = se2;
+        }
+        if (threadIdx.x == 0) counters[C_PROJ] = 0;
+    }
+}
+
+// Projection onto each block's ball plus multiplier update; v2 (= Phi x / nu)
+// is replaced by s2 - z2 - v2 for the fused CG residual.
+template <typename T>
+__global__ void k_proj_apply(typename cplx_of<T>::type* __restrict__ v2, typename cplx_of<T>::type* __restrict__ z2,
+                             const typename cplx_of<T>::type* __restrict__ ybar, const int* __restrict__ cblk,
+                             const int* __restrict__ cbeg, const int* __restrict__ cend,
+                             const double* __restrict__ eps, const double* __restrict__ scal, int R) {
+    using C = typename cplx_of<T>::type;
+    const int ch = blockIdx.x;
+    const int r = cblk[ch];
+    const double nr = sqrt(scal[S_BLOCKS + r]);
+    const double e = eps[r];
+    const T f = nr > e ? (T)(e / nr) : T(1);
+    for (int m = cbeg[ch] + threadIdx.x; m < cend[ch]; m += blockDim.x) {
+        C v = v2[m], z = z2[m], y = ybar[m];
+        T rx = v.x + z.x - y.x, ry = v.y + z.y - y.y;
+        T sx = y.x + rx * f, sy = y.y + ry * f;
+        T zx = z.x + v.x - sx, zy = z.y + v.y - sy;
+        z2[m] = cmake<C>(zx, zy);
+        v2[m] = cmake<C>(sx - zx - v.x, sy - zy - v.y);
+    }
+}
+
+// Positivity step and the image-space part of the CG residual:
+//   s3 = max(x + z3, 0); z3 += x - s3; addend = psi_out + (s3 - z3) - 2x.
+template <typename T>
+__global__ void k_positivity(const T* __restrict__ x, T* __restrict__ z3, const T* __restrict__ psi_out,
+                             T* __restrict__ addend, T* __restrict__ xprev, int64_t N) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        T xv = x[i], zz = z3[i];
+        T t = xv + zz;
+        T s3 = t > T(0) ? t : T(0);
+        T zn = zz + xv - s3;
+        z3[i] = zn;
+        addend[i] = psi_out[i] + (s3 - zn) - T(2) * xv;
+        xprev[i] = xv;
+    }
+}
+
+// CG start: r holds b - A x. p = 0 and beta = 0 so that the first direction
+// update gives p = r; rs = rs0 = r.r; the done flag is cleared.
+template <typename T>
+__global__ void k_cg_init(const T* __restrict__ r, T* __restrict__ p, int64_t N, double* part, unsigned* counters,
+                          double* scal, int* flags) {
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        T v = r[i];
+        acc += (double)v * (double)v;
+        p[i] = T(0);
+    }
+    double b = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = b;
+    if (arrive_last(counters + C_CGI)) {
+        double tot = ordered_sum(part, gridDim.x);
+        if (threadIdx.x == 0) {
+            scal[S_RS] = tot;
+            scal[S_RS0] = tot;
+            scal[S_BETA] = 0.0;
+            flags[F_CGDONE] = tot == 0.0 ? 1 : 0;
+            if (!(tot == tot)) flags[F_NAN] = 1;
+            counters[C_CGI] = 0;
+        }
+    }
+}
+
+// alpha = rs / (p . Ap)
+template <typename T>
+__global__ void k_cg_alpha(const T* __restrict__ p, const T* __restrict__ Ap, int64_t N, double* part,
+                           unsigned* counters, double* scal, int* flags) {
+    if (flags[F_CGDONE]) return;
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+        acc += (double)p[i] * (double)Ap[i];
+    double b = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = b;
+    if (arrive_last(counters + C_ALPHA)) {
+        double tot = ordered_sum(part, gridDim.x);
+        if (threadIdx.x == 0) {
+            scal[S_PAP] = tot;
+            scal[S_ALPHA] = tot > 0.0 ? scal[S_RS] / tot : 0.0;
+            counters[C_ALPHA] = 0;
+        }
+    }
+}
+
+// x += alpha p; r -= alpha Ap; rs' = r.r; beta = rs'/rs; stop test.
+template <typename T>
+__global__ void k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ Ap,
+                            int64_t N, double* part, unsigned* counters, double* scal, int* flags) {
+    if (flags[F_CGDONE]) return;
+    const T alpha = (T)scal[S_ALPHA];
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] += alpha * p[i];
+        T rv = r[i] - alpha * Ap[i];
+        r[i] = rv;
+        acc += (double)rv * (double)rv;
+    }
+    double b = block_sum(acc);
+    if (threadIdx.x == 0) part[blockIdx.x] = b;
+    if (arrive_last(counters + C_UPD)) {
+        double tot = ordered_sum(part, gridDim.x);
+        if (threadIdx.x == 0) {
+            double rs = scal[S_RS];
+            scal[S_BETA] = rs > 0.0 ? tot / rs : 0.0;
+            scal[S_RS] = tot;
+            scal[S_CGCOUNT] += 1.0;
+            if (tot == 0.0 || tot <= scal[S_TOL2] * scal[S_RS0]) flags[F_CGDONE] = 1;
+            if (!(tot == tot)) { flags[F_NAN] = 1; flags[F_CGDONE] = 1; }
+            counters[C_UPD] = 0;
+        }
+    }
+}
+
+// ||x||^2 and ||x - xprev||^2 for the relative change.
+template <typename T>
+__global__ void k_relchange(const T* __restrict__ x, const T* __restrict__ xprev, int64_t N, double* part,
+                            unsigned* counters, double* scal) {
+    double a = 0.0, d = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        double xv = x[i], dv = (double)x[i] - (double)xprev[i];
+        a += xv * xv;
+        d += dv * dv;
+    }
+    double ba = block_sum(a);
+    double bd = block_sum(d);
+    if (threadIdx.x == 0) { part[2 * blockIdx.x] = ba; part[2 * blockIdx.x + 1] = bd; }
+    if (arrive_last(counters + C_REL)) {
+        double sa = 0.0, sd = 0.0;
+        if (threadIdx.x == 0) {
+            for (unsigned k = 0; k < gridDim.x; ++k) { sa += __ldcg(part + 2 * k); sd += __ldcg(part + 2 * k + 1); }
+            scal[S_XN2] = sa;
+            scal[S_DXN2] = sd;
+            counters[C_REL] = 0;
+        }
+    }
+}
+
+// Generic reductions: mode 0 sum of squares, 1 max |.|, 2 sum, 3 sum (v - mean)^2 with mean = scal[S_SUM]/n
+template <typename T>
+__global__ void k_reduce(const T* __restrict__ v, int64_t n, int mode, double* part, unsigned* counters,
+                         double* scal, int slot) {
+    double acc = 0.0;
+    const double mean = mode == 3 ? scal[S_SUM] / (double)n : 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double a = v[i];
+        if (mode == 0) acc += a * a;
+        else if (mode == 1) acc = fmax(acc, fabs(a));
+        else if (mode == 2) acc += a;
+        else acc += (a - mean) * (a - mean);
+    }
+    if (mode == 1) {
+        __shared__ double sh[32];
+        for (int o = 16; o > 0; o >>= 1) acc = fmax(acc, __shfl_down_sync(0xffffffffu, acc, o));
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            acc = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) acc = fmax(acc, __shfl_down_sync(0xffffffffu, acc, o));
+        }
+    } else {
+        acc = block_sum(acc);
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = acc;
+    if (arrive_last(counters + C_GEN)) {
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (unsigned k = 0; k < gridDim.x; ++k) {
+                double pk = __ldcg(part + k);
+                t = mode == 1 ? fmax(t, pk) : t + pk;
+            }
+            scal[slot] = t;
+            counters[C_GEN] = 0;
+        }
+    }
+}
+
+// y (caller order) / nu -> internal order
+template <typename T>
+__global__ void k_gather_scale(const typename cplx_of<T>::type* __restrict__ y, const int* __restrict__ perm,
+                               typename cplx_of<T>::type* __restrict__ out, int64_t M, T s) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = cscale(y[perm[i]], s);
+}
+
+template <typename T>
+__global__ void k_scale_copy(const T* __restrict__ in, T* __restrict__ out, int64_t n, const double* scal, int slot) {
+    const T s = (T)(1.0 / sqrt(scal[slot]));
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[i] * s;
+}
+
+// SARA weights w = rho / (rho + |c|)
+template <typename T>
+__global__ void k_reweight(const T* __restrict__ c, T* __restrict__ w, int64_t D, T rho) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < D; i += (int64_t)gridDim.x * blockDim.x)
+        w[i] = rho / (rho + fabs(c[i]));
+}
+
+template <typename T>
+__global__ void k_check_finite(const T* __restrict__ v, int64_t n, int* flags) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (!isfinite((double)v[i])) flags[F_NAN] = 1;
+}
+
+// -------------------------------------------------------------- host side
+static int ew_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
+
+template <typename T> struct Solver {
+    using C = typename cplx_of<T>::type;
+    purify_plan* p;
+    SdmmState& s;
+    explicit Solver(purify_plan* plan) : p(plan), s(plan->sd) {}
+
+    double* scal() { return s.scal.as<double>(); }
+    double* part() { return s.part.as<double>(); }
+    unsigned* ctr() { return s.counters.as<unsigned>(); }
+    int* flags() { return reinterpret_cast<int*>(s.counters.as<unsigned>() + 16); }
+
+    void ensure() {
+        if (s.ready) return;
+        const size_t N = p->N, D = p->D, M = p->M;
+        s.x.alloc(sizeof(T) * N);
+        s.z1.alloc(sizeof(T) * D);
+        s.z2.alloc(sizeof(C) * M);
+        s.z3.alloc(sizeof(T) * N);
+        s.ybar.alloc(sizeof(C) * M);
+        s.w.alloc(sizeof(T) * D);
+        s.eps.alloc(sizeof(double) * p->R);
+        s.c1.alloc(sizeof(T) * D);
+        s.v2.alloc(sizeof(C) * M);
+        s.addend.alloc(sizeof(T) * N);
+        s.r.alloc(sizeof(T) * N);
+        s.p.alloc(sizeof(T) * N);
+        s.Ap.alloc(sizeof(T) * N);
+        s.xprev.alloc(sizeof(T) * N);
+        s.scal.alloc(sizeof(double) * (S_BLOCKS + 2 * (size_t)p->R + 8));
+        s.part.alloc(sizeof(double) * std::max<size_t>(8192, 2 * (size_t)p->nchunks + 64));
+        s.counters.alloc(sizeof(unsigned) * 32);
+        // chunk_first: first chunk index of each block (host computes from offsets)
+        std::vector<int> cf(p->R + 1, 0);
+        {
+            const int64_t CH = 4096;
+            int k = 0;
+            for (int r = 0; r < p->R; ++r) {
+                cf[r] = k;
+                k += (int)((p->offsets[r + 1] - p->offsets[r] + CH - 1) / CH);
+            }
+            cf[p->R] = k;
+        }
+        s.chunk_first.alloc(sizeof(int) * cf.size());
+        PURIFY_CUDA(cudaMemcpy(s.chunk_first.p, cf.data(), sizeof(int) * cf.size(), cudaMemcpyHostToDevice));
+        PURIFY_CUDA(cudaMemset(s.scal.p, 0, s.scal.bytes));
+        PURIFY_CUDA(cudaMemset(s.counters.p, 0, s.counters.bytes));
+        s.ready = true;
+    }
+
+    void reduce(const T* v, int64_t n, int mode, int slot) {
+        int nb = red_blocks(n);
+        Launch L(p, "reduce");
+        k_reduce<T><<<nb, RB, 0, p->stream>>>(v, n, mode, part(), ctr(), scal(), slot);
+        L.done();
+    }
+
+    double read_scal(int slot) {
+        double v;
+        PURIFY_CUDA(cudaMemcpyAsync(&v, scal() + slot, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+        PURIFY_CUDA(cudaStreamSynchronize(p->stream));
+        return v;
+    }
+
+    // ||Phi||^2 by power iteration from a fixed pseudo-random start
+    double op_norm_sq(int iters) {
+        ensure();
+        std::vector<T> x0(p->N);
+        uint64_t st = 0x9E3779B97F4A7C15ull;
+        for (int64_t i = 0; i < p->N; ++i) {
+            st += 0x9E3779B97F4A7C15ull;
+            uint64_t z = st;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            z ^= z >> 31;
+            x0[i] = (T)((double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5);
+        }
+        T* xv = s.p.template as<T>();
+        T* wv = s.Ap.template as<T>();
+        PURIFY_CUDA(cudaMemcpyAsync(xv, x0.data(), sizeof(T) * p->N, cudaMemcpyHostToDevice, p->stream));
+        reduce(xv, p->N, 0, S_NORM2);
+        {
+            Launch L(p, "scale_copy");
+            k_scale_copy<T><<<ew_blocks(p->N), 256, 0, p->stream>>>(xv, xv, p->N, scal(), S_NORM2);
+            L.done();
+        }
+        for (int it = 0; it < iters; ++it) {
+            launch_phi(p, xv, s.v2.p, false, 1.0);
+            launch_phi_adj(p, s.v2.p, wv, false, 1.0, 1, nullptr);
+            reduce(wv, p->N, 0, S_NORM2);
+            Launch L(p, "scale_copy");
+            k_scale_copy<T><<<ew_blocks(p->N), 256, 0, p->stream>>>(wv, xv, p->N, scal(), S_NORM2);
+            L.done();
+        }
+        return std::sqrt(read_scal(S_NORM2));
+    }
+
+    // objective and per-block residual of x, written to scal
+    void evaluate(const T* x) {
+        launch_psi_adj(p, x, s.c1.p);
+        {
+            Launch L(p, "prox_l1");
+            k_prox_l1<T><<<red_blocks(p->D), RB, 0, p->stream>>>(s.c1.template as<T>(), nullptr,
+                                                               s.have_w ? s.w.template as<T>() : nullptr, p->D,
+                                                               s.gamma, part(), ctr(), scal(), 1);
+            L.done();
+        }
+        launch_phi(p, x, s.v2.p, false, 1.0 / s.nu);
+        proj_norms(false);
+    }
+
+    void proj_norms(bool with_z) {
+        Launch L(p, "proj_norms");
+        k_proj_norms<T><<<p->nchunks, RB, 0, p->stream>>>(
+            s.v2.template as<C>(), with_z ? s.z2.template as<C>() : nullptr, s.ybar.template as<C>(),
+            p->chunk_blk.as<int>(), p->chunk_beg.as<int>(), p->chunk_end.as<int>(), p->nchunks, p->R,
+            s.chunk_first.template as<int>(), part(), ctr(), scal());
+        L.done();
+    }
+
+    // one SDMM iteration with exactly cg_iters CG steps (fewer only if the
+    // stop test fires, in which case the remaining kernels return at once)
+    void iteration(int cg_iters) {
+        T* x = s.x.template as<T>();
+        const double inv_nu = 1.0 / s.nu;
+        // f1
+        launch_psi_adj(p, x, s.c1.p);
+        {
+            Launch L(p, "prox_l1");
+            k_prox_l1<T><<<red_blocks(p->D), RB, 0, p->stream>>>(s.c1.template as<T>(), s.z1.template as<T>(),
+                                                               s.have_w ? s.w.template as<T>() : nullptr, p->D,
+                                                               s.gamma, part(), ctr(), scal(), 0);
+            L.done();
+        }
+        launch_psi(p, s.c1.p, s.Ap.p);  // Psi(s1 - z1) into Ap (scratch)
+        // f2
+        launch_phi(p, x, s.v2.p, false, inv_nu);
+        proj_norms(true);
+        {
+            Launch L(p, "proj_apply");
+            k_proj_apply<T><<<p->nchunks, RB, 0, p->stream>>>(s.v2.template as<C>(), s.z2.template as<C>(),
+                                                             s.ybar.template as<C>(), p->chunk_blk.as<int>(),
+                                                             p->chunk_beg.as<int>(), p->chunk_end.as<int>(),
+                                                             s.eps.template as<double>(), scal(), p->R);
+            L.done();
+        }
+        // f3 and the image-space terms of the residual
+        {
+            Launch L(p, "positivity");
+            k_positivity<T><<<ew_blocks(p->N), 256, 0, p->stream>>>(x, s.z3.template as<T>(), s.Ap.template as<T>(),
+                                                                    s.addend.template as<T>(),
+                                                                    s.xprev.template as<T>(), p->N);
+            L.done();
+        }
+        // r = b - A x
+        launch_phi_adj(p, s.v2.p, s.r.p, false, inv_nu, 1, s.addend.p);
+        {
+            Launch L(p, "cg_init");
+            k_cg_init<T><<<red_blocks(p->N), RB, 0, p->stream>>>(s.r.template as<T>(), s.p.template as<T>(), p->N,
+                                                                part(), ctr(), scal(), flags());
+            L.done();
+        }
+        const int* skip = flags() + F_CGDONE;
+        for (int k = 0; k < cg_iters; ++k) {
+            // p = r + beta p fused into the first FFT pass, then A p
+            launch_scale_pad_rows(p, nullptr, inv_nu, s.p.p, s.r.p, scal() + S_BETA, skip);
+            launch_cols_fwd(p, skip);
+            launch_degrid(p, p->tmp_vis.p, false, skip);
+            launch_grid(p, p->tmp_vis.p, false, skip);
+            launch_cols_inv(p, skip);
+            launch_rows_inv_crop(p, s.Ap.p, inv_nu, 1, s.p.p, 2.0, skip);
+            {
+                Launch L(p, "cg_alpha");
+                k_cg_alpha<T><<<red_blocks(p->N), RB, 0, p->stream>>>(s.p.template as<T>(), s.Ap.template as<T>(),
+                                                                     p->N, part(), ctr(), scal(), flags());
+                L.done();
+            }
+            {
+                Launch L(p, "cg_update");
+                k_cg_update<T><<<red_blocks(p->N), RB, 0, p->stream>>>(x, s.r.template as<T>(), s.p.template as<T>(),
+                                                                      s.Ap.template as<T>(), p->N, part(), ctr(),
+                                                                      scal(), flags());
+                L.done();
+            }
+        }
+        {
+            Launch L(p, "relchange");
+            k_relchange<T><<<red_blocks(p->N), RB, 0, p->stream>>>(x, s.xprev.template as<T>(), p->N, part(), ctr(),
+                                                                  scal());
+            L.done();
+        }
+    }
+};
+
+// ------------------------------------------------------------ entry points
+template <typename T>
+static void sdmm_solve_t(purify_plan* p, const void* y, const double* eps, const void* w, void* x_io,
+                         const purify_sdmm_params& prm, purify_sdmm_stats* st) {
+    using C = typename cplx_of<T>::type;
+    Solver<T> S(p);
+    S.ensure();
+    SdmmState& s = p->sd;
+    if (!prm.resume || s.iters_done < 0 || !s.started) {
+        PURIFY_REQUIRE(y != nullptr && eps != nullptr && x_io != nullptr, "null y, eps or x");
+        for (int r = 0; r < p->R; ++r)
+            PURIFY_REQUIRE(std::isfinite(eps[r]) && eps[r] > 0.0, "eps must be positive and finite");
+        // nu and gamma
+        s.nu = prm.nu > 0 ? prm.nu : std::sqrt(S.op_norm_sq(100));
+        if (is_host_pointer(y)) {
+            PURIFY_CUDA(cudaMemcpyAsync(p->tmp_vis.p, y, sizeof(C) * p->M, cudaMemcpyDefault, p->stream));
+            y = p->tmp_vis.p;
+        }
+        // data in internal order, scaled by 1/nu
+        PURIFY_CUDA(cudaMemsetAsync(S.flags(), 0, sizeof(int) * F_COUNT, p->stream));
+        {
+            Launch L(p, "check_finite");
+            k_check_finite<T><<<ew_blocks(2 * p->M), 256, 0, p->stream>>>((const T*)y, 2 * p->M, S.flags());
+            L.done();
+        }
+        {
+            Launch L(p, "gather_scale");
+            k_gather_scale<T><<<ew_blocks(p->M), 256, 0, p->stream>>>((const C*)y, p->perm.as<int>(),
+                                                                      s.ybar.template as<C>(), p->M, (T)(1.0 / s.nu));
+            L.done();
+        }
+        std::vector<double> en(p->R);
+        for (int r = 0; r < p->R; ++r) en[r] = eps[r] / s.nu;
+        PURIFY_CUDA(cudaMemcpyAsync(s.eps.p, en.data(), sizeof(double) * p->R, cudaMemcpyHostToDevice, p->stream));
+        s.eps_host.assign(eps, eps + p->R);
+        s.have_w = w != nullptr;
+        if (w) PURIFY_CUDA(cudaMemcpyAsync(s.w.p, w, sizeof(T) * p->D, cudaMemcpyDefault, p->stream));
+        if (prm.gamma > 0) {
+            s.gamma = prm.gamma;
+        } else {
+            // gamma = 1e-3 max |Psi^dagger Re Phi^H ybar| / nu  (= max|Psi^dagger Re Phi^H y| / nu^2)
+            launch_phi_adj(p, s.ybar.p, s.r.p, false, 1.0 / s.nu, 1, nullptr);
+            launch_psi_adj(p, s.r.p, s.c1.p);
+            S.reduce(s.c1.template as<T>(), p->D, 1, S_GMAX);
+            s.gamma = 1e-3 * S.read_scal(S_GMAX);
+        }
+        PURIFY_CUDA(cudaMemcpyAsync(s.x.p, x_io, sizeof(T) * p->N, cudaMemcpyDefault, p->stream));
+        PURIFY_CUDA(cudaMemsetAsync(s.z1.p, 0, s.z1.bytes, p->stream));
+        PURIFY_CUDA(cudaMemsetAsync(s.z2.p, 0, s.z2.bytes, p->stream));
+        PURIFY_CUDA(cudaMemsetAsync(s.z3.p, 0, s.z3.bytes, p->stream));
+        double tol2 = prm.cg_tol > 0 ? prm.cg_tol * prm.cg_tol : 0.0;
+        PURIFY_CUDA(cudaMemcpyAsync(S.scal() + S_TOL2, &tol2, sizeof(double), cudaMemcpyHostToDevice, p->stream));
+        double zero = 0.0;
+        PURIFY_CUDA(cudaMemcpyAsync(S.scal() + S_CGCOUNT, &zero, sizeof(double), cudaMemcpyHostToDevice, p->stream));
+        PURIFY_CUDA(cudaStreamSynchronize(p->stream));
+        int fl[F_COUNT];
+        PURIFY_CUDA(cudaMemcpy(fl, S.flags(), sizeof(fl), cudaMemcpyDeviceToHost));
+        if (fl[F_NAN]) throw Error{PURIFY_ENAN, "non-finite visibility"};
+        s.iters_done = 0;
+        s.started = true;
+    } else {
+        double tol2 = prm.cg_tol > 0 ? prm.cg_tol * prm.cg_tol : 0.0;
+        PURIFY_CUDA(cudaMemcpyAsync(S.scal() + S_TOL2, &tol2, sizeof(double), cudaMemcpyHostToDevice, p->stream));
+    }
+    const int cg_iters = prm.cg_iters > 0 ? prm.cg_iters : 10;
+    const int check = prm.check_every > 0 ? prm.check_every : 10;
+    const bool tol_mode = prm.rel_obj_tol > 0;
+    int done = 0;
+    purify_status status = PURIFY_OK;
+    bool converged = false;
+    for (int it = 0; it < prm.max_iter; ++it) {
+        S.iteration(cg_iters);
+        ++done;
+        if (tol_mode && ((it + 1) % check == 0 || it + 1 == prm.max_iter)) {
+            std::vector<double> sc(S_BLOCKS + 2 * p->R);
+            PURIFY_CUDA(cudaMemcpyAsync(sc.data(), S.scal(), sizeof(double) * sc.size(), cudaMemcpyDeviceToHost, p->stream));
+            PURIFY_CUDA(cudaStreamSynchronize(p->stream));
+            double obj = sc[S_OBJ], prev = sc[S_OBJ_PREV];
+            double rel = obj > 0 ? std::fabs(obj - prev) / obj : 0.0;
+            double worst = 0.0;
+            for (int r = 0; r < p->R; ++r) worst = std::max(worst, std::sqrt(sc[S_BLOCKS + p->R + r]) * s.nu / s.eps_host[r]);
+            if (rel < prm.rel_obj_tol && worst <= 1.0 + prm.eps_tol) { converged = true; break; }
+        }
+    }
+    s.iters_done += done;
+    // statistics at the returned x
+    int fl[F_COUNT];
+    PURIFY_CUDA(cudaMemcpyAsync(fl, S.flags(), sizeof(fl), cudaMemcpyDeviceToHost, p->stream));
+    double rel_num[2];
+    PURIFY_CUDA(cudaMemcpyAsync(rel_num, S.scal() + S_XN2, sizeof(rel_num), cudaMemcpyDeviceToHost, p->stream));
+    double cgc = 0.0;
+    PURIFY_CUDA(cudaMemcpyAsync(&cgc, S.scal() + S_CGCOUNT, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+    S.evaluate(s.x.template as<T>());
+    std::vector<double> sc(S_BLOCKS + 2 * p->R);
+    PURIFY_CUDA(cudaMemcpyAsync(sc.data(), S.scal(), sizeof(double) * sc.size(), cudaMemcpyDeviceToHost, p->stream));
+    PURIFY_CUDA(cudaMemcpyAsync(x_io, s.x.p, sizeof(T) * p->N, cudaMemcpyDefault, p->stream));
+    PURIFY_CUDA(cudaStreamSynchronize(p->stream));
+    if (fl[F_NAN]) status = PURIFY_ENAN;
+    else if (tol_mode && !converged) status = PURIFY_ENOTCONV;
+    if (st) {
+        st->iters = (int32_t)s.iters_done;
+        st->cg_iters_total = (int32_t)cgc;
+        st->objective = sc[S_OBJ];
+        double worst = 0.0;
+        for (int r = 0; r < p->R; ++r) worst = std::max(worst, std::sqrt(sc[S_BLOCKS + p->R + r]) * s.nu / s.eps_host[r]);
+        st->max_resid_over_eps = worst;
+        st->rel_change = rel_num[0] > 0 ? std::sqrt(rel_num[1] / rel_num[0]) : 0.0;
+        st->gamma = s.gamma;
+        st->nu = s.nu;
+        st->status = status;
+    }
+    if (status == PURIFY_ENAN) throw Error{PURIFY_ENAN, "non-finite value in the SDMM iterates"};
+    if (status == PURIFY_ENOTCONV) throw Error{PURIFY_ENOTCONV, "tolerance not reached within max_iter"};
+}
+
+void sdmm_solve(purify_plan* p, const void* y, const double* eps, const void* w, void* x,
+                const purify_sdmm_params& prm, purify_sdmm_stats* st) {
+    if (p->dtype == PURIFY_F32) sdmm_solve_t<float>(p, y, eps, w, x, prm, st);
+    else sdmm_solve_t<double>(p, y, eps, w, x, prm, st);
+}
+
+double op_norm_sq(purify_plan* p, int iters) {
+    double nrm = p->dtype == PURIFY_F32 ? Solver<float>(p).op_norm_sq(iters) : Solver<double>(p).op_norm_sq(iters);
+    return nrm;
+}
+
+template <typename T> static void reweight_t(purify_plan* p, const void* x, double rho, void* w) {
+    launch_psi_adj(p, x, w);
+    Launch L(p, "reweight");
+    k_reweight<T><<<ew_blocks(p->D), 256, 0, p->stream>>>((const T*)w, (T*)w, p->D, (T)rho);
+    L.done();
+}
+
+void reweight(purify_plan* p, const void* x, double rho, void* w) {
+    if (p->dtype == PURIFY_F32) reweight_t<float>(p, x, rho, w); else reweight_t<double>(p, x, rho, w);
+}
+
+template <typename T> static double coef_std_t(purify_plan* p, const void* x) {
+    Solver<T> S(p);
+    S.ensure();
+    T* c = p->sd.c1.template as<T>();
+    launch_psi_adj(p, x, c);
+    S.reduce(c, p->D, 2, S_SUM);
+    S.reduce(c, p->D, 3, S_NORM2);
+    return std::sqrt(S.read_scal(S_NORM2) / (double)p->D);
+}
+
+double coef_std(purify_plan* p, const void* x) {
+    return p->dtype == PURIFY_F32 ? coef_std_t<float>(p, x) : coef_std_t<double>(p, x);
+}
+
+}  // namespace purify

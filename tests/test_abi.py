@@ -1,0 +1,101 @@
+"""C ABI checks that need no GPU: the library builds, loads, exports every
+function include/purify.h declares, and the ctypes structures match the C
+layout (checked by compiling a C probe against the header with gcc)."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+from paper_1502_05037_gb300 import _lib
+from paper_1502_05037_gb300 import build as pbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "purify.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    pbuild.build()
+    return _lib.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(purify_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    fns = declared_functions()
+    for name in ("purify_plan_create", "purify_phi", "purify_phi_adj", "purify_psi", "purify_psi_adj",
+                 "purify_sdmm_solve", "purify_reweight"):
+        assert name in fns
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", _lib.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (purify_[a-z0-9_]+)", out))
+    missing = [f for f in declared_functions() if f not in exported]
+    assert not missing, missing
+    for f in declared_functions():
+        assert hasattr(lib, f)
+    assert sorted(_lib.exported_symbols()) == declared_functions()
+
+
+def test_ctypes_layout_matches_c(lib):
+    probe = r"""
+#include <stddef.h>
+#include <stdio.h>
+#include "purify.h"
+#define P(T, f) printf(#T "." #f " %zu\n", offsetof(T, f));
+int main(void) {
+  printf("desc %zu\n", sizeof(purify_plan_desc));
+  printf("info %zu\n", sizeof(purify_plan_info));
+  printf("params %zu\n", sizeof(purify_sdmm_params));
+  printf("stats %zu\n", sizeof(purify_sdmm_stats));
+  printf("ktime %zu\n", sizeof(purify_kernel_time));
+  P(purify_plan_desc, tile) P(purify_plan_desc, stream) P(purify_plan_desc, dtype) P(purify_plan_desc, block_offsets)
+  P(purify_sdmm_params, resume) P(purify_sdmm_params, check_every) P(purify_sdmm_stats, status)
+  P(purify_plan_info, workspace_bytes) P(purify_plan_info, beta)
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "probe.c")
+        exe = os.path.join(d, "probe")
+        open(src, "w").write(probe)
+        subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
+        lines = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = dict(l.rsplit(" ", 1) for l in lines if l)
+    assert int(got["desc"]) == ctypes.sizeof(_lib.purify_plan_desc)
+    assert int(got["info"]) == ctypes.sizeof(_lib.purify_plan_info)
+    assert int(got["params"]) == ctypes.sizeof(_lib.purify_sdmm_params)
+    assert int(got["stats"]) == ctypes.sizeof(_lib.purify_sdmm_stats)
+    assert int(got["ktime"]) == ctypes.sizeof(_lib.purify_kernel_time)
+    assert int(got["purify_plan_desc.tile"]) == _lib.purify_plan_desc.tile.offset
+    assert int(got["purify_plan_desc.stream"]) == _lib.purify_plan_desc.stream.offset
+    assert int(got["purify_plan_desc.dtype"]) == _lib.purify_plan_desc.dtype.offset
+    assert int(got["purify_plan_desc.block_offsets"]) == _lib.purify_plan_desc.block_offsets.offset
+    assert int(got["purify_sdmm_params.resume"]) == _lib.purify_sdmm_params.resume.offset
+    assert int(got["purify_sdmm_params.check_every"]) == _lib.purify_sdmm_params.check_every.offset
+    assert int(got["purify_sdmm_stats.status"]) == _lib.purify_sdmm_stats.status.offset
+    assert int(got["purify_plan_info.workspace_bytes"]) == _lib.purify_plan_info.workspace_bytes.offset
+    assert int(got["purify_plan_info.beta"]) == _lib.purify_plan_info.beta.offset
+
+
+def test_invalid_description_is_rejected_before_any_launch(lib):
+    # no GPU needed: validation happens on the host first
+    d = _lib.purify_plan_desc(nx=30, ny=32, M=10, u=None, v=None, R=1, kb_width=6, levels=3)
+    h = ctypes.c_void_p()
+    assert lib.purify_plan_create(ctypes.byref(d), ctypes.byref(h)) == _lib.PURIFY_EINVAL
+    assert b"powers of two" in lib.purify_last_error()
+    assert lib.purify_plan_create(None, ctypes.byref(h)) == _lib.PURIFY_EINVAL
+    assert lib.purify_phi(None, None, None) == _lib.PURIFY_EINVAL
+    assert lib.purify_plan_destroy(None) == _lib.PURIFY_OK
+
+
+def test_launch_counter_starts_finite(lib):
+    assert lib.purify_launch_count() >= 0
