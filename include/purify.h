@@ -125,7 +125,8 @@ typedef struct {
     int32_t max_iter;     /* outer SDMM iterations (exact count when rel_obj_tol == 0) */
     int32_t cg_iters;     /* conjugate-gradient iterations per x-update (cap) */
     double cg_tol;        /* 0 => exactly cg_iters CG steps (fewer only if the residual is 0);
-                             > 0 => stop when ||r|| <= cg_tol ||b|| */
+                             > 0 => stop when ||r|| <= cg_tol ||r_0||, r_0 the residual of
+                             the warm start of that x-update */
     double gamma;         /* SDMM step; <= 0 => 1e-3 max|Psi^dagger Re Phi^H y| / nu^2 */
     double nu;            /* data-term scale ||Phi||_2; <= 0 => 100 power iterations */
     double rel_obj_tol;   /* > 0: stop once the relative objective change < rel_obj_tol
@@ -163,6 +164,16 @@ typedef struct {
 purify_status purify_sdmm_solve(purify_plan *plan, const void *y, const double *eps,
                                 const void *w, void *x, const purify_sdmm_params *params,
                                 purify_sdmm_stats *stats);
+
+/* Advance the state of the last purify_sdmm_solve on this plan by `iters`
+ * further SDMM iterations (same y, eps, w, gamma, nu and CG settings),
+ * asynchronously on the plan's stream and without computing statistics.
+ * Without kernel timing enabled the iteration runs as a captured CUDA graph
+ * (captured on first use and whenever gamma, nu, w or the CG count change).
+ * The iterate stays on the device; purify_sdmm_solve with resume = 1 and
+ * max_iter = 0 returns it with statistics. Errors: EINVAL if no solve was
+ * started on the plan. */
+purify_status purify_sdmm_iterate(purify_plan *plan, int32_t iters);
 
 /* SARA weights (Sec. 1, reweighted l1): w = rho / (rho + |Psi^dagger x|),
  * x real [ny][nx], w real [q][ny][nx]; rho > 0. */

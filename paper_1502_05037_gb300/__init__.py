@@ -17,7 +17,8 @@ from ._lib import (PURIFY_F32, PURIFY_F64, PurifyError, check, load, purify_kern
 
 __all__ = [
     "Plan", "purify_plan_create", "purify_plan_destroy", "purify_phi", "purify_phi_adj", "purify_fft2",
-    "purify_psi", "purify_psi_adj", "purify_op_norm_sq", "purify_sdmm_solve", "purify_reweight",
+    "purify_psi", "purify_psi_adj", "purify_op_norm_sq", "purify_sdmm_solve", "purify_sdmm_iterate",
+    "purify_reweight",
     "purify_coef_std", "purify_launch_count", "PurifyError", "PURIFY_F32", "PURIFY_F64",
 ]
 
@@ -138,6 +139,11 @@ def purify_sdmm_solve(plan: Plan, y, eps, x, w=None, max_iter=200, cg_iters=10, 
     if raise_on_error:
         check(status)
     return st
+
+
+def purify_sdmm_iterate(plan: Plan, iters: int):
+    """Advance the plan's current SDMM state by `iters` iterations (async)."""
+    check(load().purify_sdmm_iterate(plan.handle, int(iters)))
 
 
 def purify_reweight(plan: Plan, x, rho: float, w):

@@ -91,6 +91,7 @@ _SIGS = {
     "purify_op_norm_sq": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_double)]),
     "purify_sdmm_solve": (C.c_int, [_P, _P, C.POINTER(C.c_double), _P, _P,
                                     C.POINTER(purify_sdmm_params), C.POINTER(purify_sdmm_stats)]),
+    "purify_sdmm_iterate": (C.c_int, [_P, C.c_int32]),
     "purify_reweight": (C.c_int, [_P, _P, C.c_double, _P]),
     "purify_coef_std": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
     "purify_timing_enable": (C.c_int, [_P, C.c_int32]),

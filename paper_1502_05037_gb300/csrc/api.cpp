@@ -17,6 +17,7 @@ static thread_local std::string g_last_error;
 static std::atomic<int64_t> g_launches{0};
 
 void set_error(const std::string& msg) { g_last_error = msg; }
+void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 struct KernelTimer {
     bool enabled = false;
@@ -48,6 +49,8 @@ struct KernelTimer {
         for (auto e : pool) cudaEventDestroy(e);
     }
 };
+
+bool timing_enabled(const purify_plan* p) { return p->timer && p->timer->enabled; }
 
 Launch::Launch(purify_plan* plan, const char* kname) : p(plan), name(kname) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -236,6 +239,14 @@ purify_status purify_sdmm_solve(purify_plan* p, const void* y, const double* eps
         PURIFY_REQUIRE(!params->resume || p->sd.started, "resume without a previous solve on this plan");
         if (stats) std::memset(stats, 0, sizeof(*stats));
         sdmm_solve(p, y, eps, w, x, *params, stats);
+    });
+}
+
+purify_status purify_sdmm_iterate(purify_plan* p, int32_t iters) {
+    return guarded([&] {
+        PURIFY_REQUIRE(p != nullptr && iters >= 0, "bad argument");
+        PURIFY_REQUIRE(p->sd.started, "no SDMM solve started on this plan");
+        sdmm_iterate(p, iters);
     });
 }
 

@@ -83,7 +83,22 @@ struct SdmmState {
     DevBuf chunk_first;           // int [R + 1]: first visibility chunk of each block
     bool started = false;
     double gamma = 0, nu = 0;
+    int cg_iters = 10;
     std::vector<double> eps_host;
+    // captured iteration graph
+    cudaStream_t gstream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    int g_cg = -1;
+    double g_gamma = 0, g_nu = 0;
+    bool g_have_w = false;
+    int64_t g_kernels = 0;
+    ~SdmmState() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+        if (gstream) cudaStreamDestroy(gstream);
+    }
     int64_t iters_done = 0;
     int64_t cg_total = 0;
 };
@@ -152,6 +167,9 @@ void init_filter_banks();
 void sdmm_solve(purify_plan* p, const void* y, const double* eps, const void* w, void* x,
                 const purify_sdmm_params& prm, purify_sdmm_stats* st);
 double op_norm_sq(purify_plan* p, int iters);
+void sdmm_iterate(purify_plan* p, int iters);
+void add_launches(int64_t n);
+bool timing_enabled(const purify_plan* p);
 void reweight(purify_plan* p, const void* x, double rho, void* w);
 double coef_std(purify_plan* p, const void* x);
 

@@ -564,6 +564,82 @@ template <typename T> struct Solver {
     }
 };
 
+// Run `n` iterations: eager when kernel timing is on, otherwise as replays of
+// a captured one-iteration graph on the plan's private stream, ordered after
+// and before the caller's stream with events.
+template <typename T> static void run_iterations(purify_plan* p, int n) {
+    SdmmState& s = p->sd;
+    Solver<T> S(p);
+    if (n <= 0) return;
+    if (timing_enabled(p)) {
+        for (int i = 0; i < n; ++i) S.iteration(s.cg_iters);
+        return;
+    }
+    if (!s.gstream) {
+        PURIFY_CUDA(cudaStreamCreateWithFlags(&s.gstream, cudaStreamNonBlocking));
+        PURIFY_CUDA(cudaEventCreateWithFlags(&s.ev_in, cudaEventDisableTiming));
+        PURIFY_CUDA(cudaEventCreateWithFlags(&s.ev_out, cudaEventDisableTiming));
+    }
+    cudaStream_t user = p->stream;
+    PURIFY_CUDA(cudaEventRecord(s.ev_in, user));
+    PURIFY_CUDA(cudaStreamWaitEvent(s.gstream, s.ev_in, 0));
+    int start = 0;
+    if (!s.gexec || s.g_cg != s.cg_iters || s.g_gamma != s.gamma || s.g_nu != s.nu || s.g_have_w != s.have_w) {
+        if (s.gexec) { cudaGraphExecDestroy(s.gexec); s.gexec = nullptr; }
+        p->stream = s.gstream;
+        try {
+            // one eager iteration first (sets kernel attributes outside capture)
+            S.iteration(s.cg_iters);
+            start = 1;
+            cudaGraph_t g = nullptr;
+            PURIFY_CUDA(cudaStreamBeginCapture(s.gstream, cudaStreamCaptureModeThreadLocal));
+            try {
+                S.iteration(s.cg_iters);
+            } catch (...) {
+                cudaStreamEndCapture(s.gstream, &g);
+                if (g) cudaGraphDestroy(g);
+                throw;
+            }
+            PURIFY_CUDA(cudaStreamEndCapture(s.gstream, &g));
+            size_t nn = 0;
+            PURIFY_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
+            std::vector<cudaGraphNode_t> nodes(nn);
+            PURIFY_CUDA(cudaGraphGetNodes(g, nodes.data(), &nn));
+            int64_t kn = 0;
+            for (auto nd : nodes) {
+                cudaGraphNodeType t;
+                PURIFY_CUDA(cudaGraphNodeGetType(nd, &t));
+                if (t == cudaGraphNodeTypeKernel) ++kn;
+            }
+            cudaError_t ie = cudaGraphInstantiate(&s.gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) { s.gexec = nullptr; PURIFY_CUDA(ie); }
+            s.g_kernels = kn;
+            s.g_cg = s.cg_iters;
+            s.g_gamma = s.gamma;
+            s.g_nu = s.nu;
+            s.g_have_w = s.have_w;
+            // the captured launches were counted once while capturing
+            add_launches(-kn);
+        } catch (...) {
+            p->stream = user;
+            throw;
+        }
+        p->stream = user;
+    }
+    for (int i = start; i < n; ++i) {
+        PURIFY_CUDA(cudaGraphLaunch(s.gexec, s.gstream));
+        add_launches(s.g_kernels);
+    }
+    PURIFY_CUDA(cudaEventRecord(s.ev_out, s.gstream));
+    PURIFY_CUDA(cudaStreamWaitEvent(user, s.ev_out, 0));
+}
+
+void sdmm_iterate(purify_plan* p, int iters) {
+    if (p->dtype == PURIFY_F32) run_iterations<float>(p, iters); else run_iterations<double>(p, iters);
+    p->sd.iters_done += iters;
+}
+
 // ------------------------------------------------------------ entry points
 template <typename T>
 static void sdmm_solve_t(purify_plan* p, const void* y, const double* eps, const void* w, void* x_io,
@@ -628,16 +704,21 @@ static void sdmm_solve_t(purify_plan* p, const void* y, const double* eps, const
         double tol2 = prm.cg_tol > 0 ? prm.cg_tol * prm.cg_tol : 0.0;
         PURIFY_CUDA(cudaMemcpyAsync(S.scal() + S_TOL2, &tol2, sizeof(double), cudaMemcpyHostToDevice, p->stream));
     }
-    const int cg_iters = prm.cg_iters > 0 ? prm.cg_iters : 10;
+    s.cg_iters = prm.cg_iters > 0 ? prm.cg_iters : 10;
     const int check = prm.check_every > 0 ? prm.check_every : 10;
     const bool tol_mode = prm.rel_obj_tol > 0;
     int done = 0;
     purify_status status = PURIFY_OK;
     bool converged = false;
-    for (int it = 0; it < prm.max_iter; ++it) {
-        S.iteration(cg_iters);
-        ++done;
-        if (tol_mode && ((it + 1) % check == 0 || it + 1 == prm.max_iter)) {
+    if (!tol_mode) {
+        run_iterations<T>(p, prm.max_iter);
+        done = prm.max_iter;
+    }
+    for (int it = 0; tol_mode && it < prm.max_iter; it += check) {
+        const int n = std::min(check, prm.max_iter - it);
+        run_iterations<T>(p, n);
+        done += n;
+        {
             std::vector<double> sc(S_BLOCKS + 2 * p->R);
             PURIFY_CUDA(cudaMemcpyAsync(sc.data(), S.scal(), sizeof(double) * sc.size(), cudaMemcpyDeviceToHost, p->stream));
             PURIFY_CUDA(cudaStreamSynchronize(p->stream));

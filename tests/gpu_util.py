@@ -42,3 +42,11 @@ def make_plan(nx, ny, M, J, levels=3, R=1, dtype=pk.PURIFY_F32, seed=0, sigma=np
     plan = pk.Plan(nx, ny, torch.from_numpy(u).to(DEV), torch.from_numpy(v).to(DEV), kb_width=J, levels=levels,
                    block_offsets=offs, dtype=dtype, basis_mask=mask, tile=tile)
     return plan, u, v, offs
+
+
+def snr_db(x_true, x):
+    """Reconstruction SNR in dB (computed here so that no CUDA output is fed
+    to the oracle)."""
+    x_true = np.asarray(x_true, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    return float(20.0 * np.log10(np.linalg.norm(x_true) / np.linalg.norm(x_true - x)))
