@@ -1,0 +1,456 @@
+#!/usr/bin/env python
+"""Benchmark of the SARA/SDMM imaging hot path on GB300.
+
+Workload (default): 256 x 256 sky, M = 655,360 visibilities (Gaussian (u, v)
+density), Kaiser-Bessel width J = 6, oversampling 2, Psi = Dirac + db1..db8 at
+4 levels (q = 9), R = 8 uneven blocks, FP32 operators with FP64 reductions,
+30 dB input SNR, synthetic seeded data. One step = one SDMM iteration
+(Psi^dagger + prox, Phi + block projections, positivity, Psi, Phi^dagger and
+CG_ITERS conjugate-gradient steps of Phi^dagger Phi) on the plan's resident
+state, launched as one captured CUDA graph.
+
+Passes (all in one run):
+  A  timed pass: W warm-up steps, then K steps each bracketed by CUDA events
+     on the launching stream; a 512 MiB buffer is rewritten between steps to
+     flush L2 (outside the events).                      -> value, ms_per_step
+  B  roofline pass: the same K steps launched eagerly with per-kernel CUDA
+     events; the dominant kernel's algorithmic bytes / mean duration.
+  C  end-to-end pass: K calls of purify_sdmm_solve with pinned host buffers
+     (y in, x in/out), one iteration each, wall-clock timed.  -> e2e
+  D  Phi + Phi^dagger through the C ABI (caller order).      -> Gvis/s
+  E  CPU baseline: the FP64 oracle, one SDMM iteration on a visibility
+     sample, scaled to the full workload (rank 0, N = 1 only).
+
+With torchrun (N > 1) every rank solves its own independent problem (replicas,
+weak scaling); the max over ranks of the timed region sets the time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+CG_ITERS = 8
+FLUSH_BYTES = 512 << 20
+HBM_FALLBACK_GBS = 6800.0
+
+
+# --------------------------------------------------------------- helpers
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return HBM_FALLBACK_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows]
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
+
+
+def algorithmic_bytes(name: str, info, dtype_bytes: int = 4) -> float | None:
+    """Bytes a kernel launch must move at minimum (FP32, internal order):
+    visibility kernels 8 B per (u, v) pair and 8 B per complex visibility,
+    the oversampled grid 8 B per cell read or written once, images 4 B per
+    pixel, coefficients 4 B per entry."""
+    N, M, Kx, Ky, D = info.N, info.M, info.Kx, info.Ky, info.D
+    ny = int(round(np.sqrt(N * Ky / Kx)))
+    c = 2 * dtype_bytes
+    table = {
+        "degrid": 8 * M + c * M + c * Kx * Ky,
+        "grid": 8 * M + c * M + c * Kx * Ky,
+        "fft_rows_fwd": dtype_bytes * N + c * ny * Kx,
+        "fft_cols_fwd": c * ny * Kx + c * Kx * Ky,
+        "fft_cols_inv": c * Kx * Ky + c * ny * Kx,
+        "fft_rows_inv": c * ny * Kx + 2 * dtype_bytes * N,
+        "prox_l1": 4 * dtype_bytes * D,
+        "proj_norms": 3 * c * M,
+        "proj_apply": 5 * c * M,
+        "positivity": 5 * dtype_bytes * N,
+        "cg_alpha": 2 * dtype_bytes * N,
+        "cg_update": 6 * dtype_bytes * N,
+        "cg_init": 2 * dtype_bytes * N,
+        "relchange": 2 * dtype_bytes * N,
+    }
+    return float(table[name]) if name in table else None
+
+
+def source_sha1(relpath: str) -> str:
+    return hashlib.sha1(open(os.path.join(ROOT, relpath), "rb").read()).hexdigest()
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current source of that kernel; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+        e = d.get(kernel)
+        if not e:
+            return None
+        if e.get("source_sha1") != source_sha1(e["source"]):
+            return None
+        return float(e["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+KERNEL_SOURCE = {"degrid": "paper_1502_05037_gb300/csrc/nufft.cu", "grid": "paper_1502_05037_gb300/csrc/nufft.cu"}
+
+
+# -------------------------------------------------------- problem set-up
+def setup_problem(wl_name: str, replica: int, dev):
+    import torch
+
+    import paper_1502_05037_gb300 as pk
+    from paper_1502_05037_gb300 import problem, synth
+
+    wl = synth.WORKLOADS[wl_name]
+    if replica:
+        wl = synth.Workload(**{**wl.__dict__, "index": wl.index + 1000 * replica})
+    x_true, u, v, offs, nz = wl.draw()
+    plan = pk.Plan(wl.nx, wl.ny, torch.from_numpy(u).to(dev), torch.from_numpy(v).to(dev), kb_width=wl.J,
+                   levels=wl.levels, block_offsets=offs, stream=torch.cuda.current_stream(dev))
+    xt = torch.from_numpy(x_true.astype(np.float32)).to(dev)
+    y0 = torch.empty(wl.M, dtype=torch.complex64, device=dev)
+    pk.purify_phi(plan, xt, y0)
+    sigma = problem.noise_sigma_from_norm(float(torch.linalg.vector_norm(y0.to(torch.complex128)).item()), wl.M,
+                                          wl.snr_db)
+    y = y0 + torch.from_numpy((sigma * nz).astype(np.complex64)).to(dev)
+    eps = problem.chi2_epsilon(sigma, np.diff(offs))
+    return wl, plan, y, eps, x_true
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args):
+    import torch
+
+    import paper_1502_05037_gb300 as pk
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    from paper_1502_05037_gb300 import build as pbuild
+    pbuild.build()
+    pk.load()
+
+    wl, plan, y, eps, x_true = setup_problem(args.workload, rank, dev)
+    stream = torch.cuda.current_stream(dev)
+    x = torch.zeros((wl.ny, wl.nx), dtype=torch.float32, device=dev)
+    # initialise the solver state: nu by power iteration, default gamma
+    st0 = pk.purify_sdmm_solve(plan, y, eps, x, max_iter=0, cg_iters=args.cg_iters)
+    nu, gamma = st0.nu, st0.gamma
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+
+    # ---- pass A: timed steps (graph replays)
+    for i in range(args.warmup):
+        flush.fill_(i & 0xFF)
+        pk.purify_sdmm_iterate(plan, 1)
+    barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = pk.purify_launch_count()
+    with ClockSampler(dev.index if dev.index is not None else 0) as clk:
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_((k + 7) & 0xFF)
+            evs[k][0].record(stream)
+            pk.purify_sdmm_iterate(plan, 1)
+            evs[k][1].record(stream)
+        barrier()
+        t_wall = time.perf_counter() - t_wall0
+    launches = pk.purify_launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    clocks = clk.summary()
+    value = world * args.steps / (total_ms / 1e3)
+
+    # ---- pass B: per-kernel timing of the same steps (eager launches)
+    pk.purify_timing_enable(plan, True)
+    pk.purify_timing_read(plan, reset=True)
+    for k in range(args.steps):
+        flush.fill_((k + 3) & 0xFF)
+        pk.purify_sdmm_iterate(plan, 1)
+    torch.cuda.synchronize(dev)
+    ktimes = pk.purify_timing_read(plan, reset=True)
+    pk.purify_timing_enable(plan, False)
+    dom = max(ktimes.items(), key=lambda kv: kv[1][1]) if ktimes else None
+    peak, peak_src = peaks()
+    roofline = None
+    if dom:
+        name, (nl, tms) = dom
+        per = tms / nl
+        ab = algorithmic_bytes(name, plan.info)
+        achieved = ab / (per * 1e-3) / 1e9 if ab else None
+        tr = ncu_traffic(name)
+        roofline = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "peak_source": peak_src,
+                    "unit": "GB/s", "frac": (achieved / peak if achieved else None), "traffic": tr,
+                    "algorithmic_bytes_per_launch": ab, "mean_launch_us": per * 1e3,
+                    "launches_per_step": nl / args.steps,
+                    "share_of_kernel_time": tms / sum(t for _, t in ktimes.values())}
+    kernel_table = {k: {"launches_per_step": n / args.steps, "ms_per_step": t / args.steps,
+                        "gbs": (algorithmic_bytes(k, plan.info) / (t / n * 1e-3) / 1e9
+                                if algorithmic_bytes(k, plan.info) else None)}
+                    for k, (n, t) in sorted(ktimes.items(), key=lambda kv: -kv[1][1])}
+
+    # ---- pass C: end to end through the public API with pinned host buffers
+    y_host = torch.empty(wl.M, dtype=torch.complex64, pin_memory=True)
+    y_host.copy_(y.cpu())
+    x_host = torch.zeros((wl.ny, wl.nx), dtype=torch.float32, pin_memory=True)
+    e2e_times = []
+    for k in range(args.warmup + args.steps):
+        x_host.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        pk.purify_sdmm_solve(plan, y_host.numpy(), eps, x_host.numpy(), max_iter=1, cg_iters=args.cg_iters,
+                             gamma=gamma, nu=nu)
+        t1 = time.perf_counter()
+        if k >= args.warmup:
+            e2e_times.append(t1 - t0)
+    e2e_total = sum(e2e_times)
+    if dist is not None:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e = {"value": world * args.steps / e2e_total, "unit": "iters/s",
+           "h2d_bytes_per_step": wl.M * 8 + wl.nx * wl.ny * 4, "d2h_bytes_per_step": wl.nx * wl.ny * 4,
+           "call": "purify_sdmm_solve(host y, host x, max_iter=1)"}
+
+    # ---- pass D: Phi + Phi^dagger Gvis/s (caller order, device buffers)
+    xin = torch.from_numpy(x_true.astype(np.float32)).to(dev)
+    yv = torch.empty(wl.M, dtype=torch.complex64, device=dev)
+    xa = torch.empty((wl.ny, wl.nx), dtype=torch.complex64, device=dev)
+    for _ in range(3):
+        pk.purify_phi(plan, xin, yv)
+        pk.purify_phi_adj(plan, yv, xa)
+    ph = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record(stream)
+        pk.purify_phi(plan, xin, yv)
+        b.record(stream)
+        pk.purify_phi_adj(plan, yv, xa)
+        c.record(stream)
+        ph.append((a, b, c))
+    torch.cuda.synchronize(dev)
+    t_phi = sum(a.elapsed_time(b) for a, b, _ in ph) / args.steps
+    t_adj = sum(b.elapsed_time(c) for _, b, c in ph) / args.steps
+    gvis = wl.M / ((t_phi + t_adj) * 1e-3) / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, args.cg_iters, budget_s=args.cpu_budget)
+
+    if rank == 0:
+        line = {
+            "metric": "SDMM iters/s", "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{wl.name}: {wl.nx}x{wl.ny} sky, M={wl.M}, J={wl.J}, alpha=2, q=9, "
+                                   f"L={wl.levels}, R={wl.R}, {wl.snr_db:g} dB",
+                       "cg_iters": args.cg_iters, "parallelism": f"replicas x{world}",
+                       "l2": "512 MiB buffer rewritten between timed steps"},
+            "phi_phiadj_gvis_s": gvis, "phi_ms": t_phi, "phi_adj_ms": t_adj,
+            "e2e": e2e, "gpu_launches": int(launches), "gpu_launches_per_step": launches / args.steps,
+            "wall_s_timed": t_wall, "clocks": clocks, "roofline": roofline, "cpu_baseline": cpu,
+            "kernels": kernel_table,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+# ------------------------------------------------------------- oracle arm
+def oracle_iteration_seconds(wl_name: str, cg_iters: int, vis_sample: int, seed=0):
+    """Seconds of one FP64 oracle SDMM iteration on the workload, measured on
+    a visibility sample and scaled: the sampled iteration is timed whole,
+    then the visibility-proportional steps (gridding and degridding, once per
+    Phi and Phi^dagger: cg_iters + 1 of each) are timed alone on the sample and
+    extrapolated linearly to all M visibilities."""
+    from oracle import nufft as onf
+    from oracle import sdmm as osd
+    from paper_1502_05037_gb300 import problem, synth
+
+    wl = synth.WORKLOADS[wl_name]
+    x_true, u, v, offs, nz = wl.draw()
+    g = np.random.default_rng(seed)
+    Ms = int(min(wl.M, max(1024, vis_sample)))
+    idx = np.sort(g.choice(wl.M, Ms, replace=False))
+    blk = np.searchsorted(offs, idx, side="right") - 1
+    offs_s = np.concatenate([[0], np.cumsum(np.bincount(blk, minlength=wl.R))])
+    keep = np.diff(offs_s) > 0
+    offs_s = np.concatenate([[0], np.cumsum(np.diff(offs_s)[keep])])
+    op = onf.NufftPlan(wl.nx, wl.ny, u[idx].astype(np.float64), v[idx].astype(np.float64), wl.J)
+    y0 = onf.phi(op, x_true)
+    sig = problem.noise_sigma_from_norm(float(np.linalg.norm(y0)), Ms, wl.snr_db)
+    y = y0 + sig * nz[idx]
+    eps = problem.chi2_epsilon(sig, np.diff(offs_s))
+    # fixed constants: nu and gamma change no step count of the oracle's work
+    prob = osd.Problem(op, wl.levels, y, offs_s, eps, nu=1.0, gamma=1e-4)
+    st = osd.init_state(prob, np.zeros((wl.ny, wl.nx)))
+    t0 = time.perf_counter()
+    osd.sdmm_iteration(prob, st, cg_iters)
+    t_iter = time.perf_counter() - t0
+    X = onf.fft2(onf.scale_pad(op, x_true))
+    t0 = time.perf_counter()
+    onf.degrid(op, X)
+    onf.grid(op, y)
+    t_vis = time.perf_counter() - t0
+    total = t_iter + (cg_iters + 1) * t_vis * (wl.M / Ms - 1.0)
+    return total, Ms, t_iter, t_vis
+
+
+def cpu_threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(wl, cg_iters, budget_s=20.0):
+    Ms = int(65536 * max(0.25, budget_s / 20.0))
+    total, Ms, t_iter, t_vis = oracle_iteration_seconds(wl.name, cg_iters, Ms)
+    return {"value": 1.0 / total, "unit": "iters/s", "cores": 1, "kind": "oracle",
+            "threads_available": cpu_threads(),
+            "sample": f"one FP64 oracle SDMM iteration (k_CG={cg_iters}) on {Ms} of {wl.M} visibilities "
+                      f"({t_iter:.1f} s), gridding+degridding timed alone on the sample ({t_vis:.2f} s) "
+                      f"and scaled to all visibilities; NumPy/SciPy single-threaded"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1502_05037_gb300 import synth
+    wl = synth.WORKLOADS[args.workload]
+    per_step_budget = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+    Ms = int(65536 * per_step_budget / 6.0)
+    secs = []
+    for k in range(args.warmup + args.steps):
+        total, Ms_used, t_iter, t_vis = oracle_iteration_seconds(args.workload, args.cg_iters, Ms, seed=k)
+        if k >= args.warmup:
+            secs.append(total)
+    value = args.steps / sum(secs)
+    line = {
+        "impl": "reference", "metric": "SDMM iters/s", "value": value, "unit": "iters/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{wl.name}: {wl.nx}x{wl.ny} sky, M={wl.M}, J={wl.J}, alpha=2, q=9, "
+                               f"L={wl.levels}, R={wl.R}, {wl.snr_db:g} dB", "cg_iters": args.cg_iters},
+        "cpu_baseline": {"value": value, "unit": "iters/s", "kind": "oracle", "cores": 1,
+                         "sample": f"each step: one oracle SDMM iteration on {Ms_used} of {wl.M} visibilities, "
+                                   f"visibility-proportional steps scaled to all M"},
+        "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="sara256_r8")
+    ap.add_argument("--cg-iters", type=int, default=CG_ITERS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
