@@ -156,6 +156,13 @@ def purify_coef_std(plan: Plan, x) -> float:
     return out.value
 
 
+def purify_psi_adj_static(x, c, nx: int, ny: int, levels: int, basis_mask: int = 0, dtype: int = PURIFY_F32,
+                          stream=None):
+    """Psi^dagger without a plan and without any device allocation (device
+    pointers only; see include/purify.h for the size limit and sharing)."""
+    check(load().purify_psi_adj_static(_ptr(x), _ptr(c), nx, ny, levels, basis_mask, dtype, _stream_ptr(stream)))
+
+
 def purify_timing_enable(plan: Plan, enable: bool = True):
     check(load().purify_timing_enable(plan.handle, int(bool(enable))))
 

@@ -270,6 +270,26 @@ purify_status purify_coef_std(purify_plan* p, const void* x, double* std_out) {
     });
 }
 
+purify_status purify_psi_adj_static(const void* x, void* c, int32_t nx, int32_t ny, int32_t levels,
+                                    uint32_t basis_mask, purify_dtype dtype, void* stream) {
+    return guarded([&] {
+        PURIFY_REQUIRE(x && c, "null argument");
+        PURIFY_REQUIRE(dtype == PURIFY_F32 || dtype == PURIFY_F64, "dtype must be PURIFY_F32 or PURIFY_F64");
+        PURIFY_REQUIRE(nx >= 8 && ny >= 8 && nx <= 4096 && ny <= 4096 && (nx & (nx - 1)) == 0 && (ny & (ny - 1)) == 0,
+                       "nx, ny must be powers of two in [8, 4096]");
+        PURIFY_REQUIRE(levels >= 1 && levels <= 8 && (nx >> (levels - 1)) >= 2 && (ny >> (levels - 1)) >= 2,
+                       "image too small for the number of levels");
+        const uint32_t mask = basis_mask ? basis_mask : 0x1FFu;
+        PURIFY_REQUIRE((mask & ~0x1FFu) == 0, "basis_mask has bits above db8");
+        const size_t need = psi_adj_static_bytes(nx, ny, mask, dtype);
+        PURIFY_REQUIRE(need <= psi_adj_static_capacity(),
+                       "image too large for the static scratch: needs " + std::to_string(need) + " of " +
+                           std::to_string(psi_adj_static_capacity()) + " bytes");
+        PURIFY_REQUIRE(!is_host_pointer(x) && !is_host_pointer(c), "x and c must be device pointers");
+        psi_adj_static(x, c, nx, ny, levels, mask, dtype, (cudaStream_t)stream);
+    });
+}
+
 purify_status purify_timing_enable(purify_plan* p, int32_t enable) {
     return guarded([&] {
         PURIFY_REQUIRE(p != nullptr, "null plan");

@@ -162,6 +162,10 @@ void launch_rows_inv_crop(purify_plan* p, void* out, double scale, int out_mode,
 void launch_psi_adj(purify_plan* p, const void* x, void* c);
 void launch_psi(purify_plan* p, const void* c, void* x);
 void init_filter_banks();
+// allocation-free Psi^dagger (file-scope static scratch, see wavelet.cu)
+void psi_adj_static(const void* x, void* c, int nx, int ny, int levels, unsigned mask, int dtype, cudaStream_t st);
+size_t psi_adj_static_bytes(int nx, int ny, unsigned mask, int dtype);
+size_t psi_adj_static_capacity();
 
 // solver
 void sdmm_solve(purify_plan* p, const void* y, const double* eps, const void* w, void* x,

@@ -22,6 +22,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "internal.h"
@@ -368,6 +370,124 @@ void launch_psi_adj(purify_plan* p, const void* x, void* c) {
 }
 void launch_psi(purify_plan* p, const void* c, void* x) {
     if (p->dtype == PURIFY_F32) psi_t<float>(p, c, x); else psi_t<double>(p, c, x);
+}
+
+}  // namespace purify
+
+// ------------------------------------------- allocation-free Psi^dagger
+// A plan-free variant of the multilevel analysis for callers that must not
+// allocate device memory. The low-pass ping-pong scratch of the level
+// kernels lives in one file-scope device array instead of plan buffers; every
+// device that loads this library holds it until the process exits.
+namespace purify {
+
+static const size_t kStaticScratchBytes = size_t(4) << 20;  // 4 MiB
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// Host code cannot use g_static_scratch's name as a device address: its
+// device address is looked up once per device (with that device current).
+static std::mutex g_static_mutex;
+static void* g_static_addr[64];
+
+static void* static_scratch_address() {
+    int dev = 0;
+    PURIFY_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) throw Error{PURIFY_ECUDA, "device index out of range"};
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_addr[dev]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess || ptr == nullptr) {
+            cudaGetLastError();
+            throw Error{PURIFY_ECUDA, std::string("cudaGetSymbolAddress of the static scratch failed: ") +
+                                          cudaGetErrorString(e)};
+        }
+        g_static_addr[dev] = ptr;
+    }
+    return g_static_addr[dev];
+}
+
+// Basis table of a mask: pids[z] = db index of wavelet z, planes[z] = its
+// coefficient plane (written into the static scratch by the device).
+__global__ void k_static_meta(unsigned mask, int* meta) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int z = 0, plane = 0;
+    for (int b = 0; b < 9; ++b) {
+        if (!(mask >> b & 1)) continue;
+        if (b > 0) { meta[z] = b; meta[8 + z] = plane; ++z; }
+        ++plane;
+    }
+    for (; z < 8; ++z) { meta[z] = 0; meta[8 + z] = 0; }
+}
+
+size_t psi_adj_static_bytes(int nx, int ny, unsigned mask, int dtype) {
+    int nw = 0;
+    for (int b = 1; b < 9; ++b) nw += (mask >> b & 1);
+    size_t rb = dtype == PURIFY_F32 ? 4 : 8;
+    size_t N = (size_t)nx * ny;
+    return 256 + 2 * (size_t)nw * (N / 4) * rb;
+}
+
+size_t psi_adj_static_capacity() { return kStaticScratchBytes; }
+
+template <typename T>
+static void psi_adj_static_t(const T* x, T* c, int nx, int ny, int levels, unsigned mask, cudaStream_t st) {
+    unsigned char* base = static_cast<unsigned char*>(static_scratch_address());
+    int* meta = reinterpret_cast<int*>(base);
+    const size_t N = (size_t)nx * ny;
+    int nw = 0, q = 0, dirac_plane = -1;
+    for (int b = 0; b < 9; ++b) {
+        if (!(mask >> b & 1)) continue;
+        if (b == 0) dirac_plane = q; else ++nw;
+        ++q;
+    }
+    T* bufs[2] = {reinterpret_cast<T*>(base + 256), reinterpret_cast<T*>(base + 256) + (size_t)nw * (N / 4)};
+    int maxL = 2;
+    for (int b = 1; b < 9; ++b) if (mask >> b & 1) maxL = std::max(maxL, 2 * b);
+    const T inv_sqrt_q = (T)(1.0 / std::sqrt((double)q));
+    k_static_meta<<<1, 32, 0, st>>>(mask, meta);
+    PURIFY_CUDA(cudaGetLastError());
+    add_launches(1);
+    const int* pids = meta;
+    const int* planes = meta + 8;
+    if (nw == 0) {
+        dim3 g((nx + 31) / 32, (ny + 31) / 32, 1);
+        k_dwt_level<T><<<g, 256, 0, st>>>(x, 0, nx, c, planes, (int)N, nx, nullptr, 0, ny, nx, 16, 16, pids, 0,
+                                          dirac_plane, inv_sqrt_q);
+        PURIFY_CUDA(cudaGetLastError());
+        add_launches(1);
+        return;
+    }
+    int h = ny, w = nx;
+    const T* src = x;
+    int src_stride = 0, src_ld = nx;
+    const int llstride = (int)(N / 4);
+    for (int lev = 0; lev < levels; ++lev) {
+        const bool last = lev == levels - 1;
+        const int hs = h / 2, wsub = w / 2;
+        const int TH = std::min(16, hs), TW = std::min(16, wsub);
+        const int Rin = 2 * TH + maxL - 2, Cin = 2 * TW + maxL - 2;
+        size_t sm = sizeof(T) * ((size_t)Rin * Cin + 2 * (size_t)Rin * TW);
+        int zdim = nw + ((lev == 0 && dirac_plane >= 0) ? 1 : 0);
+        dim3 g((wsub + TW - 1) / TW, (hs + TH - 1) / TH, zdim);
+        T* llo = last ? nullptr : bufs[lev & 1];
+        k_dwt_level<T><<<g, 256, sm, st>>>(src, src_stride, src_ld, c, planes, (int)N, nx, llo, llstride, h, w, TH,
+                                           TW, pids, nw, dirac_plane, inv_sqrt_q);
+        PURIFY_CUDA(cudaGetLastError());
+        add_launches(1);
+        src = llo;
+        src_stride = llstride;
+        src_ld = wsub;
+        h = hs;
+        w = wsub;
+    }
+}
+
+void psi_adj_static(const void* x, void* c, int nx, int ny, int levels, unsigned mask, int dtype,
+                    cudaStream_t st) {
+    init_filter_banks();
+    if (dtype == PURIFY_F32) psi_adj_static_t<float>((const float*)x, (float*)c, nx, ny, levels, mask, st);
+    else psi_adj_static_t<double>((const double*)x, (double*)c, nx, ny, levels, mask, st);
 }
 
 }  // namespace purify
