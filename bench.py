@@ -433,6 +433,39 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_profile_op(args):
+    """Launch one operator W + K times on the workload (for ncu captures)."""
+    import torch
+
+    import paper_1502_05037_gb300 as pk
+    from paper_1502_05037_gb300 import build as pbuild
+    pbuild.build()
+    dev = torch.device("cuda", 0)
+    wl, plan, y, eps, x_true = setup_problem(args.workload, 0, dev)
+    x = torch.from_numpy(x_true.astype(np.float32)).to(dev)
+    yv = torch.empty(wl.M, dtype=torch.complex64, device=dev)
+    xa = torch.empty((wl.ny, wl.nx), dtype=torch.complex64, device=dev)
+    c = torch.empty((plan.info.q, wl.ny, wl.nx), dtype=torch.float32, device=dev)
+    if args.profile_op == "iteration":
+        xs = torch.zeros_like(x)
+        pk.purify_sdmm_solve(plan, y, eps, xs, max_iter=0, cg_iters=args.cg_iters, nu=1.0, gamma=1e-4)
+    t0 = time.perf_counter()
+    for k in range(args.warmup + args.steps):
+        if args.profile_op == "phi":
+            pk.purify_phi(plan, x, yv)
+        elif args.profile_op == "phi_adj":
+            pk.purify_phi_adj(plan, y, xa)
+        elif args.profile_op == "psi_adj":
+            pk.purify_psi_adj(plan, x, c)
+        elif args.profile_op == "psi":
+            pk.purify_psi(plan, c, x)
+        else:
+            pk.purify_sdmm_iterate(plan, 1)
+    torch.cuda.synchronize(dev)
+    print(json.dumps({"profile_op": args.profile_op, "calls": args.warmup + args.steps,
+                      "wall_s": time.perf_counter() - t0, "launches": pk.purify_launch_count()}))
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -443,10 +476,14 @@ def main():
     ap.add_argument("--cg-iters", type=int, default=CG_ITERS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--profile-op", choices=["phi", "phi_adj", "psi", "psi_adj", "iteration"], default=None,
+                    help="only launch this operator W + K times (for ncu captures); prints no bench line")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.impl == "reference":
+    if args.profile_op:
+        run_profile_op(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

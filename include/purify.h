@@ -175,6 +175,19 @@ purify_status purify_sdmm_solve(purify_plan *plan, const void *y, const double *
  * started on the plan. */
 purify_status purify_sdmm_iterate(purify_plan *plan, int32_t iters);
 
+/* Batched channels: independent problems (one plan each, e.g. the spectral
+ * channels of one observation) advanced together. Every plan must already
+ * hold a started solve (purify_sdmm_solve). purify_batch_iterate runs
+ * `iters` SDMM iterations of every plan as replays of one captured CUDA
+ * graph whose branches (one per plan, on private streams) run concurrently;
+ * the graph is re-captured when a plan's gamma, nu, weights or CG count
+ * change. Ordered after and before work already queued on `stream`.
+ * Plans stay usable on their own; do not use them concurrently with the batch. */
+typedef struct purify_batch purify_batch;
+purify_status purify_batch_create(purify_plan *const *plans, int32_t n, void *stream, purify_batch **out);
+purify_status purify_batch_iterate(purify_batch *batch, int32_t iters);
+purify_status purify_batch_destroy(purify_batch *batch);
+
 /* SARA weights (Sec. 1, reweighted l1): w = rho / (rho + |Psi^dagger x|),
  * x real [ny][nx], w real [q][ny][nx]; rho > 0. */
 purify_status purify_reweight(purify_plan *plan, const void *x, double rho, void *w);

@@ -146,6 +146,42 @@ def purify_sdmm_iterate(plan: Plan, iters: int):
     check(load().purify_sdmm_iterate(plan.handle, int(iters)))
 
 
+class Batch:
+    """Several plans advanced together (purify_batch_*); `stream` must be a
+    non-default torch.cuda.Stream (graph capture needs one)."""
+
+    def __init__(self, plans, stream):
+        lib = load()
+        self.plans = list(plans)
+        arr = (C.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
+        h = C.c_void_p()
+        check(lib.purify_batch_create(arr, len(self.plans), _stream_ptr(stream), C.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            check(load().purify_batch_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def purify_batch_create(plans, stream) -> Batch:
+    return Batch(plans, stream)
+
+
+def purify_batch_iterate(batch: Batch, iters: int):
+    check(load().purify_batch_iterate(batch.handle, int(iters)))
+
+
+def purify_batch_destroy(batch: Batch):
+    batch.close()
+
+
 def purify_reweight(plan: Plan, x, rho: float, w):
     check(load().purify_reweight(plan.handle, _ptr(x), float(rho), _ptr(w)))
 

@@ -92,6 +92,9 @@ _SIGS = {
     "purify_sdmm_solve": (C.c_int, [_P, _P, C.POINTER(C.c_double), _P, _P,
                                     C.POINTER(purify_sdmm_params), C.POINTER(purify_sdmm_stats)]),
     "purify_sdmm_iterate": (C.c_int, [_P, C.c_int32]),
+    "purify_batch_create": (C.c_int, [C.POINTER(_P), C.c_int32, _P, C.POINTER(_P)]),
+    "purify_batch_iterate": (C.c_int, [_P, C.c_int32]),
+    "purify_batch_destroy": (C.c_int, [_P]),
     "purify_reweight": (C.c_int, [_P, _P, C.c_double, _P]),
     "purify_coef_std": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
     "purify_psi_adj_static": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_uint32, C.c_int32, _P]),

@@ -250,6 +250,42 @@ purify_status purify_sdmm_iterate(purify_plan* p, int32_t iters) {
     });
 }
 
+struct purify_batch {
+    purify::BatchState* st;
+};
+
+purify_status purify_batch_create(purify_plan* const* plans, int32_t n, void* stream, purify_batch** out) {
+    return guarded([&] {
+        PURIFY_REQUIRE(out != nullptr && plans != nullptr && n >= 1, "bad argument");
+        *out = nullptr;
+        for (int i = 0; i < n; ++i) {
+            PURIFY_REQUIRE(plans[i] != nullptr, "null plan in batch");
+            for (int j = 0; j < i; ++j) PURIFY_REQUIRE(plans[j] != plans[i], "a plan appears twice in the batch");
+        }
+        auto* b = new purify_batch{new BatchState()};
+        b->st->plans.assign(plans, plans + n);
+        b->st->stream = (cudaStream_t)stream;
+        *out = b;
+    });
+}
+
+purify_status purify_batch_iterate(purify_batch* b, int32_t iters) {
+    return guarded([&] {
+        PURIFY_REQUIRE(b != nullptr && iters >= 0, "bad argument");
+        PURIFY_REQUIRE(b->st->stream != nullptr, "a batch needs a non-default stream for graph capture");
+        batch_iterate(b->st, iters);
+    });
+}
+
+purify_status purify_batch_destroy(purify_batch* b) {
+    return guarded([&] {
+        if (!b) return;
+        if (b->st->stream) cudaStreamSynchronize(b->st->stream);
+        batch_destroy(b->st);
+        delete b;
+    });
+}
+
 purify_status purify_reweight(purify_plan* p, const void* x, double rho, void* w) {
     return guarded([&] {
         PURIFY_REQUIRE(p && x && w && rho > 0, "bad argument");

@@ -126,6 +126,7 @@ struct purify_plan {
     purify::DevBuf chunk_blk, chunk_beg, chunk_end;  // visibility chunks, each inside one block
     int nchunks = 0;
     purify::GridWork work;
+    int fft_rb = 0, fft_cb = 0;       // FFT rows / columns per block (0: heuristic)
     // workspaces
     purify::DevBuf grid;              // Ky * Kx complex
     purify::DevBuf rows;              // ny * Kx complex
@@ -156,7 +157,8 @@ void launch_degrid(purify_plan* p, void* y, bool caller_order, const int* skip_f
 void launch_grid(purify_plan* p, const void* y, bool caller_order, const int* skip_flag);
 void launch_cols_inv(purify_plan* p, const int* skip_flag);
 void launch_rows_inv_crop(purify_plan* p, void* out, double scale, int out_mode, const void* add,
-                          double add_coef, const int* skip_flag);
+                          double add_coef, const int* skip_flag, double* dot_part = nullptr,
+                          unsigned* counters = nullptr, double* scal = nullptr);
 
 // Psi / Psi^dagger
 void launch_psi_adj(purify_plan* p, const void* x, void* c);
@@ -171,11 +173,24 @@ size_t psi_adj_static_capacity();
 void sdmm_solve(purify_plan* p, const void* y, const double* eps, const void* w, void* x,
                 const purify_sdmm_params& prm, purify_sdmm_stats* st);
 double op_norm_sq(purify_plan* p, int iters);
+struct BatchState {
+    std::vector<purify_plan*> plans;
+    cudaStream_t stream = nullptr;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<double> key;
+    int64_t kernels = 0;
+};
+void batch_iterate(BatchState* b, int iters);
+void batch_destroy(BatchState* b);
 void sdmm_iterate(purify_plan* p, int iters);
 void add_launches(int64_t n);
 bool timing_enabled(const purify_plan* p);
 void reweight(purify_plan* p, const void* x, double rho, void* w);
 double coef_std(purify_plan* p, const void* x);
+
+int max_grid_tile(int dtype, int J);
 
 // plan-side helpers
 void build_gridwork(purify_plan* p, const std::vector<int>& bin_sorted, int tile);

@@ -18,6 +18,7 @@
 
 #include "internal.h"
 #include "launch.h"
+#include "reduce.cuh"
 
 namespace purify {
 
@@ -178,13 +179,15 @@ __global__ void k_cols_inv(const typename cplx_of<T>::type* __restrict__ grid,
 
 // Inverse row FFT of image rows [i0, i0+rb), then Z^T and S:
 //   out_mode 0: complex out[i][j] = scale * s * v
-//   out_mode 1: real    out[i][j] = scale * s * Re v + (add ? add[i][j] : 0)
+//   out_mode 1: real    out[i][j] = scale * s * Re v + add_coef * (add ? add[i][j] : 0)
+// With dot_part set (CG, out = A p, add = p) the kernel also forms p . A p
+// and, in the last block to finish, alpha = (r . r) / (p . A p).
 template <typename T>
 __global__ void k_rows_inv(const typename cplx_of<T>::type* __restrict__ rows, void* out,
                            const T* __restrict__ sx, const T* __restrict__ sy,
                            const typename cplx_of<T>::type* __restrict__ tw, int nx, int ny, int Kx,
                            int rb, T scale, int out_mode, const T* __restrict__ add, T add_coef,
-                           const int* __restrict__ skip) {
+                           const int* __restrict__ skip, double* dot_part, unsigned* counters, double* scal) {
     using C = typename cplx_of<T>::type;
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -198,6 +201,7 @@ __global__ void k_rows_inv(const typename cplx_of<T>::type* __restrict__ rows, v
     }
     __syncthreads();
     C* res = fft_smem<C, true>(b0, b1, Kx, ilog2(Kx), rb, Kx, 1, tw);
+    T dacc = 0;
     for (int t = threadIdx.x; t < rb * nx; t += blockDim.x) {
         int f = t / nx, j = t - f * nx;
         int i = i0 + f;
@@ -209,8 +213,24 @@ __global__ void k_rows_inv(const typename cplx_of<T>::type* __restrict__ rows, v
             reinterpret_cast<C*>(out)[idx] = cscale(v, s);
         } else {
             T r = v.x * s;
-            if (add) r += add_coef * add[idx];
+            if (add) {
+                T a = add[idx];
+                r += add_coef * a;
+                dacc += a * r;
+            }
             reinterpret_cast<T*>(out)[idx] = r;
+        }
+    }
+    if (dot_part) {
+        double b = block_sum((double)dacc);
+        if (threadIdx.x == 0) dot_part[blockIdx.x] = b;
+        if (arrive_last(counters + C_ALPHA)) {
+            double tot = ordered_sum(dot_part, gridDim.x);
+            if (threadIdx.x == 0) {
+                scal[S_PAP] = tot;
+                scal[S_ALPHA] = tot > 0.0 ? scal[S_RS] / tot : 0.0;
+                counters[C_ALPHA] = 0;
+            }
         }
     }
 }
@@ -250,85 +270,97 @@ __global__ void k_cols_full(typename cplx_of<T>::type* grid, const typename cplx
     }
 }
 
-// ------------------------------------------------------------- degridding
-// G: one thread per visibility (internal order). Output in caller order
-// through perm when perm != null.
-template <typename T, int J>
-__global__ void k_degrid(const typename cplx_of<T>::type* __restrict__ grid, const T* __restrict__ us,
-                         const T* __restrict__ vs, int M, AxisConst ax, AxisConst ay, KbPoly kp,
-                         double beta, double inv_i0beta, const int* __restrict__ perm,
-                         typename cplx_of<T>::type* __restrict__ y, const int* __restrict__ skip) {
-    using C = typename cplx_of<T>::type;
-    if (skip && *skip) return;
-    int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= M) return;
-    int kx0, ky0;
-    T phx, phy;
-    split_coord(us[m], ax, J, kx0, phx);
-    split_coord(vs[m], ay, J, ky0, phy);
-    T wx[J], wy[J];
-    if constexpr (sizeof(T) == 4) {
-        kb_weights<J>(kp, phx, wx);
-        kb_weights<J>(kp, phy, wy);
-    } else {
-        kb_weights<J>(beta, inv_i0beta, phx, wx);
-        kb_weights<J>(beta, inv_i0beta, phy, wy);
-    }
-    const int Kx = ax.K, Ky = ay.K;
-    T accx = 0, accy = 0;
-#pragma unroll
-    for (int b = 0; b < J; ++b) {
-        const C* row = grid + (size_t)((ky0 + b) & (Ky - 1)) * Kx;
-        T rx = 0, ry = 0;
-#pragma unroll
-        for (int a = 0; a < J; ++a) {
-            C g = row[(kx0 + a) & (Kx - 1)];
-            rx += wx[a] * g.x;
-            ry += wx[a] * g.y;
-        }
-        accx += wy[b] * rx;
-        accy += wy[b] * ry;
-    }
-    y[perm ? perm[m] : m] = cmake<C>(accx, accy);
-}
-
-// ---------------------------------------------------------------- gridding
-// G^H: one block per subproblem (a grid tile and a list of visibility
-// pieces). Footprints accumulate in a shared-memory copy of the tile plus a
-// (J-1) halo, then the touched part of that copy is added to the grid.
+// ------------------------------------------------------ gridding helpers
 __device__ __forceinline__ void atomic_add_c(float2* a, float2 v) { atomicAdd(a, v); }
 __device__ __forceinline__ void atomic_add_c(double2* a, double2 v) {
     atomicAdd(&a->x, v.x);
     atomicAdd(&a->y, v.y);
 }
 
-template <typename T, int J>
-__global__ void k_grid(const typename cplx_of<T>::type* __restrict__ yin, const T* __restrict__ us,
-                       const T* __restrict__ vs, AxisConst ax, AxisConst ay, KbPoly kp, double beta,
-                       double inv_i0beta, const int* __restrict__ perm, const int* __restrict__ sub_bin,
-                       const int* __restrict__ piece_off, const int* __restrict__ piece_start,
-                       const int* __restrict__ piece_len, int tile, int tiles_x,
-                       typename cplx_of<T>::type* __restrict__ grid, const int* __restrict__ skip) {
+// Visibility pieces of one subproblem, flattened: a block loads the piece
+// starts and the running piece lengths into shared memory so that any thread
+// can map a flat index q to its visibility with a binary search.
+#define PURIFY_MAX_PIECES 128
+
+__device__ __forceinline__ int load_pieces(const int* __restrict__ piece_off, const int* __restrict__ piece_start,
+                                           const int* __restrict__ piece_len, int s, int* pst, int* pcum) {
+    const int p0 = piece_off[s], np = piece_off[s + 1] - p0;
+    if (threadIdx.x < np) pst[threadIdx.x] = piece_start[p0 + threadIdx.x];
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int k = 0; k < np; ++k) { pcum[k] = acc; acc += piece_len[p0 + k]; }
+        pcum[np] = acc;
+    }
+    return np;
+}
+
+// visibility of flat index q (0 <= q < pcum[np])
+__device__ __forceinline__ int flat_vis(const int* pst, const int* pcum, int np, int q) {
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (pcum[mid] <= q) lo = mid; else hi = mid - 1;
+    }
+    return pst[lo] + (q - pcum[lo]);
+}
+
+// G^H, warp-private tiles. A block owns one subproblem (a grid tile and a
+// list of visibility pieces) and holds WARPS private copies of the tile plus
+// its (J-1) halo in shared memory (interleaved complex, row stride S with
+// S = J mod 16 so the J*J taps of one visibility fall on distinct banks).
+// The subproblem's visibilities are dealt to the warps 32 at a time: every
+// lane evaluates the split coordinate and the 2J kernel weights of one
+// visibility into a per-warp staging area; then the warp scatters the 32
+// staged visibilities one after another, lane l adding tap (l mod J, l / J)
+// (and tap l + 32 when J*J > 32) with a plain read-add-write. Lanes of a warp
+// touch distinct cells and warps touch distinct copies, so no shared-memory
+// atomic is needed. Finally the copies are summed in warp order and the
+// non-zero cells of the tile are added to the grid.
+template <int J> struct GridStage {
+    // floats per staged visibility: wx[J], wy[J], re, im, cell offset (-1:
+    // not in this tile), lx, ly; odd so that the 32 lanes of a warp store
+    // their records on distinct banks
+    static constexpr int F = 2 * J + 5;
+};
+
+template <typename T, int J, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32)
+k_grid_wp(const typename cplx_of<T>::type* __restrict__ yin, const T* __restrict__ us, const T* __restrict__ vs,
+          AxisConst ax, AxisConst ay, KbPoly kp, double beta, double inv_i0beta, const int* __restrict__ perm,
+          const int* __restrict__ sub_bin, const int* __restrict__ piece_off, const int* __restrict__ piece_start,
+          const int* __restrict__ piece_len, int tile, int tiles_x, int S,
+          typename cplx_of<T>::type* __restrict__ grid, const int* __restrict__ skip) {
     using C = typename cplx_of<T>::type;
+    constexpr int F = GridStage<J>::F;
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int PT = tile + J - 1;
-    T* tre = reinterpret_cast<T*>(smem_raw);
-    T* tim = tre + PT * PT;
-    int* bbox = reinterpret_cast<int*>(tim + PT * PT);  // min row, max row, min col, max col
+    const int PT = tile + J - 1;             // rows of a tile copy
+    const int cells = PT * S;                // complex cells of one copy
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    C* tiles = reinterpret_cast<C*>(smem_raw);                              // [WARPS][PT][S]
+    T* stage = reinterpret_cast<T*>(tiles + (size_t)WARPS * cells);         // [WARPS][32][F]
+    int* pst = reinterpret_cast<int*>(stage + (size_t)WARPS * 32 * F);      // [MAX_PIECES]
+    int* pcum = pst + PURIFY_MAX_PIECES;                                    // [MAX_PIECES + 1]
+    C* mt = tiles + (size_t)warp * cells;
+    T* mst = stage + (size_t)warp * 32 * F;
+    for (int t = threadIdx.x; t < WARPS * cells; t += blockDim.x) tiles[t] = cmake<C>(T(0), T(0));
     const int s = blockIdx.x;
+    const int np = load_pieces(piece_off, piece_start, piece_len, s, pst, pcum);
+    __syncthreads();
     const int bin = sub_bin[s];
     const int oy = (bin / tiles_x) * tile, ox = (bin % tiles_x) * tile;
     const int Kx = ax.K, Ky = ay.K;
-    for (int t = threadIdx.x; t < PT * PT; t += blockDim.x) { tre[t] = T(0); tim[t] = T(0); }
-    if (threadIdx.x == 0) { bbox[0] = PT; bbox[1] = -1; bbox[2] = PT; bbox[3] = -1; }
-    __syncthreads();
-    int lymin = PT, lymax = -1, lxmin = PT, lxmax = -1;
-    const int p0 = piece_off[s], p1 = piece_off[s + 1];
-    for (int pc = p0; pc < p1; ++pc) {
-        const int st = piece_start[pc], len = piece_len[pc];
-        for (int q = threadIdx.x; q < len; q += blockDim.x) {
-            const int m = st + q;
+    const int total = pcum[np];
+    // tap handled by this lane in the first and second round
+    const int a0 = lane % J, b0 = lane / J;
+    const int t1 = lane + 32;
+    const int a1 = t1 % J, b1 = t1 / J;
+    const bool second = (J * J > 32) && (t1 < J * J);
+    for (int base = warp * 32; base < total; base += WARPS * 32) {
+        const int q = base + lane;
+        const int nv = min(32, total - base);
+        if (q < total) {
+            const int m = flat_vis(pst, pcum, np, q);
             int kx0, ky0;
             T phx, phy;
             split_coord(us[m], ax, J, kx0, phx);
@@ -342,25 +374,20 @@ __global__ void k_grid(const typename cplx_of<T>::type* __restrict__ yin, const 
                 kb_weights<J>(beta, inv_i0beta, phy, wy);
             }
             C yv = yin[perm ? perm[m] : m];
-            int lx = ((kx0 & (Kx - 1)) - ox), ly = ((ky0 & (Ky - 1)) - oy);
+            int lx = (kx0 & (Kx - 1)) - ox, ly = (ky0 & (Ky - 1)) - oy;
+            T* rec = mst + lane * F;
             if (lx >= 0 && lx < tile && ly >= 0 && ly < tile) {
-                lxmin = min(lxmin, lx); lxmax = max(lxmax, lx + J - 1);
-                lymin = min(lymin, ly); lymax = max(lymax, ly + J - 1);
 #pragma unroll
-                for (int b = 0; b < J; ++b) {
-                    T wb = wy[b];
-                    T yb_re = wb * yv.x, yb_im = wb * yv.y;
-                    T* rre = tre + (ly + b) * PT + lx;
-                    T* rim = tim + (ly + b) * PT + lx;
-#pragma unroll
-                    for (int a = 0; a < J; ++a) {
-                        atomicAdd(rre + a, wx[a] * yb_re);
-                        atomicAdd(rim + a, wx[a] * yb_im);
-                    }
-                }
+                for (int a = 0; a < J; ++a) { rec[a] = wx[a]; rec[J + a] = wy[a]; }
+                rec[2 * J] = yv.x;
+                rec[2 * J + 1] = yv.y;
+                rec[2 * J + 2] = (T)(ly * S + lx);
+                rec[2 * J + 3] = (T)lx;
+                rec[2 * J + 4] = (T)ly;
             } else {
-                // coordinate outside this tile (never expected: the plan bins
+                // coordinate outside this tile (not expected: the plan bins
                 // with the same split); add straight to the grid
+                rec[2 * J + 2] = T(-1);
 #pragma unroll
                 for (int b = 0; b < J; ++b)
 #pragma unroll
@@ -371,33 +398,183 @@ __global__ void k_grid(const typename cplx_of<T>::type* __restrict__ yin, const 
                     }
             }
         }
-    }
-    if (lymax >= 0) {
-        atomicMin(&bbox[0], lymin); atomicMax(&bbox[1], lymax);
-        atomicMin(&bbox[2], lxmin); atomicMax(&bbox[3], lxmax);
+        __syncwarp();
+        // two staged visibilities at a time when their footprints cannot share
+        // a cell (independent read-add-write chains), one at a time otherwise
+        const int off0 = b0 * S + a0, off1 = b1 * S + a1;
+        int v = 0;
+        while (v < nv) {
+            const T* ra = mst + v * F;
+            const int oa = (int)ra[2 * J + 2];
+            const bool va = oa >= 0;
+            bool pair = false;
+            int ob = 0;
+            const T* rb = ra + F;
+            if (v + 1 < nv && va) {
+                ob = (int)rb[2 * J + 2];
+                const T dx = ra[2 * J + 3] - rb[2 * J + 3], dy = ra[2 * J + 4] - rb[2 * J + 4];
+                pair = ob >= 0 && (fabs(dx) >= T(J) || fabs(dy) >= T(J));
+            }
+            if (pair) {
+                const T yra = ra[2 * J], yia = ra[2 * J + 1], yrb = rb[2 * J], yib = rb[2 * J + 1];
+                if (b0 < J) {
+                    const T wa = ra[a0] * ra[J + b0], wb = rb[a0] * rb[J + b0];
+                    C* ca = mt + oa + off0;
+                    C* cb = mt + ob + off0;
+                    C xa = *ca, xb = *cb;
+                    xa.x += wa * yra; xa.y += wa * yia;
+                    xb.x += wb * yrb; xb.y += wb * yib;
+                    *ca = xa;
+                    *cb = xb;
+                }
+                if (second) {
+                    const T wa = ra[a1] * ra[J + b1], wb = rb[a1] * rb[J + b1];
+                    C* ca = mt + oa + off1;
+                    C* cb = mt + ob + off1;
+                    C xa = *ca, xb = *cb;
+                    xa.x += wa * yra; xa.y += wa * yia;
+                    xb.x += wb * yrb; xb.y += wb * yib;
+                    *ca = xa;
+                    *cb = xb;
+                }
+                v += 2;
+                continue;
+            }
+            if (va) {
+                const T yr = ra[2 * J], yi = ra[2 * J + 1];
+                if (b0 < J) {
+                    const T w = ra[a0] * ra[J + b0];
+                    C* cell = mt + oa + off0;
+                    C cur = *cell;
+                    cur.x += w * yr;
+                    cur.y += w * yi;
+                    *cell = cur;
+                }
+                if (second) {
+                    const T w = ra[a1] * ra[J + b1];
+                    C* cell = mt + oa + off1;
+                    C cur = *cell;
+                    cur.x += w * yr;
+                    cur.y += w * yi;
+                    *cell = cur;
+                }
+            }
+            v += 1;
+        }
+        __syncwarp();
     }
     __syncthreads();
-    const int r0 = bbox[0], r1 = bbox[1], q0 = bbox[2], q1 = bbox[3];
-    if (r1 < 0) return;
-    const int w = q1 - q0 + 1;
-    const int cells = (r1 - r0 + 1) * w;
-    for (int t = threadIdx.x; t < cells; t += blockDim.x) {
-        int r = r0 + t / w, c = q0 + t % w;
-        T re = tre[r * PT + c], im = tim[r * PT + c];
+    // sum the copies in warp order and add the non-zero cells to the grid
+    for (int t = threadIdx.x; t < PT * PT; t += blockDim.x) {
+        const int r = t / PT, c = t - r * PT;
+        const int o = r * S + c;
+        T re = 0, im = 0;
+#pragma unroll
+        for (int w = 0; w < WARPS; ++w) {
+            C v = tiles[(size_t)w * cells + o];
+            re += v.x;
+            im += v.y;
+        }
         if (re != T(0) || im != T(0))
             atomic_add_c(grid + (size_t)((oy + r) & (Ky - 1)) * Kx + ((ox + c) & (Kx - 1)), cmake<C>(re, im));
     }
 }
 
+// G with the tile staged in shared memory: a block owns one subproblem,
+// copies the tile plus its (J-1) halo from the grid, then every thread
+// interpolates visibilities of the subproblem from the shared copy.
+template <typename T, int J>
+__global__ void __launch_bounds__(128)
+k_degrid_tile(const typename cplx_of<T>::type* __restrict__ grid, const T* __restrict__ us, const T* __restrict__ vs,
+              AxisConst ax, AxisConst ay, KbPoly kp, double beta, double inv_i0beta, const int* __restrict__ perm,
+              const int* __restrict__ sub_bin, const int* __restrict__ piece_off,
+              const int* __restrict__ piece_start, const int* __restrict__ piece_len, int tile, int tiles_x,
+              typename cplx_of<T>::type* __restrict__ y, const int* __restrict__ skip) {
+    using C = typename cplx_of<T>::type;
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int PT = tile + J - 1;
+    C* tl = reinterpret_cast<C*>(smem_raw);                   // [PT][PT]
+    int* pst = reinterpret_cast<int*>(tl + PT * PT);
+    int* pcum = pst + PURIFY_MAX_PIECES;
+    const int s = blockIdx.x;
+    const int bin = sub_bin[s];
+    const int oy = (bin / tiles_x) * tile, ox = (bin % tiles_x) * tile;
+    const int Kx = ax.K, Ky = ay.K;
+    for (int t = threadIdx.x; t < PT * PT; t += blockDim.x) {
+        const int r = t / PT, c = t - r * PT;
+        tl[t] = grid[(size_t)((oy + r) & (Ky - 1)) * Kx + ((ox + c) & (Kx - 1))];
+    }
+    const int np = load_pieces(piece_off, piece_start, piece_len, s, pst, pcum);
+    __syncthreads();
+    const int total = pcum[np];
+    for (int q = threadIdx.x; q < total; q += blockDim.x) {
+        const int m = flat_vis(pst, pcum, np, q);
+        int kx0, ky0;
+        T phx, phy;
+        split_coord(us[m], ax, J, kx0, phx);
+        split_coord(vs[m], ay, J, ky0, phy);
+        T wx[J], wy[J];
+        if constexpr (sizeof(T) == 4) {
+            kb_weights<J>(kp, phx, wx);
+            kb_weights<J>(kp, phy, wy);
+        } else {
+            kb_weights<J>(beta, inv_i0beta, phx, wx);
+            kb_weights<J>(beta, inv_i0beta, phy, wy);
+        }
+        int lx = (kx0 & (Kx - 1)) - ox, ly = (ky0 & (Ky - 1)) - oy;
+        T accx = 0, accy = 0;
+        if (lx >= 0 && lx < tile && ly >= 0 && ly < tile) {
+#pragma unroll
+            for (int b = 0; b < J; ++b) {
+                const C* row = tl + (ly + b) * PT + lx;
+                T rx = 0, ry = 0;
+#pragma unroll
+                for (int a = 0; a < J; ++a) {
+                    C g = row[a];
+                    rx += wx[a] * g.x;
+                    ry += wx[a] * g.y;
+                }
+                accx += wy[b] * rx;
+                accy += wy[b] * ry;
+            }
+        } else {
+#pragma unroll
+            for (int b = 0; b < J; ++b) {
+                const C* row = grid + (size_t)((ky0 + b) & (Ky - 1)) * Kx;
+                T rx = 0, ry = 0;
+#pragma unroll
+                for (int a = 0; a < J; ++a) {
+                    C g = row[(kx0 + a) & (Kx - 1)];
+                    rx += wx[a] * g.x;
+                    ry += wx[a] * g.y;
+                }
+                accx += wy[b] * rx;
+                accy += wy[b] * ry;
+            }
+        }
+        y[perm ? perm[m] : m] = cmake<C>(accx, accy);
+    }
+}
+
 // ------------------------------------------------------------- launchers
-static int rows_per_block(int K) { return std::max(1, std::min(8, 1024 / K)); }
+// FFT launch shapes: enough blocks to cover the 152 SMs about twice, one
+// radix-4 butterfly per thread per pass where possible.
+template <typename T> static int rows_per_block(int nrows, int K) {
+    size_t cbytes = sizeof(typename cplx_of<T>::type);
+    int rb = std::max(1, std::min(8, nrows / 256));
+    while (rb > 1 && (2 * (size_t)rb * K * cbytes > 160 * 1024 || nrows % rb)) rb >>= 1;
+    return rb;
+}
 
 template <typename T> static int cols_per_block(int Ky, int Kx) {
     size_t cbytes = sizeof(typename cplx_of<T>::type);
-    int cb = 8;
+    int cb = std::max(1, std::min(8, Kx / 256));
     while (cb > 1 && (2 * (size_t)cb * Ky * cbytes > 160 * 1024 || Kx % cb)) cb >>= 1;
     return cb;
 }
+
+static int fft_threads(int nb, int n) { return std::max(64, std::min(256, nb * n / 4)); }
 
 template <typename K> static void set_smem(K kernel, size_t bytes) {
     if (bytes > 48 * 1024) PURIFY_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
@@ -407,12 +584,12 @@ template <typename T>
 static void rows_fwd_t(purify_plan* p, const void* x, double scale, void* pdir, const void* rvec,
                        const double* beta_dev, const int* skip) {
     using C = typename cplx_of<T>::type;
-    int rb = rows_per_block(p->Kx);
+    int rb = p->fft_rb > 0 ? p->fft_rb : rows_per_block<T>(p->ny, p->Kx);
     while (p->ny % rb) rb >>= 1;
     size_t sm = 2 * (size_t)rb * p->Kx * sizeof(C);
     set_smem(k_rows_fwd<T>, sm);
     Launch L(p, "fft_rows_fwd");
-    k_rows_fwd<T><<<p->ny / rb, 256, sm, p->stream>>>(
+    k_rows_fwd<T><<<p->ny / rb, fft_threads(rb, p->Kx), sm, p->stream>>>(
         (const T*)x, p->rows.as<C>(), p->sx.as<T>(), p->sy.as<T>(), p->twx.as<C>(), p->nx, p->ny, p->Kx,
         rb, (T)scale, (T*)pdir, (const T*)rvec, beta_dev, skip);
     L.done();
@@ -420,65 +597,89 @@ static void rows_fwd_t(purify_plan* p, const void* x, double scale, void* pdir, 
 
 template <typename T> static void cols_fwd_t(purify_plan* p, const int* skip) {
     using C = typename cplx_of<T>::type;
-    int cb = cols_per_block<T>(p->Ky, p->Kx);
+    int cb = p->fft_cb > 0 ? p->fft_cb : cols_per_block<T>(p->Ky, p->Kx);
     size_t sm = 2 * (size_t)cb * p->Ky * sizeof(C);
     set_smem(k_cols_fwd<T>, sm);
     Launch L(p, "fft_cols_fwd");
-    k_cols_fwd<T><<<p->Kx / cb, 256, sm, p->stream>>>(p->rows.as<C>(), p->grid.as<C>(), p->twy.as<C>(),
+    k_cols_fwd<T><<<p->Kx / cb, fft_threads(cb, p->Ky), sm, p->stream>>>(p->rows.as<C>(), p->grid.as<C>(), p->twy.as<C>(),
                                                       p->ny, p->Kx, p->Ky, cb, skip);
     L.done();
 }
 
 template <typename T> static void cols_inv_t(purify_plan* p, const int* skip) {
     using C = typename cplx_of<T>::type;
-    int cb = cols_per_block<T>(p->Ky, p->Kx);
+    int cb = p->fft_cb > 0 ? p->fft_cb : cols_per_block<T>(p->Ky, p->Kx);
     size_t sm = 2 * (size_t)cb * p->Ky * sizeof(C);
     set_smem(k_cols_inv<T>, sm);
     Launch L(p, "fft_cols_inv");
-    k_cols_inv<T><<<p->Kx / cb, 256, sm, p->stream>>>(p->grid.as<C>(), p->rows.as<C>(), p->twy.as<C>(),
+    k_cols_inv<T><<<p->Kx / cb, fft_threads(cb, p->Ky), sm, p->stream>>>(p->grid.as<C>(), p->rows.as<C>(), p->twy.as<C>(),
                                                       p->ny, p->Kx, p->Ky, cb, skip);
     L.done();
 }
 
 template <typename T>
 static void rows_inv_t(purify_plan* p, void* out, double scale, int out_mode, const void* add, double add_coef,
-                       const int* skip) {
+                       const int* skip, double* dot_part, unsigned* counters, double* scal) {
     using C = typename cplx_of<T>::type;
-    int rb = rows_per_block(p->Kx);
+    int rb = p->fft_rb > 0 ? p->fft_rb : rows_per_block<T>(p->ny, p->Kx);
     while (p->ny % rb) rb >>= 1;
     size_t sm = 2 * (size_t)rb * p->Kx * sizeof(C);
     set_smem(k_rows_inv<T>, sm);
     Launch L(p, "fft_rows_inv");
-    k_rows_inv<T><<<p->ny / rb, 256, sm, p->stream>>>(p->rows.as<C>(), out, p->sx.as<T>(), p->sy.as<T>(),
+    k_rows_inv<T><<<p->ny / rb, fft_threads(rb, p->Kx), sm, p->stream>>>(p->rows.as<C>(), out, p->sx.as<T>(), p->sy.as<T>(),
                                                       p->twx.as<C>(), p->nx, p->ny, p->Kx, rb, (T)scale,
-                                                      out_mode, (const T*)add, (T)add_coef, skip);
+                                                      out_mode, (const T*)add, (T)add_coef, skip, dot_part,
+                                                      counters, scal);
     L.done();
 }
 
 template <typename T, int J> static void degrid_tj(purify_plan* p, void* y, bool caller_order, const int* skip) {
     using C = typename cplx_of<T>::type;
-    int M = (int)p->M;
+    if (p->work.nsub == 0) return;
+    const int tile = p->work.tile, PT = tile + J - 1;
+    size_t sm = sizeof(C) * (size_t)PT * PT + sizeof(int) * (2 * PURIFY_MAX_PIECES + 1);
+    set_smem(k_degrid_tile<T, J>, sm);
     Launch L(p, "degrid");
-    k_degrid<T, J><<<(M + 255) / 256, 256, 0, p->stream>>>(
-        p->grid.as<C>(), p->us.as<T>(), p->vs.as<T>(), M, p->ax, p->ay, p->kbp, p->beta, 1.0 / p->i0beta,
-        caller_order ? p->perm.as<int>() : nullptr, (C*)y, skip);
+    k_degrid_tile<T, J><<<p->work.nsub, 128, sm, p->stream>>>(
+        p->grid.as<C>(), p->us.as<T>(), p->vs.as<T>(), p->ax, p->ay, p->kbp, p->beta, 1.0 / p->i0beta,
+        caller_order ? p->perm.as<int>() : nullptr, p->work.sub_bin.as<int>(), p->work.piece_off.as<int>(),
+        p->work.piece_start.as<int>(), p->work.piece_len.as<int>(), tile, p->work.tiles_x, (C*)y, skip);
     L.done();
+}
+
+// row stride of a shared tile copy (complex cells): at least tile + J - 1
+// and equal to J modulo 16, so that the taps of one visibility handled by a
+// half-warp fall on distinct 8-byte bank pairs
+static int grid_row_stride(int tile, int J) {
+    int S = tile + J - 1;
+    while (S % 16 != J % 16) ++S;
+    return S;
+}
+
+template <typename T> static constexpr int grid_warps() { return sizeof(T) == 4 ? 8 : 4; }
+
+template <typename T, int J>
+static size_t grid_smem_bytes(int tile) {
+    const int PT = tile + J - 1, S = grid_row_stride(tile, J);
+    return sizeof(T) * ((size_t)grid_warps<T>() * 2 * PT * S + (size_t)grid_warps<T>() * 32 * GridStage<J>::F) +
+           sizeof(int) * (2 * PURIFY_MAX_PIECES + 1);
 }
 
 template <typename T, int J>
 static void grid_tj(purify_plan* p, const void* y, bool caller_order, const int* skip) {
     using C = typename cplx_of<T>::type;
+    constexpr int W = grid_warps<T>();
     PURIFY_CUDA(cudaMemsetAsync(p->grid.p, 0, p->grid.bytes, p->stream));
     if (p->work.nsub == 0) return;
-    int PT = p->work.tile + J - 1;
-    size_t sm = 2 * (size_t)PT * PT * sizeof(T) + 4 * sizeof(int);
-    set_smem(k_grid<T, J>, sm);
+    const int tile = p->work.tile;
+    const int S = grid_row_stride(tile, J);
+    size_t sm = grid_smem_bytes<T, J>(tile);
+    set_smem(k_grid_wp<T, J, W>, sm);
     Launch L(p, "grid");
-    k_grid<T, J><<<p->work.nsub, 256, sm, p->stream>>>(
+    k_grid_wp<T, J, W><<<p->work.nsub, W * 32, sm, p->stream>>>(
         (const C*)y, p->us.as<T>(), p->vs.as<T>(), p->ax, p->ay, p->kbp, p->beta, 1.0 / p->i0beta,
         caller_order ? p->perm.as<int>() : nullptr, p->work.sub_bin.as<int>(), p->work.piece_off.as<int>(),
-        p->work.piece_start.as<int>(), p->work.piece_len.as<int>(), p->work.tile, p->work.tiles_x, p->grid.as<C>(),
-        skip);
+        p->work.piece_start.as<int>(), p->work.piece_len.as<int>(), tile, p->work.tiles_x, S, p->grid.as<C>(), skip);
     L.done();
 }
 
@@ -499,6 +700,25 @@ template <int J> static void degrid_d(purify_plan* p, void* y, bool c, const int
 template <int J> static void grid_f(purify_plan* p, const void* y, bool c, const int* s) { grid_tj<float, J>(p, y, c, s); }
 template <int J> static void grid_d(purify_plan* p, const void* y, bool c, const int* s) { grid_tj<double, J>(p, y, c, s); }
 
+template <int J> static int max_tile_f() {
+    int t = 64;
+    while (t > 8 && grid_smem_bytes<float, J>(t) > 200 * 1024) t >>= 1;
+    return t;
+}
+template <int J> static int max_tile_d() {
+    int t = 64;
+    while (t > 8 && grid_smem_bytes<double, J>(t) > 200 * 1024) t >>= 1;
+    return t;
+}
+
+// Largest gridding tile whose shared-memory tile copies fit a block.
+int max_grid_tile(int dtype, int J) {
+    int t = 8;
+    if (dtype == PURIFY_F32) { PURIFY_J_DISPATCH(J, t = max_tile_f, ); }
+    else { PURIFY_J_DISPATCH(J, t = max_tile_d, ); }
+    return t;
+}
+
 void launch_scale_pad_rows(purify_plan* p, const void* x, double scale, void* pdir, const void* rvec,
                            const double* beta_dev, const int* skip) {
     if (p->dtype == PURIFY_F32) rows_fwd_t<float>(p, x, scale, pdir, rvec, beta_dev, skip);
@@ -511,9 +731,9 @@ void launch_cols_inv(purify_plan* p, const int* skip) {
     if (p->dtype == PURIFY_F32) cols_inv_t<float>(p, skip); else cols_inv_t<double>(p, skip);
 }
 void launch_rows_inv_crop(purify_plan* p, void* out, double scale, int out_mode, const void* add, double add_coef,
-                          const int* skip) {
-    if (p->dtype == PURIFY_F32) rows_inv_t<float>(p, out, scale, out_mode, add, add_coef, skip);
-    else rows_inv_t<double>(p, out, scale, out_mode, add, add_coef, skip);
+                          const int* skip, double* dot_part, unsigned* counters, double* scal) {
+    if (p->dtype == PURIFY_F32) rows_inv_t<float>(p, out, scale, out_mode, add, add_coef, skip, dot_part, counters, scal);
+    else rows_inv_t<double>(p, out, scale, out_mode, add, add_coef, skip, dot_part, counters, scal);
 }
 void launch_degrid(purify_plan* p, void* y, bool caller_order, const int* skip) {
     if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, degrid_f, p, y, caller_order, skip); }
@@ -539,7 +759,7 @@ void launch_phi_adj(purify_plan* p, const void* y, void* out, bool caller_order,
 
 template <typename T> static void fft2_t(purify_plan* p, void* grid, bool inverse) {
     using C = typename cplx_of<T>::type;
-    int rb = rows_per_block(p->Kx);
+    int rb = rows_per_block<T>(p->Ky, p->Kx);
     while (p->Ky % rb) rb >>= 1;
     size_t smr = 2 * (size_t)rb * p->Kx * sizeof(C);
     int cb = cols_per_block<T>(p->Ky, p->Kx);
@@ -547,13 +767,13 @@ template <typename T> static void fft2_t(purify_plan* p, void* grid, bool invers
     if (inverse) {
         set_smem(k_rows_full<T, true>, smr);
         set_smem(k_cols_full<T, true>, smc);
-        { Launch L(p, "fft_full_rows"); k_rows_full<T, true><<<p->Ky / rb, 256, smr, p->stream>>>((C*)grid, p->twx.as<C>(), p->Kx, rb); L.done(); }
-        { Launch L(p, "fft_full_cols"); k_cols_full<T, true><<<p->Kx / cb, 256, smc, p->stream>>>((C*)grid, p->twy.as<C>(), p->Kx, p->Ky, cb); L.done(); }
+        { Launch L(p, "fft_full_rows"); k_rows_full<T, true><<<p->Ky / rb, fft_threads(rb, p->Kx), smr, p->stream>>>((C*)grid, p->twx.as<C>(), p->Kx, rb); L.done(); }
+        { Launch L(p, "fft_full_cols"); k_cols_full<T, true><<<p->Kx / cb, fft_threads(cb, p->Ky), smc, p->stream>>>((C*)grid, p->twy.as<C>(), p->Kx, p->Ky, cb); L.done(); }
     } else {
         set_smem(k_rows_full<T, false>, smr);
         set_smem(k_cols_full<T, false>, smc);
-        { Launch L(p, "fft_full_rows"); k_rows_full<T, false><<<p->Ky / rb, 256, smr, p->stream>>>((C*)grid, p->twx.as<C>(), p->Kx, rb); L.done(); }
-        { Launch L(p, "fft_full_cols"); k_cols_full<T, false><<<p->Kx / cb, 256, smc, p->stream>>>((C*)grid, p->twy.as<C>(), p->Kx, p->Ky, cb); L.done(); }
+        { Launch L(p, "fft_full_rows"); k_rows_full<T, false><<<p->Ky / rb, fft_threads(rb, p->Kx), smr, p->stream>>>((C*)grid, p->twx.as<C>(), p->Kx, rb); L.done(); }
+        { Launch L(p, "fft_full_cols"); k_cols_full<T, false><<<p->Kx / cb, fft_threads(cb, p->Ky), smc, p->stream>>>((C*)grid, p->twy.as<C>(), p->Kx, p->Ky, cb); L.done(); }
     }
 }
 

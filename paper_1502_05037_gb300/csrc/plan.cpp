@@ -5,7 +5,11 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
+#include <map>
+#include <mutex>
 #include <numeric>
+#include <tuple>
 #include <vector>
 
 #include "host_tables.h"
@@ -57,33 +61,46 @@ template <typename T> static std::vector<T> cast_vec(const std::vector<double>& 
     return o;
 }
 
+// Grid cell of each visibility's first tap (wrapped), as computed by the
+// kernels.
 template <typename T>
-static void sort_visibilities(purify_plan* p, const std::vector<T>& u, const std::vector<T>& v, int tile,
-                              std::vector<int>& perm, std::vector<int>& bin_sorted) {
-    const int64_t M = p->M;
-    const int tx = p->Kx / tile, ty = p->Ky / tile, nbins = tx * ty;
-    std::vector<int> bin(M);
-    for (int64_t m = 0; m < M; ++m) {
+static void first_tap_cells(purify_plan* p, const std::vector<T>& u, const std::vector<T>& v, std::vector<int>& cx,
+                            std::vector<int>& cy) {
+    cx.resize(p->M);
+    cy.resize(p->M);
+    for (int64_t m = 0; m < p->M; ++m) {
         int kx0, ky0;
         T phx, phy;
         split_coord(u[m], p->ax, p->J, kx0, phx);
         split_coord(v[m], p->ay, p->J, ky0, phy);
-        int bx = (kx0 & (p->Kx - 1)) / tile, by = (ky0 & (p->Ky - 1)) / tile;
-        bin[m] = by * tx + bx;
+        cx[m] = kx0 & (p->Kx - 1);
+        cy[m] = ky0 & (p->Ky - 1);
+    }
+}
+
+// Sort the visibilities of each block by a hierarchical tile key: the
+// tmax-tile index, then the quadrant at each halving down to tmin. Every
+// power-of-two tile size between tmin and tmax then covers a contiguous run
+// of the sorted order, so candidate gridding tiles can be compared without
+// re-sorting. Stable (counting sort), so the order is deterministic.
+static void sort_hierarchical(purify_plan* p, const std::vector<int>& cx, const std::vector<int>& cy, int tmin,
+                              int tmax, std::vector<int>& perm) {
+    const int64_t M = p->M;
+    const int nkeys = (p->Kx / tmin) * (p->Ky / tmin);
+    std::vector<int> key(M);
+    for (int64_t m = 0; m < M; ++m) {
+        int k = (cy[m] / tmax) * (p->Kx / tmax) + cx[m] / tmax;
+        for (int t = tmax / 2; t >= tmin; t /= 2) k = k * 4 + ((cy[m] / t) & 1) * 2 + ((cx[m] / t) & 1);
+        key[m] = k;
     }
     perm.resize(M);
-    bin_sorted.resize(M);
-    std::vector<int64_t> count(nbins + 1);
+    std::vector<int64_t> count(nkeys + 1);
     for (int r = 0; r < p->R; ++r) {
         const int64_t a = p->offsets[r], b = p->offsets[r + 1];
         std::fill(count.begin(), count.end(), 0);
-        for (int64_t m = a; m < b; ++m) count[bin[m] + 1]++;
-        for (int k = 0; k < nbins; ++k) count[k + 1] += count[k];
-        for (int64_t m = a; m < b; ++m) {
-            int64_t dst = a + count[bin[m]]++;
-            perm[dst] = (int)m;
-            bin_sorted[dst] = bin[m];
-        }
+        for (int64_t m = a; m < b; ++m) count[key[m] + 1]++;
+        for (int k = 0; k < nkeys; ++k) count[k + 1] += count[k];
+        for (int64_t m = a; m < b; ++m) perm[a + count[key[m]]++] = (int)m;
     }
 }
 
@@ -108,21 +125,27 @@ void build_gridwork(purify_plan* p, const std::vector<int>& bin_sorted, int tile
         }
     }
     (void)M;
-    const int CMAX = 2048;  // visibilities per subproblem
+    // visibilities per subproblem: about four subproblems per resident
+    // block on 152 SMs for large M, within [256, 4096]
+    int CMAX = (int)std::min<int64_t>(4096, std::max<int64_t>(256, p->M / (152 * 2 * 4)));
+    CMAX = (CMAX + 255) / 256 * 256;
+    const int PMAX = 128;   // pieces per subproblem (shared-memory table size)
     std::vector<int> sub_bin, piece_off, pst, plen;
     for (int b = 0; b < nbins; ++b) {
-        int in_sub = 0;
+        int in_sub = 0, pieces = 0;
         bool open = false;
         for (auto run : runs[b]) {
             int s = run.first, len = run.second;
             while (len > 0) {
-                if (!open || in_sub >= CMAX) {
+                if (!open || in_sub >= CMAX || pieces >= PMAX) {
+                    pieces = 0;
                     sub_bin.push_back(b);
                     piece_off.push_back((int)pst.size());
                     in_sub = 0;
                     open = true;
                 }
                 int take = std::min(len, CMAX - in_sub);
+                ++pieces;
                 pst.push_back(s);
                 plen.push_back(take);
                 s += take;
@@ -138,6 +161,97 @@ void build_gridwork(purify_plan* p, const std::vector<int>& bin_sorted, int tile
     upload(w.piece_off, piece_off);
     upload(w.piece_start, pst);
     upload(w.piece_len, plen);
+}
+
+// ---------------------------------------------------------------- autotuner
+// Launch shapes picked by timing on the plan's own data: the gridding tile
+// (work list rebuilt from the same hierarchical order) and the rows/columns
+// per block of the FFT passes. Results are cached per problem shape.
+struct TuneKey {
+    int nx, ny, J, dtype, mlog, R;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(nx, ny, J, dtype, mlog, R) < std::tie(o.nx, o.ny, o.J, o.dtype, o.mlog, o.R);
+    }
+};
+struct TuneVal { int tile, rb, cb; };
+static std::mutex g_tune_mutex;
+static std::map<TuneKey, TuneVal> g_tune_cache;
+
+static float time_ms(cudaStream_t s, const std::function<void()>& f, int reps) {
+    cudaEvent_t a, b;
+    PURIFY_CUDA(cudaEventCreate(&a));
+    PURIFY_CUDA(cudaEventCreate(&b));
+    f();  // warm-up
+    PURIFY_CUDA(cudaEventRecord(a, s));
+    for (int i = 0; i < reps; ++i) f();
+    PURIFY_CUDA(cudaEventRecord(b, s));
+    PURIFY_CUDA(cudaEventSynchronize(b));
+    float ms = 0.f;
+    PURIFY_CUDA(cudaEventElapsedTime(&ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return ms / reps;
+}
+
+template <typename T, typename BinsFor>
+static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_for, bool tune) {
+    using C = typename cplx_of<T>::type;
+    int mlog = 0;
+    while ((int64_t(1) << (mlog + 1)) <= p->M) ++mlog;
+    TuneKey key{p->nx, p->ny, p->J, p->dtype, mlog, std::min(p->R, 64)};
+    TuneVal val{p->work.tile, 0, 0};
+    bool cached = false;
+    if (tune) {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) { val = it->second; cached = true; }
+    }
+    if (tune && !cached) {
+        // deterministic test data in the workspaces
+        std::vector<T> img(2 * (size_t)p->N), vis(2 * (size_t)p->M);
+        uint64_t st = 12345;
+        auto rnd = [&]() { st = st * 6364136223846793005ull + 1442695040888963407ull; return (T)((double)(st >> 11) * 0x1.0p-53 - 0.5); };
+        for (auto& x : img) x = rnd();
+        for (auto& x : vis) x = rnd();
+        PURIFY_CUDA(cudaMemcpy(p->tmp_img.p, img.data(), sizeof(T) * img.size(), cudaMemcpyHostToDevice));
+        PURIFY_CUDA(cudaMemcpy(p->tmp_vis.p, vis.data(), sizeof(T) * vis.size(), cudaMemcpyHostToDevice));
+        T* ximg = p->tmp_img.as<T>();
+        C* yv = p->tmp_vis.as<C>();
+        // FFT launch shapes
+        float best = 1e30f;
+        for (int rb = 1; rb <= 8; rb *= 2) {
+            if (p->ny % rb || 2 * (size_t)rb * p->Kx * sizeof(C) > 160 * 1024) continue;
+            p->fft_rb = rb;
+            float ms = time_ms(p->stream, [&] { launch_scale_pad_rows(p, ximg, 1.0, nullptr, nullptr, nullptr, nullptr); }, 5);
+            if (ms < best) { best = ms; val.rb = rb; }
+        }
+        best = 1e30f;
+        for (int cb = 1; cb <= 8; cb *= 2) {
+            if (p->Kx % cb || 2 * (size_t)cb * p->Ky * sizeof(C) > 160 * 1024) continue;
+            p->fft_cb = cb;
+            float ms = time_ms(p->stream, [&] { launch_cols_fwd(p, nullptr); }, 5);
+            if (ms < best) { best = ms; val.cb = cb; }
+        }
+        p->fft_rb = val.rb;
+        p->fft_cb = val.cb;
+        // gridding tile
+        if (cand.size() > 1 && p->M >= 32768) {
+            best = 1e30f;
+            for (int t : cand) {
+                build_gridwork(p, bins_for(t), t);
+                float ms = time_ms(p->stream, [&] {
+                    launch_phi(p, ximg, yv, false, 1.0);
+                    launch_phi_adj(p, yv, p->tmp_img.p, false, 1.0, 0, nullptr);
+                }, 3);
+                if (ms < best) { best = ms; val.tile = t; }
+            }
+        }
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tune_cache[key] = val;
+    }
+    p->fft_rb = val.rb;
+    p->fft_cb = val.cb;
+    build_gridwork(p, bins_for(val.tile), val.tile);
 }
 
 template <typename T> static void finish_plan(purify_plan* p) {
@@ -159,17 +273,32 @@ template <typename T> static void finish_plan(purify_plan* p) {
         if (std::fabs((double)u[m]) > 3.2 || std::fabs((double)v[m]) > 3.2)
             throw Error{PURIFY_EINVAL, "(u, v) outside [-pi, pi]"};
     }
-    int tile = d.tile > 0 ? d.tile : 32;
-    tile = std::min(tile, std::min(p->Kx, p->Ky));
-    std::vector<int> perm, bin_sorted;
-    sort_visibilities<T>(p, u, v, tile, perm, bin_sorted);
+    const int kmin = std::min(p->Kx, p->Ky);
+    const int tmax = std::min(std::min(64, kmin), max_grid_tile(p->dtype, p->J));
+    int tmin = std::min(16, tmax);
+    if (d.tile > 0 && d.tile < tmin) tmin = std::max(8, d.tile);
+    std::vector<int> cx, cy, perm;
+    first_tap_cells<T>(p, u, v, cx, cy);
+    sort_hierarchical(p, cx, cy, tmin, tmax, perm);
     std::vector<T> us(p->M), vs(p->M);
     for (int64_t i = 0; i < p->M; ++i) { us[i] = u[perm[i]]; vs[i] = v[perm[i]]; }
     upload(p->us, us);
     upload(p->vs, vs);
     upload(p->perm, perm);
     upload(p->d_offsets, p->offsets);
-    build_gridwork(p, bin_sorted, tile);
+    std::vector<int> scx(p->M), scy(p->M);
+    for (int64_t i = 0; i < p->M; ++i) { scx[i] = cx[perm[i]]; scy[i] = cy[perm[i]]; }
+    auto bins_for = [&](int t) {
+        std::vector<int> bins(p->M);
+        const int tx = p->Kx / t;
+        for (int64_t i = 0; i < p->M; ++i) bins[i] = (scy[i] / t) * tx + scx[i] / t;
+        return bins;
+    };
+    std::vector<int> cand;
+    if (d.tile > 0) cand.push_back(std::max(tmin, std::min(d.tile, tmax)));
+    else for (int t = tmin; t <= tmax; t *= 2) cand.push_back(t);
+    p->work.tile = cand.size() == 1 ? cand[0] : 32;
+    if (std::find(cand.begin(), cand.end(), p->work.tile) == cand.end()) p->work.tile = cand.back();
     // visibility chunks for the per-block segmented reductions
     {
         const int64_t CH = 4096;
@@ -202,6 +331,7 @@ template <typename T> static void finish_plan(purify_plan* p) {
     p->tmp_vis.alloc(sizeof(C) * (size_t)p->M);
     p->workspace_bytes = (int64_t)(p->grid.bytes + p->rows.bytes + p->ll0.bytes + p->ll1.bytes + p->tmp_img.bytes +
                                    p->tmp_vis.bytes + p->us.bytes + p->vs.bytes + p->perm.bytes);
+    autotune<T>(p, cand, bins_for, d.tile == 0);
 }
 
 purify_plan* create_plan(const purify_plan_desc* d) {

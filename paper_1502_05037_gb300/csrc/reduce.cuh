@@ -1,0 +1,77 @@
+// Deterministic reduction helpers and the scalar slots of the SDMM solver
+// state shared by the solver kernels and the fused operator kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+namespace purify {
+
+// ----------------------------------------------------------- scalar slots
+enum Slot {
+    S_RS = 0,        // r.r
+    S_RS0 = 1,       // r0.r0 of the current x-update
+    S_BETA = 2,
+    S_ALPHA = 3,
+    S_PAP = 4,
+    S_OBJ = 5,       // ||W Psi^dagger x||_1 at the iterate entering the iteration
+    S_OBJ_PREV = 6,
+    S_CGCOUNT = 7,   // CG steps done (running total)
+    S_XN2 = 8,       // ||x_new||^2
+    S_DXN2 = 9,      // ||x_new - x_old||^2
+    S_TOL2 = 10,     // cg_tol^2
+    S_GMAX = 11,     // max |.| reduction result
+    S_NORM2 = 12,    // generic norm^2 result
+    S_SUM = 13,      // generic sum result
+    S_BLOCKS = 32    // then R entries of ||r_i||^2, then R of ||Phi_i x/nu - ybar_i||^2
+};
+enum Counter { C_PROX = 0, C_PROJ, C_CGI, C_ALPHA, C_UPD, C_REL, C_GEN, C_COUNT };
+enum Flag { F_CGDONE = 0, F_NAN = 1, F_COUNT = 4 };
+
+static constexpr int RB = 256;                 // threads per reduction block
+static inline int red_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + RB * 4 - 1) / (RB * 4), 152 * 8)); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over the thread block (result valid in thread 0).
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double sh[32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        v = warp_sum(v);
+    }
+    return v;
+}
+
+// True in every thread of the last block to arrive; partials written before
+// the call by other blocks are then visible.
+__device__ __forceinline__ bool arrive_last(unsigned* counter) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// Ordered sum of part[0..n) by the calling block (result in thread 0).
+__device__ __forceinline__ double ordered_sum(const double* part, int n) {
+    double v = 0.0;
+    // each thread sums a strided subsequence, then the block combines them
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += __ldcg(part + i);
+    return block_sum(v);
+}
+
+
+}  // namespace purify

@@ -12,8 +12,12 @@
 // The CG residual b - A x is formed with a single adjoint: Phi x / nu is
 // already at hand from the projection step, so
 //   b - A x = Psi(s1 - z1) + (s3 - z3) - 2 x + Re Phi^H (s2 - z2 - Phi x / nu) / nu.
-// Reductions (norms, dot products, objective) are FP64 with a fixed order:
-// per-block partials, summed in index order by the last block to finish.
+// Reductions (norms, dot products, objective) have a fixed order: each thread
+// accumulates its few elements (at most 16) in the plan precision, the
+// thread, warp and block partials are summed in FP64, and the block partials
+// are summed in index order by the last block to finish. (GB300 issues FP64
+// arithmetic at a small fraction of the FP32 rate, so per-element FP64 work
+// would bound these kernels.)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,73 +27,9 @@
 
 #include "internal.h"
 #include "launch.h"
+#include "reduce.cuh"
 
 namespace purify {
-
-// ----------------------------------------------------------- scalar slots
-enum Slot {
-    S_RS = 0,        // r.r
-    S_RS0 = 1,       // r0.r0 of the current x-update
-    S_BETA = 2,
-    S_ALPHA = 3,
-    S_PAP = 4,
-    S_OBJ = 5,       // ||W Psi^dagger x||_1 at the iterate entering the iteration
-    S_OBJ_PREV = 6,
-    S_CGCOUNT = 7,   // CG steps done (running total)
-    S_XN2 = 8,       // ||x_new||^2
-    S_DXN2 = 9,      // ||x_new - x_old||^2
-    S_TOL2 = 10,     // cg_tol^2
-    S_GMAX = 11,     // max |.| reduction result
-    S_NORM2 = 12,    // generic norm^2 result
-    S_SUM = 13,      // generic sum result
-    S_BLOCKS = 32    // then R entries of ||r_i||^2, then R of ||Phi_i x/nu - ybar_i||^2
-};
-enum Counter { C_PROX = 0, C_PROJ, C_CGI, C_ALPHA, C_UPD, C_REL, C_GEN, C_COUNT };
-enum Flag { F_CGDONE = 0, F_NAN = 1, F_COUNT = 4 };
-
-static const int RB = 256;                 // threads per reduction block
-static int red_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + RB * 4 - 1) / (RB * 4), 152 * 8)); }
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Sum over the thread block (result valid in thread 0).
-__device__ double block_sum(double v) {
-    __shared__ double sh[32];
-    v = warp_sum(v);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
-        v = warp_sum(v);
-    }
-    return v;
-}
-
-// True in every thread of the last block to arrive; partials written before
-// the call by other blocks are then visible.
-__device__ bool arrive_last(unsigned* counter) {
-    __shared__ bool last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (last) __threadfence();
-    return last;
-}
-
-// Ordered sum of part[0..n) by the calling block (result in thread 0).
-__device__ double ordered_sum(const double* part, int n) {
-    double v = 0.0;
-    // each thread sums a strided subsequence, then the block combines them
-    for (int i = threadIdx.x; i < n; i += blockDim.x) v += __ldcg(part + i);
-    return block_sum(v);
-}
 
 // ------------------------------------------------------------ kernels
 // prox of gamma ||W .||_1 with the multiplier update; c holds Psi^dagger x on
@@ -97,11 +37,11 @@ __device__ double ordered_sum(const double* part, int n) {
 template <typename T>
 __global__ void k_prox_l1(T* __restrict__ c, T* __restrict__ z1, const T* __restrict__ w, int64_t D, double gamma,
                           double* part, unsigned* counters, double* scal, int eval_only) {
-    double obj = 0.0;
+    T obj = 0;  // per-thread partial in the plan precision, FP64 across threads
     for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < D; d += (int64_t)gridDim.x * blockDim.x) {
         T v = c[d];
         T wd = w ? w[d] : T(1);
-        obj += fabs((double)wd * (double)v);
+        obj += fabs(wd * v);
         if (eval_only) continue;
         T zz = z1[d];
         T t = v + zz;
@@ -112,7 +52,7 @@ __global__ void k_prox_l1(T* __restrict__ c, T* __restrict__ z1, const T* __rest
         z1[d] = zn;
         c[d] = s - zn;
     }
-    double b = block_sum(obj);
+    double b = block_sum((double)obj);
     if (threadIdx.x == 0) part[blockIdx.x] = b;
     if (arrive_last(counters + C_PROX)) {
         double tot = ordered_sum(part, gridDim.x);
@@ -134,19 +74,19 @@ __global__ void k_proj_norms(const typename cplx_of<T>::type* __restrict__ v2,
                              const int* __restrict__ chunk_first, double* part, unsigned* counters, double* scal) {
     using C = typename cplx_of<T>::type;
     const int ch = blockIdx.x;
-    double a = 0.0, e = 0.0;
+    T a = 0, e = 0;  // per-thread partials (at most 16 terms), FP64 across threads
     for (int m = cbeg[ch] + threadIdx.x; m < cend[ch]; m += blockDim.x) {
         C v = v2[m], y = ybar[m];
-        double rx = (double)v.x - (double)y.x, ry = (double)v.y - (double)y.y;
+        T rx = v.x - y.x, ry = v.y - y.y;
         e += rx * rx + ry * ry;
         if (z2) {
             C z = z2[m];
-            double tx = (double)(v.x + z.x - y.x), ty = (double)(v.y + z.y - y.y);
+            T tx = rx + z.x, ty = ry + z.y;
             a += tx * tx + ty * ty;
         }
     }
-    double sa = block_sum(a);
-    double se = block_sum(e);
+    double sa = block_sum((double)a);
+    double se = block_sum((double)e);
     if (threadIdx.x == 0) { part[2 * ch] = sa; part[2 * ch + 1] = se; }
     if (arrive_last(counters + C_PROJ)) {
         // chunk_first[r] .. chunk_first[r+1] are block r's chunks
@@ -207,13 +147,13 @@ __global__ void k_positivity(const T* __restrict__ x, T* __restrict__ z3, const 
 template <typename T>
 __global__ void k_cg_init(const T* __restrict__ r, T* __restrict__ p, int64_t N, double* part, unsigned* counters,
                           double* scal, int* flags) {
-    double acc = 0.0;
+    T acc = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         T v = r[i];
-        acc += (double)v * (double)v;
+        acc += v * v;
         p[i] = T(0);
     }
-    double b = block_sum(acc);
+    double b = block_sum((double)acc);
     if (threadIdx.x == 0) part[blockIdx.x] = b;
     if (arrive_last(counters + C_CGI)) {
         double tot = ordered_sum(part, gridDim.x);
@@ -228,40 +168,20 @@ __global__ void k_cg_init(const T* __restrict__ r, T* __restrict__ p, int64_t N,
     }
 }
 
-// alpha = rs / (p . Ap)
-template <typename T>
-__global__ void k_cg_alpha(const T* __restrict__ p, const T* __restrict__ Ap, int64_t N, double* part,
-                           unsigned* counters, double* scal, int* flags) {
-    if (flags[F_CGDONE]) return;
-    double acc = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-        acc += (double)p[i] * (double)Ap[i];
-    double b = block_sum(acc);
-    if (threadIdx.x == 0) part[blockIdx.x] = b;
-    if (arrive_last(counters + C_ALPHA)) {
-        double tot = ordered_sum(part, gridDim.x);
-        if (threadIdx.x == 0) {
-            scal[S_PAP] = tot;
-            scal[S_ALPHA] = tot > 0.0 ? scal[S_RS] / tot : 0.0;
-            counters[C_ALPHA] = 0;
-        }
-    }
-}
-
 // x += alpha p; r -= alpha Ap; rs' = r.r; beta = rs'/rs; stop test.
 template <typename T>
 __global__ void k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ Ap,
                             int64_t N, double* part, unsigned* counters, double* scal, int* flags) {
     if (flags[F_CGDONE]) return;
     const T alpha = (T)scal[S_ALPHA];
-    double acc = 0.0;
+    T acc = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         x[i] += alpha * p[i];
         T rv = r[i] - alpha * Ap[i];
         r[i] = rv;
-        acc += (double)rv * (double)rv;
+        acc += rv * rv;
     }
-    double b = block_sum(acc);
+    double b = block_sum((double)acc);
     if (threadIdx.x == 0) part[blockIdx.x] = b;
     if (arrive_last(counters + C_UPD)) {
         double tot = ordered_sum(part, gridDim.x);
@@ -281,14 +201,14 @@ __global__ void k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __res
 template <typename T>
 __global__ void k_relchange(const T* __restrict__ x, const T* __restrict__ xprev, int64_t N, double* part,
                             unsigned* counters, double* scal) {
-    double a = 0.0, d = 0.0;
+    T a = 0, d = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        double xv = x[i], dv = (double)x[i] - (double)xprev[i];
+        T xv = x[i], dv = x[i] - xprev[i];
         a += xv * xv;
         d += dv * dv;
     }
-    double ba = block_sum(a);
-    double bd = block_sum(d);
+    double ba = block_sum((double)a);
+    double bd = block_sum((double)d);
     if (threadIdx.x == 0) { part[2 * blockIdx.x] = ba; part[2 * blockIdx.x + 1] = bd; }
     if (arrive_last(counters + C_REL)) {
         double sa = 0.0, sd = 0.0;
@@ -540,13 +460,8 @@ template <typename T> struct Solver {
             launch_degrid(p, p->tmp_vis.p, false, skip);
             launch_grid(p, p->tmp_vis.p, false, skip);
             launch_cols_inv(p, skip);
-            launch_rows_inv_crop(p, s.Ap.p, inv_nu, 1, s.p.p, 2.0, skip);
-            {
-                Launch L(p, "cg_alpha");
-                k_cg_alpha<T><<<red_blocks(p->N), RB, 0, p->stream>>>(s.p.template as<T>(), s.Ap.template as<T>(),
-                                                                     p->N, part(), ctr(), scal(), flags());
-                L.done();
-            }
+            // A p = 2 p + Re Phi^H Phi p / nu^2, with p . A p and alpha fused in
+            launch_rows_inv_crop(p, s.Ap.p, inv_nu, 1, s.p.p, 2.0, skip, part(), ctr(), scal());
             {
                 Launch L(p, "cg_update");
                 k_cg_update<T><<<red_blocks(p->N), RB, 0, p->stream>>>(x, s.r.template as<T>(), s.p.template as<T>(),
@@ -633,6 +548,122 @@ template <typename T> static void run_iterations(purify_plan* p, int n) {
     }
     PURIFY_CUDA(cudaEventRecord(s.ev_out, s.gstream));
     PURIFY_CUDA(cudaStreamWaitEvent(user, s.ev_out, 0));
+}
+
+// --------------------------------------------------------- batched plans
+void batch_destroy(BatchState* b) {
+    if (!b) return;
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    for (auto& st : b->streams) cudaStreamDestroy(st);
+    for (auto& e : b->events) cudaEventDestroy(e);
+    delete b;
+}
+
+static void iteration_on(purify_plan* p) {
+    if (p->dtype == PURIFY_F32) Solver<float>(p).iteration(p->sd.cg_iters);
+    else Solver<double>(p).iteration(p->sd.cg_iters);
+}
+
+void batch_iterate(BatchState* b, int iters) {
+    const size_t n = b->plans.size();
+    if (iters <= 0 || n == 0) return;
+    for (auto* p : b->plans)
+        if (!p->sd.started) throw Error{PURIFY_EINVAL, "every plan of a batch needs a started solve"};
+    if (b->streams.empty()) {
+        b->streams.resize(n);
+        b->events.resize(n + 1);
+        for (size_t i = 0; i < n; ++i) PURIFY_CUDA(cudaStreamCreateWithFlags(&b->streams[i], cudaStreamNonBlocking));
+        for (auto& e : b->events) PURIFY_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    // the captured graph depends on each plan's constants
+    std::vector<double> key;
+    for (auto* p : b->plans) {
+        key.push_back(p->sd.gamma);
+        key.push_back(p->sd.nu);
+        key.push_back(p->sd.have_w ? 1.0 : 0.0);
+        key.push_back((double)p->sd.cg_iters);
+    }
+    bool timed = false;
+    for (auto* p : b->plans) timed = timed || timing_enabled(p);
+    if (timed) {
+        // kernel timing records events around every launch: run eagerly
+        std::vector<cudaStream_t> saved(n);
+        for (size_t i = 0; i < n; ++i) saved[i] = b->plans[i]->stream;
+        try {
+            for (int it = 0; it < iters; ++it) {
+                PURIFY_CUDA(cudaEventRecord(b->events[n], b->stream));
+                for (size_t i = 0; i < n; ++i) {
+                    PURIFY_CUDA(cudaStreamWaitEvent(b->streams[i], b->events[n], 0));
+                    b->plans[i]->stream = b->streams[i];
+                    iteration_on(b->plans[i]);
+                    PURIFY_CUDA(cudaEventRecord(b->events[i], b->streams[i]));
+                    PURIFY_CUDA(cudaStreamWaitEvent(b->stream, b->events[i], 0));
+                }
+            }
+        } catch (...) {
+            for (size_t i = 0; i < n; ++i) b->plans[i]->stream = saved[i];
+            throw;
+        }
+        for (size_t i = 0; i < n; ++i) b->plans[i]->stream = saved[i];
+        for (auto* p : b->plans) p->sd.iters_done += iters;
+        return;
+    }
+    int start = 0;
+    if (!b->gexec || key != b->key) {
+        if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+        std::vector<cudaStream_t> saved(n);
+        for (size_t i = 0; i < n; ++i) saved[i] = b->plans[i]->stream;
+        auto fork_join = [&](bool capture) {
+            PURIFY_CUDA(cudaEventRecord(b->events[n], b->stream));
+            for (size_t i = 0; i < n; ++i) {
+                PURIFY_CUDA(cudaStreamWaitEvent(b->streams[i], b->events[n], 0));
+                b->plans[i]->stream = b->streams[i];
+                iteration_on(b->plans[i]);
+                PURIFY_CUDA(cudaEventRecord(b->events[i], b->streams[i]));
+                PURIFY_CUDA(cudaStreamWaitEvent(b->stream, b->events[i], 0));
+            }
+            (void)capture;
+        };
+        try {
+            fork_join(false);  // one eager iteration (sets kernel attributes outside capture)
+            start = 1;
+            cudaGraph_t g = nullptr;
+            PURIFY_CUDA(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            try {
+                fork_join(true);
+            } catch (...) {
+                cudaStreamEndCapture(b->stream, &g);
+                if (g) cudaGraphDestroy(g);
+                throw;
+            }
+            PURIFY_CUDA(cudaStreamEndCapture(b->stream, &g));
+            size_t nn = 0;
+            PURIFY_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
+            std::vector<cudaGraphNode_t> nodes(nn);
+            PURIFY_CUDA(cudaGraphGetNodes(g, nodes.data(), &nn));
+            int64_t kn = 0;
+            for (auto nd : nodes) {
+                cudaGraphNodeType t;
+                PURIFY_CUDA(cudaGraphNodeGetType(nd, &t));
+                if (t == cudaGraphNodeTypeKernel) ++kn;
+            }
+            cudaError_t ie = cudaGraphInstantiate(&b->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) { b->gexec = nullptr; PURIFY_CUDA(ie); }
+            b->kernels = kn;
+            b->key = key;
+            add_launches(-kn);
+        } catch (...) {
+            for (size_t i = 0; i < n; ++i) b->plans[i]->stream = saved[i];
+            throw;
+        }
+        for (size_t i = 0; i < n; ++i) b->plans[i]->stream = saved[i];
+    }
+    for (int i = start; i < iters; ++i) {
+        PURIFY_CUDA(cudaGraphLaunch(b->gexec, b->stream));
+        add_launches(b->kernels);
+    }
+    for (auto* p : b->plans) p->sd.iters_done += iters;
 }
 
 void sdmm_iterate(purify_plan* p, int iters) {

@@ -8,7 +8,7 @@ from paper_1502_05037_gb300 import synth
 
 DEV = torch.device("cuda:0")
 
-# spec tolerances: relative l2 of operator outputs
+# operator tolerances: relative l2 error of outputs, FP32 and FP64 plans
 TOL = {pk.PURIFY_F32: 1e-5, pk.PURIFY_F64: 1e-12}
 
 
