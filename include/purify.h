@@ -221,6 +221,17 @@ purify_status purify_coef_std(purify_plan *plan, const void *x, double *std_out)
 purify_status purify_psi_adj_static(const void *x, void *c, int32_t nx, int32_t ny, int32_t levels,
                                     uint32_t basis_mask, purify_dtype dtype, void *stream);
 
+/* Learned warm start building block (the paper has no learned component;
+ * the U-Net only changes SDMM's starting point): 'same' k x k convolution
+ * (k = 1 or 3, zero padding, cross-correlation) of x [B][H][W][Cin] (NHWC,
+ * FP32, DEVICE) with w [Cout][k][k][Cin] (FP32, DEVICE) and bias [Cout]
+ * (DEVICE or NULL), optional ReLU, into out [B][H][W][Cout] (FP32, DEVICE).
+ * x and w are rounded to BF16 and multiplied on the tensor cores (tcgen05)
+ * with FP32 accumulation. Cout <= 256. Synchronous; allocates staging.
+ * Errors: EINVAL (shape), ETIMEOUT (a bounded device wait gave up), ECUDA. */
+purify_status purify_conv2d(const float *x, int32_t B, int32_t H, int32_t W, int32_t Cin, const float *w,
+                            const float *bias, int32_t Cout, int32_t k, int32_t relu, float *out, void *stream);
+
 /* Per-kernel device timing for profiling: when enabled, every kernel launch
  * of the plan is bracketed by CUDA events on the plan's stream. */
 purify_status purify_timing_enable(purify_plan *plan, int32_t enable);

@@ -199,6 +199,15 @@ def purify_psi_adj_static(x, c, nx: int, ny: int, levels: int, basis_mask: int =
     check(load().purify_psi_adj_static(_ptr(x), _ptr(c), nx, ny, levels, basis_mask, dtype, _stream_ptr(stream)))
 
 
+def purify_conv2d(x, w, bias, out, k: int, relu: bool = False, stream=None):
+    """Tensor-core BF16 convolution (see include/purify.h): x [B][H][W][Cin],
+    w [Cout][k][k][Cin], out [B][H][W][Cout], FP32 device tensors."""
+    B, H, W, Cin = x.shape
+    Cout = w.shape[0]
+    check(load().purify_conv2d(_ptr(x), B, H, W, Cin, _ptr(w), _ptr(bias), Cout, k, int(bool(relu)), _ptr(out),
+                               _stream_ptr(stream)))
+
+
 def purify_timing_enable(plan: Plan, enable: bool = True):
     check(load().purify_timing_enable(plan.handle, int(bool(enable))))
 

@@ -98,6 +98,8 @@ _SIGS = {
     "purify_reweight": (C.c_int, [_P, _P, C.c_double, _P]),
     "purify_coef_std": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
     "purify_psi_adj_static": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_uint32, C.c_int32, _P]),
+    "purify_conv2d": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, _P, C.c_int32, C.c_int32,
+                                C.c_int32, _P, _P]),
     "purify_timing_enable": (C.c_int, [_P, C.c_int32]),
     "purify_timing_read": (C.c_int32, [_P, C.POINTER(purify_kernel_time), C.c_int32, C.c_int32]),
     "purify_launch_count": (C.c_int64, []),

@@ -326,6 +326,19 @@ purify_status purify_psi_adj_static(const void* x, void* c, int32_t nx, int32_t 
     });
 }
 
+purify_status purify_conv2d(const float* x, int32_t B, int32_t H, int32_t W, int32_t Cin, const float* w,
+                            const float* bias, int32_t Cout, int32_t k, int32_t relu, float* out, void* stream) {
+    return guarded([&] {
+        PURIFY_REQUIRE(x && w && out, "null argument");
+        PURIFY_REQUIRE(B >= 1 && H >= 1 && W >= 1 && Cin >= 1 && Cout >= 1 && Cout <= 256 && (k == 1 || k == 3),
+                       "conv2d: bad shape (Cout <= 256, k = 1 or 3)");
+        PURIFY_REQUIRE(!is_host_pointer(x) && !is_host_pointer(w) && !is_host_pointer(out) &&
+                           (!bias || !is_host_pointer(bias)),
+                       "conv2d: device pointers required");
+        conv2d_f32(x, B, H, W, Cin, w, bias, Cout, k, relu, out, (cudaStream_t)stream);
+    });
+}
+
 purify_status purify_timing_enable(purify_plan* p, int32_t enable) {
     return guarded([&] {
         PURIFY_REQUIRE(p != nullptr, "null plan");

@@ -169,6 +169,10 @@ void psi_adj_static(const void* x, void* c, int nx, int ny, int levels, unsigned
 size_t psi_adj_static_bytes(int nx, int ny, unsigned mask, int dtype);
 size_t psi_adj_static_capacity();
 
+// learned warm start
+void conv2d_f32(const float* x, int B, int H, int W, int Cin, const float* w, const float* bias, int Cout, int k,
+                int relu, float* out, cudaStream_t st);
+
 // solver
 void sdmm_solve(purify_plan* p, const void* y, const double* eps, const void* w, void* x,
                 const purify_sdmm_params& prm, purify_sdmm_stats* st);
