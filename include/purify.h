@@ -232,6 +232,36 @@ purify_status purify_psi_adj_static(const void *x, void *c, int32_t nx, int32_t 
 purify_status purify_conv2d(const float *x, int32_t B, int32_t H, int32_t W, int32_t Cin, const float *w,
                             const float *bias, int32_t Cout, int32_t k, int32_t relu, float *out, void *stream);
 
+/* Learned warm-start network (not in the paper): a U-Net of `levels` levels
+ * and base width `base` on H x W single-channel images (NHWC with C = 1),
+ * BF16 tensor-core convolutions with FP32 accumulation, FP32 parameters,
+ * gradients and Adam state. Architecture per level: conv3x3+ReLU twice,
+ * 2x2 max pooling (encoder); x2 upsampling + conv3x3+ReLU, concatenation with
+ * the skip, conv3x3+ReLU twice (decoder); 1x1 head added to the input.
+ * Parameters are one FP32 vector, layer by layer (weights [Cout][k][k][Cin]
+ * then biases), layers in the order e0a, e0b, e1a, ..., ba, bb, then for
+ * each decoder level from the deepest: du, da, db; head last.
+ * Images x, y, targets are DEVICE FP32 [B][H][W], B <= max_batch. */
+typedef struct purify_unet purify_unet;
+purify_status purify_unet_create(int32_t H, int32_t W, int32_t levels, int32_t base, int32_t max_batch,
+                                 uint64_t seed, void *stream, purify_unet **out);
+purify_status purify_unet_destroy(purify_unet *net);
+int64_t purify_unet_num_params(const purify_unet *net);
+/* Copy the parameter vector out / in (host or device pointers). */
+purify_status purify_unet_get_params(purify_unet *net, float *out);
+purify_status purify_unet_set_params(purify_unet *net, const float *in);
+/* y = net(x); asynchronous. */
+purify_status purify_unet_forward(purify_unet *net, const float *x, float *y, int32_t B);
+/* Mean-squared-error loss against `target` and its gradient with respect to
+ * every parameter (copied to grads, host or device, when not NULL);
+ * synchronous, loss to *loss (host) when not NULL. */
+purify_status purify_unet_gradients(purify_unet *net, const float *x, const float *target, int32_t B, float *grads,
+                                    double *loss);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the batch; asynchronous
+ * unless loss (host) is requested. */
+purify_status purify_unet_train_step(purify_unet *net, const float *x, const float *target, int32_t B, float lr,
+                                     double *loss);
+
 /* Per-kernel device timing for profiling: when enabled, every kernel launch
  * of the plan is bracketed by CUDA events on the plan's stream. */
 purify_status purify_timing_enable(purify_plan *plan, int32_t enable);

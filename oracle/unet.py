@@ -16,6 +16,12 @@ Architecture with L levels and base width c (channels c, 2c, 4c, ... ):
                    conv3x3 -> ReLU -> conv3x3 -> ReLU
   head:            conv1x1 (c -> 1), output = input + head (residual)
 Weights are [Cout][kh][kw][Cin]; biases [Cout].
+
+`forward` and `backward` take an optional `q` (a rounding function, identity
+by default). Given one, the network is evaluated with q applied exactly where
+a reduced-precision implementation stores its tensor-core operands: the input,
+every weight, every ReLU output, and every gradient entering a convolution's
+backward. The default is plain FP64.
 """
 from __future__ import annotations
 
@@ -122,17 +128,23 @@ def init_params(levels=4, base=32, seed=0):
     return params
 
 
-def forward(params, x, levels=4, base=32):
+def _ident(a):
+    return a
+
+
+def forward(params, x, levels=4, base=32, q=None):
     """x [B][H][W][1] -> prediction [B][H][W][1]; returns (pred, cache)."""
-    cache = {}
-    h = x
+    q = q or _ident
+    params = {k: (q(v) if k.endswith(".w") else v) for k, v in params.items()}
+    cache = {"params": params, "q": q}
+    h = q(x)
     skips = []
     for l in range(levels - 1):
         for s in ("a", "b"):
             name = f"e{l}{s}"
             cache[name + ".in"] = h
             z = conv2d(h, params[name + ".w"], params[name + ".b"])
-            h = relu(z)
+            h = q(relu(z))
             cache[name + ".out"] = h
         skips.append(h)
         cache[f"p{l}.in"] = h
@@ -140,19 +152,19 @@ def forward(params, x, levels=4, base=32):
     for s in ("a", "b"):
         name = "b" + s
         cache[name + ".in"] = h
-        h = relu(conv2d(h, params[name + ".w"], params[name + ".b"]))
+        h = q(relu(conv2d(h, params[name + ".w"], params[name + ".b"])))
         cache[name + ".out"] = h
     for l in reversed(range(levels - 1)):
         name = f"d{l}u"
         hu = upsample2(h)
         cache[name + ".in"] = hu
-        h = relu(conv2d(hu, params[name + ".w"], params[name + ".b"]))
+        h = q(relu(conv2d(hu, params[name + ".w"], params[name + ".b"])))
         cache[name + ".out"] = h
         h = np.concatenate([skips[l], h], axis=-1)
         for s in ("a", "b"):
             name = f"d{l}{s}"
             cache[name + ".in"] = h
-            h = relu(conv2d(h, params[name + ".w"], params[name + ".b"]))
+            h = q(relu(conv2d(h, params[name + ".w"], params[name + ".b"])))
             cache[name + ".out"] = h
     cache["head.in"] = h
     pred = x + conv2d(h, params["head.w"], params["head.b"])
@@ -161,32 +173,34 @@ def forward(params, x, levels=4, base=32):
 
 def backward(params, x, cache, gpred, levels=4, base=32):
     """Gradients of the loss with respect to every parameter, given
-    dLoss/dpred."""
+    dLoss/dpred (uses the weights and rounding recorded by `forward`)."""
+    params = cache["params"]
+    q = cache["q"]
     grads = {}
-    gh, gw, gb = conv2d_backward(cache["head.in"], params["head.w"], gpred)
+    gh, gw, gb = conv2d_backward(cache["head.in"], params["head.w"], q(gpred))
     grads["head.w"], grads["head.b"] = gw, gb
     gskips = {}
     for l in range(levels - 1):
         c = base << l
         for s in ("b", "a"):
             name = f"d{l}{s}"
-            gz = gh * (cache[name + ".out"] > 0)
+            gz = q(gh * (cache[name + ".out"] > 0))
             gh, grads[name + ".w"], grads[name + ".b"] = conv2d_backward(cache[name + ".in"], params[name + ".w"], gz)
         gskips[l] = gh[..., :c]
         gh = gh[..., c:]
         name = f"d{l}u"
-        gz = gh * (cache[name + ".out"] > 0)
+        gz = q(gh * (cache[name + ".out"] > 0))
         ghu, grads[name + ".w"], grads[name + ".b"] = conv2d_backward(cache[name + ".in"], params[name + ".w"], gz)
         gh = upsample2_backward(ghu)
     for s in ("b", "a"):
         name = "b" + s
-        gz = gh * (cache[name + ".out"] > 0)
+        gz = q(gh * (cache[name + ".out"] > 0))
         gh, grads[name + ".w"], grads[name + ".b"] = conv2d_backward(cache[name + ".in"], params[name + ".w"], gz)
     for l in reversed(range(levels - 1)):
         gh = maxpool2_backward(cache[f"p{l}.in"], gh) + gskips[l]
         for s in ("b", "a"):
             name = f"e{l}{s}"
-            gz = gh * (cache[name + ".out"] > 0)
+            gz = q(gh * (cache[name + ".out"] > 0))
             gh, grads[name + ".w"], grads[name + ".b"] = conv2d_backward(cache[name + ".in"], params[name + ".w"], gz)
     return grads
 

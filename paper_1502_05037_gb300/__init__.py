@@ -208,6 +208,51 @@ def purify_conv2d(x, w, bias, out, k: int, relu: bool = False, stream=None):
                                _stream_ptr(stream)))
 
 
+class Unet:
+    """The learned warm-start network (purify_unet_*). Tensors are FP32
+    device arrays [B][H][W]."""
+
+    def __init__(self, H, W, levels=4, base=32, max_batch=8, seed=0, stream=None):
+        lib = load()
+        h = C.c_void_p()
+        check(lib.purify_unet_create(H, W, levels, base, max_batch, seed, _stream_ptr(stream), C.byref(h)))
+        self.handle = h
+        self.H, self.W, self.levels, self.base, self.max_batch = H, W, levels, base, max_batch
+        self.num_params = int(lib.purify_unet_num_params(h))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            check(load().purify_unet_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self, out):
+        check(load().purify_unet_get_params(self.handle, _ptr(out)))
+
+    def set_params(self, p):
+        check(load().purify_unet_set_params(self.handle, _ptr(p)))
+
+    def forward(self, x, y):
+        check(load().purify_unet_forward(self.handle, _ptr(x), _ptr(y), int(x.shape[0])))
+
+    def gradients(self, x, target, grads=None) -> float:
+        loss = C.c_double()
+        check(load().purify_unet_gradients(self.handle, _ptr(x), _ptr(target), int(x.shape[0]), _ptr(grads),
+                                           C.byref(loss)))
+        return loss.value
+
+    def train_step(self, x, target, lr, want_loss=False):
+        loss = C.c_double()
+        check(load().purify_unet_train_step(self.handle, _ptr(x), _ptr(target), int(x.shape[0]), float(lr),
+                                            C.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+
 def purify_timing_enable(plan: Plan, enable: bool = True):
     check(load().purify_timing_enable(plan.handle, int(bool(enable))))
 

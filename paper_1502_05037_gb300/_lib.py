@@ -100,6 +100,15 @@ _SIGS = {
     "purify_psi_adj_static": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_uint32, C.c_int32, _P]),
     "purify_conv2d": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, _P, C.c_int32, C.c_int32,
                                 C.c_int32, _P, _P]),
+    "purify_unet_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, _P,
+                                     C.POINTER(_P)]),
+    "purify_unet_destroy": (C.c_int, [_P]),
+    "purify_unet_num_params": (C.c_int64, [_P]),
+    "purify_unet_get_params": (C.c_int, [_P, _P]),
+    "purify_unet_set_params": (C.c_int, [_P, _P]),
+    "purify_unet_forward": (C.c_int, [_P, _P, _P, C.c_int32]),
+    "purify_unet_gradients": (C.c_int, [_P, _P, _P, C.c_int32, _P, C.POINTER(C.c_double)]),
+    "purify_unet_train_step": (C.c_int, [_P, _P, _P, C.c_int32, C.c_float, C.POINTER(C.c_double)]),
     "purify_timing_enable": (C.c_int, [_P, C.c_int32]),
     "purify_timing_read": (C.c_int32, [_P, C.POINTER(purify_kernel_time), C.c_int32, C.c_int32]),
     "purify_launch_count": (C.c_int64, []),

@@ -339,6 +339,76 @@ purify_status purify_conv2d(const float* x, int32_t B, int32_t H, int32_t W, int
     });
 }
 
+struct purify_unet {
+    purify::Unet* u;
+    int H, W, maxB;
+};
+
+purify_status purify_unet_create(int32_t H, int32_t W, int32_t levels, int32_t base, int32_t max_batch,
+                                 uint64_t seed, void* stream, purify_unet** out) {
+    return guarded([&] {
+        PURIFY_REQUIRE(out != nullptr, "null output pointer");
+        *out = nullptr;
+        Unet* u = unet_create(H, W, levels, base, max_batch, seed, (cudaStream_t)stream);
+        *out = new purify_unet{u, H, W, max_batch};
+    });
+}
+
+purify_status purify_unet_destroy(purify_unet* net) {
+    return guarded([&] {
+        if (!net) return;
+        unet_destroy(net->u);
+        delete net;
+    });
+}
+
+int64_t purify_unet_num_params(const purify_unet* net) { return net ? unet_nparams(*net->u) : -1; }
+
+purify_status purify_unet_get_params(purify_unet* net, float* out) {
+    return guarded([&] {
+        PURIFY_REQUIRE(net && out, "null argument");
+        unet_get(*net->u, 0, out);
+    });
+}
+
+purify_status purify_unet_set_params(purify_unet* net, const float* in) {
+    return guarded([&] {
+        PURIFY_REQUIRE(net && in, "null argument");
+        unet_set_params(*net->u, in);
+    });
+}
+
+purify_status purify_unet_forward(purify_unet* net, const float* x, float* y, int32_t B) {
+    return guarded([&] {
+        PURIFY_REQUIRE(net && x && y && B >= 1 && B <= net->maxB, "bad argument");
+        PURIFY_REQUIRE(!is_host_pointer(x) && !is_host_pointer(y), "device pointers required");
+        unet_forward(*net->u, x, B, y);
+    });
+}
+
+purify_status purify_unet_gradients(purify_unet* net, const float* x, const float* target, int32_t B, float* grads,
+                                    double* loss) {
+    return guarded([&] {
+        PURIFY_REQUIRE(net && x && target && B >= 1 && B <= net->maxB, "bad argument");
+        PURIFY_REQUIRE(!is_host_pointer(x) && !is_host_pointer(target), "device pointers required");
+        unet_gradients(*net->u, x, target, B);
+        double l = unet_read_loss(*net->u);
+        if (loss) *loss = l;
+        if (grads) unet_get(*net->u, 1, grads);
+    });
+}
+
+purify_status purify_unet_train_step(purify_unet* net, const float* x, const float* target, int32_t B, float lr,
+                                     double* loss) {
+    return guarded([&] {
+        PURIFY_REQUIRE(net && x && target && B >= 1 && B <= net->maxB && lr > 0, "bad argument");
+        PURIFY_REQUIRE(!is_host_pointer(x) && !is_host_pointer(target), "device pointers required");
+        unet_gradients(*net->u, x, target, B);
+        unet_adam(*net->u, lr);
+        if (loss) *loss = unet_read_loss(*net->u);
+    });
+}
+
 purify_status purify_timing_enable(purify_plan* p, int32_t enable) {
     return guarded([&] {
         PURIFY_REQUIRE(p != nullptr, "null plan");

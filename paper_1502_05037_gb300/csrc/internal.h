@@ -46,6 +46,11 @@ struct DevBuf {
     DevBuf() = default;
     DevBuf(const DevBuf&) = delete;
     DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        return *this;
+    }
 };
 
 // Wavelet filter table: for basis p (1..8) the low-pass h and high-pass g,
@@ -172,6 +177,17 @@ size_t psi_adj_static_capacity();
 // learned warm start
 void conv2d_f32(const float* x, int B, int H, int W, int Cin, const float* w, const float* bias, int Cout, int k,
                 int relu, float* out, cudaStream_t st);
+
+struct Unet;
+Unet* unet_create(int H, int W, int L, int base, int maxB, uint64_t seed, cudaStream_t st);
+void unet_destroy(Unet* u);
+void unet_forward(Unet& u, const float* x, int B, float* out);
+void unet_gradients(Unet& u, const float* x, const float* target, int B);
+double unet_read_loss(Unet& u);
+void unet_adam(Unet& u, float lr);
+void unet_set_params(Unet& u, const float* p);
+void unet_get(Unet& u, int what, float* out);
+int64_t unet_nparams(Unet& u);
 
 // solver
 void sdmm_solve(purify_plan* p, const void* y, const double* eps, const void* w, void* x,

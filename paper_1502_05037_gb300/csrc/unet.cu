@@ -23,24 +23,9 @@
 
 #include "internal.h"
 #include "tc.cuh"
+#include "unet.h"
 
 namespace purify {
-
-using bf16 = __nv_bfloat16;
-
-struct ConvArgs {
-    const bf16* in;          // NHWC, channel stride in_cs, first channel in_co
-    int B, H, W, Cin, in_cs, in_co;
-    const bf16* w;           // [Npad][k][k][Cinp], zero padded
-    int k, Cinp, Npad;
-    const float* bias;       // [Cout] or null
-    int Cout, relu;
-    bf16* out;               // NHWC BF16 (channel stride out_cs, offset out_co) or null
-    int out_cs, out_co;
-    float* out_f32;          // NHWC FP32 [pixels][Cout] or null
-    const float* residual;   // added to out_f32 when not null ([pixels][Cout])
-    int* err;                // set to 1 when a bounded wait gives up
-};
 
 static constexpr int CONV_KC = 64;          // K elements per chunk
 static constexpr uint32_t WAIT_LIMIT = 1u << 24;
@@ -86,7 +71,10 @@ __global__ void __launch_bounds__(128) k_conv_tc(ConvArgs a) {
         const int dy = tap / a.k - half, dx = tap % a.k - half;
         const int yy = py + dy, xx = px + dx;
         const bool inside = qok && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-        const bf16* src = inside ? a.in + ((size_t)(pb * a.H + yy) * a.W + xx) * a.in_cs + a.in_co : a.in;
+        const int sh = a.up ? 1 : 0;
+        const int Hs = a.H >> sh, Ws = a.W >> sh;
+        const bf16* src =
+            inside ? a.in + ((size_t)(pb * Hs + (yy >> sh)) * Ws + (xx >> sh)) * a.in_cs + a.in_co : a.in;
         for (int c0 = 0; c0 < a.Cinp; c0 += CONV_KC) {
             const int kc = min(CONV_KC, a.Cinp - c0);        // multiple of 16
             const int kcu = kc / 8;                           // 16-byte units per row
@@ -206,7 +194,7 @@ __global__ void k_pack_weights(const float* __restrict__ w, bf16* __restrict__ w
     }
 }
 
-static int round16(int v) { return (v + 15) / 16 * 16; }
+int round16(int v) { return (v + 15) / 16 * 16; }
 
 // Convolution of FP32 NHWC input through BF16 tensor cores (test and
 // inference entry; allocates its staging buffers).

@@ -37,3 +37,90 @@ def test_conv2d_matches_oracle(B, H, W, Cin, Cout, k, relu):
     if relu:
         want = un.relu(want)
     assert rel(out.cpu().numpy(), want) <= 1e-5
+
+
+def oracle_params_from_flat(flat, levels, base):
+    """Split the library's flat parameter vector by the oracle's layer list."""
+    params, off = {}, 0
+    for name, cout, k, cin in un.layer_shapes(levels, base):
+        nw = cout * k * k * cin
+        params[name + ".w"] = flat[off:off + nw].reshape(cout, k, k, cin).astype(np.float64)
+        off += nw
+        params[name + ".b"] = flat[off:off + cout].astype(np.float64)
+        off += cout
+    assert off == flat.size
+    return params
+
+
+def flat_from_oracle(grads, levels, base):
+    return np.concatenate([np.concatenate([grads[n + ".w"].ravel(), grads[n + ".b"].ravel()])
+                           for n, *_ in un.layer_shapes(levels, base)])
+
+
+@pytest.fixture(scope="module")
+def small_net():
+    levels, base, H, W, B = 3, 8, 32, 32, 2
+    net = pk.Unet(H, W, levels, base, max_batch=B, seed=5)
+    flat = np.empty(net.num_params, dtype=np.float32)
+    net.get_params(flat)
+    g = np.random.default_rng(6)
+    # non-zero biases exercise the bias path
+    params = oracle_params_from_flat(flat, levels, base)
+    for k in params:
+        if k.endswith(".b"):
+            params[k] = g.standard_normal(params[k].shape) * 0.05
+    flat = flat_from_oracle(params, levels, base).astype(np.float32)
+    net.set_params(flat)
+    params = oracle_params_from_flat(flat, levels, base)
+    x = g.standard_normal((B, H, W)).astype(np.float32)
+    t = g.standard_normal((B, H, W)).astype(np.float32)
+    return net, params, x, t, levels, base
+
+
+def test_unet_forward_matches_oracle(small_net):
+    net, params, x, t, levels, base = small_net
+    xd = torch.from_numpy(x).to(DEV)
+    y = torch.empty_like(xd)
+    net.forward(xd, y)
+    pred, _ = un.forward(params, x[..., None].astype(np.float64), levels, base)
+    # compare the network's correction (output minus the residual input)
+    assert rel(y.cpu().numpy() - x, pred[..., 0] - x) <= 3e-2
+
+
+@pytest.mark.parametrize("rounding,tol_layer,tol_all", [("bf16", 3e-2, 1.5e-2), ("fp64", 2e-1, 5e-2)])
+def test_unet_gradients_match_oracle(small_net, rounding, tol_layer, tol_all):
+    # "bf16": the oracle rounds where the CUDA path stores BF16 tensor-core
+    # operands (weights, input, ReLU outputs, gradients entering a backward
+    # convolution), so only accumulation order, and the BF16 roundings, ReLU
+    # masks and pooling choices it flips, differ; "fp64": the plain oracle.
+    # Tolerances: on this 3-level network at initialisation the oracle's own
+    # weight gradients move by 2-7 % per layer when its activations are
+    # perturbed at the BF16 rounding level, so a per-layer deviation of a few
+    # percent is rounding, while a wrong index or a missing term gives O(1).
+    net, params, x, t, levels, base = small_net
+    q = bf16_round if rounding == "bf16" else None
+    xd, td = torch.from_numpy(x).to(DEV), torch.from_numpy(t).to(DEV)
+    grads = torch.empty(net.num_params, dtype=torch.float32, device=DEV)
+    loss = net.gradients(xd, td, grads)
+    pred, cache = un.forward(params, x[..., None].astype(np.float64), levels, base, q=q)
+    want_loss, gpred = un.mse(pred, t[..., None].astype(np.float64))
+    assert abs(loss - want_loss) <= 1e-3 * want_loss
+    want = un.backward(params, x[..., None].astype(np.float64), cache, gpred, levels, base)
+    got = oracle_params_from_flat(grads.cpu().numpy(), levels, base)
+    errs = {k: rel(got[k], want[k]) for k in want if np.linalg.norm(want[k]) > 0}
+    bad = {k: round(e, 4) for k, e in errs.items() if e > tol_layer}
+    assert not bad, bad
+    assert rel(flat_from_oracle(got, levels, base), flat_from_oracle(want, levels, base)) <= tol_all
+
+
+def test_unet_training_reduces_loss():
+    H = W = 32
+    net = pk.Unet(H, W, 3, 8, max_batch=4, seed=9)
+    g = np.random.default_rng(10)
+    x = torch.from_numpy(g.standard_normal((4, H, W)).astype(np.float32)).to(DEV)
+    t = 0.5 * x   # the network must learn to halve its input
+    first = net.train_step(x, t, 1e-3, want_loss=True)
+    for _ in range(60):
+        net.train_step(x, t, 1e-3)
+    last = net.train_step(x, t, 1e-3, want_loss=True)
+    assert last < 0.5 * first
