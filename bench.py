@@ -301,6 +301,26 @@ def run_ours(args):
            "h2d_bytes_per_step": wl.M * 8 + wl.nx * wl.ny * 4, "d2h_bytes_per_step": wl.nx * wl.ny * 4,
            "call": "purify_sdmm_solve(host y, host x, max_iter=1)"}
 
+    # ---- pass A': the same timed steps with the circulant-embedded CG normal operator
+    toep = None
+    if args.toeplitz_pass:
+        xt0 = torch.zeros((wl.ny, wl.nx), dtype=torch.float32, device=dev)
+        pk.purify_sdmm_solve(plan, y, eps, xt0, max_iter=0, cg_iters=args.cg_iters, gamma=gamma, nu=nu, toeplitz=True)
+        for i in range(args.warmup):
+            flush.fill_(i & 0xFF)
+            pk.purify_sdmm_iterate(plan, 1)
+        torch.cuda.synchronize(dev)
+        tev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.fill_((k + 11) & 0xFF)
+            tev[k][0].record(stream)
+            pk.purify_sdmm_iterate(plan, 1)
+            tev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        tms = sum(a.elapsed_time(b) for a, b in tev)
+        toep = {"value": args.steps / (tms / 1e3), "unit": "iters/s", "ms_per_step": tms / args.steps,
+                "note": "CG normal operator by circulant embedding of the exact model (separate parity class)"}
+
     # ---- pass D: Phi + Phi^dagger Gvis/s (caller order, device buffers)
     xin = torch.from_numpy(x_true.astype(np.float32)).to(dev)
     yv = torch.empty(wl.M, dtype=torch.complex64, device=dev)
@@ -339,6 +359,7 @@ def run_ours(args):
             "phi_phiadj_gvis_s": gvis, "phi_ms": t_phi, "phi_adj_ms": t_adj,
             "e2e": e2e, "gpu_launches": int(launches), "gpu_launches_per_step": launches / args.steps,
             "wall_s_timed": t_wall, "clocks": clocks, "roofline": roofline, "cpu_baseline": cpu,
+            "toeplitz_cg": toep,
             "kernels": kernel_table,
         }
         print(json.dumps(line), flush=True)
@@ -466,6 +487,85 @@ def run_profile_op(args):
                       "wall_s": time.perf_counter() - t0, "launches": pk.purify_launch_count()}))
 
 
+def run_warmstart(args):
+    """Time-to-tolerance of SDMM from the learned warm start versus from zero
+    on held-out problems (all GPU work through the C ABI)."""
+    import torch
+
+    import paper_1502_05037_gb300 as pk
+    from paper_1502_05037_gb300 import build as pbuild
+    from paper_1502_05037_gb300 import warmstart as ws
+    pbuild.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    t_all = time.perf_counter()
+    # training data: W = I SDMM solutions of seeded problems
+    dirty, target = [], []
+    t0 = time.perf_counter()
+    for i in range(0, args.train_samples, 32):
+        probs = [ws.make_problem(ws.TRAIN_SEED0 + s, dev) for s in range(i, min(i + 32, args.train_samples))]
+        sols = ws.solve_batch(probs, args.target_iters, dev)
+        for p, x in zip(probs, sols):
+            dirty.append(p.dirty)
+            target.append(x)
+        for p in probs:
+            p.plan.close()
+    inputs = torch.stack(dirty).contiguous()
+    targets = torch.stack(target).contiguous()
+    t_data = time.perf_counter() - t0
+    print(f"[warmstart] {len(dirty)} targets in {t_data:.1f} s", file=sys.stderr, flush=True)
+    net = pk.Unet(ws.N_SIDE, ws.N_SIDE, 4, 32, max_batch=args.batch, seed=1)
+    t0 = time.perf_counter()
+    losses = ws.train(net, inputs, targets, args.epochs, args.batch, args.lr)
+    torch.cuda.synchronize(dev)
+    t_train = time.perf_counter() - t0
+    print(f"[warmstart] trained {args.epochs} epochs in {t_train:.1f} s, losses {losses}", file=sys.stderr, flush=True)
+    del inputs, targets
+    # evaluation on held-out seeds
+    rows = []
+    for s in range(args.eval_samples):
+        p = ws.make_problem(ws.EVAL_SEED0 + s, dev)
+        zero = torch.zeros((ws.N_SIDE, ws.N_SIDE), dtype=torch.float32, device=dev)
+        ws.start(p, zero)                      # nu and gamma, shared by both arms
+        pk.purify_sdmm_iterate(p.plan, args.ref_iters)
+        xr = torch.empty_like(zero)
+        ref = ws.current(p, xr)
+        t_plain, it_plain, x_plain, st_plain = ws.time_to_tolerance(p, zero.clone(), ref.objective)
+        pred = torch.empty_like(zero)
+
+        def infer():
+            net.forward(p.dirty.view(1, ws.N_SIDE, ws.N_SIDE), pred.view(1, ws.N_SIDE, ws.N_SIDE))
+            return torch.clamp_min(pred, 0.0).contiguous()
+
+        t_warm, it_warm, x_warm, st_warm = ws.time_to_tolerance(p, None, ref.objective, pre=infer)
+        snr = lambda x: float(20 * np.log10(np.linalg.norm(p.x_true) / np.linalg.norm(p.x_true - x.cpu().numpy())))
+        rows.append((t_plain, it_plain, t_warm, it_warm, snr(x_plain), snr(x_warm), snr(xr)))
+        print(f"[warmstart] eval {s}: plain {t_plain:.3f} s / {it_plain} it, learned {t_warm:.3f} s / {it_warm} it",
+              file=sys.stderr, flush=True)
+        p.plan.close()
+    arr = np.array(rows)
+    speedup = arr[:, 0].sum() / arr[:, 2].sum()
+    line = {
+        "metric": "time-to-tolerance learned vs plain", "value": speedup, "unit": "x (plain seconds / learned seconds)",
+        "higher_is_better": True, "n_gpus": 1, "dtype": "f32 SDMM, bf16 U-Net", "data": "synthetic",
+        "config": {"workload": f"{ws.N_SIDE}x{ws.N_SIDE} sky, M={ws.M_VIS}, J={ws.J}, L={ws.LEVELS}, R=1, "
+                               f"{ws.SNR_DB:g} dB; U-Net 4 levels base 32",
+                   "train_samples": args.train_samples, "eval_samples": args.eval_samples,
+                   "target_iters": args.target_iters, "ref_iters": args.ref_iters, "epochs": args.epochs,
+                   "batch": args.batch, "lr": args.lr,
+                   "tolerance": "objective <= (1+1e-3) reference and every ||y_i - Phi_i x||/eps_i <= 1+1e-3"},
+        "plain": {"seconds_mean": float(arr[:, 0].mean()), "iters_mean": float(arr[:, 1].mean())},
+        "learned": {"seconds_mean": float(arr[:, 2].mean()), "iters_mean": float(arr[:, 3].mean())},
+        "snr_db": {"plain": float(arr[:, 4].mean()), "learned": float(arr[:, 5].mean()),
+                   "reference": float(arr[:, 6].mean()),
+                   "max_abs_diff_learned_vs_plain": float(np.abs(arr[:, 5] - arr[:, 4]).max())},
+        "train_loss": {"first_epoch": losses[0], "last_epoch": losses[-1]},
+        "seconds": {"data": t_data, "train": t_train, "total": time.perf_counter() - t_all},
+        "gpu_launches": pk.purify_launch_count(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -476,12 +576,25 @@ def main():
     ap.add_argument("--cg-iters", type=int, default=CG_ITERS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-toeplitz-pass", dest="toeplitz_pass", action="store_false",
+                    help="skip the extra timed pass with the circulant-embedded CG normal operator")
+    ap.add_argument("--warmstart", action="store_true",
+                    help="time-to-tolerance of the learned warm start versus zero start (trains the U-Net)")
+    ap.add_argument("--train-samples", type=int, default=2000)
+    ap.add_argument("--eval-samples", type=int, default=200)
+    ap.add_argument("--target-iters", type=int, default=300)
+    ap.add_argument("--ref-iters", type=int, default=1500)
+    ap.add_argument("--epochs", type=int, default=8)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--profile-op", choices=["phi", "phi_adj", "psi", "psi_adj", "iteration"], default=None,
                     help="only launch this operator W + K times (for ncu captures); prints no bench line")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.profile_op:
+    if args.warmstart:
+        run_warmstart(args)
+    elif args.profile_op:
         run_profile_op(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -135,6 +135,12 @@ typedef struct {
     int32_t check_every;  /* stopping test interval (iterations), 0 => 10 */
     int32_t resume;       /* 1: continue the previous solve on this plan (same y, eps, w,
                              gamma, nu); x is then output only */
+    int32_t toeplitz;     /* 1: the CG x-update applies Re Phi^H Phi by circulant (Toeplitz)
+                             embedding of the exact model's point-spread function
+                             sum_m exp(i w_m . d) (computed once per solve with the
+                             adjoint NUFFT), instead of a gridding / degridding pair per
+                             CG step; the operator then differs from the NUFFT one by the
+                             NUFFT error. Needs oversample 2. */
 } purify_sdmm_params;
 
 /* Statistics of a solve, evaluated at the returned x. */

@@ -122,6 +122,7 @@ class Problem:
     nu: float | None = None       # ||Phi||_2
     gamma: float | None = None
     weights: np.ndarray | None = None   # [q][ny][nx] or None for W = I
+    normal: str = "nufft"               # CG normal operator: "nufft" or "exact"
 
     def __post_init__(self):
         self.y = np.asarray(self.y, dtype=np.complex128)
@@ -152,7 +153,11 @@ class Problem:
         return np.real(nufft.phi_adj(self.plan, y)) / self.nu
 
     def apply_A(self, x):
-        """(2 I + Re Phi^H Phi / nu^2) x."""
+        """(2 I + Re Phi^H Phi / nu^2) x; with normal == "exact" the normal
+        operator of the exact model (brute-force DFT) replaces the NUFFT one."""
+        if self.normal == "exact":
+            p = self.plan
+            return 2.0 * x + np.real(nufft.phi_exact_adj(nufft.phi_exact(x, p.u, p.v), p.u, p.v, p.nx, p.ny)) / self.nu ** 2
         return 2.0 * x + self.phi_n_adj_re(self.phi_n(x))
 
     def w(self):

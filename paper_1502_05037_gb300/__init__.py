@@ -124,7 +124,8 @@ def purify_op_norm_sq(plan: Plan, iters: int = 100) -> float:
 
 
 def purify_sdmm_solve(plan: Plan, y, eps, x, w=None, max_iter=200, cg_iters=10, cg_tol=0.0, gamma=0.0, nu=0.0,
-                      rel_obj_tol=0.0, eps_tol=0.0, check_every=0, resume=False, raise_on_error=True):
+                      rel_obj_tol=0.0, eps_tol=0.0, check_every=0, resume=False, toeplitz=False,
+                      raise_on_error=True):
     """Solve problem (3); x is updated in place. Returns purify_sdmm_stats."""
     eps_np = None
     eps_ptr = None
@@ -133,7 +134,7 @@ def purify_sdmm_solve(plan: Plan, y, eps, x, w=None, max_iter=200, cg_iters=10, 
         eps_ptr = eps_np.ctypes.data_as(C.POINTER(C.c_double))
     prm = purify_sdmm_params(max_iter=max_iter, cg_iters=cg_iters, cg_tol=cg_tol, gamma=gamma, nu=nu,
                              rel_obj_tol=rel_obj_tol, eps_tol=eps_tol, check_every=check_every,
-                             resume=int(bool(resume)))
+                             resume=int(bool(resume)), toeplitz=int(bool(toeplitz)))
     st = purify_sdmm_stats()
     status = load().purify_sdmm_solve(plan.handle, _ptr(y), eps_ptr, _ptr(w), _ptr(x), C.byref(prm), C.byref(st))
     if raise_on_error:

@@ -57,6 +57,7 @@ class purify_sdmm_params(C.Structure):
         ("eps_tol", C.c_double),
         ("check_every", C.c_int32),
         ("resume", C.c_int32),
+        ("toeplitz", C.c_int32),
     ]
 
 

@@ -89,6 +89,9 @@ struct SdmmState {
     bool started = false;
     double gamma = 0, nu = 0;
     int cg_iters = 10;
+    bool toeplitz = false;        // CG normal operator by circulant embedding
+    DevBuf toep;                  // [Ky][Kx] real multiplier of the embedded normal operator
+    double toep_nu = 0;
     std::vector<double> eps_host;
     // captured iteration graph
     cudaStream_t gstream = nullptr;
@@ -97,6 +100,7 @@ struct SdmmState {
     int g_cg = -1;
     double g_gamma = 0, g_nu = 0;
     bool g_have_w = false;
+    bool g_toep = false;
     int64_t g_kernels = 0;
     ~SdmmState() {
         if (gexec) cudaGraphExecDestroy(gexec);
@@ -123,6 +127,7 @@ struct purify_plan {
     purify::AxisConst ax, ay;
     purify::KbPoly kbp;
     purify::DevBuf sx, sy;            // per-axis correction (dtype)
+    purify::DevBuf onesx, onesy;      // all-ones tables (transforms without the correction)
     purify::DevBuf twx, twy;          // twiddles (complex dtype)
     purify::DevBuf wmeta;             // int[16]: wavelet db index and plane per basis
     purify::DevBuf us, vs;            // sorted coordinates (dtype)
@@ -156,14 +161,14 @@ void launch_phi_adj(purify_plan* p, const void* y, void* out, bool caller_order,
 void launch_fft2(purify_plan* p, void* grid, bool inverse);
 // Phi stages used by the solver's fused forms
 void launch_scale_pad_rows(purify_plan* p, const void* x, double scale, void* pdir, const void* rvec,
-                           const double* beta_dev, const int* skip_flag);
+                           const double* beta_dev, const int* skip_flag, bool corr = true);
 void launch_cols_fwd(purify_plan* p, const int* skip_flag);
 void launch_degrid(purify_plan* p, void* y, bool caller_order, const int* skip_flag);
 void launch_grid(purify_plan* p, const void* y, bool caller_order, const int* skip_flag);
-void launch_cols_inv(purify_plan* p, const int* skip_flag);
+void launch_cols_inv(purify_plan* p, const int* skip_flag, const void* mult = nullptr);
 void launch_rows_inv_crop(purify_plan* p, void* out, double scale, int out_mode, const void* add,
                           double add_coef, const int* skip_flag, double* dot_part = nullptr,
-                          unsigned* counters = nullptr, double* scal = nullptr);
+                          unsigned* counters = nullptr, double* scal = nullptr, bool corr = true);
 
 // Psi / Psi^dagger
 void launch_psi_adj(purify_plan* p, const void* x, void* c);

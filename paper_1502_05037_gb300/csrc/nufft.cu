@@ -156,7 +156,7 @@ template <typename T>
 __global__ void k_cols_inv(const typename cplx_of<T>::type* __restrict__ grid,
                            typename cplx_of<T>::type* __restrict__ rows,
                            const typename cplx_of<T>::type* __restrict__ tw, int ny, int Kx, int Ky,
-                           int cb, const int* __restrict__ skip) {
+                           int cb, const int* __restrict__ skip, const T* __restrict__ mult) {
     using C = typename cplx_of<T>::type;
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -166,7 +166,10 @@ __global__ void k_cols_inv(const typename cplx_of<T>::type* __restrict__ grid,
     const int tot = cb * Ky;
     for (int t = threadIdx.x; t < tot; t += blockDim.x) {
         int k = t / cb, f = t - k * cb;
-        b0[t] = grid[(size_t)k * Kx + c0 + f];
+        size_t g = (size_t)k * Kx + c0 + f;
+        C v = grid[g];
+        if (mult) v = cscale(v, mult[g]);
+        b0[t] = v;
     }
     __syncthreads();
     C* res = fft_smem<C, true>(b0, b1, Ky, ilog2(Ky), cb, 1, cb, tw);
@@ -582,7 +585,7 @@ template <typename K> static void set_smem(K kernel, size_t bytes) {
 
 template <typename T>
 static void rows_fwd_t(purify_plan* p, const void* x, double scale, void* pdir, const void* rvec,
-                       const double* beta_dev, const int* skip) {
+                       const double* beta_dev, const int* skip, bool corr) {
     using C = typename cplx_of<T>::type;
     int rb = p->fft_rb > 0 ? p->fft_rb : rows_per_block<T>(p->ny, p->Kx);
     while (p->ny % rb) rb >>= 1;
@@ -590,7 +593,8 @@ static void rows_fwd_t(purify_plan* p, const void* x, double scale, void* pdir, 
     set_smem(k_rows_fwd<T>, sm);
     Launch L(p, "fft_rows_fwd");
     k_rows_fwd<T><<<p->ny / rb, fft_threads(rb, p->Kx), sm, p->stream>>>(
-        (const T*)x, p->rows.as<C>(), p->sx.as<T>(), p->sy.as<T>(), p->twx.as<C>(), p->nx, p->ny, p->Kx,
+        (const T*)x, p->rows.as<C>(), corr ? p->sx.as<T>() : p->onesx.as<T>(),
+        corr ? p->sy.as<T>() : p->onesy.as<T>(), p->twx.as<C>(), p->nx, p->ny, p->Kx,
         rb, (T)scale, (T*)pdir, (const T*)rvec, beta_dev, skip);
     L.done();
 }
@@ -606,27 +610,29 @@ template <typename T> static void cols_fwd_t(purify_plan* p, const int* skip) {
     L.done();
 }
 
-template <typename T> static void cols_inv_t(purify_plan* p, const int* skip) {
+template <typename T> static void cols_inv_t(purify_plan* p, const int* skip, const void* mult) {
     using C = typename cplx_of<T>::type;
     int cb = p->fft_cb > 0 ? p->fft_cb : cols_per_block<T>(p->Ky, p->Kx);
     size_t sm = 2 * (size_t)cb * p->Ky * sizeof(C);
     set_smem(k_cols_inv<T>, sm);
     Launch L(p, "fft_cols_inv");
     k_cols_inv<T><<<p->Kx / cb, fft_threads(cb, p->Ky), sm, p->stream>>>(p->grid.as<C>(), p->rows.as<C>(), p->twy.as<C>(),
-                                                      p->ny, p->Kx, p->Ky, cb, skip);
+                                                      p->ny, p->Kx, p->Ky, cb, skip, (const T*)mult);
     L.done();
 }
 
 template <typename T>
 static void rows_inv_t(purify_plan* p, void* out, double scale, int out_mode, const void* add, double add_coef,
-                       const int* skip, double* dot_part, unsigned* counters, double* scal) {
+                       const int* skip, double* dot_part, unsigned* counters, double* scal, bool corr) {
     using C = typename cplx_of<T>::type;
     int rb = p->fft_rb > 0 ? p->fft_rb : rows_per_block<T>(p->ny, p->Kx);
     while (p->ny % rb) rb >>= 1;
     size_t sm = 2 * (size_t)rb * p->Kx * sizeof(C);
     set_smem(k_rows_inv<T>, sm);
     Launch L(p, "fft_rows_inv");
-    k_rows_inv<T><<<p->ny / rb, fft_threads(rb, p->Kx), sm, p->stream>>>(p->rows.as<C>(), out, p->sx.as<T>(), p->sy.as<T>(),
+    k_rows_inv<T><<<p->ny / rb, fft_threads(rb, p->Kx), sm, p->stream>>>(p->rows.as<C>(), out,
+                                                      corr ? p->sx.as<T>() : p->onesx.as<T>(),
+                                                      corr ? p->sy.as<T>() : p->onesy.as<T>(),
                                                       p->twx.as<C>(), p->nx, p->ny, p->Kx, rb, (T)scale,
                                                       out_mode, (const T*)add, (T)add_coef, skip, dot_part,
                                                       counters, scal);
@@ -720,20 +726,22 @@ int max_grid_tile(int dtype, int J) {
 }
 
 void launch_scale_pad_rows(purify_plan* p, const void* x, double scale, void* pdir, const void* rvec,
-                           const double* beta_dev, const int* skip) {
-    if (p->dtype == PURIFY_F32) rows_fwd_t<float>(p, x, scale, pdir, rvec, beta_dev, skip);
-    else rows_fwd_t<double>(p, x, scale, pdir, rvec, beta_dev, skip);
+                           const double* beta_dev, const int* skip, bool corr) {
+    if (p->dtype == PURIFY_F32) rows_fwd_t<float>(p, x, scale, pdir, rvec, beta_dev, skip, corr);
+    else rows_fwd_t<double>(p, x, scale, pdir, rvec, beta_dev, skip, corr);
 }
 void launch_cols_fwd(purify_plan* p, const int* skip) {
     if (p->dtype == PURIFY_F32) cols_fwd_t<float>(p, skip); else cols_fwd_t<double>(p, skip);
 }
-void launch_cols_inv(purify_plan* p, const int* skip) {
-    if (p->dtype == PURIFY_F32) cols_inv_t<float>(p, skip); else cols_inv_t<double>(p, skip);
+void launch_cols_inv(purify_plan* p, const int* skip, const void* mult) {
+    if (p->dtype == PURIFY_F32) cols_inv_t<float>(p, skip, mult); else cols_inv_t<double>(p, skip, mult);
 }
 void launch_rows_inv_crop(purify_plan* p, void* out, double scale, int out_mode, const void* add, double add_coef,
-                          const int* skip, double* dot_part, unsigned* counters, double* scal) {
-    if (p->dtype == PURIFY_F32) rows_inv_t<float>(p, out, scale, out_mode, add, add_coef, skip, dot_part, counters, scal);
-    else rows_inv_t<double>(p, out, scale, out_mode, add, add_coef, skip, dot_part, counters, scal);
+                          const int* skip, double* dot_part, unsigned* counters, double* scal, bool corr) {
+    if (p->dtype == PURIFY_F32)
+        rows_inv_t<float>(p, out, scale, out_mode, add, add_coef, skip, dot_part, counters, scal, corr);
+    else
+        rows_inv_t<double>(p, out, scale, out_mode, add, add_coef, skip, dot_part, counters, scal, corr);
 }
 void launch_degrid(purify_plan* p, void* y, bool caller_order, const int* skip) {
     if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, degrid_f, p, y, caller_order, skip); }

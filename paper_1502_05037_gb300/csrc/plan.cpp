@@ -260,6 +260,8 @@ template <typename T> static void finish_plan(purify_plan* p) {
     // correction tables and twiddles
     upload(p->sx, cast_vec<T>(correction_axis(p->nx, p->Kx, p->J, p->beta)));
     upload(p->sy, cast_vec<T>(correction_axis(p->ny, p->Ky, p->J, p->beta)));
+    upload(p->onesx, std::vector<T>(p->nx, T(1)));
+    upload(p->onesy, std::vector<T>(p->ny, T(1)));
     upload(p->twx, cast_vec<T>(twiddles(p->Kx)));
     upload(p->twy, cast_vec<T>(twiddles(p->Ky)));
     // coordinates to host

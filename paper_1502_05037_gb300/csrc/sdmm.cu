@@ -104,25 +104,27 @@ __global__ void k_proj_norms(const typename cplx_of<T>::type* __restrict__ v2,
 }
 
 // Projection onto each block's ball plus multiplier update; v2 (= Phi x / nu)
-// is replaced by s2 - z2 - v2 for the fused CG residual.
+// is replaced by s2 - z2 - v2 for the fused CG residual (by s2 - z2 when
+// keep_v: the embedded normal operator forms A x separately).
 template <typename T>
 __global__ void k_proj_apply(typename cplx_of<T>::type* __restrict__ v2, typename cplx_of<T>::type* __restrict__ z2,
                              const typename cplx_of<T>::type* __restrict__ ybar, const int* __restrict__ cblk,
                              const int* __restrict__ cbeg, const int* __restrict__ cend,
-                             const double* __restrict__ eps, const double* __restrict__ scal, int R) {
+                             const double* __restrict__ eps, const double* __restrict__ scal, int R, int keep_v) {
     using C = typename cplx_of<T>::type;
     const int ch = blockIdx.x;
     const int r = cblk[ch];
     const double nr = sqrt(scal[S_BLOCKS + r]);
     const double e = eps[r];
     const T f = nr > e ? (T)(e / nr) : T(1);
+    const T vk = keep_v ? T(0) : T(1);
     for (int m = cbeg[ch] + threadIdx.x; m < cend[ch]; m += blockDim.x) {
         C v = v2[m], z = z2[m], y = ybar[m];
         T rx = v.x + z.x - y.x, ry = v.y + z.y - y.y;
         T sx = y.x + rx * f, sy = y.y + ry * f;
         T zx = z.x + v.x - sx, zy = z.y + v.y - sy;
         z2[m] = cmake<C>(zx, zy);
-        v2[m] = cmake<C>(sx - zx - v.x, sy - zy - v.y);
+        v2[m] = cmake<C>(sx - zx - vk * v.x, sy - zy - vk * v.y);
     }
 }
 
@@ -288,6 +290,35 @@ __global__ void k_check_finite(const T* __restrict__ v, int64_t n, int* flags) {
         if (!isfinite((double)v[i])) flags[F_NAN] = 1;
 }
 
+// Circulant embedding of the point-spread function: psf is the complex
+// [2ny][2nx] image A^H 1 (pixel (i, j) at lag d = (j - nx, i - ny)); the
+// kernel on the [Ky][Kx] = [2ny][2nx] periodic grid holds psf(d) at d mod K.
+template <typename T>
+__global__ void k_circulant(const typename cplx_of<T>::type* __restrict__ psf, typename cplx_of<T>::type* __restrict__ c,
+                            int nx, int ny) {
+    const int Kx = 2 * nx, Ky = 2 * ny;
+    const int64_t n = (int64_t)Kx * Ky;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        int i = (int)(t / Kx), j = (int)(t % Kx);          // psf pixel
+        int d1 = j - nx, d2 = i - ny;                       // lag
+        int k1 = d1 & (Kx - 1), k2 = d2 & (Ky - 1);
+        c[(size_t)k2 * Kx + k1] = psf[t];
+    }
+}
+
+// multiplier = Re(c_hat) * s (the transform of a Hermitian kernel is real)
+template <typename T>
+__global__ void k_real_scale(const typename cplx_of<T>::type* __restrict__ c, T* __restrict__ m, int64_t n, double s) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        m[t] = (T)((double)c[t].x * s);
+}
+
+template <typename T>
+__global__ void k_fill_one(typename cplx_of<T>::type* __restrict__ y, int64_t n) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        y[t] = cmake<typename cplx_of<T>::type>(T(1), T(0));
+}
+
 // -------------------------------------------------------------- host side
 static int ew_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
 
@@ -387,6 +418,51 @@ template <typename T> struct Solver {
         return std::sqrt(read_scal(S_NORM2));
     }
 
+    // Normal operator of the exact model by circulant embedding (Toeplitz):
+    // A^H A x = psf * x with psf(d) = sum_m exp(i w_m . d) over lags |d| < n,
+    // embedded in the plan's 2n x 2n grid; psf comes from the adjoint NUFFT of
+    // a vector of ones on a 2n x 2n image. Multiplier = c_hat / (K^2 nu^2).
+    void setup_toeplitz() {
+        if (s.toep.p && s.toep_nu == s.nu) return;
+        PURIFY_REQUIRE(p->Kx == 2 * p->nx && p->Ky == 2 * p->ny, "toeplitz needs oversample 2");
+        purify_plan_desc d2 = p->desc;
+        d2.nx = 2 * p->nx;
+        d2.ny = 2 * p->ny;
+        d2.M = p->M;
+        d2.u = p->us.p;
+        d2.v = p->vs.p;
+        d2.R = 1;
+        d2.block_offsets = nullptr;
+        d2.levels = 1;
+        d2.basis_mask = 1;
+        d2.tile = p->work.tile;
+        d2.stream = p->stream;
+        purify_plan* q = create_plan(&d2);
+        try {
+            k_fill_one<T><<<ew_blocks(q->M), 256, 0, p->stream>>>(q->tmp_vis.template as<C>(), q->M);
+            PURIFY_CUDA(cudaGetLastError());
+            add_launches(1);
+            launch_phi_adj(q, q->tmp_vis.p, q->tmp_img.p, false, 1.0, 0, nullptr);
+            k_circulant<T><<<ew_blocks(4 * p->N), 256, 0, p->stream>>>(q->tmp_img.template as<C>(), p->grid.as<C>(),
+                                                                       p->nx, p->ny);
+            PURIFY_CUDA(cudaGetLastError());
+            add_launches(1);
+            PURIFY_CUDA(cudaStreamSynchronize(p->stream));
+        } catch (...) {
+            delete q;
+            throw;
+        }
+        delete q;
+        launch_fft2(p, p->grid.p, false);
+        const int64_t nk = (int64_t)p->Kx * p->Ky;
+        if (!s.toep.p) s.toep.alloc(sizeof(T) * nk);
+        k_real_scale<T><<<ew_blocks(nk), 256, 0, p->stream>>>(p->grid.as<C>(), s.toep.template as<T>(), nk,
+                                                             1.0 / ((double)nk * s.nu * s.nu));
+        PURIFY_CUDA(cudaGetLastError());
+        add_launches(1);
+        s.toep_nu = s.nu;
+    }
+
     // objective and per-block residual of x, written to scal
     void evaluate(const T* x) {
         launch_psi_adj(p, x, s.c1.p);
@@ -433,7 +509,8 @@ template <typename T> struct Solver {
             k_proj_apply<T><<<p->nchunks, RB, 0, p->stream>>>(s.v2.template as<C>(), s.z2.template as<C>(),
                                                              s.ybar.template as<C>(), p->chunk_blk.as<int>(),
                                                              p->chunk_beg.as<int>(), p->chunk_end.as<int>(),
-                                                             s.eps.template as<double>(), scal(), p->R);
+                                                             s.eps.template as<double>(), scal(), p->R,
+                                                             s.toeplitz ? 1 : 0);
             L.done();
         }
         // f3 and the image-space terms of the residual
@@ -446,6 +523,13 @@ template <typename T> struct Solver {
         }
         // r = b - A x
         launch_phi_adj(p, s.v2.p, s.r.p, false, inv_nu, 1, s.addend.p);
+        if (s.toeplitz) {
+            // r -= (normal operator by circulant embedding) x
+            launch_scale_pad_rows(p, x, 1.0, nullptr, nullptr, nullptr, nullptr, false);
+            launch_cols_fwd(p, nullptr);
+            launch_cols_inv(p, nullptr, s.toep.p);
+            launch_rows_inv_crop(p, s.r.p, -1.0, 1, s.r.p, 1.0, nullptr, nullptr, nullptr, nullptr, false);
+        }
         {
             Launch L(p, "cg_init");
             k_cg_init<T><<<red_blocks(p->N), RB, 0, p->stream>>>(s.r.template as<T>(), s.p.template as<T>(), p->N,
@@ -454,6 +538,13 @@ template <typename T> struct Solver {
         }
         const int* skip = flags() + F_CGDONE;
         for (int k = 0; k < cg_iters; ++k) {
+            if (s.toeplitz) {
+                // p = r + beta p, then A p = 2 p + (embedded normal operator) p
+                launch_scale_pad_rows(p, nullptr, 1.0, s.p.p, s.r.p, scal() + S_BETA, skip, false);
+                launch_cols_fwd(p, skip);
+                launch_cols_inv(p, skip, s.toep.p);
+                launch_rows_inv_crop(p, s.Ap.p, 1.0, 1, s.p.p, 2.0, skip, part(), ctr(), scal(), false);
+            } else {
             // p = r + beta p fused into the first FFT pass, then A p
             launch_scale_pad_rows(p, nullptr, inv_nu, s.p.p, s.r.p, scal() + S_BETA, skip);
             launch_cols_fwd(p, skip);
@@ -462,6 +553,7 @@ template <typename T> struct Solver {
             launch_cols_inv(p, skip);
             // A p = 2 p + Re Phi^H Phi p / nu^2, with p . A p and alpha fused in
             launch_rows_inv_crop(p, s.Ap.p, inv_nu, 1, s.p.p, 2.0, skip, part(), ctr(), scal());
+            }
             {
                 Launch L(p, "cg_update");
                 k_cg_update<T><<<red_blocks(p->N), RB, 0, p->stream>>>(x, s.r.template as<T>(), s.p.template as<T>(),
@@ -499,7 +591,8 @@ template <typename T> static void run_iterations(purify_plan* p, int n) {
     PURIFY_CUDA(cudaEventRecord(s.ev_in, user));
     PURIFY_CUDA(cudaStreamWaitEvent(s.gstream, s.ev_in, 0));
     int start = 0;
-    if (!s.gexec || s.g_cg != s.cg_iters || s.g_gamma != s.gamma || s.g_nu != s.nu || s.g_have_w != s.have_w) {
+    if (!s.gexec || s.g_cg != s.cg_iters || s.g_gamma != s.gamma || s.g_nu != s.nu || s.g_have_w != s.have_w ||
+        s.g_toep != s.toeplitz) {
         if (s.gexec) { cudaGraphExecDestroy(s.gexec); s.gexec = nullptr; }
         p->stream = s.gstream;
         try {
@@ -534,6 +627,7 @@ template <typename T> static void run_iterations(purify_plan* p, int n) {
             s.g_gamma = s.gamma;
             s.g_nu = s.nu;
             s.g_have_w = s.have_w;
+            s.g_toep = s.toeplitz;
             // the captured launches were counted once while capturing
             add_launches(-kn);
         } catch (...) {
@@ -582,6 +676,7 @@ void batch_iterate(BatchState* b, int iters) {
         key.push_back(p->sd.nu);
         key.push_back(p->sd.have_w ? 1.0 : 0.0);
         key.push_back((double)p->sd.cg_iters);
+        key.push_back(p->sd.toeplitz ? 1.0 : 0.0);
     }
     bool timed = false;
     for (auto* p : b->plans) timed = timed || timing_enabled(p);
@@ -717,6 +812,8 @@ static void sdmm_solve_t(purify_plan* p, const void* y, const double* eps, const
             S.reduce(s.c1.template as<T>(), p->D, 1, S_GMAX);
             s.gamma = 1e-3 * S.read_scal(S_GMAX);
         }
+        s.toeplitz = prm.toeplitz != 0;
+        if (s.toeplitz) S.setup_toeplitz();
         PURIFY_CUDA(cudaMemcpyAsync(s.x.p, x_io, sizeof(T) * p->N, cudaMemcpyDefault, p->stream));
         PURIFY_CUDA(cudaMemsetAsync(s.z1.p, 0, s.z1.bytes, p->stream));
         PURIFY_CUDA(cudaMemsetAsync(s.z2.p, 0, s.z2.bytes, p->stream));

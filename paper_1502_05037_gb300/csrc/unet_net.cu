@@ -108,63 +108,79 @@ __global__ void k_upsample_bwd(const float* __restrict__ ghi, float* __restrict_
     }
 }
 
-// Weight and bias gradients of a k x k convolution on the CUDA cores:
-//   dW[co][tap][ci] += sum_p gz[p][co] * x[p + tap][ci],  db[co] += sum_p gz[p][co]
-// Block: 32 output x 32 input channels of one tap over a chunk of pixels.
+// Weight gradients of a k x k convolution on the CUDA cores, one tap per
+// block row of the grid:
+//   dW[co][tap][ci] += sum_p gz[p][co] * x[p + tap][ci]
+// a register-tiled GEMM (64 x 64 output tile, 4 x 4 per thread, K = 16
+// pixels per shared-memory stage) over a chunk of pixels, added to dW with
+// one atomic per output and block.
 __global__ void __launch_bounds__(256) k_dw(const bf16* __restrict__ gz, int Cout, const bf16* __restrict__ x, int xcs,
                                             int xco, int Cin, int B, int H, int W, int up, int k, int pch,
-                                            float* __restrict__ dW, float* __restrict__ db) {
-    constexpr int PT = 64;
-    __shared__ float gs[PT][33];
-    __shared__ __align__(16) float xs[PT][36];
-    const int co0 = blockIdx.x * 32, ci0 = blockIdx.y * 32;
+                                            float* __restrict__ dW) {
+    constexpr int BK = 16;
+    __shared__ __align__(16) float gs[BK][64];
+    __shared__ __align__(16) float xs[BK][64];
+    const int co0 = blockIdx.x * 64, ci0 = blockIdx.y * 64;
     const int tap = blockIdx.z % (k * k), chunk = blockIdx.z / (k * k);
     const int dy = tap / k - k / 2, dx = tap % k - k / 2;
-    const int tid = threadIdx.x;
-    const int col = tid / 8, ci4 = (tid % 8) * 4;
+    const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
     const int64_t P = (int64_t)B * H * W;
     const int64_t p0 = (int64_t)chunk * pch, p1 = min(P, p0 + pch);
     const int sh = up ? 1 : 0;
     const int Hs = H >> sh, Ws = W >> sh;
-    float acc[4] = {0, 0, 0, 0};
-    float bacc = 0.f;
-    const bool do_bias = (blockIdx.y == 0 && tap == 0);
-    for (int64_t pb = p0; pb < p1; pb += PT) {
-        for (int t = tid; t < PT * 32; t += 256) {
-            int pp = t / 32, c = t % 32;
-            int64_t p = pb + pp;
-            float gv = 0.f, xv = 0.f;
-            if (p < p1) {
-                if (co0 + c < Cout) gv = __bfloat162float(gz[p * Cout + co0 + c]);
-                int b = (int)(p / (H * W));
-                int rem = (int)(p - (int64_t)b * H * W);
-                int yy = rem / W + dy, xx = rem % W + dx;
-                if (ci0 + c < Cin && yy >= 0 && yy < H && xx >= 0 && xx < W)
-                    xv = __bfloat162float(x[((size_t)(b * Hs + (yy >> sh)) * Ws + (xx >> sh)) * xcs + xco + ci0 + c]);
+    float acc[4][4] = {};
+    const int lk = tid / 16, lj = (tid % 16) * 4;   // this thread's loads: row lk, columns lj..lj+3
+    for (int64_t pb = p0; pb < p1; pb += BK) {
+        const int64_t p = pb + lk;
+        float gv[4] = {0, 0, 0, 0}, xv[4] = {0, 0, 0, 0};
+        if (p < p1) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (co0 + lj + e < Cout) gv[e] = __bfloat162float(gz[p * Cout + co0 + lj + e]);
+            const int b = (int)(p / (H * W));
+            const int rem = (int)(p - (int64_t)b * H * W);
+            const int yy = rem / W + dy, xx = rem % W + dx;
+            if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+                const bf16* src = x + ((size_t)(b * Hs + (yy >> sh)) * Ws + (xx >> sh)) * xcs + xco + ci0 + lj;
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    if (ci0 + lj + e < Cin) xv[e] = __bfloat162float(src[e]);
             }
-            gs[pp][c] = gv;
-            xs[pp][c] = xv;
         }
+        *reinterpret_cast<float4*>(&gs[lk][lj]) = make_float4(gv[0], gv[1], gv[2], gv[3]);
+        *reinterpret_cast<float4*>(&xs[lk][lj]) = make_float4(xv[0], xv[1], xv[2], xv[3]);
         __syncthreads();
-#pragma unroll 8
-        for (int pp = 0; pp < PT; ++pp) {
-            float g = gs[pp][col];
-            float4 xv = *reinterpret_cast<const float4*>(&xs[pp][ci4]);
-            acc[0] += g * xv.x;
-            acc[1] += g * xv.y;
-            acc[2] += g * xv.z;
-            acc[3] += g * xv.w;
-            if (do_bias && ci4 == 0) bacc += g;
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float4 a = *reinterpret_cast<const float4*>(&gs[kk][ty * 4]);
+            float4 c = *reinterpret_cast<const float4*>(&xs[kk][tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w}, cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * cv[j];
         }
         __syncthreads();
     }
-    const int co = co0 + col;
-    if (co < Cout) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int co = co0 + ty * 4 + i;
+        if (co >= Cout) continue;
+#pragma unroll
         for (int j = 0; j < 4; ++j) {
-            int ci = ci0 + ci4 + j;
-            if (ci < Cin) atomicAdd(&dW[((size_t)co * k * k + tap) * Cin + ci], acc[j]);
+            const int ci = ci0 + tx * 4 + j;
+            if (ci < Cin) atomicAdd(&dW[((size_t)co * k * k + tap) * Cin + ci], acc[i][j]);
         }
-        if (do_bias && ci4 == 0) atomicAdd(&db[co], bacc);
+    }
+}
+
+// db[co] += sum over a chunk of pixels of gz[p][co]
+__global__ void k_db(const bf16* __restrict__ gz, int Cout, int64_t P, int pch, float* __restrict__ db) {
+    const int64_t p0 = (int64_t)blockIdx.x * pch, p1 = min(P, p0 + pch);
+    for (int co = threadIdx.x; co < Cout; co += blockDim.x) {
+        float s = 0.f;
+        for (int64_t p = p0; p < p1; ++p) s += __bfloat162float(gz[p * Cout + co]);
+        atomicAdd(&db[co], s);
     }
 }
 
@@ -454,13 +470,18 @@ static void bwd_dx(Unet& u, UnetLayer& l, int B, int lev, const bf16* gz, float*
 static void bwd_dw(Unet& u, UnetLayer& l, int B, int lev, const bf16* gz, const bf16* x, int xcs, int xco, int up) {
     const int H = u.H >> lev, W = u.W >> lev;
     const int64_t P = (int64_t)B * H * W;
-    const int pch = 2048;
+    // pixel chunk per block: about 8 blocks per SM over all taps and tiles
+    const int tiles = ((l.cout + 63) / 64) * ((l.cin + 63) / 64) * l.k * l.k;
+    int64_t want = std::max<int64_t>(1, (152 * 8) / tiles);
+    int pch = (int)std::max<int64_t>(256, (P + want - 1) / want);
+    pch = (pch + 15) / 16 * 16;
     const int nchunk = (int)((P + pch - 1) / pch);
-    dim3 g((l.cout + 31) / 32, (l.cin + 31) / 32, l.k * l.k * nchunk);
-    k_dw<<<g, 256, 0, u.st>>>(gz, l.cout, x, xcs, xco, l.cin, B, H, W, up, l.k, pch, u.grads.as<float>() + l.woff,
-                              u.grads.as<float>() + l.boff);
+    dim3 g((l.cout + 63) / 64, (l.cin + 63) / 64, l.k * l.k * nchunk);
+    k_dw<<<g, 256, 0, u.st>>>(gz, l.cout, x, xcs, xco, l.cin, B, H, W, up, l.k, pch, u.grads.as<float>() + l.woff);
+    const int dch = 1024;
+    k_db<<<(int)((P + dch - 1) / dch), 64, 0, u.st>>>(gz, l.cout, P, dch, u.grads.as<float>() + l.boff);
     PURIFY_CUDA(cudaGetLastError());
-    add_launches(1);
+    add_launches(2);
 }
 
 static void relu_grad(Unet& u, const float* g, int gs, int go, const bf16* act, int as, int ao, int64_t P, int C) {

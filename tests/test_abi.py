@@ -58,7 +58,7 @@ int main(void) {
   printf("stats %zu\n", sizeof(purify_sdmm_stats));
   printf("ktime %zu\n", sizeof(purify_kernel_time));
   P(purify_plan_desc, tile) P(purify_plan_desc, stream) P(purify_plan_desc, dtype) P(purify_plan_desc, block_offsets)
-  P(purify_sdmm_params, resume) P(purify_sdmm_params, check_every) P(purify_sdmm_stats, status)
+  P(purify_sdmm_params, resume) P(purify_sdmm_params, check_every) P(purify_sdmm_params, toeplitz) P(purify_sdmm_stats, status)
   P(purify_plan_info, workspace_bytes) P(purify_plan_info, beta)
   return 0;
 }
@@ -81,6 +81,7 @@ int main(void) {
     assert int(got["purify_plan_desc.block_offsets"]) == _lib.purify_plan_desc.block_offsets.offset
     assert int(got["purify_sdmm_params.resume"]) == _lib.purify_sdmm_params.resume.offset
     assert int(got["purify_sdmm_params.check_every"]) == _lib.purify_sdmm_params.check_every.offset
+    assert int(got["purify_sdmm_params.toeplitz"]) == _lib.purify_sdmm_params.toeplitz.offset
     assert int(got["purify_sdmm_stats.status"]) == _lib.purify_sdmm_stats.status.offset
     assert int(got["purify_plan_info.workspace_bytes"]) == _lib.purify_plan_info.workspace_bytes.offset
     assert int(got["purify_plan_info.beta"]) == _lib.purify_plan_info.beta.offset

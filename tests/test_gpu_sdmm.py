@@ -149,3 +149,19 @@ def test_full_size_iteration_against_sampled_properties():
     ratios = [np.linalg.norm(r[offs[i]:offs[i + 1]]) / eps[i] for i in range(len(eps))]
     assert abs(max(ratios) - st.max_resid_over_eps) <= 1e-4 * max(ratios)
     assert snr_db(x_true, xr) > 3.0
+
+
+def test_toeplitz_trajectory_against_exact_normal_operator():
+    # the CG normal operator by circulant embedding equals the exact model's
+    # A^H A up to the NUFFT error of its point-spread function
+    dtype = pk.PURIFY_F32
+    plan, prob, x_true = problem(32, 3000, 6, 2, 3, dtype, seed=7)
+    prob.normal = "exact"
+    iters, cg = 12, 8
+    ref = osd.sdmm_solve(prob, np.zeros((32, 32)), iters, cg)
+    x, st = gpu_solve(plan, prob, dtype, iters, cg, toeplitz=True)
+    assert rel(x.cpu().numpy(), ref.x) <= 1e-3
+    # and stays close to the NUFFT-operator trajectory
+    prob.normal = "nufft"
+    ref2 = osd.sdmm_solve(prob, np.zeros((32, 32)), iters, cg)
+    assert rel(x.cpu().numpy(), ref2.x) <= 1e-2
