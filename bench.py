@@ -143,6 +143,33 @@ def algorithmic_bytes(name: str, info, dtype_bytes: int = 4) -> float | None:
     return float(table[name]) if name in table else None
 
 
+def algorithmic_flops(name: str, info) -> float | None:
+    """FP32 operations a launch must perform (kernel weights evaluated from
+    J per-tap polynomials of degree J + 5 per axis, J*J taps of a real weight
+    times a complex value; FFT passes 5 n log2 n per length-n transform)."""
+    import math
+    J, M = info.J, info.M
+    deg = min(14, J + 5)
+    weights = 2 * J * (deg + 1) * 2          # Horner: one FMA (2 flops) per coefficient
+    taps = J * J * (1 + 4)                    # weight product + complex multiply-accumulate
+    ny = int(round(np.sqrt(info.N * info.Ky / info.Kx)))
+    table = {
+        "grid": M * (weights + taps),
+        "degrid": M * (weights + taps),
+        "fft_rows_fwd": ny * 5 * info.Kx * math.log2(info.Kx),
+        "fft_rows_inv": ny * 5 * info.Kx * math.log2(info.Kx),
+        "fft_cols_fwd": info.Kx * 5 * info.Ky * math.log2(info.Ky),
+        "fft_cols_inv": info.Kx * 5 * info.Ky * math.log2(info.Ky),
+    }
+    return float(table[name]) if name in table else None
+
+
+def fp32_peak_tflops(sm_mhz: float | None) -> float:
+    """Non-tensor FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2
+    flops (FMA) x clock (the sampled maximum SM clock, else 2070 MHz)."""
+    return 152 * 128 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
+
+
 def source_sha1(relpath: str) -> str:
     return hashlib.sha1(open(os.path.join(ROOT, relpath), "rb").read()).hexdigest()
 
@@ -175,18 +202,21 @@ def setup_problem(wl_name: str, replica: int, dev):
     import paper_1502_05037_gb300 as pk
     from paper_1502_05037_gb300 import problem, synth
 
-    wl = synth.WORKLOADS[wl_name]
+    wl = synth.WORKLOADS[wl_name] if isinstance(wl_name, str) else wl_name
     if replica:
         wl = synth.Workload(**{**wl.__dict__, "index": wl.index + 1000 * replica})
     x_true, u, v, offs, nz = wl.draw()
+    f64 = wl.dtype == "f64"
+    rt, ct = (torch.float64, torch.complex128) if f64 else (torch.float32, torch.complex64)
     plan = pk.Plan(wl.nx, wl.ny, torch.from_numpy(u).to(dev), torch.from_numpy(v).to(dev), kb_width=wl.J,
-                   levels=wl.levels, block_offsets=offs, stream=torch.cuda.current_stream(dev))
-    xt = torch.from_numpy(x_true.astype(np.float32)).to(dev)
-    y0 = torch.empty(wl.M, dtype=torch.complex64, device=dev)
+                   levels=wl.levels, block_offsets=offs, stream=torch.cuda.current_stream(dev),
+                   dtype=pk.PURIFY_F64 if f64 else pk.PURIFY_F32)
+    xt = torch.from_numpy(x_true).to(rt).to(dev)
+    y0 = torch.empty(wl.M, dtype=ct, device=dev)
     pk.purify_phi(plan, xt, y0)
     sigma = problem.noise_sigma_from_norm(float(torch.linalg.vector_norm(y0.to(torch.complex128)).item()), wl.M,
                                           wl.snr_db)
-    y = y0 + torch.from_numpy((sigma * nz).astype(np.complex64)).to(dev)
+    y = y0 + torch.from_numpy(sigma * nz).to(ct).to(dev)
     eps = problem.chi2_epsilon(sigma, np.diff(offs))
     return wl, plan, y, eps, x_true
 
@@ -213,7 +243,9 @@ def run_ours(args):
 
     wl, plan, y, eps, x_true = setup_problem(args.workload, rank, dev)
     stream = torch.cuda.current_stream(dev)
-    x = torch.zeros((wl.ny, wl.nx), dtype=torch.float32, device=dev)
+    rdt = torch.float64 if wl.dtype == "f64" else torch.float32
+    cdt = torch.complex128 if wl.dtype == "f64" else torch.complex64
+    x = torch.zeros((wl.ny, wl.nx), dtype=rdt, device=dev)
     # initialise the solver state: nu by power iteration, default gamma
     st0 = pk.purify_sdmm_solve(plan, y, eps, x, max_iter=0, cg_iters=args.cg_iters)
     nu, gamma = st0.nu, st0.gamma
@@ -265,23 +297,36 @@ def run_ours(args):
     if dom:
         name, (nl, tms) = dom
         per = tms / nl
-        ab = algorithmic_bytes(name, plan.info)
-        achieved = ab / (per * 1e-3) / 1e9 if ab else None
+        ab = algorithmic_bytes(name, plan.info, 8 if wl.dtype == "f64" else 4)
+        af = algorithmic_flops(name, plan.info)
         tr = ncu_traffic(name)
-        roofline = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "peak_source": peak_src,
-                    "unit": "GB/s", "frac": (achieved / peak if achieved else None), "traffic": tr,
-                    "algorithmic_bytes_per_launch": ab, "mean_launch_us": per * 1e3,
-                    "launches_per_step": nl / args.steps,
-                    "share_of_kernel_time": tms / sum(t for _, t in ktimes.values())}
+        alu_peak = fp32_peak_tflops(clocks.get("sm_max_mhz"))
+        # the binding resource by arithmetic intensity against the ridge point
+        ai = (af / ab) if (af and ab) else 0.0
+        ridge = alu_peak * 1e12 / (peak * 1e9)
+        common = {"kernel": name, "traffic": tr, "algorithmic_bytes_per_launch": ab,
+                  "algorithmic_flops_per_launch": af, "mean_launch_us": per * 1e3,
+                  "launches_per_step": nl / args.steps, "arithmetic_intensity": ai, "ridge_flop_per_byte": ridge,
+                  "share_of_kernel_time": tms / sum(t for _, t in ktimes.values()),
+                  "hbm_gbs": ab / (per * 1e-3) / 1e9 if ab else None, "hbm_peak": peak, "hbm_peak_source": peak_src}
+        if af and ai > ridge:
+            achieved = af / (per * 1e-3) / 1e12
+            roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                        "frac": achieved / alu_peak, "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x clock",
+                        **common}
+        else:
+            achieved = ab / (per * 1e-3) / 1e9 if ab else None
+            roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": (achieved / peak if achieved else None), "peak_source": peak_src, **common}
     kernel_table = {k: {"launches_per_step": n / args.steps, "ms_per_step": t / args.steps,
-                        "gbs": (algorithmic_bytes(k, plan.info) / (t / n * 1e-3) / 1e9
+                        "gbs": (algorithmic_bytes(k, plan.info, 8 if wl.dtype == "f64" else 4) / (t / n * 1e-3) / 1e9
                                 if algorithmic_bytes(k, plan.info) else None)}
                     for k, (n, t) in sorted(ktimes.items(), key=lambda kv: -kv[1][1])}
 
     # ---- pass C: end to end through the public API with pinned host buffers
-    y_host = torch.empty(wl.M, dtype=torch.complex64, pin_memory=True)
+    y_host = torch.empty(wl.M, dtype=cdt, pin_memory=True)
     y_host.copy_(y.cpu())
-    x_host = torch.zeros((wl.ny, wl.nx), dtype=torch.float32, pin_memory=True)
+    x_host = torch.zeros((wl.ny, wl.nx), dtype=rdt, pin_memory=True)
     e2e_times = []
     for k in range(args.warmup + args.steps):
         x_host.zero_()
@@ -297,14 +342,15 @@ def run_ours(args):
         t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_total = float(t.item())
+    rb = 8 if wl.dtype == "f64" else 4
     e2e = {"value": world * args.steps / e2e_total, "unit": "iters/s",
-           "h2d_bytes_per_step": wl.M * 8 + wl.nx * wl.ny * 4, "d2h_bytes_per_step": wl.nx * wl.ny * 4,
+           "h2d_bytes_per_step": wl.M * 2 * rb + wl.nx * wl.ny * rb, "d2h_bytes_per_step": wl.nx * wl.ny * rb,
            "call": "purify_sdmm_solve(host y, host x, max_iter=1)"}
 
     # ---- pass A': the same timed steps with the circulant-embedded CG normal operator
     toep = None
     if args.toeplitz_pass:
-        xt0 = torch.zeros((wl.ny, wl.nx), dtype=torch.float32, device=dev)
+        xt0 = torch.zeros((wl.ny, wl.nx), dtype=rdt, device=dev)
         pk.purify_sdmm_solve(plan, y, eps, xt0, max_iter=0, cg_iters=args.cg_iters, gamma=gamma, nu=nu, toeplitz=True)
         for i in range(args.warmup):
             flush.fill_(i & 0xFF)
@@ -322,9 +368,9 @@ def run_ours(args):
                 "note": "CG normal operator by circulant embedding of the exact model (separate parity class)"}
 
     # ---- pass D: Phi + Phi^dagger Gvis/s (caller order, device buffers)
-    xin = torch.from_numpy(x_true.astype(np.float32)).to(dev)
-    yv = torch.empty(wl.M, dtype=torch.complex64, device=dev)
-    xa = torch.empty((wl.ny, wl.nx), dtype=torch.complex64, device=dev)
+    xin = torch.from_numpy(x_true).to(rdt).to(dev)
+    yv = torch.empty(wl.M, dtype=cdt, device=dev)
+    xa = torch.empty((wl.ny, wl.nx), dtype=cdt, device=dev)
     for _ in range(3):
         pk.purify_phi(plan, xin, yv)
         pk.purify_phi_adj(plan, yv, xa)
@@ -351,7 +397,7 @@ def run_ours(args):
         line = {
             "metric": "SDMM iters/s", "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": wl.dtype, "data": "synthetic",
             "config": {"workload": f"{wl.name}: {wl.nx}x{wl.ny} sky, M={wl.M}, J={wl.J}, alpha=2, q=9, "
                                    f"L={wl.levels}, R={wl.R}, {wl.snr_db:g} dB",
                        "cg_iters": args.cg_iters, "parallelism": f"replicas x{world}",
@@ -487,6 +533,72 @@ def run_profile_op(args):
                       "wall_s": time.perf_counter() - t0, "launches": pk.purify_launch_count()}))
 
 
+def run_channels(args):
+    """Batched channels: 32 independent 512 x 512 problems (M ~ U(0.5N, 5N),
+    R ~ U{4..16}) advanced together by one captured graph per iteration."""
+    import torch
+
+    import paper_1502_05037_gb300 as pk
+    from paper_1502_05037_gb300 import build as pbuild
+    from paper_1502_05037_gb300 import synth
+    pbuild.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    chans = []
+    for ch in range(args.channels):
+        wl = synth.channel_workload(ch)
+        _, plan, y, eps, _ = setup_problem(wl, 0, dev)
+        x = torch.zeros((wl.ny, wl.nx), dtype=torch.float32, device=dev)
+        pk.purify_sdmm_solve(plan, y, eps, x, max_iter=0, cg_iters=args.cg_iters)
+        chans.append((wl, plan, y, eps))
+    torch.cuda.synchronize(dev)
+    stream = torch.cuda.Stream(dev)
+    batch = pk.Batch([c[1] for c in chans], stream)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for i in range(args.warmup):
+        pk.purify_batch_iterate(batch, 1)
+    stream.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = pk.purify_launch_count()
+    with ClockSampler(0) as clk:
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            torch.cuda.synchronize(dev)
+            evs[k][0].record(stream)
+            pk.purify_batch_iterate(batch, 1)
+            evs[k][1].record(stream)
+        stream.synchronize()
+    launches = pk.purify_launch_count() - launches0
+    tms = sum(a.elapsed_time(b) for a, b in evs)
+    # the same iterations one channel after another (each plan's own graph)
+    for c in chans:
+        pk.purify_sdmm_iterate(c[1], 1)
+    torch.cuda.synchronize(dev)
+    seq = []
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for c in chans:
+            pk.purify_sdmm_iterate(c[1], 1)
+        b.record()
+        seq.append((a, b))
+    torch.cuda.synchronize(dev)
+    tseq = sum(a.elapsed_time(b) for a, b in seq)
+    M_tot = sum(c[0].M for c in chans)
+    line = {
+        "metric": "SDMM iters/s (channel-iterations, batched)", "value": len(chans) * args.steps / (tms / 1e3),
+        "unit": "channel-iters/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": tms / args.steps, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{len(chans)} channels of 512x512, M in [0.5N, 5N] (total {M_tot}), J=6, q=9, L=4, "
+                               f"R in 4..16, 30 dB", "cg_iters": args.cg_iters},
+        "sequential_ms_per_step": tseq / args.steps, "batched_speedup": tseq / tms,
+        "gpu_launches": int(launches), "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_warmstart(args):
     """Time-to-tolerance of SDMM from the learned warm start versus from zero
     on held-out problems (all GPU work through the C ABI)."""
@@ -578,6 +690,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-toeplitz-pass", dest="toeplitz_pass", action="store_false",
                     help="skip the extra timed pass with the circulant-embedded CG normal operator")
+    ap.add_argument("--channels32", action="store_true",
+                    help="batched independent 512x512 channel problems (one graph per iteration)")
+    ap.add_argument("--channels", type=int, default=32)
     ap.add_argument("--warmstart", action="store_true",
                     help="time-to-tolerance of the learned warm start versus zero start (trains the U-Net)")
     ap.add_argument("--train-samples", type=int, default=2000)
@@ -592,7 +707,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.warmstart:
+    if args.channels32:
+        run_channels(args)
+    elif args.warmstart:
         run_warmstart(args)
     elif args.profile_op:
         run_profile_op(args)

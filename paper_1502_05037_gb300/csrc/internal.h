@@ -135,7 +135,8 @@ struct purify_plan {
     purify::DevBuf d_offsets;         // int64 [R + 1]
     purify::DevBuf chunk_blk, chunk_beg, chunk_end;  // visibility chunks, each inside one block
     int nchunks = 0;
-    purify::GridWork work;
+    purify::GridWork work;            // gridding work list (tile of the G^H kernel)
+    purify::GridWork dwork;           // degridding work list (tile of the G kernel)
     int fft_rb = 0, fft_cb = 0;       // FFT rows / columns per block (0: heuristic)
     // workspaces
     purify::DevBuf grid;              // Ky * Kx complex
@@ -218,7 +219,7 @@ double coef_std(purify_plan* p, const void* x);
 int max_grid_tile(int dtype, int J);
 
 // plan-side helpers
-void build_gridwork(purify_plan* p, const std::vector<int>& bin_sorted, int tile);
+void build_gridwork(purify_plan* p, const std::vector<int>& bin_sorted, int tile, GridWork& w);
 purify_plan* create_plan(const purify_plan_desc* d);
 bool is_host_pointer(const void* ptr);
 

@@ -321,9 +321,9 @@ __device__ __forceinline__ int flat_vis(const int* pst, const int* pcum, int np,
 // non-zero cells of the tile are added to the grid.
 template <int J> struct GridStage {
     // floats per staged visibility: wx[J], wy[J], re, im, cell offset (-1:
-    // not in this tile), lx, ly; odd so that the 32 lanes of a warp store
-    // their records on distinct banks
-    static constexpr int F = 2 * J + 5;
+    // not in this tile); odd so that the 32 lanes of a warp store their
+    // records on distinct banks
+    static constexpr int F = 2 * J + 3;
 };
 
 template <typename T, int J, int WARPS>
@@ -385,8 +385,6 @@ k_grid_wp(const typename cplx_of<T>::type* __restrict__ yin, const T* __restrict
                 rec[2 * J] = yv.x;
                 rec[2 * J + 1] = yv.y;
                 rec[2 * J + 2] = (T)(ly * S + lx);
-                rec[2 * J + 3] = (T)lx;
-                rec[2 * J + 4] = (T)ly;
             } else {
                 // coordinate outside this tile (not expected: the plan bins
                 // with the same split); add straight to the grid
@@ -402,67 +400,40 @@ k_grid_wp(const typename cplx_of<T>::type* __restrict__ yin, const T* __restrict
             }
         }
         __syncwarp();
-        // two staged visibilities at a time when their footprints cannot share
-        // a cell (independent read-add-write chains), one at a time otherwise
+        // Visibilities arrive sorted by grid cell inside each tile, so runs of
+        // consecutive records share their J x J cells: each lane adds the run's
+        // contributions to its tap in registers and touches shared memory once
+        // per run (one read-add-write per tap instead of one per visibility).
         const int off0 = b0 * S + a0, off1 = b1 * S + a1;
-        int v = 0;
-        while (v < nv) {
-            const T* ra = mst + v * F;
-            const int oa = (int)ra[2 * J + 2];
-            const bool va = oa >= 0;
-            bool pair = false;
-            int ob = 0;
-            const T* rb = ra + F;
-            if (v + 1 < nv && va) {
-                ob = (int)rb[2 * J + 2];
-                const T dx = ra[2 * J + 3] - rb[2 * J + 3], dy = ra[2 * J + 4] - rb[2 * J + 4];
-                pair = ob >= 0 && (fabs(dx) >= T(J) || fabs(dy) >= T(J));
+        int cur = -1;
+        T r0 = 0, i0 = 0, r1 = 0, i1 = 0;
+        for (int v = 0; v < nv; ++v) {
+            const T* rec = mst + v * F;
+            const int o = (int)rec[2 * J + 2];
+            if (o < 0) continue;
+            if (o != cur) {
+                if (cur >= 0) {
+                    if (b0 < J) { C* cell = mt + cur + off0; C c = *cell; c.x += r0; c.y += i0; *cell = c; }
+                    if (second) { C* cell = mt + cur + off1; C c = *cell; c.x += r1; c.y += i1; *cell = c; }
+                }
+                cur = o;
+                r0 = i0 = r1 = i1 = T(0);
             }
-            if (pair) {
-                const T yra = ra[2 * J], yia = ra[2 * J + 1], yrb = rb[2 * J], yib = rb[2 * J + 1];
-                if (b0 < J) {
-                    const T wa = ra[a0] * ra[J + b0], wb = rb[a0] * rb[J + b0];
-                    C* ca = mt + oa + off0;
-                    C* cb = mt + ob + off0;
-                    C xa = *ca, xb = *cb;
-                    xa.x += wa * yra; xa.y += wa * yia;
-                    xb.x += wb * yrb; xb.y += wb * yib;
-                    *ca = xa;
-                    *cb = xb;
-                }
-                if (second) {
-                    const T wa = ra[a1] * ra[J + b1], wb = rb[a1] * rb[J + b1];
-                    C* ca = mt + oa + off1;
-                    C* cb = mt + ob + off1;
-                    C xa = *ca, xb = *cb;
-                    xa.x += wa * yra; xa.y += wa * yia;
-                    xb.x += wb * yrb; xb.y += wb * yib;
-                    *ca = xa;
-                    *cb = xb;
-                }
-                v += 2;
-                continue;
+            const T yr = rec[2 * J], yi = rec[2 * J + 1];
+            if (b0 < J) {
+                const T w = rec[a0] * rec[J + b0];
+                r0 += w * yr;
+                i0 += w * yi;
             }
-            if (va) {
-                const T yr = ra[2 * J], yi = ra[2 * J + 1];
-                if (b0 < J) {
-                    const T w = ra[a0] * ra[J + b0];
-                    C* cell = mt + oa + off0;
-                    C cur = *cell;
-                    cur.x += w * yr;
-                    cur.y += w * yi;
-                    *cell = cur;
-                }
-                if (second) {
-                    const T w = ra[a1] * ra[J + b1];
-                    C* cell = mt + oa + off1;
-                    C cur = *cell;
-                    cur.x += w * yr;
-                    cur.y += w * yi;
-                    *cell = cur;
-                }
+            if (second) {
+                const T w = rec[a1] * rec[J + b1];
+                r1 += w * yr;
+                i1 += w * yi;
             }
-            v += 1;
+        }
+        if (cur >= 0) {
+            if (b0 < J) { C* cell = mt + cur + off0; C c = *cell; c.x += r0; c.y += i0; *cell = c; }
+            if (second) { C* cell = mt + cur + off1; C c = *cell; c.x += r1; c.y += i1; *cell = c; }
         }
         __syncwarp();
     }
@@ -641,15 +612,16 @@ static void rows_inv_t(purify_plan* p, void* out, double scale, int out_mode, co
 
 template <typename T, int J> static void degrid_tj(purify_plan* p, void* y, bool caller_order, const int* skip) {
     using C = typename cplx_of<T>::type;
-    if (p->work.nsub == 0) return;
-    const int tile = p->work.tile, PT = tile + J - 1;
+    const GridWork& w = p->dwork;
+    if (w.nsub == 0) return;
+    const int tile = w.tile, PT = tile + J - 1;
     size_t sm = sizeof(C) * (size_t)PT * PT + sizeof(int) * (2 * PURIFY_MAX_PIECES + 1);
     set_smem(k_degrid_tile<T, J>, sm);
     Launch L(p, "degrid");
-    k_degrid_tile<T, J><<<p->work.nsub, 128, sm, p->stream>>>(
+    k_degrid_tile<T, J><<<w.nsub, 128, sm, p->stream>>>(
         p->grid.as<C>(), p->us.as<T>(), p->vs.as<T>(), p->ax, p->ay, p->kbp, p->beta, 1.0 / p->i0beta,
-        caller_order ? p->perm.as<int>() : nullptr, p->work.sub_bin.as<int>(), p->work.piece_off.as<int>(),
-        p->work.piece_start.as<int>(), p->work.piece_len.as<int>(), tile, p->work.tiles_x, (C*)y, skip);
+        caller_order ? p->perm.as<int>() : nullptr, w.sub_bin.as<int>(), w.piece_off.as<int>(),
+        w.piece_start.as<int>(), w.piece_len.as<int>(), tile, w.tiles_x, (C*)y, skip);
     L.done();
 }
 

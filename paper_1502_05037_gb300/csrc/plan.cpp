@@ -101,11 +101,24 @@ static void sort_hierarchical(purify_plan* p, const std::vector<int>& cx, const 
         for (int64_t m = a; m < b; ++m) count[key[m] + 1]++;
         for (int k = 0; k < nkeys; ++k) count[k + 1] += count[k];
         for (int64_t m = a; m < b; ++m) perm[a + count[key[m]]++] = (int)m;
+        // inside each finest tile, order by grid cell (then by index), so that
+        // visibilities sharing a first tap are adjacent
+        int64_t i = a;
+        while (i < b) {
+            int64_t j = i;
+            const int k0 = key[perm[i]];
+            while (j < b && key[perm[j]] == k0) ++j;
+            if (j - i > 1)
+                std::sort(perm.begin() + i, perm.begin() + j, [&](int x, int y) {
+                    const int cx1 = (cy[x] % tmin) * tmin + cx[x] % tmin, cx2 = (cy[y] % tmin) * tmin + cx[y] % tmin;
+                    return cx1 != cx2 ? cx1 < cx2 : x < y;
+                });
+            i = j;
+        }
     }
 }
 
-void build_gridwork(purify_plan* p, const std::vector<int>& bin_sorted, int tile) {
-    GridWork& w = p->work;
+void build_gridwork(purify_plan* p, const std::vector<int>& bin_sorted, int tile, GridWork& w) {
     w.tile = tile;
     w.tiles_x = p->Kx / tile;
     w.tiles_y = p->Ky / tile;
@@ -173,7 +186,7 @@ struct TuneKey {
         return std::tie(nx, ny, J, dtype, mlog, R) < std::tie(o.nx, o.ny, o.J, o.dtype, o.mlog, o.R);
     }
 };
-struct TuneVal { int tile, rb, cb; };
+struct TuneVal { int tile, dtile, rb, cb; };
 static std::mutex g_tune_mutex;
 static std::map<TuneKey, TuneVal> g_tune_cache;
 
@@ -199,7 +212,7 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
     int mlog = 0;
     while ((int64_t(1) << (mlog + 1)) <= p->M) ++mlog;
     TuneKey key{p->nx, p->ny, p->J, p->dtype, mlog, std::min(p->R, 64)};
-    TuneVal val{p->work.tile, 0, 0};
+    TuneVal val{p->work.tile, p->work.tile, 0, 0};
     bool cached = false;
     if (tune) {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
@@ -234,16 +247,16 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
         }
         p->fft_rb = val.rb;
         p->fft_cb = val.cb;
-        // gridding tile
+        // gridding and degridding tiles, each timed on its own kernel
         if (cand.size() > 1 && p->M >= 32768) {
-            best = 1e30f;
+            float bg = 1e30f, bd = 1e30f;
             for (int t : cand) {
-                build_gridwork(p, bins_for(t), t);
-                float ms = time_ms(p->stream, [&] {
-                    launch_phi(p, ximg, yv, false, 1.0);
-                    launch_phi_adj(p, yv, p->tmp_img.p, false, 1.0, 0, nullptr);
-                }, 3);
-                if (ms < best) { best = ms; val.tile = t; }
+                build_gridwork(p, bins_for(t), t, p->work);
+                build_gridwork(p, bins_for(t), t, p->dwork);
+                float mg = time_ms(p->stream, [&] { launch_grid(p, yv, false, nullptr); }, 3);
+                float md = time_ms(p->stream, [&] { launch_degrid(p, yv, false, nullptr); }, 3);
+                if (mg < bg) { bg = mg; val.tile = t; }
+                if (md < bd) { bd = md; val.dtile = t; }
             }
         }
         std::lock_guard<std::mutex> lk(g_tune_mutex);
@@ -251,7 +264,8 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
     }
     p->fft_rb = val.rb;
     p->fft_cb = val.cb;
-    build_gridwork(p, bins_for(val.tile), val.tile);
+    build_gridwork(p, bins_for(val.tile), val.tile, p->work);
+    build_gridwork(p, bins_for(val.dtile), val.dtile, p->dwork);
 }
 
 template <typename T> static void finish_plan(purify_plan* p) {
