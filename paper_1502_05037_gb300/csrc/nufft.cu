@@ -307,150 +307,158 @@ __device__ __forceinline__ int flat_vis(const int* pst, const int* pcum, int np,
     return pst[lo] + (q - pcum[lo]);
 }
 
-// G^H, warp-private tiles. A block owns one subproblem (a grid tile and a
-// list of visibility pieces) and holds WARPS private copies of the tile plus
-// its (J-1) halo in shared memory (interleaved complex, row stride S with
-// S = J mod 16 so the J*J taps of one visibility fall on distinct banks).
-// The subproblem's visibilities are dealt to the warps 32 at a time: every
-// lane evaluates the split coordinate and the 2J kernel weights of one
-// visibility into a per-warp staging area; then the warp scatters the 32
-// staged visibilities one after another, lane l adding tap (l mod J, l / J)
-// (and tap l + 32 when J*J > 32) with a plain read-add-write. Lanes of a warp
-// touch distinct cells and warps touch distinct copies, so no shared-memory
-// atomic is needed. Finally the copies are summed in warp order and the
-// non-zero cells of the tile are added to the grid.
+// G^H by cell runs. A block owns one subproblem: a grid tile and an explicit
+// list of its visibilities ordered by first-tap cell across all measurement
+// blocks, so that visibilities sharing their J x J cells are adjacent. The
+// tile plus its (J-1) halo is one shared-memory array (row stride S).
+// The list is cut into WARPS * G contiguous segments, G = 32 / J per warp;
+// group g of a warp (lanes gJ .. gJ+J-1) walks its segment in order, lane b
+// holding row b of the current run's J x J patch in 2J registers:
+//   patch[b][a] += wx[a] * (wy[b] * y)   for every visibility of the run,
+// and adding the patch to the shared tile with shared-memory atomics only
+// when the first-tap cell changes. The 2J weights and the split of each
+// visibility are evaluated once, by one lane, into a per-warp staging area
+// (P records per group per batch, P = 32 / G). Finally the tile's non-zero
+// cells are added to the grid.
 template <int J> struct GridStage {
-    // floats per staged visibility: wx[J], wy[J], re, im, cell offset (-1:
-    // not in this tile); odd so that the 32 lanes of a warp store their
-    // records on distinct banks
+    static constexpr int G = 32 / J;      // visibility groups per warp
+    static constexpr int P = 32 / G;      // records a group stages per batch
+    static constexpr int NB = G * P;      // records per warp batch
+    // words per staged visibility: wx[J], wy[J], re, im, cell offset (-1:
+    // empty or not in this tile); odd so that lanes storing their records
+    // fall on distinct banks
     static constexpr int F = 2 * J + 3;
 };
 
+template <typename T> __device__ __forceinline__ T int_bits(int v);
+template <> __device__ __forceinline__ float int_bits<float>(int v) { return __int_as_float(v); }
+template <> __device__ __forceinline__ double int_bits<double>(int v) { return __longlong_as_double((long long)v); }
+__device__ __forceinline__ int bits_int(float v) { return __float_as_int(v); }
+__device__ __forceinline__ int bits_int(double v) { return (int)__double_as_longlong(v); }
+
 template <typename T, int J, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32)
-k_grid_wp(const typename cplx_of<T>::type* __restrict__ yin, const T* __restrict__ us, const T* __restrict__ vs,
-          AxisConst ax, AxisConst ay, KbPoly kp, double beta, double inv_i0beta, const int* __restrict__ perm,
-          const int* __restrict__ sub_bin, const int* __restrict__ piece_off, const int* __restrict__ piece_start,
-          const int* __restrict__ piece_len, int tile, int tiles_x, int S,
-          typename cplx_of<T>::type* __restrict__ grid, const int* __restrict__ skip) {
+k_grid_runs(const typename cplx_of<T>::type* __restrict__ yin, const T* __restrict__ us, const T* __restrict__ vs,
+            AxisConst ax, AxisConst ay, KbPoly kp, double beta, double inv_i0beta, const int* __restrict__ perm,
+            const int* __restrict__ sub_bin, const int* __restrict__ sub_off, const int* __restrict__ list, int tile,
+            int tiles_x, int S, typename cplx_of<T>::type* __restrict__ grid, const int* __restrict__ skip) {
     using C = typename cplx_of<T>::type;
-    constexpr int F = GridStage<J>::F;
+    using GS = GridStage<J>;
+    constexpr int G = GS::G, P = GS::P, NB = GS::NB, F = GS::F;
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int PT = tile + J - 1;             // rows of a tile copy
-    const int cells = PT * S;                // complex cells of one copy
+    const int PT = tile + J - 1;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    C* tiles = reinterpret_cast<C*>(smem_raw);                              // [WARPS][PT][S]
-    T* stage = reinterpret_cast<T*>(tiles + (size_t)WARPS * cells);         // [WARPS][32][F]
-    int* pst = reinterpret_cast<int*>(stage + (size_t)WARPS * 32 * F);      // [MAX_PIECES]
-    int* pcum = pst + PURIFY_MAX_PIECES;                                    // [MAX_PIECES + 1]
-    C* mt = tiles + (size_t)warp * cells;
-    T* mst = stage + (size_t)warp * 32 * F;
-    for (int t = threadIdx.x; t < WARPS * cells; t += blockDim.x) tiles[t] = cmake<C>(T(0), T(0));
+    C* mt = reinterpret_cast<C*>(smem_raw);                            // [PT][S]
+    T* mst = reinterpret_cast<T*>(mt + (size_t)PT * S) + (size_t)warp * NB * F;   // [NB][F]
+    for (int t = threadIdx.x; t < PT * S; t += blockDim.x) mt[t] = cmake<C>(T(0), T(0));
     const int s = blockIdx.x;
-    const int np = load_pieces(piece_off, piece_start, piece_len, s, pst, pcum);
-    __syncthreads();
     const int bin = sub_bin[s];
     const int oy = (bin / tiles_x) * tile, ox = (bin % tiles_x) * tile;
     const int Kx = ax.K, Ky = ay.K;
-    const int total = pcum[np];
-    // tap handled by this lane in the first and second round
-    const int a0 = lane % J, b0 = lane / J;
-    const int t1 = lane + 32;
-    const int a1 = t1 % J, b1 = t1 / J;
-    const bool second = (J * J > 32) && (t1 < J * J);
-    for (int base = warp * 32; base < total; base += WARPS * 32) {
-        const int q = base + lane;
-        const int nv = min(32, total - base);
-        if (q < total) {
-            const int m = flat_vis(pst, pcum, np, q);
-            int kx0, ky0;
-            T phx, phy;
-            split_coord(us[m], ax, J, kx0, phx);
-            split_coord(vs[m], ay, J, ky0, phy);
-            T wx[J], wy[J];
-            if constexpr (sizeof(T) == 4) {
-                kb_weights<J>(kp, phx, wx);
-                kb_weights<J>(kp, phy, wy);
-            } else {
-                kb_weights<J>(beta, inv_i0beta, phx, wx);
-                kb_weights<J>(beta, inv_i0beta, phy, wy);
+    const int q0 = sub_off[s], total = sub_off[s + 1] - q0;
+    constexpr int NSEG = WARPS * G;
+    // segment sg covers list positions [total * sg / NSEG, total * (sg + 1) / NSEG)
+    auto seg_lo = [&](int sg) { return (int)(((long long)total * sg) / NSEG); };
+    // staging role: lane (gs, js) evaluates record js of group gs
+    const int gs = lane / P, js = lane - gs * P;
+    const int lo1 = seg_lo(warp * G + gs), len1 = (gs < G) ? seg_lo(warp * G + gs + 1) - lo1 : 0;
+    // scatter role: lane (g, b) holds row b of group g's patch
+    const int g = lane / J, b = lane - g * J;
+    const int nbatch = ((total + NSEG - 1) / NSEG + P - 1) / P;
+    __syncthreads();
+    int cur = -1;
+    T ar[J], ai[J];
+#pragma unroll
+    for (int a = 0; a < J; ++a) ar[a] = ai[a] = T(0);
+    for (int k = 0; k < nbatch; ++k) {
+        if (gs < G) {
+            T* rec = mst + (gs * P + js) * F;
+            const int pos = k * P + js;
+            int off = -1;
+            if (pos < len1) {
+                const int m = list[q0 + lo1 + pos];
+                int kx0, ky0;
+                T phx, phy;
+                split_coord(us[m], ax, J, kx0, phx);
+                split_coord(vs[m], ay, J, ky0, phy);
+                T wx[J], wy[J];
+                if constexpr (sizeof(T) == 4) {
+                    kb_weights<J>(kp, phx, wx);
+                    kb_weights<J>(kp, phy, wy);
+                } else {
+                    kb_weights<J>(beta, inv_i0beta, phx, wx);
+                    kb_weights<J>(beta, inv_i0beta, phy, wy);
+                }
+                const C yv = yin[perm ? perm[m] : m];
+                const int lx = (kx0 & (Kx - 1)) - ox, ly = (ky0 & (Ky - 1)) - oy;
+                if (lx >= 0 && lx < tile && ly >= 0 && ly < tile) {
+#pragma unroll
+                    for (int a = 0; a < J; ++a) { rec[a] = wx[a]; rec[J + a] = wy[a]; }
+                    rec[2 * J] = yv.x;
+                    rec[2 * J + 1] = yv.y;
+                    off = ly * S + lx;
+                } else {
+                    // coordinate outside this tile (not expected: the plan
+                    // bins with the same split); add straight to the grid
+#pragma unroll
+                    for (int bb = 0; bb < J; ++bb)
+#pragma unroll
+                        for (int a = 0; a < J; ++a) {
+                            T w = wy[bb] * wx[a];
+                            atomic_add_c(grid + (size_t)((ky0 + bb) & (Ky - 1)) * Kx + ((kx0 + a) & (Kx - 1)),
+                                         cmake<C>(w * yv.x, w * yv.y));
+                        }
+                }
             }
-            C yv = yin[perm ? perm[m] : m];
-            int lx = (kx0 & (Kx - 1)) - ox, ly = (ky0 & (Ky - 1)) - oy;
-            T* rec = mst + lane * F;
-            if (lx >= 0 && lx < tile && ly >= 0 && ly < tile) {
-#pragma unroll
-                for (int a = 0; a < J; ++a) { rec[a] = wx[a]; rec[J + a] = wy[a]; }
-                rec[2 * J] = yv.x;
-                rec[2 * J + 1] = yv.y;
-                rec[2 * J + 2] = (T)(ly * S + lx);
-            } else {
-                // coordinate outside this tile (not expected: the plan bins
-                // with the same split); add straight to the grid
-                rec[2 * J + 2] = T(-1);
-#pragma unroll
-                for (int b = 0; b < J; ++b)
-#pragma unroll
-                    for (int a = 0; a < J; ++a) {
-                        T w = wy[b] * wx[a];
-                        atomic_add_c(grid + (size_t)((ky0 + b) & (Ky - 1)) * Kx + ((kx0 + a) & (Kx - 1)),
-                                     cmake<C>(w * yv.x, w * yv.y));
-                    }
-            }
+            rec[2 * J + 2] = int_bits<T>(off);
         }
         __syncwarp();
-        // Visibilities arrive sorted by grid cell inside each tile, so runs of
-        // consecutive records share their J x J cells: each lane adds the run's
-        // contributions to its tap in registers and touches shared memory once
-        // per run (one read-add-write per tap instead of one per visibility).
-        const int off0 = b0 * S + a0, off1 = b1 * S + a1;
-        int cur = -1;
-        T r0 = 0, i0 = 0, r1 = 0, i1 = 0;
-        for (int v = 0; v < nv; ++v) {
-            const T* rec = mst + v * F;
-            const int o = (int)rec[2 * J + 2];
-            if (o < 0) continue;
-            if (o != cur) {
-                if (cur >= 0) {
-                    if (b0 < J) { C* cell = mt + cur + off0; C c = *cell; c.x += r0; c.y += i0; *cell = c; }
-                    if (second) { C* cell = mt + cur + off1; C c = *cell; c.x += r1; c.y += i1; *cell = c; }
+        if (g < G) {
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                const T* rec = mst + (g * P + j) * F;
+                const int o = bits_int(rec[2 * J + 2]);
+                if (o >= 0) {
+                    if (o != cur) {
+                        if (cur >= 0) {
+                            C* row = mt + cur + b * S;
+#pragma unroll
+                            for (int a = 0; a < J; ++a) {
+                                atomicAdd(&row[a].x, ar[a]);
+                                atomicAdd(&row[a].y, ai[a]);
+                                ar[a] = ai[a] = T(0);
+                            }
+                        }
+                        cur = o;
+                    }
+                    const T wyb = rec[J + b];
+                    const T zr = wyb * rec[2 * J], zi = wyb * rec[2 * J + 1];
+#pragma unroll
+                    for (int a = 0; a < J; ++a) {
+                        const T wxa = rec[a];
+                        ar[a] = fma(wxa, zr, ar[a]);
+                        ai[a] = fma(wxa, zi, ai[a]);
+                    }
                 }
-                cur = o;
-                r0 = i0 = r1 = i1 = T(0);
             }
-            const T yr = rec[2 * J], yi = rec[2 * J + 1];
-            if (b0 < J) {
-                const T w = rec[a0] * rec[J + b0];
-                r0 += w * yr;
-                i0 += w * yi;
-            }
-            if (second) {
-                const T w = rec[a1] * rec[J + b1];
-                r1 += w * yr;
-                i1 += w * yi;
-            }
-        }
-        if (cur >= 0) {
-            if (b0 < J) { C* cell = mt + cur + off0; C c = *cell; c.x += r0; c.y += i0; *cell = c; }
-            if (second) { C* cell = mt + cur + off1; C c = *cell; c.x += r1; c.y += i1; *cell = c; }
         }
         __syncwarp();
     }
+    if (g < G && cur >= 0) {
+        C* row = mt + cur + b * S;
+#pragma unroll
+        for (int a = 0; a < J; ++a) {
+            atomicAdd(&row[a].x, ar[a]);
+            atomicAdd(&row[a].y, ai[a]);
+        }
+    }
     __syncthreads();
-    // sum the copies in warp order and add the non-zero cells to the grid
     for (int t = threadIdx.x; t < PT * PT; t += blockDim.x) {
         const int r = t / PT, c = t - r * PT;
-        const int o = r * S + c;
-        T re = 0, im = 0;
-#pragma unroll
-        for (int w = 0; w < WARPS; ++w) {
-            C v = tiles[(size_t)w * cells + o];
-            re += v.x;
-            im += v.y;
-        }
-        if (re != T(0) || im != T(0))
-            atomic_add_c(grid + (size_t)((oy + r) & (Ky - 1)) * Kx + ((ox + c) & (Kx - 1)), cmake<C>(re, im));
+        const C v = mt[r * S + c];
+        if (v.x != T(0) || v.y != T(0))
+            atomic_add_c(grid + (size_t)((oy + r) & (Ky - 1)) * Kx + ((ox + c) & (Kx - 1)), v);
     }
 }
 
@@ -625,13 +633,12 @@ template <typename T, int J> static void degrid_tj(purify_plan* p, void* y, bool
     L.done();
 }
 
-// row stride of a shared tile copy (complex cells): at least tile + J - 1
-// and equal to J modulo 16, so that the taps of one visibility handled by a
-// half-warp fall on distinct 8-byte bank pairs
+// row stride of the shared gridding tile (complex cells): at least
+// tile + J - 1 and odd, so that the J rows of one patch held by a lane group
+// fall on distinct 8-byte bank pairs
 static int grid_row_stride(int tile, int J) {
     int S = tile + J - 1;
-    while (S % 16 != J % 16) ++S;
-    return S;
+    return S | 1;
 }
 
 template <typename T> static constexpr int grid_warps() { return sizeof(T) == 4 ? 8 : 4; }
@@ -639,8 +646,7 @@ template <typename T> static constexpr int grid_warps() { return sizeof(T) == 4 
 template <typename T, int J>
 static size_t grid_smem_bytes(int tile) {
     const int PT = tile + J - 1, S = grid_row_stride(tile, J);
-    return sizeof(T) * ((size_t)grid_warps<T>() * 2 * PT * S + (size_t)grid_warps<T>() * 32 * GridStage<J>::F) +
-           sizeof(int) * (2 * PURIFY_MAX_PIECES + 1);
+    return sizeof(T) * (2 * (size_t)PT * S + (size_t)grid_warps<T>() * GridStage<J>::NB * GridStage<J>::F);
 }
 
 template <typename T, int J>
@@ -652,13 +658,20 @@ static void grid_tj(purify_plan* p, const void* y, bool caller_order, const int*
     const int tile = p->work.tile;
     const int S = grid_row_stride(tile, J);
     size_t sm = grid_smem_bytes<T, J>(tile);
-    set_smem(k_grid_wp<T, J, W>, sm);
+    set_smem(k_grid_runs<T, J, W>, sm);
     Launch L(p, "grid");
-    k_grid_wp<T, J, W><<<p->work.nsub, W * 32, sm, p->stream>>>(
+    k_grid_runs<T, J, W><<<p->work.nsub, W * 32, sm, p->stream>>>(
         (const C*)y, p->us.as<T>(), p->vs.as<T>(), p->ax, p->ay, p->kbp, p->beta, 1.0 / p->i0beta,
-        caller_order ? p->perm.as<int>() : nullptr, p->work.sub_bin.as<int>(), p->work.piece_off.as<int>(),
-        p->work.piece_start.as<int>(), p->work.piece_len.as<int>(), tile, p->work.tiles_x, S, p->grid.as<C>(), skip);
+        caller_order ? p->perm.as<int>() : nullptr, p->work.sub_bin.as<int>(), p->work.sub_off.as<int>(),
+        p->work.list.as<int>(), tile, p->work.tiles_x, S, p->grid.as<C>(), skip);
     L.done();
+}
+
+// Visibilities per gridding subproblem are a multiple of this unit: every
+// group of every warp then stages full batches when the subproblem is full.
+int grid_list_unit(int dtype, int J) {
+    const int G = 32 / J, P = 32 / G;
+    return (dtype == PURIFY_F32 ? grid_warps<float>() : grid_warps<double>()) * G * P;
 }
 
 #define PURIFY_J_DISPATCH(J, FN, ...)                                     \

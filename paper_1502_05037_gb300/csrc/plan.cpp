@@ -176,6 +176,56 @@ void build_gridwork(purify_plan* p, const std::vector<int>& bin_sorted, int tile
     upload(w.piece_len, plen);
 }
 
+// Gridding work: every visibility of a tile (from all measurement blocks) in
+// first-tap-cell order, cut into subproblems of at most CMAX visibilities (a
+// multiple of the kernel's batch unit) and listed largest first, so that the
+// longest blocks are scheduled first. cell_order is the internal indices
+// sorted by first-tap cell (stable), so a stable pass by tile keeps the cell
+// order inside each tile.
+void build_gridlist(purify_plan* p, const std::vector<int>& bins, const std::vector<int>& cell_order, int tile,
+                    GridWork& w) {
+    w.tile = tile;
+    w.tiles_x = p->Kx / tile;
+    w.tiles_y = p->Ky / tile;
+    const int nbins = w.tiles_x * w.tiles_y;
+    const int64_t M = p->M;
+    std::vector<int64_t> start(nbins + 1, 0);
+    for (int64_t m = 0; m < M; ++m) start[bins[m] + 1]++;
+    for (int b = 0; b < nbins; ++b) start[b + 1] += start[b];
+    std::vector<int> order(M);
+    {
+        std::vector<int64_t> pos(start.begin(), start.end() - 1);
+        for (int64_t i = 0; i < M; ++i) {
+            const int m = cell_order[i];
+            order[pos[bins[m]]++] = m;
+        }
+    }
+    const int unit = grid_list_unit(p->dtype, p->J);
+    const int64_t want = M / (152 * 4);
+    const int64_t k = std::max<int64_t>(1, std::min<int64_t>(16, (want + unit / 2) / unit));
+    const int64_t CMAX = k * unit;
+    struct Sub { int bin; int64_t start; int len; };
+    std::vector<Sub> subs;
+    for (int b = 0; b < nbins; ++b)
+        for (int64_t s = start[b]; s < start[b + 1]; s += CMAX)
+            subs.push_back({b, s, (int)std::min<int64_t>(CMAX, start[b + 1] - s)});
+    std::stable_sort(subs.begin(), subs.end(), [](const Sub& a, const Sub& b) { return a.len > b.len; });
+    std::vector<int> list(M), sub_bin, sub_off;
+    int64_t q = 0;
+    for (const Sub& sb : subs) {
+        sub_bin.push_back(sb.bin);
+        sub_off.push_back((int)q);
+        std::copy(order.begin() + sb.start, order.begin() + sb.start + sb.len, list.begin() + q);
+        q += sb.len;
+    }
+    sub_off.push_back((int)q);
+    w.nsub = (int)subs.size();
+    w.npieces = 0;
+    upload(w.sub_bin, sub_bin);
+    upload(w.sub_off, sub_off);
+    upload(w.list, list);
+}
+
 // ---------------------------------------------------------------- autotuner
 // Launch shapes picked by timing on the plan's own data: the gridding tile
 // (work list rebuilt from the same hierarchical order) and the rows/columns
@@ -207,7 +257,8 @@ static float time_ms(cudaStream_t s, const std::function<void()>& f, int reps) {
 }
 
 template <typename T, typename BinsFor>
-static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_for, bool tune) {
+static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_for,
+                     const std::vector<int>& cell_order, bool tune) {
     using C = typename cplx_of<T>::type;
     int mlog = 0;
     while ((int64_t(1) << (mlog + 1)) <= p->M) ++mlog;
@@ -251,8 +302,9 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
         if (cand.size() > 1 && p->M >= 32768) {
             float bg = 1e30f, bd = 1e30f;
             for (int t : cand) {
-                build_gridwork(p, bins_for(t), t, p->work);
-                build_gridwork(p, bins_for(t), t, p->dwork);
+                const std::vector<int> bins = bins_for(t);
+                build_gridlist(p, bins, cell_order, t, p->work);
+                build_gridwork(p, bins, t, p->dwork);
                 float mg = time_ms(p->stream, [&] { launch_grid(p, yv, false, nullptr); }, 3);
                 float md = time_ms(p->stream, [&] { launch_degrid(p, yv, false, nullptr); }, 3);
                 if (mg < bg) { bg = mg; val.tile = t; }
@@ -264,7 +316,7 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
     }
     p->fft_rb = val.rb;
     p->fft_cb = val.cb;
-    build_gridwork(p, bins_for(val.tile), val.tile, p->work);
+    build_gridlist(p, bins_for(val.tile), cell_order, val.tile, p->work);
     build_gridwork(p, bins_for(val.dtile), val.dtile, p->dwork);
 }
 
@@ -347,7 +399,16 @@ template <typename T> static void finish_plan(purify_plan* p) {
     p->tmp_vis.alloc(sizeof(C) * (size_t)p->M);
     p->workspace_bytes = (int64_t)(p->grid.bytes + p->rows.bytes + p->ll0.bytes + p->ll1.bytes + p->tmp_img.bytes +
                                    p->tmp_vis.bytes + p->us.bytes + p->vs.bytes + p->perm.bytes);
-    autotune<T>(p, cand, bins_for, d.tile == 0);
+    // internal indices ordered by first-tap cell (stable counting sort)
+    std::vector<int> cell_order(p->M);
+    {
+        const int64_t ncell = (int64_t)p->Kx * p->Ky;
+        std::vector<int64_t> pos(ncell + 1, 0);
+        for (int64_t i = 0; i < p->M; ++i) pos[(int64_t)scy[i] * p->Kx + scx[i] + 1]++;
+        for (int64_t c = 0; c < ncell; ++c) pos[c + 1] += pos[c];
+        for (int64_t i = 0; i < p->M; ++i) cell_order[pos[(int64_t)scy[i] * p->Kx + scx[i]]++] = (int)i;
+    }
+    autotune<T>(p, cand, bins_for, cell_order, d.tile == 0);
 }
 
 purify_plan* create_plan(const purify_plan_desc* d) {
