@@ -65,13 +65,12 @@ template <typename T> struct FilterBank {
 // Gridding work list: subproblem s covers grid tile sub_bin[s] and the
 // visibility pieces piece_off[s] .. piece_off[s+1]-1; piece k is the internal
 // index range [piece_start[k], piece_start[k] + piece_len[k]).
-// Gridding/degridding work list. Degridding uses pieces (contiguous runs of
-// the internal order); gridding uses an explicit visibility list per
-// subproblem (list[sub_off[s] .. sub_off[s + 1]), ordered by first-tap cell).
+// Gridding/degridding work list: subproblem s is grid tile sub_bin[s] and
+// the visibilities list[sub_off[s] .. sub_off[s + 1]) (internal indices,
+// ordered by first-tap cell).
 struct GridWork {
-    int nsub = 0, npieces = 0, tile = 32, tiles_x = 0, tiles_y = 0;
-    DevBuf sub_bin, piece_off, piece_start, piece_len;
-    DevBuf sub_off, list;
+    int nsub = 0, tile = 32, units = 4, tiles_x = 0, tiles_y = 0;
+    DevBuf sub_bin, sub_off, list;
 };
 
 // SDMM device state (allocated on first solve).
@@ -222,11 +221,11 @@ double coef_std(purify_plan* p, const void* x);
 
 int max_grid_tile(int dtype, int J);
 int grid_list_unit(int dtype, int J);
+bool fft_shape_ok(int nb, int K, int dtype);
 
 // plan-side helpers
-void build_gridwork(purify_plan* p, const std::vector<int>& bin_sorted, int tile, GridWork& w);
 void build_gridlist(purify_plan* p, const std::vector<int>& bins, const std::vector<int>& cell_order, int tile,
-                    GridWork& w);
+                    int units, GridWork& w);
 purify_plan* create_plan(const purify_plan_desc* d);
 bool is_host_pointer(const void* ptr);
 

@@ -23,64 +23,141 @@
 namespace purify {
 
 // --------------------------------------------------------------- FFT core
-// `nb` independent length-n FFTs held in shared memory; element k of FFT f
-// lives at f*fs + k*ks. Returns the buffer holding the result.
-template <typename C, bool INV>
-__device__ C* fft_smem(C* src, C* dst, int n, int logn, int nb, int fs, int ks, const C* __restrict__ tw) {
-    const int tid = threadIdx.x, T = blockDim.x;
-    int Ns = 1;
-    if (logn & 1) {
-        const int half = n >> 1;
-        for (int t = tid; t < nb * half; t += T) {
-            int f = t % nb, j = t / nb;
-            C v0 = src[f * fs + j * ks];
-            C v1 = src[f * fs + (j + half) * ks];
-            dst[f * fs + (2 * j) * ks] = cadd(v0, v1);
-            dst[f * fs + (2 * j + 1) * ks] = csub(v0, v1);
-        }
-        __syncthreads();
-        C* s = src; src = dst; dst = s;
-        Ns = 2;
+// Length-N transforms (N = 2^logN >= 16) by Stockham autosort stages, N / 8
+// threads per transform, eight values per thread in registers. A stage of
+// radix r over span Ns (the product of the earlier radices) takes butterfly
+// j's inputs v_k = x[j + k N / r], multiplies v_k by W_{r Ns}^{(j mod Ns) k},
+// forms the r-point DFT V_q = sum_k v_k W_r^{k q} and writes V_q to
+// ((j - j mod Ns) r + j mod Ns + q Ns). The first stage (Ns = 1, radix 2, 4
+// or 8 so that the rest are radix 8) needs no twiddles and reads the input
+// through `load`; the last (Ns = N / 8) writes element j + q N / 8 through
+// `store`; the stages in between exchange through shared memory (`slot`).
+// Forward uses W_n = exp(-2 pi i / n), inverse its conjugate (unnormalised).
+template <typename C, bool INV> __device__ __forceinline__ C mul_neg_i(C a) {
+    // forward: -i a; inverse: +i a
+    return INV ? cmake<C>(-a.y, a.x) : cmake<C>(a.y, -a.x);
+}
+
+template <typename C, bool INV> __device__ __forceinline__ void dft2(C& a0, C& a1) {
+    C t = a0;
+    a0 = cadd(t, a1);
+    a1 = csub(t, a1);
+}
+
+// 4-point DFT, natural order in and out
+template <typename C, bool INV> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+    C t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = mul_neg_i<C, INV>(csub(a1, a3));
+    a0 = cadd(t0, t2);
+    a1 = cadd(t1, t3);
+    a2 = csub(t0, t2);
+    a3 = csub(t1, t3);
+}
+
+// 8-point DFT, natural order in and out: two 4-point DFTs of the even and odd
+// samples combined with W_8^q.
+template <typename C, bool INV> __device__ __forceinline__ void dft8(C (&v)[8]) {
+    using T = decltype(C::x);
+    const T h = T(0.70710678118654752440084436210484904);   // 1 / sqrt(2)
+    dft4<C, INV>(v[0], v[2], v[4], v[6]);
+    dft4<C, INV>(v[1], v[3], v[5], v[7]);
+    // odd part times W_8^q, q = 1, 2, 3
+    C o1 = v[3], o2 = v[5], o3 = v[7];
+    // W_8 = (1 -+ i) / sqrt(2), W_8^3 = (-1 -+ i) / sqrt(2)
+    if (INV) {
+        o1 = cmake<C>(h * (o1.x - o1.y), h * (o1.x + o1.y));
+        o3 = cmake<C>(-h * (o3.x + o3.y), h * (o3.x - o3.y));
+    } else {
+        o1 = cmake<C>(h * (o1.x + o1.y), h * (o1.y - o1.x));
+        o3 = cmake<C>(h * (o3.y - o3.x), -h * (o3.x + o3.y));
     }
-    const int quarter = n >> 2;
-    while (Ns < n) {
-        const int tstride = n / (4 * Ns);
-        for (int t = tid; t < nb * quarter; t += T) {
-            int f = t % nb, j = t / nb;
-            int k = j & (Ns - 1);
-            C v0 = src[f * fs + j * ks];
-            C v1 = src[f * fs + (j + quarter) * ks];
-            C v2 = src[f * fs + (j + 2 * quarter) * ks];
-            C v3 = src[f * fs + (j + 3 * quarter) * ks];
-            if (Ns > 1) {
-                C w1 = tw[k * tstride], w2 = tw[2 * k * tstride], w3 = tw[3 * k * tstride];
-                if (INV) { v1 = cmulconj(v1, w1); v2 = cmulconj(v2, w2); v3 = cmulconj(v3, w3); }
-                else { v1 = cmul(v1, w1); v2 = cmul(v2, w2); v3 = cmul(v3, w3); }
-            }
-            C a0 = cadd(v0, v2), a1 = csub(v0, v2), a2 = cadd(v1, v3), a3 = csub(v1, v3);
-            // -i * a3 for the forward transform, +i * a3 for the inverse
-            C ia3 = INV ? cmake<C>(-a3.y, a3.x) : cmake<C>(a3.y, -a3.x);
-            int o = (j - k) * 4 + k;
-            dst[f * fs + o * ks] = cadd(a0, a2);
-            dst[f * fs + (o + Ns) * ks] = cadd(a1, ia3);
-            dst[f * fs + (o + 2 * Ns) * ks] = csub(a0, a2);
-            dst[f * fs + (o + 3 * Ns) * ks] = csub(a1, ia3);
+    o2 = mul_neg_i<C, INV>(o2);
+    const C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, o1);
+    v[5] = csub(e1, o1);
+    v[2] = cadd(e2, o2);
+    v[6] = csub(e2, o2);
+    v[3] = cadd(e3, o3);
+    v[7] = csub(e3, o3);
+}
+
+// shared-memory index of element n with one pad slot per 8 (keeps the
+// stride-8 writes of the early stages off a single bank)
+__device__ __forceinline__ int fft_pad(int n) { return n + (n >> 3); }
+__host__ __device__ inline int fft_padded(int n) { return n + (n >> 3); }
+
+template <typename C, bool INV, typename Load, typename Store, typename Slot>
+__device__ __forceinline__ void fft_reg(int N, int logN, int t, const C* __restrict__ tw, Load load, Store store,
+                                        Slot slot) {
+    const int N8 = N >> 3;
+    const int r0 = (logN % 3 == 0) ? 8 : (logN % 3 == 1 ? 2 : 4);
+    C v[8];
+    if (r0 == 8) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = load(t + k * N8);
+        dft8<C, INV>(v);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) slot(t * 8 + q) = v[q];
+    } else if (r0 == 4) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = load(t + k * N8);
+        // butterflies j = t (inputs k = 0, 2, 4, 6) and j = t + N/8 (1, 3, 5, 7)
+        dft4<C, INV>(v[0], v[2], v[4], v[6]);
+        dft4<C, INV>(v[1], v[3], v[5], v[7]);
+        const int j1 = t + N8;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            slot(t * 4 + q) = v[2 * q];
+            slot(j1 * 4 + q) = v[2 * q + 1];
         }
-        __syncthreads();
-        C* s = src; src = dst; dst = s;
-        Ns <<= 2;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = load(t + k * N8);
+        // butterflies j = t + m N/8, m < 4, inputs m and m + 4
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            dft2<C, INV>(v[m], v[m + 4]);
+            slot((t + m * N8) * 2) = v[m];
+            slot((t + m * N8) * 2 + 1) = v[m + 4];
+        }
     }
-    return src;
+    for (int Ns = r0; Ns < N; Ns <<= 3) {
+        __syncthreads();
+        const int kk = t & (Ns - 1);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = slot(t + k * N8);
+        const int ts = kk * (N8 / Ns);
+#pragma unroll
+        for (int k = 1; k < 8; ++k) {
+            const C w = tw[k * ts];
+            v[k] = INV ? cmulconj(v[k], w) : cmul(v[k], w);
+        }
+        dft8<C, INV>(v);
+        if (Ns == N8) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) store(t + q * N8, v[q]);
+        } else {
+            __syncthreads();
+            const int base = (t - kk) * 8 + kk;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) slot(base + q * Ns) = v[q];
+        }
+    }
 }
 
 __host__ __device__ inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
 
 // ------------------------------------------------------------ row passes
+// Row kernels: a block holds rb transforms of length Kx, thread
+// (f, t) = (tid / (Kx/8), tid mod (Kx/8)); row f's shared slots are
+// [f * pad(Kx), (f + 1) * pad(Kx)).
+//
 // S Z and the forward row FFT: rows [i0, i0+rb) of the image to rows[i][0..Kx).
 // When pdir != null the kernel first forms p = r + beta p in place (CG
 // direction update) and transforms the new p.
 template <typename T>
-__global__ void k_rows_fwd(const T* __restrict__ x, typename cplx_of<T>::type* __restrict__ rows,
+__global__ void __launch_bounds__(1024) k_rows_fwd(const T* __restrict__ x, typename cplx_of<T>::type* __restrict__ rows,
                            const T* __restrict__ sx, const T* __restrict__ sy,
                            const typename cplx_of<T>::type* __restrict__ tw, int nx, int ny, int Kx,
                            int rb, T scale, T* pdir, const T* __restrict__ rvec,
@@ -88,20 +165,18 @@ __global__ void k_rows_fwd(const T* __restrict__ x, typename cplx_of<T>::type* _
     using C = typename cplx_of<T>::type;
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* b0 = reinterpret_cast<C*>(smem_raw);
-    C* b1 = b0 + rb * Kx;
-    const int i0 = blockIdx.x * rb;
-    const int tot = rb * Kx;
+    const int N8 = Kx >> 3;
+    const int f = threadIdx.x / N8, t = threadIdx.x - f * N8;
+    C* buf = reinterpret_cast<C*>(smem_raw) + f * fft_padded(Kx);
+    const int i = blockIdx.x * rb + f;
     const T beta = beta_dev ? (T)(*beta_dev) : T(0);
-    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-        int f = t / Kx, p1 = t - f * Kx;
-        int i = i0 + f;
+    const T rs = sy[i] * scale;
+    auto load = [&](int p1) -> C {
         // pixel column j with (j - nx/2) mod Kx == p1
-        int n1 = p1 < Kx / 2 ? p1 : p1 - Kx;
-        int j = n1 + nx / 2;
+        const int j = (p1 < Kx / 2 ? p1 : p1 - Kx) + nx / 2;
         T val = T(0);
         if (j >= 0 && j < nx) {
-            size_t idx = (size_t)i * nx + j;
+            const size_t idx = (size_t)i * nx + j;
             T xv;
             if (pdir) {
                 xv = rvec[idx] + beta * pdir[idx];
@@ -109,75 +184,67 @@ __global__ void k_rows_fwd(const T* __restrict__ x, typename cplx_of<T>::type* _
             } else {
                 xv = x[idx];
             }
-            val = xv * sx[j] * sy[i] * scale;
+            val = xv * sx[j] * rs;
         }
-        b0[t] = cmake<C>(val, T(0));
-    }
-    __syncthreads();
-    C* res = fft_smem<C, false>(b0, b1, Kx, ilog2(Kx), rb, Kx, 1, tw);
-    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-        int f = t / Kx, k = t - f * Kx;
-        rows[(size_t)(i0 + f) * Kx + k] = res[t];
-    }
+        return cmake<C>(val, T(0));
+    };
+    auto store = [&](int k, C v) { rows[(size_t)i * Kx + k] = v; };
+    auto slot = [&](int n) -> C& { return buf[fft_pad(n)]; };
+    fft_reg<C, false>(Kx, ilog2(Kx), t, tw, load, store, slot);
 }
 
+// Column kernels: a block holds cb adjacent columns, thread
+// (t, f) = (tid / cb, tid mod cb) so that a warp's global accesses cover cb
+// consecutive cells of each row; element n of column f sits in shared slot
+// pad(n) * cb + f.
+//
 // Forward column FFT over columns [c0, c0+cb): the only non-zero grid rows
 // are p2 = (i - ny/2) mod Ky for image rows i.
 template <typename T>
-__global__ void k_cols_fwd(const typename cplx_of<T>::type* __restrict__ rows,
+__global__ void __launch_bounds__(1024) k_cols_fwd(const typename cplx_of<T>::type* __restrict__ rows,
                            typename cplx_of<T>::type* __restrict__ grid,
                            const typename cplx_of<T>::type* __restrict__ tw, int ny, int Kx, int Ky,
                            int cb, const int* __restrict__ skip) {
     using C = typename cplx_of<T>::type;
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* b0 = reinterpret_cast<C*>(smem_raw);
-    C* b1 = b0 + cb * Ky;
-    const int c0 = blockIdx.x * cb;
-    const int tot = cb * Ky;
-    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-        int k = t / cb, f = t - k * cb;
-        int n2 = k < Ky / 2 ? k : k - Ky;
-        int i = n2 + ny / 2;
-        C v = cmake<C>(T(0), T(0));
-        if (i >= 0 && i < ny) v = rows[(size_t)i * Kx + c0 + f];
-        b0[t] = v;
-    }
-    __syncthreads();
-    C* res = fft_smem<C, false>(b0, b1, Ky, ilog2(Ky), cb, 1, cb, tw);
-    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-        int k = t / cb, f = t - k * cb;
-        grid[(size_t)k * Kx + c0 + f] = res[t];
-    }
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    const int t = threadIdx.x / cb, f = threadIdx.x - t * cb;
+    const int c = blockIdx.x * cb + f;
+    auto load = [&](int k) -> C {
+        const int i = (k < Ky / 2 ? k : k - Ky) + ny / 2;
+        return (i >= 0 && i < ny) ? rows[(size_t)i * Kx + c] : cmake<C>(T(0), T(0));
+    };
+    auto store = [&](int k, C v) { grid[(size_t)k * Kx + c] = v; };
+    auto slot = [&](int n) -> C& { return buf[fft_pad(n) * cb + f]; };
+    fft_reg<C, false>(Ky, ilog2(Ky), t, tw, load, store, slot);
 }
 
-// Inverse column FFT over columns [c0, c0+cb), keeping only the image rows.
+// Inverse column FFT over columns [c0, c0+cb) (grid optionally multiplied
+// elementwise by `mult` first), keeping only the image rows.
 template <typename T>
-__global__ void k_cols_inv(const typename cplx_of<T>::type* __restrict__ grid,
+__global__ void __launch_bounds__(1024) k_cols_inv(const typename cplx_of<T>::type* __restrict__ grid,
                            typename cplx_of<T>::type* __restrict__ rows,
                            const typename cplx_of<T>::type* __restrict__ tw, int ny, int Kx, int Ky,
                            int cb, const int* __restrict__ skip, const T* __restrict__ mult) {
     using C = typename cplx_of<T>::type;
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* b0 = reinterpret_cast<C*>(smem_raw);
-    C* b1 = b0 + cb * Ky;
-    const int c0 = blockIdx.x * cb;
-    const int tot = cb * Ky;
-    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-        int k = t / cb, f = t - k * cb;
-        size_t g = (size_t)k * Kx + c0 + f;
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    const int t = threadIdx.x / cb, f = threadIdx.x - t * cb;
+    const int c = blockIdx.x * cb + f;
+    auto load = [&](int k) -> C {
+        const size_t g = (size_t)k * Kx + c;
         C v = grid[g];
         if (mult) v = cscale(v, mult[g]);
-        b0[t] = v;
-    }
-    __syncthreads();
-    C* res = fft_smem<C, true>(b0, b1, Ky, ilog2(Ky), cb, 1, cb, tw);
-    for (int t = threadIdx.x; t < ny * cb; t += blockDim.x) {
-        int i = t / cb, f = t - i * cb;
-        int p2 = (i - ny / 2) & (Ky - 1);
-        rows[(size_t)i * Kx + c0 + f] = res[p2 * cb + f];
-    }
+        return v;
+    };
+    auto store = [&](int p2, C v) {
+        const int i = (p2 + ny / 2) & (Ky - 1);
+        if (i < ny) rows[(size_t)i * Kx + c] = v;
+    };
+    auto slot = [&](int n) -> C& { return buf[fft_pad(n) * cb + f]; };
+    fft_reg<C, true>(Ky, ilog2(Ky), t, tw, load, store, slot);
 }
 
 // Inverse row FFT of image rows [i0, i0+rb), then Z^T and S:
@@ -185,8 +252,8 @@ __global__ void k_cols_inv(const typename cplx_of<T>::type* __restrict__ grid,
 //   out_mode 1: real    out[i][j] = scale * s * Re v + add_coef * (add ? add[i][j] : 0)
 // With dot_part set (CG, out = A p, add = p) the kernel also forms p . A p
 // and, in the last block to finish, alpha = (r . r) / (p . A p).
-template <typename T>
-__global__ void k_rows_inv(const typename cplx_of<T>::type* __restrict__ rows, void* out,
+template <typename T, int MAXT>
+__global__ void __launch_bounds__(MAXT) k_rows_inv(const typename cplx_of<T>::type* __restrict__ rows, void* out,
                            const T* __restrict__ sx, const T* __restrict__ sy,
                            const typename cplx_of<T>::type* __restrict__ tw, int nx, int ny, int Kx,
                            int rb, T scale, int out_mode, const T* __restrict__ add, T add_coef,
@@ -194,36 +261,32 @@ __global__ void k_rows_inv(const typename cplx_of<T>::type* __restrict__ rows, v
     using C = typename cplx_of<T>::type;
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* b0 = reinterpret_cast<C*>(smem_raw);
-    C* b1 = b0 + rb * Kx;
-    const int i0 = blockIdx.x * rb;
-    const int tot = rb * Kx;
-    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-        int f = t / Kx, k = t - f * Kx;
-        b0[t] = rows[(size_t)(i0 + f) * Kx + k];
-    }
-    __syncthreads();
-    C* res = fft_smem<C, true>(b0, b1, Kx, ilog2(Kx), rb, Kx, 1, tw);
+    const int N8 = Kx >> 3;
+    const int f = threadIdx.x / N8, t = threadIdx.x - f * N8;
+    C* buf = reinterpret_cast<C*>(smem_raw) + f * fft_padded(Kx);
+    const int i = blockIdx.x * rb + f;
+    const T rs = sy[i] * scale;
     T dacc = 0;
-    for (int t = threadIdx.x; t < rb * nx; t += blockDim.x) {
-        int f = t / nx, j = t - f * nx;
-        int i = i0 + f;
-        int p1 = (j - nx / 2) & (Kx - 1);
-        C v = res[f * Kx + p1];
-        T s = sx[j] * sy[i] * scale;
-        size_t idx = (size_t)i * nx + j;
+    auto load = [&](int k) -> C { return rows[(size_t)i * Kx + k]; };
+    auto store = [&](int p1, C v) {
+        const int j = (p1 + nx / 2) & (Kx - 1);
+        if (j >= nx) return;
+        const T s = sx[j] * rs;
+        const size_t idx = (size_t)i * nx + j;
         if (out_mode == 0) {
             reinterpret_cast<C*>(out)[idx] = cscale(v, s);
         } else {
             T r = v.x * s;
             if (add) {
-                T a = add[idx];
+                const T a = add[idx];
                 r += add_coef * a;
                 dacc += a * r;
             }
             reinterpret_cast<T*>(out)[idx] = r;
         }
-    }
+    };
+    auto slot = [&](int n) -> C& { return buf[fft_pad(n)]; };
+    fft_reg<C, true>(Kx, ilog2(Kx), t, tw, load, store, slot);
     if (dot_part) {
         double b = block_sum((double)dacc);
         if (threadIdx.x == 0) dot_part[blockIdx.x] = b;
@@ -239,38 +302,35 @@ __global__ void k_rows_inv(const typename cplx_of<T>::type* __restrict__ rows, v
 }
 
 // Plain in-place 2-D FFT pieces (purify_fft2): full row pass / column pass.
+// In place is safe: every input element is read in the first stage, before
+// the first barrier, and every output is written in the last.
 template <typename T, bool INV>
-__global__ void k_rows_full(typename cplx_of<T>::type* grid, const typename cplx_of<T>::type* __restrict__ tw,
+__global__ void __launch_bounds__(1024) k_rows_full(typename cplx_of<T>::type* grid, const typename cplx_of<T>::type* __restrict__ tw,
                             int Kx, int rb) {
     using C = typename cplx_of<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* b0 = reinterpret_cast<C*>(smem_raw);
-    C* b1 = b0 + rb * Kx;
-    const size_t base = (size_t)blockIdx.x * rb * Kx;
-    for (int t = threadIdx.x; t < rb * Kx; t += blockDim.x) b0[t] = grid[base + t];
-    __syncthreads();
-    C* res = fft_smem<C, INV>(b0, b1, Kx, ilog2(Kx), rb, Kx, 1, tw);
-    for (int t = threadIdx.x; t < rb * Kx; t += blockDim.x) grid[base + t] = res[t];
+    const int N8 = Kx >> 3;
+    const int f = threadIdx.x / N8, t = threadIdx.x - f * N8;
+    C* buf = reinterpret_cast<C*>(smem_raw) + f * fft_padded(Kx);
+    C* row = grid + ((size_t)blockIdx.x * rb + f) * Kx;
+    auto load = [&](int k) -> C { return row[k]; };
+    auto store = [&](int k, C v) { row[k] = v; };
+    auto slot = [&](int n) -> C& { return buf[fft_pad(n)]; };
+    fft_reg<C, INV>(Kx, ilog2(Kx), t, tw, load, store, slot);
 }
 
 template <typename T, bool INV>
-__global__ void k_cols_full(typename cplx_of<T>::type* grid, const typename cplx_of<T>::type* __restrict__ tw,
+__global__ void __launch_bounds__(1024) k_cols_full(typename cplx_of<T>::type* grid, const typename cplx_of<T>::type* __restrict__ tw,
                             int Kx, int Ky, int cb) {
     using C = typename cplx_of<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* b0 = reinterpret_cast<C*>(smem_raw);
-    C* b1 = b0 + cb * Ky;
-    const int c0 = blockIdx.x * cb;
-    for (int t = threadIdx.x; t < cb * Ky; t += blockDim.x) {
-        int k = t / cb, f = t - k * cb;
-        b0[t] = grid[(size_t)k * Kx + c0 + f];
-    }
-    __syncthreads();
-    C* res = fft_smem<C, INV>(b0, b1, Ky, ilog2(Ky), cb, 1, cb, tw);
-    for (int t = threadIdx.x; t < cb * Ky; t += blockDim.x) {
-        int k = t / cb, f = t - k * cb;
-        grid[(size_t)k * Kx + c0 + f] = res[t];
-    }
+    C* buf = reinterpret_cast<C*>(smem_raw);
+    const int t = threadIdx.x / cb, f = threadIdx.x - t * cb;
+    const int c = blockIdx.x * cb + f;
+    auto load = [&](int k) -> C { return grid[(size_t)k * Kx + c]; };
+    auto store = [&](int k, C v) { grid[(size_t)k * Kx + c] = v; };
+    auto slot = [&](int n) -> C& { return buf[fft_pad(n) * cb + f]; };
+    fft_reg<C, INV>(Ky, ilog2(Ky), t, tw, load, store, slot);
 }
 
 // ------------------------------------------------------ gridding helpers
@@ -278,33 +338,6 @@ __device__ __forceinline__ void atomic_add_c(float2* a, float2 v) { atomicAdd(a,
 __device__ __forceinline__ void atomic_add_c(double2* a, double2 v) {
     atomicAdd(&a->x, v.x);
     atomicAdd(&a->y, v.y);
-}
-
-// Visibility pieces of one subproblem, flattened: a block loads the piece
-// starts and the running piece lengths into shared memory so that any thread
-// can map a flat index q to its visibility with a binary search.
-#define PURIFY_MAX_PIECES 128
-
-__device__ __forceinline__ int load_pieces(const int* __restrict__ piece_off, const int* __restrict__ piece_start,
-                                           const int* __restrict__ piece_len, int s, int* pst, int* pcum) {
-    const int p0 = piece_off[s], np = piece_off[s + 1] - p0;
-    if (threadIdx.x < np) pst[threadIdx.x] = piece_start[p0 + threadIdx.x];
-    if (threadIdx.x == 0) {
-        int acc = 0;
-        for (int k = 0; k < np; ++k) { pcum[k] = acc; acc += piece_len[p0 + k]; }
-        pcum[np] = acc;
-    }
-    return np;
-}
-
-// visibility of flat index q (0 <= q < pcum[np])
-__device__ __forceinline__ int flat_vis(const int* pst, const int* pcum, int np, int q) {
-    int lo = 0, hi = np - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (pcum[mid] <= q) lo = mid; else hi = mid - 1;
-    }
-    return pst[lo] + (q - pcum[lo]);
 }
 
 // G^H by cell runs. A block owns one subproblem: a grid tile and an explicit
@@ -469,16 +502,13 @@ template <typename T, int J>
 __global__ void __launch_bounds__(128)
 k_degrid_tile(const typename cplx_of<T>::type* __restrict__ grid, const T* __restrict__ us, const T* __restrict__ vs,
               AxisConst ax, AxisConst ay, KbPoly kp, double beta, double inv_i0beta, const int* __restrict__ perm,
-              const int* __restrict__ sub_bin, const int* __restrict__ piece_off,
-              const int* __restrict__ piece_start, const int* __restrict__ piece_len, int tile, int tiles_x,
-              typename cplx_of<T>::type* __restrict__ y, const int* __restrict__ skip) {
+              const int* __restrict__ sub_bin, const int* __restrict__ sub_off, const int* __restrict__ list,
+              int tile, int tiles_x, typename cplx_of<T>::type* __restrict__ y, const int* __restrict__ skip) {
     using C = typename cplx_of<T>::type;
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int PT = tile + J - 1;
     C* tl = reinterpret_cast<C*>(smem_raw);                   // [PT][PT]
-    int* pst = reinterpret_cast<int*>(tl + PT * PT);
-    int* pcum = pst + PURIFY_MAX_PIECES;
     const int s = blockIdx.x;
     const int bin = sub_bin[s];
     const int oy = (bin / tiles_x) * tile, ox = (bin % tiles_x) * tile;
@@ -487,11 +517,10 @@ k_degrid_tile(const typename cplx_of<T>::type* __restrict__ grid, const T* __res
         const int r = t / PT, c = t - r * PT;
         tl[t] = grid[(size_t)((oy + r) & (Ky - 1)) * Kx + ((ox + c) & (Kx - 1))];
     }
-    const int np = load_pieces(piece_off, piece_start, piece_len, s, pst, pcum);
     __syncthreads();
-    const int total = pcum[np];
+    const int q0 = sub_off[s], total = sub_off[s + 1] - q0;
     for (int q = threadIdx.x; q < total; q += blockDim.x) {
-        const int m = flat_vis(pst, pcum, np, q);
+        const int m = list[q0 + q];
         int kx0, ky0;
         T phx, phy;
         split_coord(us[m], ax, J, kx0, phx);
@@ -540,23 +569,28 @@ k_degrid_tile(const typename cplx_of<T>::type* __restrict__ grid, const T* __res
 }
 
 // ------------------------------------------------------------- launchers
-// FFT launch shapes: enough blocks to cover the 152 SMs about twice, one
-// radix-4 butterfly per thread per pass where possible.
+// FFT launch shapes: K / 8 threads per transform; transforms per block
+// (rows rb, columns cb) chosen so that a block has at most 512 threads and
+// the grid covers the 152 SMs about twice; the autotuner may override.
+static int fft_block_limit(int K, size_t cbytes) {
+    int nb = 1;
+    while (nb < 8 && 2 * nb * (K / 8) <= 512 && 2 * (size_t)nb * fft_padded(K) * cbytes <= 160 * 1024) nb *= 2;
+    return nb;
+}
 template <typename T> static int rows_per_block(int nrows, int K) {
-    size_t cbytes = sizeof(typename cplx_of<T>::type);
-    int rb = std::max(1, std::min(8, nrows / 256));
-    while (rb > 1 && (2 * (size_t)rb * K * cbytes > 160 * 1024 || nrows % rb)) rb >>= 1;
+    int rb = std::min(fft_block_limit(K, sizeof(typename cplx_of<T>::type)), std::max(1, nrows / 256));
+    while (rb > 1 && nrows % rb) rb >>= 1;
     return rb;
 }
-
 template <typename T> static int cols_per_block(int Ky, int Kx) {
-    size_t cbytes = sizeof(typename cplx_of<T>::type);
-    int cb = std::max(1, std::min(8, Kx / 256));
-    while (cb > 1 && (2 * (size_t)cb * Ky * cbytes > 160 * 1024 || Kx % cb)) cb >>= 1;
+    int cb = std::min(fft_block_limit(Ky, sizeof(typename cplx_of<T>::type)), std::max(1, Kx / 256));
+    while (cb > 1 && Kx % cb) cb >>= 1;
     return cb;
 }
-
-static int fft_threads(int nb, int n) { return std::max(64, std::min(256, nb * n / 4)); }
+bool fft_shape_ok(int nb, int K, int dtype) {
+    const size_t cbytes = dtype == PURIFY_F32 ? 8 : 16;
+    return nb * (K / 8) <= 1024 && (size_t)nb * fft_padded(K) * cbytes <= 160 * 1024;
+}
 
 template <typename K> static void set_smem(K kernel, size_t bytes) {
     if (bytes > 48 * 1024) PURIFY_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
@@ -568,10 +602,10 @@ static void rows_fwd_t(purify_plan* p, const void* x, double scale, void* pdir, 
     using C = typename cplx_of<T>::type;
     int rb = p->fft_rb > 0 ? p->fft_rb : rows_per_block<T>(p->ny, p->Kx);
     while (p->ny % rb) rb >>= 1;
-    size_t sm = 2 * (size_t)rb * p->Kx * sizeof(C);
+    size_t sm = (size_t)rb * fft_padded(p->Kx) * sizeof(C);
     set_smem(k_rows_fwd<T>, sm);
     Launch L(p, "fft_rows_fwd");
-    k_rows_fwd<T><<<p->ny / rb, fft_threads(rb, p->Kx), sm, p->stream>>>(
+    k_rows_fwd<T><<<p->ny / rb, rb * (p->Kx / 8), sm, p->stream>>>(
         (const T*)x, p->rows.as<C>(), corr ? p->sx.as<T>() : p->onesx.as<T>(),
         corr ? p->sy.as<T>() : p->onesy.as<T>(), p->twx.as<C>(), p->nx, p->ny, p->Kx,
         rb, (T)scale, (T*)pdir, (const T*)rvec, beta_dev, skip);
@@ -581,10 +615,10 @@ static void rows_fwd_t(purify_plan* p, const void* x, double scale, void* pdir, 
 template <typename T> static void cols_fwd_t(purify_plan* p, const int* skip) {
     using C = typename cplx_of<T>::type;
     int cb = p->fft_cb > 0 ? p->fft_cb : cols_per_block<T>(p->Ky, p->Kx);
-    size_t sm = 2 * (size_t)cb * p->Ky * sizeof(C);
+    size_t sm = (size_t)cb * fft_padded(p->Ky) * sizeof(C);
     set_smem(k_cols_fwd<T>, sm);
     Launch L(p, "fft_cols_fwd");
-    k_cols_fwd<T><<<p->Kx / cb, fft_threads(cb, p->Ky), sm, p->stream>>>(p->rows.as<C>(), p->grid.as<C>(), p->twy.as<C>(),
+    k_cols_fwd<T><<<p->Kx / cb, cb * (p->Ky / 8), sm, p->stream>>>(p->rows.as<C>(), p->grid.as<C>(), p->twy.as<C>(),
                                                       p->ny, p->Kx, p->Ky, cb, skip);
     L.done();
 }
@@ -592,10 +626,10 @@ template <typename T> static void cols_fwd_t(purify_plan* p, const int* skip) {
 template <typename T> static void cols_inv_t(purify_plan* p, const int* skip, const void* mult) {
     using C = typename cplx_of<T>::type;
     int cb = p->fft_cb > 0 ? p->fft_cb : cols_per_block<T>(p->Ky, p->Kx);
-    size_t sm = 2 * (size_t)cb * p->Ky * sizeof(C);
+    size_t sm = (size_t)cb * fft_padded(p->Ky) * sizeof(C);
     set_smem(k_cols_inv<T>, sm);
     Launch L(p, "fft_cols_inv");
-    k_cols_inv<T><<<p->Kx / cb, fft_threads(cb, p->Ky), sm, p->stream>>>(p->grid.as<C>(), p->rows.as<C>(), p->twy.as<C>(),
+    k_cols_inv<T><<<p->Kx / cb, cb * (p->Ky / 8), sm, p->stream>>>(p->grid.as<C>(), p->rows.as<C>(), p->twy.as<C>(),
                                                       p->ny, p->Kx, p->Ky, cb, skip, (const T*)mult);
     L.done();
 }
@@ -606,15 +640,17 @@ static void rows_inv_t(purify_plan* p, void* out, double scale, int out_mode, co
     using C = typename cplx_of<T>::type;
     int rb = p->fft_rb > 0 ? p->fft_rb : rows_per_block<T>(p->ny, p->Kx);
     while (p->ny % rb) rb >>= 1;
-    size_t sm = 2 * (size_t)rb * p->Kx * sizeof(C);
-    set_smem(k_rows_inv<T>, sm);
+    size_t sm = (size_t)rb * fft_padded(p->Kx) * sizeof(C);
+    const int nt = rb * (p->Kx / 8);
+    // the fused epilogue needs more than 64 registers: blocks of at most 512
+    // threads get them, 1024-thread blocks (8192-point rows) take spills
+    auto kern = nt <= 512 ? k_rows_inv<T, 512> : k_rows_inv<T, 1024>;
+    set_smem(kern, sm);
     Launch L(p, "fft_rows_inv");
-    k_rows_inv<T><<<p->ny / rb, fft_threads(rb, p->Kx), sm, p->stream>>>(p->rows.as<C>(), out,
-                                                      corr ? p->sx.as<T>() : p->onesx.as<T>(),
-                                                      corr ? p->sy.as<T>() : p->onesy.as<T>(),
-                                                      p->twx.as<C>(), p->nx, p->ny, p->Kx, rb, (T)scale,
-                                                      out_mode, (const T*)add, (T)add_coef, skip, dot_part,
-                                                      counters, scal);
+    kern<<<p->ny / rb, nt, sm, p->stream>>>(p->rows.as<C>(), out, corr ? p->sx.as<T>() : p->onesx.as<T>(),
+                                            corr ? p->sy.as<T>() : p->onesy.as<T>(), p->twx.as<C>(), p->nx, p->ny,
+                                            p->Kx, rb, (T)scale, out_mode, (const T*)add, (T)add_coef, skip,
+                                            dot_part, counters, scal);
     L.done();
 }
 
@@ -623,13 +659,13 @@ template <typename T, int J> static void degrid_tj(purify_plan* p, void* y, bool
     const GridWork& w = p->dwork;
     if (w.nsub == 0) return;
     const int tile = w.tile, PT = tile + J - 1;
-    size_t sm = sizeof(C) * (size_t)PT * PT + sizeof(int) * (2 * PURIFY_MAX_PIECES + 1);
+    size_t sm = sizeof(C) * (size_t)PT * PT;
     set_smem(k_degrid_tile<T, J>, sm);
     Launch L(p, "degrid");
     k_degrid_tile<T, J><<<w.nsub, 128, sm, p->stream>>>(
         p->grid.as<C>(), p->us.as<T>(), p->vs.as<T>(), p->ax, p->ay, p->kbp, p->beta, 1.0 / p->i0beta,
-        caller_order ? p->perm.as<int>() : nullptr, w.sub_bin.as<int>(), w.piece_off.as<int>(),
-        w.piece_start.as<int>(), w.piece_len.as<int>(), tile, w.tiles_x, (C*)y, skip);
+        caller_order ? p->perm.as<int>() : nullptr, w.sub_bin.as<int>(), w.sub_off.as<int>(), w.list.as<int>(),
+        tile, w.tiles_x, (C*)y, skip);
     L.done();
 }
 
@@ -753,20 +789,20 @@ void launch_phi_adj(purify_plan* p, const void* y, void* out, bool caller_order,
 template <typename T> static void fft2_t(purify_plan* p, void* grid, bool inverse) {
     using C = typename cplx_of<T>::type;
     int rb = rows_per_block<T>(p->Ky, p->Kx);
-    while (p->Ky % rb) rb >>= 1;
-    size_t smr = 2 * (size_t)rb * p->Kx * sizeof(C);
+    size_t smr = (size_t)rb * fft_padded(p->Kx) * sizeof(C);
     int cb = cols_per_block<T>(p->Ky, p->Kx);
-    size_t smc = 2 * (size_t)cb * p->Ky * sizeof(C);
+    size_t smc = (size_t)cb * fft_padded(p->Ky) * sizeof(C);
+    const int tr = rb * (p->Kx / 8), tc = cb * (p->Ky / 8);
     if (inverse) {
         set_smem(k_rows_full<T, true>, smr);
         set_smem(k_cols_full<T, true>, smc);
-        { Launch L(p, "fft_full_rows"); k_rows_full<T, true><<<p->Ky / rb, fft_threads(rb, p->Kx), smr, p->stream>>>((C*)grid, p->twx.as<C>(), p->Kx, rb); L.done(); }
-        { Launch L(p, "fft_full_cols"); k_cols_full<T, true><<<p->Kx / cb, fft_threads(cb, p->Ky), smc, p->stream>>>((C*)grid, p->twy.as<C>(), p->Kx, p->Ky, cb); L.done(); }
+        { Launch L(p, "fft_full_rows"); k_rows_full<T, true><<<p->Ky / rb, tr, smr, p->stream>>>((C*)grid, p->twx.as<C>(), p->Kx, rb); L.done(); }
+        { Launch L(p, "fft_full_cols"); k_cols_full<T, true><<<p->Kx / cb, tc, smc, p->stream>>>((C*)grid, p->twy.as<C>(), p->Kx, p->Ky, cb); L.done(); }
     } else {
         set_smem(k_rows_full<T, false>, smr);
         set_smem(k_cols_full<T, false>, smc);
-        { Launch L(p, "fft_full_rows"); k_rows_full<T, false><<<p->Ky / rb, fft_threads(rb, p->Kx), smr, p->stream>>>((C*)grid, p->twx.as<C>(), p->Kx, rb); L.done(); }
-        { Launch L(p, "fft_full_cols"); k_cols_full<T, false><<<p->Kx / cb, fft_threads(cb, p->Ky), smc, p->stream>>>((C*)grid, p->twy.as<C>(), p->Kx, p->Ky, cb); L.done(); }
+        { Launch L(p, "fft_full_rows"); k_rows_full<T, false><<<p->Ky / rb, tr, smr, p->stream>>>((C*)grid, p->twx.as<C>(), p->Kx, rb); L.done(); }
+        { Launch L(p, "fft_full_cols"); k_cols_full<T, false><<<p->Kx / cb, tc, smc, p->stream>>>((C*)grid, p->twy.as<C>(), p->Kx, p->Ky, cb); L.done(); }
     }
 }
 

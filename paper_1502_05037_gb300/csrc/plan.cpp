@@ -118,72 +118,14 @@ static void sort_hierarchical(purify_plan* p, const std::vector<int>& cx, const 
     }
 }
 
-void build_gridwork(purify_plan* p, const std::vector<int>& bin_sorted, int tile, GridWork& w) {
-    w.tile = tile;
-    w.tiles_x = p->Kx / tile;
-    w.tiles_y = p->Ky / tile;
-    const int nbins = w.tiles_x * w.tiles_y;
-    // pieces: maximal runs of one bin inside one block, grouped by bin
-    std::vector<std::vector<std::pair<int, int>>> runs(nbins);
-    const int64_t M = p->M;
-    int64_t m = 0;
-    for (int r = 0; r < p->R; ++r) {
-        m = p->offsets[r];
-        const int64_t end = p->offsets[r + 1];
-        while (m < end) {
-            int b = bin_sorted[m];
-            int64_t s = m;
-            while (m < end && bin_sorted[m] == b) ++m;
-            runs[b].push_back({(int)s, (int)(m - s)});
-        }
-    }
-    (void)M;
-    // visibilities per subproblem: about four subproblems per resident
-    // block on 152 SMs for large M, within [256, 4096]
-    int CMAX = (int)std::min<int64_t>(4096, std::max<int64_t>(256, p->M / (152 * 2 * 4)));
-    CMAX = (CMAX + 255) / 256 * 256;
-    const int PMAX = 128;   // pieces per subproblem (shared-memory table size)
-    std::vector<int> sub_bin, piece_off, pst, plen;
-    for (int b = 0; b < nbins; ++b) {
-        int in_sub = 0, pieces = 0;
-        bool open = false;
-        for (auto run : runs[b]) {
-            int s = run.first, len = run.second;
-            while (len > 0) {
-                if (!open || in_sub >= CMAX || pieces >= PMAX) {
-                    pieces = 0;
-                    sub_bin.push_back(b);
-                    piece_off.push_back((int)pst.size());
-                    in_sub = 0;
-                    open = true;
-                }
-                int take = std::min(len, CMAX - in_sub);
-                ++pieces;
-                pst.push_back(s);
-                plen.push_back(take);
-                s += take;
-                len -= take;
-                in_sub += take;
-            }
-        }
-    }
-    piece_off.push_back((int)pst.size());
-    w.nsub = (int)sub_bin.size();
-    w.npieces = (int)pst.size();
-    upload(w.sub_bin, sub_bin);
-    upload(w.piece_off, piece_off);
-    upload(w.piece_start, pst);
-    upload(w.piece_len, plen);
-}
-
-// Gridding work: every visibility of a tile (from all measurement blocks) in
-// first-tap-cell order, cut into subproblems of at most CMAX visibilities (a
-// multiple of the kernel's batch unit) and listed largest first, so that the
-// longest blocks are scheduled first. cell_order is the internal indices
+// Gridding/degridding work: every visibility of a tile (from all measurement
+// blocks) in first-tap-cell order, cut into subproblems of at most `units`
+// times the gridding kernel's batch unit and listed largest first, so that
+// the longest blocks are scheduled first. cell_order is the internal indices
 // sorted by first-tap cell (stable), so a stable pass by tile keeps the cell
 // order inside each tile.
 void build_gridlist(purify_plan* p, const std::vector<int>& bins, const std::vector<int>& cell_order, int tile,
-                    GridWork& w) {
+                    int units, GridWork& w) {
     w.tile = tile;
     w.tiles_x = p->Kx / tile;
     w.tiles_y = p->Ky / tile;
@@ -200,10 +142,8 @@ void build_gridlist(purify_plan* p, const std::vector<int>& bins, const std::vec
             order[pos[bins[m]]++] = m;
         }
     }
-    const int unit = grid_list_unit(p->dtype, p->J);
-    const int64_t want = M / (152 * 4);
-    const int64_t k = std::max<int64_t>(1, std::min<int64_t>(16, (want + unit / 2) / unit));
-    const int64_t CMAX = k * unit;
+    w.units = units;
+    const int64_t CMAX = (int64_t)units * grid_list_unit(p->dtype, p->J);
     struct Sub { int bin; int64_t start; int len; };
     std::vector<Sub> subs;
     for (int b = 0; b < nbins; ++b)
@@ -220,23 +160,23 @@ void build_gridlist(purify_plan* p, const std::vector<int>& bins, const std::vec
     }
     sub_off.push_back((int)q);
     w.nsub = (int)subs.size();
-    w.npieces = 0;
     upload(w.sub_bin, sub_bin);
     upload(w.sub_off, sub_off);
     upload(w.list, list);
 }
 
 // ---------------------------------------------------------------- autotuner
-// Launch shapes picked by timing on the plan's own data: the gridding tile
-// (work list rebuilt from the same hierarchical order) and the rows/columns
-// per block of the FFT passes. Results are cached per problem shape.
+// Launch shapes picked by timing on the plan's own data: the tile and the
+// subproblem size of gridding and of degridding (work lists rebuilt from the
+// same cell order) and the rows/columns per block of the FFT passes. Results
+// are cached per problem shape.
 struct TuneKey {
     int nx, ny, J, dtype, mlog, R;
     bool operator<(const TuneKey& o) const {
         return std::tie(nx, ny, J, dtype, mlog, R) < std::tie(o.nx, o.ny, o.J, o.dtype, o.mlog, o.R);
     }
 };
-struct TuneVal { int tile, dtile, rb, cb; };
+struct TuneVal { int tile, dtile, rb, cb, units, dunits; };
 static std::mutex g_tune_mutex;
 static std::map<TuneKey, TuneVal> g_tune_cache;
 
@@ -263,7 +203,11 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
     int mlog = 0;
     while ((int64_t(1) << (mlog + 1)) <= p->M) ++mlog;
     TuneKey key{p->nx, p->ny, p->J, p->dtype, mlog, std::min(p->R, 64)};
-    TuneVal val{p->work.tile, p->work.tile, 0, 0};
+    // default subproblem size: about four subproblems per SM's worth of
+    // visibilities, in batch units
+    const int64_t unit = grid_list_unit(p->dtype, p->J);
+    const int u0 = (int)std::max<int64_t>(1, std::min<int64_t>(16, (p->M / (152 * 4) + unit / 2) / unit));
+    TuneVal val{p->work.tile, p->work.tile, 0, 0, u0, u0};
     bool cached = false;
     if (tune) {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
@@ -284,14 +228,14 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
         // FFT launch shapes
         float best = 1e30f;
         for (int rb = 1; rb <= 8; rb *= 2) {
-            if (p->ny % rb || 2 * (size_t)rb * p->Kx * sizeof(C) > 160 * 1024) continue;
+            if (p->ny % rb || !fft_shape_ok(rb, p->Kx, p->dtype)) continue;
             p->fft_rb = rb;
             float ms = time_ms(p->stream, [&] { launch_scale_pad_rows(p, ximg, 1.0, nullptr, nullptr, nullptr, nullptr); }, 5);
             if (ms < best) { best = ms; val.rb = rb; }
         }
         best = 1e30f;
         for (int cb = 1; cb <= 8; cb *= 2) {
-            if (p->Kx % cb || 2 * (size_t)cb * p->Ky * sizeof(C) > 160 * 1024) continue;
+            if (p->Kx % cb || !fft_shape_ok(cb, p->Ky, p->dtype)) continue;
             p->fft_cb = cb;
             float ms = time_ms(p->stream, [&] { launch_cols_fwd(p, nullptr); }, 5);
             if (ms < best) { best = ms; val.cb = cb; }
@@ -303,12 +247,14 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
             float bg = 1e30f, bd = 1e30f;
             for (int t : cand) {
                 const std::vector<int> bins = bins_for(t);
-                build_gridlist(p, bins, cell_order, t, p->work);
-                build_gridwork(p, bins, t, p->dwork);
-                float mg = time_ms(p->stream, [&] { launch_grid(p, yv, false, nullptr); }, 3);
-                float md = time_ms(p->stream, [&] { launch_degrid(p, yv, false, nullptr); }, 3);
-                if (mg < bg) { bg = mg; val.tile = t; }
-                if (md < bd) { bd = md; val.dtile = t; }
+                for (int u : {1, 2, 4, 8}) {
+                    build_gridlist(p, bins, cell_order, t, u, p->work);
+                    build_gridlist(p, bins, cell_order, t, u, p->dwork);
+                    float mg = time_ms(p->stream, [&] { launch_grid(p, yv, false, nullptr); }, 3);
+                    float md = time_ms(p->stream, [&] { launch_degrid(p, yv, false, nullptr); }, 3);
+                    if (mg < bg) { bg = mg; val.tile = t; val.units = u; }
+                    if (md < bd) { bd = md; val.dtile = t; val.dunits = u; }
+                }
             }
         }
         std::lock_guard<std::mutex> lk(g_tune_mutex);
@@ -316,8 +262,8 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
     }
     p->fft_rb = val.rb;
     p->fft_cb = val.cb;
-    build_gridlist(p, bins_for(val.tile), cell_order, val.tile, p->work);
-    build_gridwork(p, bins_for(val.dtile), val.dtile, p->dwork);
+    build_gridlist(p, bins_for(val.tile), cell_order, val.tile, val.units, p->work);
+    build_gridlist(p, bins_for(val.dtile), cell_order, val.dtile, val.dunits, p->dwork);
 }
 
 template <typename T> static void finish_plan(purify_plan* p) {

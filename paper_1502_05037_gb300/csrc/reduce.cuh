@@ -38,17 +38,32 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Sum over the thread block (result valid in thread 0).
+// Sum over the first n lanes of a warp whose members are `mask` (result valid
+// in lane 0); lane 0's additions are those of warp_sum when n = 32.
+__device__ __forceinline__ double warp_sum_n(double v, unsigned mask, int n) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double w = __shfl_down_sync(mask, v, o);
+        if (lane + o < n) v += w;
+    }
+    return v;
+}
+
+// Sum over the thread block (result valid in thread 0); any block size,
+// including a partial last warp.
 __device__ __forceinline__ double block_sum(double v) {
     __shared__ double sh[32];
-    v = warp_sum(v);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    const int n = min(32, (int)blockDim.x - wid * 32);
+    v = n == 32 ? warp_sum(v) : warp_sum_n(v, n == 32 ? 0xffffffffu : ((1u << n) - 1u), n);
     __syncthreads();
     if (lane == 0) sh[wid] = v;
     __syncthreads();
     if (wid == 0) {
-        v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
-        v = warp_sum(v);
+        v = lane < nw ? sh[lane] : 0.0;
+        v = n == 32 ? warp_sum(v) : warp_sum_n(v, n == 32 ? 0xffffffffu : ((1u << n) - 1u), n);
     }
     return v;
 }
