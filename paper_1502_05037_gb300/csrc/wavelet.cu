@@ -40,18 +40,97 @@ template <typename T> __device__ __forceinline__ const FilterBank<T>& fbank();
 template <> __device__ __forceinline__ const FilterBank<float>& fbank<float>() { return c_bank_f; }
 template <> __device__ __forceinline__ const FilterBank<double>& fbank<double>() { return c_bank_d; }
 
-__device__ __forceinline__ int pmod(int a, int m) { int r = a % m; return r < 0 ? r + m : r; }
+// Tile geometry (compile time): analysis blocks own a DWT_T x DWT_T tile of
+// every sub-band; synthesis blocks own an (2 SYN_T) x (2 SYN_T) output tile.
+// Band sizes are powers of two, so periodic wrapping is a mask.
+static constexpr int DWT_T = 16;
+static constexpr int SYN_T = 8;
+static constexpr int SYN_GROUP = 64;   // threads per basis in a synthesis block
+
+// The filter taps of basis pb in registers (unused entries are zero).
+template <typename T, int L> struct Taps {
+    T h[L], g[L];
+    __device__ __forceinline__ void load(int pb) {
+        const FilterBank<T>& fb = fbank<T>();
+#pragma unroll
+        for (int n = 0; n < L; ++n) { h[n] = fb.h[pb][n]; g[n] = fb.g[pb][n]; }
+    }
+};
+
+// Runs STMT with the compile-time constant L equal to the filter length LEN
+// (2, 4, ..., 16).
+#define PURIFY_WITH_LENGTH(LEN, STMT)                                  \
+    switch (LEN) {                                                     \
+        case 2: { constexpr int L = 2; STMT; } break;                  \
+        case 4: { constexpr int L = 4; STMT; } break;                  \
+        case 6: { constexpr int L = 6; STMT; } break;                  \
+        case 8: { constexpr int L = 8; STMT; } break;                  \
+        case 10: { constexpr int L = 10; STMT; } break;                \
+        case 12: { constexpr int L = 12; STMT; } break;                \
+        case 14: { constexpr int L = 14; STMT; } break;                \
+        default: { constexpr int L = 16; STMT; } break;                \
+    }
 
 // ------------------------------------------------------------- analysis
+// One analysis level of basis pb on the sub-band tile at (ky0, kx0).
+template <typename T, int L>
+__device__ __forceinline__ void dwt_tile(const T* __restrict__ in, int src_ld, T* __restrict__ out, int nx,
+                                         T* __restrict__ llo, int h, int w, int ky0, int kx0, int pb, T inv_sqrt_q,
+                                         T* smem) {
+    constexpr int RS = 2 * DWT_T + L - 2, CS = 2 * DWT_T + L - 2;
+    Taps<T, L> f;
+    f.load(pb);
+    const int hs = h >> 1, wsub = w >> 1;
+    const int th = min(DWT_T, hs - ky0), tw = min(DWT_T, wsub - kx0);
+    const int Rin = 2 * th + L - 2, Cin = 2 * tw + L - 2;
+    T* tin = smem;                 // [RS][CS]
+    T* ta = tin + RS * CS;         // [RS][DWT_T] row low-pass
+    T* td = ta + RS * DWT_T;       // [RS][DWT_T] row high-pass
+    for (int t = threadIdx.x; t < Rin * CS; t += blockDim.x) {
+        const int r = t / CS, c = t - r * CS;
+        if (c < Cin) tin[t] = in[(size_t)((2 * ky0 + r) & (h - 1)) * src_ld + ((2 * kx0 + c) & (w - 1))];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < Rin * DWT_T; t += blockDim.x) {
+        const int r = t / DWT_T, k = t - r * DWT_T;
+        if (k < tw) {
+            const T* row = tin + r * CS + 2 * k;
+            T a = 0, d = 0;
+#pragma unroll
+            for (int n = 0; n < L; ++n) { a += f.h[n] * row[n]; d += f.g[n] * row[n]; }
+            ta[t] = a;
+            td[t] = d;
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < DWT_T * DWT_T; t += blockDim.x) {
+        const int ky = t / DWT_T, kx = t - ky * DWT_T;
+        if (ky >= th || kx >= tw) continue;
+        T ll = 0, lh = 0, hl = 0, hh = 0;
+#pragma unroll
+        for (int n = 0; n < L; ++n) {
+            const T av = ta[(2 * ky + n) * DWT_T + kx], dv = td[(2 * ky + n) * DWT_T + kx];
+            ll += f.h[n] * av; lh += f.g[n] * av;
+            hl += f.h[n] * dv; hh += f.g[n] * dv;
+        }
+        const int gy = ky0 + ky, gx = kx0 + kx;
+        if (llo) llo[(size_t)gy * wsub + gx] = ll;
+        else out[(size_t)gy * nx + gx] = ll * inv_sqrt_q;
+        out[(size_t)gy * nx + wsub + gx] = hl * inv_sqrt_q;
+        out[(size_t)(hs + gy) * nx + gx] = lh * inv_sqrt_q;
+        out[(size_t)(hs + gy) * nx + wsub + gx] = hh * inv_sqrt_q;
+    }
+}
+
+// One analysis level for every wavelet basis (blockIdx.z < nw) and, at the
+// first level, the Dirac plane (blockIdx.z == nw, a 2TH x 2TW image tile).
 template <typename T>
 __global__ void k_dwt_level(const T* __restrict__ src, int src_basis_stride, int src_ld,
                             T* __restrict__ coef, const int* __restrict__ planes, int N, int nx,
                             T* __restrict__ ll_out, int ll_basis_stride, int h, int w, int TH, int TW,
                             const int* __restrict__ pids, int nw, int dirac_plane, T inv_sqrt_q) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const FilterBank<T>& fb = fbank<T>();
     const int z = blockIdx.z;
-    const int hs = h >> 1, wsub = w >> 1;
     if (z == nw) {
         // Dirac plane: coef[dirac] = x / sqrt(q) over a 2TH x 2TW image tile
         const int r0 = blockIdx.y * 2 * TH, c0 = blockIdx.x * 2 * TW;
@@ -62,87 +141,68 @@ __global__ void k_dwt_level(const T* __restrict__ src, int src_basis_stride, int
         return;
     }
     const int pb = pids[z];              // db index 1..8
-    const int L = fb.len[pb];
-    const T* hf = fb.h[pb];
-    const T* gf = fb.g[pb];
     const T* in = src + (size_t)z * src_basis_stride;
-    const int ky0 = blockIdx.y * TH, kx0 = blockIdx.x * TW;
-    const int th = min(TH, hs - ky0), tw_ = min(TW, wsub - kx0);
-    const int Rin = 2 * th + L - 2, Cin = 2 * tw_ + L - 2;
-    T* tin = reinterpret_cast<T*>(smem_raw);            // Rin x Cin
-    T* ta = tin + Rin * Cin;                            // Rin x tw_  (row low-pass)
-    T* td = ta + Rin * tw_;                             // Rin x tw_  (row high-pass)
-    for (int t = threadIdx.x; t < Rin * Cin; t += blockDim.x) {
-        int r = t / Cin, c = t - r * Cin;
-        int gr = pmod(2 * ky0 + r, h), gc = pmod(2 * kx0 + c, w);
-        tin[t] = in[(size_t)gr * src_ld + gc];
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < Rin * tw_; t += blockDim.x) {
-        int r = t / tw_, k = t - r * tw_;
-        const T* row = tin + r * Cin + 2 * k;
-        T a = 0, d = 0;
-        for (int n = 0; n < L; ++n) { a += hf[n] * row[n]; d += gf[n] * row[n]; }
-        ta[t] = a;
-        td[t] = d;
-    }
-    __syncthreads();
     T* out = coef + (size_t)planes[z] * N;
-    for (int t = threadIdx.x; t < th * tw_; t += blockDim.x) {
-        int ky = t / tw_, kx = t - ky * tw_;
-        T ll = 0, lh = 0, hl = 0, hh = 0;
-        for (int n = 0; n < L; ++n) {
-            T av = ta[(2 * ky + n) * tw_ + kx], dv = td[(2 * ky + n) * tw_ + kx];
-            ll += hf[n] * av; lh += gf[n] * av;
-            hl += hf[n] * dv; hh += gf[n] * dv;
-        }
-        int gy = ky0 + ky, gx = kx0 + kx;
-        if (ll_out) ll_out[(size_t)z * ll_basis_stride + (size_t)gy * wsub + gx] = ll;
-        else out[(size_t)gy * nx + gx] = ll * inv_sqrt_q;
-        out[(size_t)gy * nx + wsub + gx] = hl * inv_sqrt_q;
-        out[(size_t)(hs + gy) * nx + gx] = lh * inv_sqrt_q;
-        out[(size_t)(hs + gy) * nx + wsub + gx] = hh * inv_sqrt_q;
-    }
+    T* llo = ll_out ? ll_out + (size_t)z * ll_basis_stride : nullptr;
+    const int ky0 = blockIdx.y * DWT_T, kx0 = blockIdx.x * DWT_T;
+    T* smem = reinterpret_cast<T*>(smem_raw);
+    PURIFY_WITH_LENGTH(fbank<T>().len[pb],
+                       (dwt_tile<T, L>(in, src_ld, out, nx, llo, h, w, ky0, kx0, pb, inv_sqrt_q, smem)));
+}
+
+// Shared memory of one analysis block (filters up to maxL taps).
+static size_t dwt_smem_bytes(int maxL, size_t tbytes) {
+    const size_t RS = 2 * DWT_T + maxL - 2;
+    return tbytes * (RS * RS + 2 * RS * DWT_T);
 }
 
 // ------------------------------------------------------------ synthesis
-// Reconstruct the 2TH x 2TW output tile at (oy0, ox0) of an h x w band for
-// basis pb from its four sub-bands. `ll` points at the low-pass sub-band
-// (row stride ll_ld); the three detail sub-bands are read from `det` (the
-// basis' coefficient plane, row stride nx). Result goes to acc (per-thread
-// registers, outputs t = threadIdx.x + i * blockDim.x).
-template <typename T, int PER>
-__device__ void synth_tile(const T* __restrict__ ll, int ll_ld, const T* __restrict__ det, int nx, int h, int w,
-                           int oy0, int ox0, int th2, int tw2, const T* hf, const T* gf, int L, T* smem,
-                           T (&acc)[PER]) {
+// Reconstruct the th2 x tw2 output tile at (oy0, ox0) of an h x w band for
+// basis pb from its four sub-bands, by the thread group (gt of gn threads).
+// `ll` points at the low-pass sub-band (row stride ll_ld); the three detail
+// sub-bands are read from `det` (the basis' coefficient plane, row stride
+// nx). Output t = gt + i * gn of the tile (row-major, stride tw2) is added to
+// acc[i].
+template <typename T, int L, int PER>
+__device__ __forceinline__ void synth_tile(const T* __restrict__ ll, int ll_ld, const T* __restrict__ det, int nx,
+                                           int h, int w, int oy0, int ox0, int th2, int tw2, int pb, T* smem, int gt,
+                                           int gn, T (&acc)[PER]) {
+    constexpr int KS = SYN_T + L / 2;            // sub-band tile stride (rows and columns)
+    Taps<T, L> f;
+    f.load(pb);
     const int hs = h >> 1, wsub = w >> 1;
     const int Kr = th2 / 2 + L / 2, Kc = tw2 / 2 + L / 2;
     const int ky_lo = oy0 / 2 - L / 2, kx_lo = ox0 / 2 - L / 2;
     T* sLL = smem;
-    T* sHL = sLL + Kr * Kc;   // row-detail, column-approx: (ky, wsub + kx)
-    T* sLH = sHL + Kr * Kc;   // row-approx, column-detail: (hs + ky, kx)
-    T* sHH = sLH + Kr * Kc;
-    T* sA = sHH + Kr * Kc;    // th2 x Kc: column synthesis of the row-approx half
-    T* sD = sA + th2 * Kc;    // th2 x Kc: column synthesis of the row-detail half
-    __syncthreads();
-    for (int t = threadIdx.x; t < Kr * Kc; t += blockDim.x) {
-        int r = t / Kc, c = t - r * Kc;
-        int ky = pmod(ky_lo + r, hs), kx = pmod(kx_lo + c, wsub);
+    T* sHL = sLL + KS * KS;   // row-detail, column-approx: (ky, wsub + kx)
+    T* sLH = sHL + KS * KS;   // row-approx, column-detail: (hs + ky, kx)
+    T* sHH = sLH + KS * KS;
+    T* sA = sHH + KS * KS;    // [2 SYN_T][KS]: column synthesis of the row-approx half
+    T* sD = sA + 2 * SYN_T * KS;
+    for (int t = gt; t < Kr * KS; t += gn) {
+        const int r = t / KS, c = t - r * KS;
+        if (c >= Kc) continue;
+        const int ky = (ky_lo + r) & (hs - 1), kx = (kx_lo + c) & (wsub - 1);
         sLL[t] = ll[(size_t)ky * ll_ld + kx];
         sHL[t] = det[(size_t)ky * nx + wsub + kx];
         sLH[t] = det[(size_t)(hs + ky) * nx + kx];
         sHH[t] = det[(size_t)(hs + ky) * nx + wsub + kx];
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < th2 * Kc; t += blockDim.x) {
-        int mr = t / Kc, c = t - mr * Kc;
-        int m = oy0 + mr;
+    for (int t = gt; t < th2 * KS; t += gn) {
+        const int mr = t / KS, c = t - mr * KS;
+        if (c >= Kc) continue;
+        // output row m = oy0 + mr takes the taps n of its parity; sub-band
+        // row (m - n) / 2 - ky_lo = (mr - par) / 2 + L / 2 - j for n = 2 j + par
+        const int par = mr & 1;
+        const int r0 = ((mr - par) >> 1) + L / 2;
         T a = 0, d = 0;
-        for (int n = (m & 1); n < L; n += 2) {
-            int e = m - n - 2 * ky_lo;   // even, in [1, th2 + L - 1]
-            int r = e >> 1;
-            a += hf[n] * sLL[r * Kc + c] + gf[n] * sLH[r * Kc + c];
-            d += hf[n] * sHL[r * Kc + c] + gf[n] * sHH[r * Kc + c];
+#pragma unroll
+        for (int j = 0; j < L / 2; ++j) {
+            const T hn = par ? f.h[2 * j + 1] : f.h[2 * j], gn_ = par ? f.g[2 * j + 1] : f.g[2 * j];
+            const int r = r0 - j;
+            a += hn * sLL[r * KS + c] + gn_ * sLH[r * KS + c];
+            d += hn * sHL[r * KS + c] + gn_ * sHH[r * KS + c];
         }
         sA[t] = a;
         sD[t] = d;
@@ -150,88 +210,109 @@ __device__ void synth_tile(const T* __restrict__ ll, int ll_ld, const T* __restr
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
-        int t = threadIdx.x + i * blockDim.x;
+        const int t = gt + i * gn;
         if (t < th2 * tw2) {
-            int mr = t / tw2, mc = t - mr * tw2;
-            int m = ox0 + mc;
-            T s = 0;
-            for (int n = (m & 1); n < L; n += 2) {
-                int c = (m - n - 2 * kx_lo) >> 1;
-                s += hf[n] * sA[mr * Kc + c] + gf[n] * sD[mr * Kc + c];
+            const int mr = t / tw2, mc = t - mr * tw2;
+            const int par = mc & 1;
+            const int c0 = ((mc - par) >> 1) + L / 2;
+            T sacc = 0;
+#pragma unroll
+            for (int j = 0; j < L / 2; ++j) {
+                const T hn = par ? f.h[2 * j + 1] : f.h[2 * j], gn_ = par ? f.g[2 * j + 1] : f.g[2 * j];
+                const int c = c0 - j;
+                sacc += hn * sA[mr * KS + c] + gn_ * sD[mr * KS + c];
             }
-            acc[i] += s;
+            acc[i] += sacc;
         }
     }
+    __syncthreads();
 }
 
-// One synthesis level for every wavelet basis (blockIdx.z): writes the
-// reconstructed h x w band of basis z into ll_out (row stride w).
+// Shared memory of one synthesis tile (filters up to maxL taps).
+static size_t synth_smem_elems(int maxL) {
+    const size_t KS = SYN_T + maxL / 2;
+    return 4 * KS * KS + 2 * (2 * SYN_T) * KS;
+}
+
+// One synthesis level for every wavelet basis (blockIdx.z), SYN_LEVEL_THREADS
+// threads per block: writes the reconstructed h x w band of basis z into
+// ll_out (row stride w).
+static constexpr int SYN_LEVEL_THREADS = 128;
 template <typename T>
-__global__ void k_idwt_level(const T* __restrict__ ll_in, int ll_basis_stride, int ll_ld,
-                             const T* __restrict__ coef, const int* __restrict__ planes, int N, int nx,
-                             T* __restrict__ ll_out, int out_basis_stride, int h, int w, int TH, int TW,
-                             const int* __restrict__ pids) {
+__global__ void __launch_bounds__(SYN_LEVEL_THREADS)
+k_idwt_level(const T* __restrict__ ll_in, int ll_basis_stride, int ll_ld, const T* __restrict__ coef,
+             const int* __restrict__ planes, int N, int nx, T* __restrict__ ll_out, int out_basis_stride, int h,
+             int w, const int* __restrict__ pids) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const FilterBank<T>& fb = fbank<T>();
-    constexpr int PER = 4;
+    constexpr int PER = (4 * SYN_T * SYN_T + SYN_LEVEL_THREADS - 1) / SYN_LEVEL_THREADS;
     const int z = blockIdx.z;
     const int pb = pids[z];
-    const int L = fb.len[pb];
-    const int oy0 = blockIdx.y * 2 * TH, ox0 = blockIdx.x * 2 * TW;
-    const int th2 = min(2 * TH, h - oy0), tw2 = min(2 * TW, w - ox0);
+    const int oy0 = blockIdx.y * 2 * SYN_T, ox0 = blockIdx.x * 2 * SYN_T;
+    const int th2 = min(2 * SYN_T, h - oy0), tw2 = min(2 * SYN_T, w - ox0);
     const T* det = coef + (size_t)planes[z] * N;
     const T* ll = ll_in ? ll_in + (size_t)z * ll_basis_stride : det;
     const int ld = ll_in ? ll_ld : nx;
     T acc[PER];
 #pragma unroll
     for (int i = 0; i < PER; ++i) acc[i] = 0;
-    synth_tile<T, PER>(ll, ld, det, nx, h, w, oy0, ox0, th2, tw2, fb.h[pb], fb.g[pb], L,
-                       reinterpret_cast<T*>(smem_raw), acc);
+    T* smem = reinterpret_cast<T*>(smem_raw);
+    PURIFY_WITH_LENGTH(fbank<T>().len[pb],
+                       (synth_tile<T, L, PER>(ll, ld, det, nx, h, w, oy0, ox0, th2, tw2, pb, smem,
+                                              (int)threadIdx.x, SYN_LEVEL_THREADS, acc)));
     T* out = ll_out + (size_t)z * out_basis_stride;
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
-        int t = threadIdx.x + i * blockDim.x;
+        const int t = threadIdx.x + i * SYN_LEVEL_THREADS;
         if (t < th2 * tw2) {
-            int mr = t / tw2, mc = t - mr * tw2;
+            const int mr = t / tw2, mc = t - mr * tw2;
             out[(size_t)(oy0 + mr) * w + ox0 + mc] = acc[i];
         }
     }
 }
 
 // Finest synthesis level summed over all wavelet bases plus the Dirac plane:
-// x = (c_dirac + sum_z W_z^T c_z) / sqrt(q). When `level_one_from_coef` is
-// set (L == 1) the low-pass bands come from the coefficient planes.
+// x = (c_dirac + sum_z W_z^T c_z) / sqrt(q). Thread group z (SYN_GROUP
+// threads) synthesises basis z's contribution to the block's output tile;
+// the partial tiles are then added in basis order. When `ll_in` is null
+// (L == 1) the low-pass bands come from the coefficient planes.
 template <typename T>
 __global__ void k_idwt_final(const T* __restrict__ ll_in, int ll_basis_stride, const T* __restrict__ coef,
-                             const int* __restrict__ planes, int N, int nx, int ny, int TH, int TW,
+                             const int* __restrict__ planes, int N, int nx, int ny, int group_elems,
                              const int* __restrict__ pids, int nw, int dirac_plane,
                              T inv_sqrt_q, T* __restrict__ x) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const FilterBank<T>& fb = fbank<T>();
-    constexpr int PER = 4;
-    const int oy0 = blockIdx.y * 2 * TH, ox0 = blockIdx.x * 2 * TW;
-    const int th2 = min(2 * TH, ny - oy0), tw2 = min(2 * TW, nx - ox0);
+    constexpr int PER = (4 * SYN_T * SYN_T + SYN_GROUP - 1) / SYN_GROUP;
+    const int oy0 = blockIdx.y * 2 * SYN_T, ox0 = blockIdx.x * 2 * SYN_T;
+    const int th2 = min(2 * SYN_T, ny - oy0), tw2 = min(2 * SYN_T, nx - ox0);
+    const int z = threadIdx.x / SYN_GROUP, gt = threadIdx.x - z * SYN_GROUP;
+    const size_t per_group = (size_t)group_elems;   // shared elements of one group's tile
+    T* part = reinterpret_cast<T*>(smem_raw);                       // [nw][4 SYN_T^2] partial tiles
+    T* gsm = part + (size_t)nw * 4 * SYN_T * SYN_T + (size_t)z * per_group;
     T acc[PER];
 #pragma unroll
     for (int i = 0; i < PER; ++i) acc[i] = 0;
-    for (int z = 0; z < nw; ++z) {
+    if (z < nw) {
         const int pb = pids[z];
         const T* det = coef + (size_t)planes[z] * N;
         const T* ll = ll_in ? ll_in + (size_t)z * ll_basis_stride : det;
         const int ld = ll_in ? (nx >> 1) : nx;
-        synth_tile<T, PER>(ll, ld, det, nx, ny, nx, oy0, ox0, th2, tw2, fb.h[pb], fb.g[pb], fb.len[pb],
-                           reinterpret_cast<T*>(smem_raw), acc);
-    }
+        PURIFY_WITH_LENGTH(fbank<T>().len[pb],
+                           (synth_tile<T, L, PER>(ll, ld, det, nx, ny, nx, oy0, ox0, th2, tw2, pb, gsm, gt,
+                                                  SYN_GROUP, acc)));
 #pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        int t = threadIdx.x + i * blockDim.x;
-        if (t < th2 * tw2) {
-            int mr = t / tw2, mc = t - mr * tw2;
-            size_t idx = (size_t)(oy0 + mr) * nx + ox0 + mc;
-            T v = acc[i];
-            if (dirac_plane >= 0) v += coef[(size_t)dirac_plane * N + idx];
-            x[idx] = v * inv_sqrt_q;
+        for (int i = 0; i < PER; ++i) {
+            const int t = gt + i * SYN_GROUP;
+            if (t < 4 * SYN_T * SYN_T) part[(size_t)z * 4 * SYN_T * SYN_T + t] = acc[i];
         }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < th2 * tw2; t += blockDim.x) {
+        const int mr = t / tw2, mc = t - mr * tw2;
+        T v = 0;
+        for (int zz = 0; zz < nw; ++zz) v += part[(size_t)zz * 4 * SYN_T * SYN_T + t];
+        const size_t idx = (size_t)(oy0 + mr) * nx + ox0 + mc;
+        if (dirac_plane >= 0) v += coef[(size_t)dirac_plane * N + idx];
+        x[idx] = v * inv_sqrt_q;
     }
 }
 
@@ -307,11 +388,10 @@ template <typename T> static void psi_adj_t(purify_plan* p, const void* xv, void
     for (int lev = 0; lev < p->levels; ++lev) {
         const bool last = lev == p->levels - 1;
         const int hs = h / 2, wsub = w / 2;
-        const int TH = std::min(16, hs), TW = std::min(16, wsub);
+        const int TH = std::min(DWT_T, hs), TW = std::min(DWT_T, wsub);
         int maxL = 2;
         for (int b : p->bases) if (b > 0) maxL = std::max(maxL, 2 * b);
-        const int Rin = 2 * TH + maxL - 2, Cin = 2 * TW + maxL - 2;
-        size_t sm = sizeof(T) * ((size_t)Rin * Cin + 2 * (size_t)Rin * TW);
+        const size_t sm = dwt_smem_bytes(maxL, sizeof(T));
         int zdim = wl.nw + ((lev == 0 && wl.dirac_plane >= 0) ? 1 : 0);
         dim3 g((wsub + TW - 1) / TW, (hs + TH - 1) / TH, zdim);
         T* llo = last ? nullptr : bufs[lev & 1];
@@ -341,27 +421,29 @@ template <typename T> static void psi_t(purify_plan* p, const void* cv, void* xv
     const T* ll_in = nullptr;  // coarsest level reads LL from the coefficients
     int ll_ld = p->nx;
     // levels L .. 2 reconstruct low-pass bands into scratch
+    const size_t group_elems = synth_smem_elems(maxL);
     for (int lev = p->levels - 1; lev >= 1 && wl.nw > 0; --lev) {
         const int h = p->ny >> lev, w = p->nx >> lev;
-        const int TH = std::min(8, h / 2), TW = std::min(8, w / 2);
-        const int Kr = TH + maxL / 2, Kc = TW + maxL / 2;
-        size_t sm = sizeof(T) * (4 * (size_t)Kr * Kc + 2 * (size_t)(2 * TH) * Kc);
-        dim3 g((w + 2 * TW - 1) / (2 * TW), (h + 2 * TH - 1) / (2 * TH), wl.nw);
+        const size_t sm = sizeof(T) * group_elems;
+        dim3 g((w + 2 * SYN_T - 1) / (2 * SYN_T), (h + 2 * SYN_T - 1) / (2 * SYN_T), wl.nw);
         T* out = bufs[lev & 1];
+        if (sm > 48 * 1024) PURIFY_CUDA(cudaFuncSetAttribute(k_idwt_level<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         Launch L(p, "idwt_level");
-        k_idwt_level<T><<<g, 256, sm, p->stream>>>(ll_in, llstride, ll_ld, c, plane_array(p), N, p->nx, out,
-                                                   llstride, h, w, TH, TW, pid_array(p));
+        k_idwt_level<T><<<g, SYN_LEVEL_THREADS, sm, p->stream>>>(ll_in, llstride, ll_ld, c, plane_array(p), N,
+                                                                 p->nx, out, llstride, h, w, pid_array(p));
         L.done();
         ll_in = out;
         ll_ld = w;
     }
-    const int TH = std::min(8, p->ny / 2), TW = std::min(8, p->nx / 2);
-    const int Kr = TH + maxL / 2, Kc = TW + maxL / 2;
-    size_t sm = sizeof(T) * (4 * (size_t)Kr * Kc + 2 * (size_t)(2 * TH) * Kc);
-    dim3 g((p->nx + 2 * TW - 1) / (2 * TW), (p->ny + 2 * TH - 1) / (2 * TH), 1);
+    // finest level: one thread group per basis, partial tiles summed in order
+    const size_t sm = sizeof(T) * ((size_t)wl.nw * 4 * SYN_T * SYN_T + (size_t)wl.nw * group_elems);
+    dim3 g((p->nx + 2 * SYN_T - 1) / (2 * SYN_T), (p->ny + 2 * SYN_T - 1) / (2 * SYN_T), 1);
+    const int threads = std::max(1, wl.nw) * SYN_GROUP;
+    if (sm > 48 * 1024) PURIFY_CUDA(cudaFuncSetAttribute(k_idwt_final<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     Launch L(p, "idwt_final");
-    k_idwt_final<T><<<g, 256, sm, p->stream>>>(ll_in, llstride, c, plane_array(p), N, p->nx, p->ny, TH, TW,
-                                               pid_array(p), wl.nw, wl.dirac_plane, inv_sqrt_q, x);
+    k_idwt_final<T><<<g, threads, sm, p->stream>>>(ll_in, llstride, c, plane_array(p), N, p->nx, p->ny,
+                                                   (int)group_elems, pid_array(p), wl.nw, wl.dirac_plane,
+                                                   inv_sqrt_q, x);
     L.done();
 }
 
@@ -465,9 +547,8 @@ static void psi_adj_static_t(const T* x, T* c, int nx, int ny, int levels, unsig
     for (int lev = 0; lev < levels; ++lev) {
         const bool last = lev == levels - 1;
         const int hs = h / 2, wsub = w / 2;
-        const int TH = std::min(16, hs), TW = std::min(16, wsub);
-        const int Rin = 2 * TH + maxL - 2, Cin = 2 * TW + maxL - 2;
-        size_t sm = sizeof(T) * ((size_t)Rin * Cin + 2 * (size_t)Rin * TW);
+        const int TH = std::min(DWT_T, hs), TW = std::min(DWT_T, wsub);
+        const size_t sm = dwt_smem_bytes(maxL, sizeof(T));
         int zdim = nw + ((lev == 0 && dirac_plane >= 0) ? 1 : 0);
         dim3 g((wsub + TW - 1) / TW, (hs + TH - 1) / TH, zdim);
         T* llo = last ? nullptr : bufs[lev & 1];
