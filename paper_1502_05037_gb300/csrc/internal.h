@@ -99,6 +99,10 @@ struct SdmmState {
     // captured iteration graph
     cudaStream_t gstream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // side stream of an iteration's visibility branch (forked and joined
+    // with events, so it is part of the captured graph)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int g_cg = -1;
     double g_gamma = 0, g_nu = 0;
@@ -110,6 +114,9 @@ struct SdmmState {
         if (ev_in) cudaEventDestroy(ev_in);
         if (ev_out) cudaEventDestroy(ev_out);
         if (gstream) cudaStreamDestroy(gstream);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (side) cudaStreamDestroy(side);
     }
     int64_t iters_done = 0;
     int64_t cg_total = 0;

@@ -180,27 +180,56 @@ struct TuneVal { int tile, dtile, rb, cb, units, dunits; };
 static std::mutex g_tune_mutex;
 static std::map<TuneKey, TuneVal> g_tune_cache;
 
-// Mean time of one call of f: two untimed calls, then the best of three
-// timed runs of `reps` calls each (the minimum discards runs disturbed by
-// clock ramps or other work on the device).
-static float time_ms(cudaStream_t s, const std::function<void()>& f, int reps) {
-    cudaEvent_t a, b;
-    PURIFY_CUDA(cudaEventCreate(&a));
-    PURIFY_CUDA(cudaEventCreate(&b));
-    f();
-    f();
+// Mean device time of one call of f, which launches work on p->stream: the
+// calls are captured `reps` times into a CUDA graph on a private stream (so
+// host launch overhead does not count), and the best of three graph launches
+// after an untimed one is taken (the minimum discards runs disturbed by clock
+// ramps or other work on the device).
+static float time_ms(purify_plan* p, const std::function<void()>& f, int reps) {
+    cudaStream_t user = p->stream, ts = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
     float best = 1e30f;
-    for (int trial = 0; trial < 3; ++trial) {
-        PURIFY_CUDA(cudaEventRecord(a, s));
-        for (int i = 0; i < reps; ++i) f();
-        PURIFY_CUDA(cudaEventRecord(b, s));
-        PURIFY_CUDA(cudaEventSynchronize(b));
-        float ms = 0.f;
-        PURIFY_CUDA(cudaEventElapsedTime(&ms, a, b));
-        best = std::min(best, ms / reps);
+    auto cleanup = [&] {
+        p->stream = user;
+        if (ge) cudaGraphExecDestroy(ge);
+        if (g) cudaGraphDestroy(g);
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+        if (ts) cudaStreamDestroy(ts);
+    };
+    try {
+        PURIFY_CUDA(cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking));
+        PURIFY_CUDA(cudaEventCreate(&a));
+        PURIFY_CUDA(cudaEventCreate(&b));
+        PURIFY_CUDA(cudaDeviceSynchronize());
+        p->stream = ts;
+        f();  // outside the capture: sets kernel attributes
+        PURIFY_CUDA(cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal));
+        try {
+            for (int i = 0; i < reps; ++i) f();
+        } catch (...) {
+            cudaStreamEndCapture(ts, &g);
+            throw;
+        }
+        PURIFY_CUDA(cudaStreamEndCapture(ts, &g));
+        PURIFY_CUDA(cudaGraphInstantiate(&ge, g, 0));
+        PURIFY_CUDA(cudaGraphLaunch(ge, ts));
+        for (int trial = 0; trial < 3; ++trial) {
+            PURIFY_CUDA(cudaEventRecord(a, ts));
+            PURIFY_CUDA(cudaGraphLaunch(ge, ts));
+            PURIFY_CUDA(cudaEventRecord(b, ts));
+            PURIFY_CUDA(cudaEventSynchronize(b));
+            float ms = 0.f;
+            PURIFY_CUDA(cudaEventElapsedTime(&ms, a, b));
+            best = std::min(best, ms / reps);
+        }
+    } catch (...) {
+        cleanup();
+        throw;
     }
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
+    cleanup();
     return best;
 }
 
@@ -235,19 +264,20 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
         C* yv = p->tmp_vis.as<C>();
         // bring the clocks up before the first candidate is timed
         for (int i = 0; i < 40; ++i) launch_cols_fwd(p, nullptr);
+        PURIFY_CUDA(cudaStreamSynchronize(p->stream));
         // FFT launch shapes
         float best = 1e30f;
         for (int rb = 1; rb <= 8; rb *= 2) {
             if (p->ny % rb || !fft_shape_ok(rb, p->Kx, p->dtype)) continue;
             p->fft_rb = rb;
-            float ms = time_ms(p->stream, [&] { launch_scale_pad_rows(p, ximg, 1.0, nullptr, nullptr, nullptr, nullptr); }, 5);
+            float ms = time_ms(p, [&] { launch_scale_pad_rows(p, ximg, 1.0, nullptr, nullptr, nullptr, nullptr); }, 10);
             if (ms < best) { best = ms; val.rb = rb; }
         }
         best = 1e30f;
         for (int cb = 1; cb <= 8; cb *= 2) {
             if (p->Kx % cb || !fft_shape_ok(cb, p->Ky, p->dtype)) continue;
             p->fft_cb = cb;
-            float ms = time_ms(p->stream, [&] { launch_cols_fwd(p, nullptr); }, 5);
+            float ms = time_ms(p, [&] { launch_cols_fwd(p, nullptr); }, 10);
             if (ms < best) { best = ms; val.cb = cb; }
         }
         p->fft_rb = val.rb;
@@ -260,8 +290,8 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
                 for (int u : {1, 2, 4, 8}) {
                     build_gridlist(p, bins, cell_order, t, u, p->work);
                     build_gridlist(p, bins, cell_order, t, u, p->dwork);
-                    float mg = time_ms(p->stream, [&] { launch_grid(p, yv, false, nullptr); }, 3);
-                    float md = time_ms(p->stream, [&] { launch_degrid(p, yv, false, nullptr); }, 3);
+                    float mg = time_ms(p, [&] { launch_grid(p, yv, false, nullptr); }, 5);
+                    float md = time_ms(p, [&] { launch_degrid(p, yv, false, nullptr); }, 5);
                     if (mg < bg) { bg = mg; val.tile = t; val.units = u; }
                     if (md < bd) { bd = md; val.dtile = t; val.dunits = u; }
                 }

@@ -330,6 +330,10 @@ template <typename T> struct Solver {
 
     double* scal() { return s.scal.as<double>(); }
     double* part() { return s.part.as<double>(); }
+    // the projection norms keep their partial sums apart from every other
+    // reduction, so that they can run beside the wavelet branch
+    static constexpr size_t kProjPart = 4096;
+    double* proj_part() { return s.part.as<double>() + kProjPart; }
     unsigned* ctr() { return s.counters.as<unsigned>(); }
     int* flags() { return reinterpret_cast<int*>(s.counters.as<unsigned>() + 16); }
 
@@ -351,7 +355,7 @@ template <typename T> struct Solver {
         s.Ap.alloc(sizeof(T) * N);
         s.xprev.alloc(sizeof(T) * N);
         s.scal.alloc(sizeof(double) * (S_BLOCKS + 2 * (size_t)p->R + 8));
-        s.part.alloc(sizeof(double) * std::max<size_t>(8192, 2 * (size_t)p->nchunks + 64));
+        s.part.alloc(sizeof(double) * (kProjPart + std::max<size_t>(8192, 2 * (size_t)p->nchunks + 64)));
         s.counters.alloc(sizeof(unsigned) * 32);
         // chunk_first: first chunk index of each block (host computes from offsets)
         std::vector<int> cf(p->R + 1, 0);
@@ -482,7 +486,7 @@ template <typename T> struct Solver {
         k_proj_norms<T><<<p->nchunks, RB, 0, p->stream>>>(
             s.v2.template as<C>(), with_z ? s.z2.template as<C>() : nullptr, s.ybar.template as<C>(),
             p->chunk_blk.as<int>(), p->chunk_beg.as<int>(), p->chunk_end.as<int>(), p->nchunks, p->R,
-            s.chunk_first.template as<int>(), part(), ctr(), scal());
+            s.chunk_first.template as<int>(), proj_part(), ctr(), scal());
         L.done();
     }
 
@@ -491,6 +495,41 @@ template <typename T> struct Solver {
     void iteration(int cg_iters) {
         T* x = s.x.template as<T>();
         const double inv_nu = 1.0 / s.nu;
+        // The visibility branch (f2: Phi x, block projections) and the
+        // wavelet branch (f1: Psi^dagger, prox, Psi; then f3) read only x and
+        // their own state, so the visibility branch runs on a side stream
+        // (joined before Phi^dagger). Eager timing runs keep one stream.
+        const bool fork = !timing_enabled(p);
+        cudaStream_t main_stream = p->stream;
+        if (fork) {
+            if (!s.side) {
+                PURIFY_CUDA(cudaStreamCreateWithFlags(&s.side, cudaStreamNonBlocking));
+                PURIFY_CUDA(cudaEventCreateWithFlags(&s.ev_fork, cudaEventDisableTiming));
+                PURIFY_CUDA(cudaEventCreateWithFlags(&s.ev_join, cudaEventDisableTiming));
+            }
+            PURIFY_CUDA(cudaEventRecord(s.ev_fork, main_stream));
+            PURIFY_CUDA(cudaStreamWaitEvent(s.side, s.ev_fork, 0));
+            p->stream = s.side;
+        }
+        try {
+            // f2
+            launch_phi(p, x, s.v2.p, false, inv_nu);
+            proj_norms(true);
+            {
+                Launch L(p, "proj_apply");
+                k_proj_apply<T><<<p->nchunks, RB, 0, p->stream>>>(s.v2.template as<C>(), s.z2.template as<C>(),
+                                                                 s.ybar.template as<C>(), p->chunk_blk.as<int>(),
+                                                                 p->chunk_beg.as<int>(), p->chunk_end.as<int>(),
+                                                                 s.eps.template as<double>(), scal(), p->R,
+                                                                 s.toeplitz ? 1 : 0);
+                L.done();
+            }
+            if (fork) PURIFY_CUDA(cudaEventRecord(s.ev_join, s.side));
+        } catch (...) {
+            p->stream = main_stream;
+            throw;
+        }
+        p->stream = main_stream;
         // f1
         launch_psi_adj(p, x, s.c1.p);
         {
@@ -501,18 +540,6 @@ template <typename T> struct Solver {
             L.done();
         }
         launch_psi(p, s.c1.p, s.Ap.p);  // Psi(s1 - z1) into Ap (scratch)
-        // f2
-        launch_phi(p, x, s.v2.p, false, inv_nu);
-        proj_norms(true);
-        {
-            Launch L(p, "proj_apply");
-            k_proj_apply<T><<<p->nchunks, RB, 0, p->stream>>>(s.v2.template as<C>(), s.z2.template as<C>(),
-                                                             s.ybar.template as<C>(), p->chunk_blk.as<int>(),
-                                                             p->chunk_beg.as<int>(), p->chunk_end.as<int>(),
-                                                             s.eps.template as<double>(), scal(), p->R,
-                                                             s.toeplitz ? 1 : 0);
-            L.done();
-        }
         // f3 and the image-space terms of the residual
         {
             Launch L(p, "positivity");
@@ -521,6 +548,7 @@ template <typename T> struct Solver {
                                                                     s.xprev.template as<T>(), p->N);
             L.done();
         }
+        if (fork) PURIFY_CUDA(cudaStreamWaitEvent(p->stream, s.ev_join, 0));
         // r = b - A x
         launch_phi_adj(p, s.v2.p, s.r.p, false, inv_nu, 1, s.addend.p);
         if (s.toeplitz) {
