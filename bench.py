@@ -127,6 +127,9 @@ def algorithmic_bytes(name: str, info, dtype_bytes: int = 4) -> float | None:
     table = {
         "degrid": 8 * M + c * M + c * Kx * Ky,
         "grid": 8 * M + c * M + c * Kx * Ky,
+        # G^H G of the forward grid: coordinates once, the grid read once and
+        # the output grid written once (no visibility vector)
+        "normal_gg": 8 * M + 2 * c * Kx * Ky,
         "fft_rows_fwd": dtype_bytes * N + c * ny * Kx,
         "fft_cols_fwd": c * ny * Kx + c * Kx * Ky,
         "fft_cols_inv": c * Kx * Ky + c * ny * Kx,
@@ -155,6 +158,7 @@ def algorithmic_flops(name: str, info) -> float | None:
     ny = int(round(np.sqrt(info.N * info.Ky / info.Kx)))
     table = {
         "grid": M * (weights + taps),
+        "normal_gg": M * (weights + 2 * taps),
         "degrid": M * (weights + taps),
         "fft_rows_fwd": ny * 5 * info.Kx * math.log2(info.Kx),
         "fft_rows_inv": ny * 5 * info.Kx * math.log2(info.Kx),
@@ -192,7 +196,8 @@ def ncu_traffic(kernel: str):
         return None
 
 
-KERNEL_SOURCE = {"degrid": "paper_1502_05037_gb300/csrc/nufft.cu", "grid": "paper_1502_05037_gb300/csrc/nufft.cu"}
+KERNEL_SOURCE = {"degrid": "paper_1502_05037_gb300/csrc/nufft.cu", "grid": "paper_1502_05037_gb300/csrc/nufft.cu",
+                 "normal_gg": "paper_1502_05037_gb300/csrc/nufft.cu"}
 
 
 # -------------------------------------------------------- problem set-up

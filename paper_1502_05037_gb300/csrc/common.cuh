@@ -45,6 +45,14 @@ struct KbPoly {
     float coef[PURIFY_MAX_J][PURIFY_MAX_DEG + 1];
 };
 
+// Per-visibility record of the run-ordered gridding work: the fractional
+// tap offsets of both axes and the internal visibility index.
+struct alignas(16) RunRecF { float phx, phy; int m, pad; };
+struct alignas(8) RunRecD { double phx, phy; int m, pad; };
+template <typename T> struct RunRecOf;
+template <> struct RunRecOf<float> { using type = RunRecF; };
+template <> struct RunRecOf<double> { using type = RunRecD; };
+
 // Split kappa = coord * K / (2 pi) into the first tap k0 = floor(kappa - J/2) + 1
 // (unwrapped) and phi = (kappa - J/2) - floor(kappa - J/2) in [0, 1), so that
 // the tap offsets are t_a = phi + J/2 - 1 - a. Float path: the product is

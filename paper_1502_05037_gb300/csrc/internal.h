@@ -73,6 +73,17 @@ struct GridWork {
     DevBuf sub_bin, sub_off, list;
 };
 
+// Run-ordered gridding work: a run is a set of visibilities sharing their
+// first-tap cell (at most a fixed length; longer cells are cut); runs are
+// sorted by length, longest first, and taken G = 32 / J at a time by a warp
+// (one run per lane group). Run r has cell[r] = (cy << 16) | cx, its records
+// rec[start[r] .. start[r] + len[r]); the run count is padded to a multiple
+// of G with empty runs.
+struct RunWork {
+    int nsets = 0, nruns = 0, G = 1;
+    DevBuf rec, cell, start, len;
+};
+
 // SDMM device state (allocated on first solve).
 struct SdmmState {
     bool ready = false;
@@ -147,9 +158,11 @@ struct purify_plan {
     int nchunks = 0;
     purify::GridWork work;            // gridding work list (tile of the G^H kernel)
     purify::GridWork dwork;           // degridding work list (tile of the G kernel)
+    purify::RunWork runs;             // run-ordered work of the fused normal operator
     int fft_rb = 0, fft_cb = 0;       // FFT rows / columns per block (0: heuristic)
     // workspaces
-    purify::DevBuf grid;              // Ky * Kx complex
+    purify::DevBuf grid;              // Ky * Kx complex (forward transform output)
+    purify::DevBuf gacc;              // Ky * Kx complex gridding output, then a 256-byte work counter
     purify::DevBuf rows;              // ny * Kx complex
     purify::DevBuf ll0, ll1;          // wavelet low-pass scratch (dtype, 8 * N / 4 each)
     purify::DevBuf stage_in, stage_out;  // host-pointer staging
@@ -176,7 +189,15 @@ void launch_scale_pad_rows(purify_plan* p, const void* x, double scale, void* pd
 void launch_cols_fwd(purify_plan* p, const int* skip_flag);
 void launch_degrid(purify_plan* p, void* y, bool caller_order, const int* skip_flag);
 void launch_grid(purify_plan* p, const void* y, bool caller_order, const int* skip_flag);
+// inverse column pass: reads the gridding output (gacc), or with `mult` the
+// forward grid multiplied elementwise by mult
 void launch_cols_inv(purify_plan* p, const int* skip_flag, const void* mult = nullptr);
+// G^H G of the grid (the oversampled image after F Z S): for every
+// visibility the J x J interpolation of the forward grid spread back with the
+// same weights, into gacc (the visibility values are never stored)
+void launch_normal_gg(purify_plan* p, const int* skip_flag);
+// G^H by runs (same output as launch_grid)
+void launch_grid_sets(purify_plan* p, const void* y, bool caller_order, const int* skip_flag);
 void launch_rows_inv_crop(purify_plan* p, void* out, double scale, int out_mode, const void* add,
                           double add_coef, const int* skip_flag, double* dot_part = nullptr,
                           unsigned* counters = nullptr, double* scal = nullptr, bool corr = true);

@@ -495,6 +495,133 @@ k_grid_runs(const typename cplx_of<T>::type* __restrict__ yin, const T* __restri
     }
 }
 
+// G^H (and the fused G^H G) by run sets. Each warp repeatedly takes the
+// next set of G = 32 / J runs from a global counter; lane group g (lanes
+// gJ .. gJ+J-1) walks run g of the set, which holds visibilities sharing one
+// first-tap cell (cx, cy). For each visibility lane b evaluates tap b of both
+// axes (wx[b], wy[b]) and the group exchanges the wx by shuffles; lane b
+// accumulates row b of the cell's J x J patch in registers,
+//   patch[b][a] += wx[a] * (wy[b] * y),
+// and the set's runs (sorted by length, so a set's runs are about equally
+// long) are flushed together with vector global reductions after the longest
+// run of the set. With FUSED the visibility value is not read but
+// interpolated from the forward grid X: lane b holds row b of X's J x J patch
+// at the run's cell (loaded once per run),
+//   y = sum_b wy[b] sum_a wx[a] X[cy + b][cx + a],
+// summed over the group by shuffles, so G^H G X needs no visibility vector.
+template <int DEG> __device__ __forceinline__ float kb_tap_poly(const float (&c)[DEG + 1], float phi) {
+    const float z = fmaf(2.0f, phi, -1.0f);
+    float acc = c[DEG];
+#pragma unroll
+    for (int i = DEG - 1; i >= 0; --i) acc = fmaf(acc, z, c[i]);
+    return acc;
+}
+__device__ __forceinline__ double kb_tap_exact(int J, int a, double beta, double inv_i0beta, double phi) {
+    const double t = phi + (0.5 * J - 1.0 - a);
+    const double r = 1.0 - (2.0 * t / J) * (2.0 * t / J);
+    return r > 0.0 ? bessel_i0_series(beta * sqrt(r)) * inv_i0beta : (r == 0.0 ? inv_i0beta : 0.0);
+}
+
+template <typename T, int J, int WARPS, bool FUSED>
+__global__ void __launch_bounds__(WARPS * 32)
+k_grid_sets(const typename cplx_of<T>::type* __restrict__ yin, const typename cplx_of<T>::type* __restrict__ X,
+            const typename RunRecOf<T>::type* __restrict__ recs, const int* __restrict__ run_cell,
+            const int* __restrict__ run_start, const int* __restrict__ run_len, int nsets,
+            const int* __restrict__ perm, KbPoly kp, double beta, double inv_i0beta, int Kx, int Ky,
+            typename cplx_of<T>::type* __restrict__ out, unsigned* __restrict__ next_set,
+            const int* __restrict__ skip) {
+    using C = typename cplx_of<T>::type;
+    using Rec = typename RunRecOf<T>::type;
+    constexpr int G = 32 / J;
+    constexpr int DEG = kb_poly_deg(J);
+    if (skip && *skip) return;
+    const int lane = threadIdx.x & 31;
+    const int g = lane / J, b = lane - g * J;
+    const bool act = g < G;
+    const int gg = act ? g : 0;
+    const int src = gg * J;
+    float cf[DEG + 1];
+#pragma unroll
+    for (int i = 0; i <= DEG; ++i) cf[i] = kp.coef[b][i];
+    for (;;) {
+        int set = 0;
+        if (lane == 0) set = (int)atomicAdd(next_set, 1u);
+        set = __shfl_sync(0xffffffffu, set, 0);
+        if (set >= nsets) break;
+        const int r = set * G + gg;
+        const int len = act ? run_len[r] : 0;
+        const int lmax = run_len[set * G];   // the set's longest run
+        const unsigned cell = (unsigned)run_cell[r];
+        const int start = run_start[r];
+        const int cx = (int)(cell & 0xFFFFu), cy = (int)(cell >> 16);
+        const size_t rowoff = (size_t)((cy + b) & (Ky - 1)) * Kx;
+        T xr[J], xi[J];
+        if constexpr (FUSED) {
+#pragma unroll
+            for (int a = 0; a < J; ++a) {
+                C v = cmake<C>(T(0), T(0));
+                if (len > 0) v = X[rowoff + ((cx + a) & (Kx - 1))];
+                xr[a] = v.x;
+                xi[a] = v.y;
+            }
+        }
+        T ar[J], ai[J];
+#pragma unroll
+        for (int a = 0; a < J; ++a) ar[a] = ai[a] = T(0);
+        Rec rn{};
+        if (len > 0) rn = recs[start];
+        for (int k = 0; k < lmax; ++k) {
+            const Rec rc = rn;
+            if (k + 1 < len) rn = recs[start + k + 1];
+            const bool valid = k < len;
+            C yv = cmake<C>(T(0), T(0));
+            if constexpr (!FUSED) {
+                if (valid) yv = yin[perm ? perm[rc.m] : rc.m];
+            }
+            T wxb, wyb;
+            if constexpr (sizeof(T) == 4) {
+                wxb = kb_tap_poly<DEG>(cf, rc.phx);
+                wyb = kb_tap_poly<DEG>(cf, rc.phy);
+            } else {
+                wxb = kb_tap_exact(J, b, beta, inv_i0beta, rc.phx);
+                wyb = kb_tap_exact(J, b, beta, inv_i0beta, rc.phy);
+            }
+            T wx[J];
+#pragma unroll
+            for (int a = 0; a < J; ++a) wx[a] = __shfl_sync(0xffffffffu, wxb, src + a);
+            if constexpr (FUSED) {
+                T rx = 0, ry = 0;
+#pragma unroll
+                for (int a = 0; a < J; ++a) {
+                    rx = fma(wx[a], xr[a], rx);
+                    ry = fma(wx[a], xi[a], ry);
+                }
+                const T tr = wyb * rx, ti = wyb * ry;
+                T sr = 0, si = 0;
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    sr += __shfl_sync(0xffffffffu, tr, src + j);
+                    si += __shfl_sync(0xffffffffu, ti, src + j);
+                }
+                yv = cmake<C>(sr, si);
+            }
+            if (valid) {
+                const T zr = wyb * yv.x, zi = wyb * yv.y;
+#pragma unroll
+                for (int a = 0; a < J; ++a) {
+                    ar[a] = fma(wx[a], zr, ar[a]);
+                    ai[a] = fma(wx[a], zi, ai[a]);
+                }
+            }
+        }
+        if (len > 0) {
+            C* row = out + rowoff;
+#pragma unroll
+            for (int a = 0; a < J; ++a) atomic_add_c(row + ((cx + a) & (Kx - 1)), cmake<C>(ar[a], ai[a]));
+        }
+    }
+}
+
 // G with the tile staged in shared memory: a block owns one subproblem,
 // copies the tile plus its (J-1) halo from the grid, then every thread
 // interpolates visibilities of the subproblem from the shared copy.
@@ -629,7 +756,9 @@ template <typename T> static void cols_inv_t(purify_plan* p, const int* skip, co
     size_t sm = (size_t)cb * fft_padded(p->Ky) * sizeof(C);
     set_smem(k_cols_inv<T>, sm);
     Launch L(p, "fft_cols_inv");
-    k_cols_inv<T><<<p->Kx / cb, cb * (p->Ky / 8), sm, p->stream>>>(p->grid.as<C>(), p->rows.as<C>(), p->twy.as<C>(),
+    // the adjoint reads the gridding output; the circulant path the forward grid
+    const C* src = mult ? p->grid.as<C>() : p->gacc.as<C>();
+    k_cols_inv<T><<<p->Kx / cb, cb * (p->Ky / 8), sm, p->stream>>>(src, p->rows.as<C>(), p->twy.as<C>(),
                                                       p->ny, p->Kx, p->Ky, cb, skip, (const T*)mult);
     L.done();
 }
@@ -689,7 +818,7 @@ template <typename T, int J>
 static void grid_tj(purify_plan* p, const void* y, bool caller_order, const int* skip) {
     using C = typename cplx_of<T>::type;
     constexpr int W = grid_warps<T>();
-    PURIFY_CUDA(cudaMemsetAsync(p->grid.p, 0, p->grid.bytes, p->stream));
+    PURIFY_CUDA(cudaMemsetAsync(p->gacc.p, 0, p->gacc.bytes, p->stream));
     if (p->work.nsub == 0) return;
     const int tile = p->work.tile;
     const int S = grid_row_stride(tile, J);
@@ -699,7 +828,7 @@ static void grid_tj(purify_plan* p, const void* y, bool caller_order, const int*
     k_grid_runs<T, J, W><<<p->work.nsub, W * 32, sm, p->stream>>>(
         (const C*)y, p->us.as<T>(), p->vs.as<T>(), p->ax, p->ay, p->kbp, p->beta, 1.0 / p->i0beta,
         caller_order ? p->perm.as<int>() : nullptr, p->work.sub_bin.as<int>(), p->work.sub_off.as<int>(),
-        p->work.list.as<int>(), tile, p->work.tiles_x, S, p->grid.as<C>(), skip);
+        p->work.list.as<int>(), tile, p->work.tiles_x, S, p->gacc.as<C>(), skip);
     L.done();
 }
 
@@ -726,6 +855,49 @@ template <int J> static void degrid_f(purify_plan* p, void* y, bool c, const int
 template <int J> static void degrid_d(purify_plan* p, void* y, bool c, const int* s) { degrid_tj<double, J>(p, y, c, s); }
 template <int J> static void grid_f(purify_plan* p, const void* y, bool c, const int* s) { grid_tj<float, J>(p, y, c, s); }
 template <int J> static void grid_d(purify_plan* p, const void* y, bool c, const int* s) { grid_tj<double, J>(p, y, c, s); }
+
+
+// Run-set launches: a persistent grid of 8-warp blocks (four per SM, or
+// fewer when there is less work) taking sets from the counter stored after
+// the gridding output (cleared by the same memset).
+template <typename T, int J, bool FUSED>
+static void grid_sets_tj(purify_plan* p, const void* y, bool caller_order, const int* skip) {
+    using C = typename cplx_of<T>::type;
+    constexpr int W = 8;
+    PURIFY_CUDA(cudaMemsetAsync(p->gacc.p, 0, p->gacc.bytes, p->stream));
+    const RunWork& rw = p->runs;
+    if (rw.nsets == 0) return;
+    static int per_sm = 0;   // resident blocks per SM of this instantiation
+    if (per_sm == 0) {
+        PURIFY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_sets<T, J, W, FUSED>, W * 32, 0));
+        per_sm = std::max(1, per_sm);
+    }
+    int sms = 0, dev = 0;
+    PURIFY_CUDA(cudaGetDevice(&dev));
+    PURIFY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = std::max(1, std::min(sms * per_sm, (rw.nsets + W - 1) / W));
+    unsigned* ctr = reinterpret_cast<unsigned*>(static_cast<unsigned char*>(p->gacc.p) +
+                                                sizeof(C) * (size_t)p->Kx * p->Ky);
+    Launch L(p, FUSED ? "normal_gg" : "grid");
+    k_grid_sets<T, J, W, FUSED><<<blocks, W * 32, 0, p->stream>>>(
+        (const C*)y, p->grid.as<C>(), rw.rec.as<typename RunRecOf<T>::type>(), rw.cell.as<int>(),
+        rw.start.as<int>(), rw.len.as<int>(), rw.nsets, caller_order ? p->perm.as<int>() : nullptr, p->kbp,
+        p->beta, 1.0 / p->i0beta, p->Kx, p->Ky, p->gacc.as<C>(), ctr, skip);
+    L.done();
+}
+template <int J> static void normal_f(purify_plan* p, const int* s) { grid_sets_tj<float, J, true>(p, nullptr, false, s); }
+template <int J> static void normal_d(purify_plan* p, const int* s) { grid_sets_tj<double, J, true>(p, nullptr, false, s); }
+template <int J> static void gsets_f(purify_plan* p, const void* y, bool c, const int* s) { grid_sets_tj<float, J, false>(p, y, c, s); }
+template <int J> static void gsets_d(purify_plan* p, const void* y, bool c, const int* s) { grid_sets_tj<double, J, false>(p, y, c, s); }
+
+void launch_normal_gg(purify_plan* p, const int* skip) {
+    if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, normal_f, p, skip); }
+    else { PURIFY_J_DISPATCH(p->J, normal_d, p, skip); }
+}
+void launch_grid_sets(purify_plan* p, const void* y, bool caller_order, const int* skip) {
+    if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, gsets_f, p, y, caller_order, skip); }
+    else { PURIFY_J_DISPATCH(p->J, gsets_d, p, y, caller_order, skip); }
+}
 
 template <int J> static int max_tile_f() {
     int t = 64;

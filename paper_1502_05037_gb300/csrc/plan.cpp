@@ -306,6 +306,55 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
     build_gridlist(p, bins_for(val.dtile), cell_order, val.dtile, val.dunits, p->dwork);
 }
 
+// Run-ordered work (see RunWork): runs of equal first-tap cell in the cell
+// order, cut at kRunMax visibilities, sorted by length (longest first,
+// stable), padded to a multiple of G; records in run order.
+static const int kRunMax = 48;
+template <typename T>
+static void build_runwork(purify_plan* p, const std::vector<T>& us, const std::vector<T>& vs,
+                          const std::vector<int>& scx, const std::vector<int>& scy, const std::vector<int>& cell_order) {
+    using Rec = typename RunRecOf<T>::type;
+    struct Run { int cell; int64_t first; int len; };
+    std::vector<Run> runs;
+    const int64_t M = p->M;
+    int64_t i = 0;
+    while (i < M) {
+        const int m0 = cell_order[i];
+        int64_t j = i + 1;
+        while (j < M && j - i < kRunMax && scx[cell_order[j]] == scx[m0] && scy[cell_order[j]] == scy[m0]) ++j;
+        runs.push_back({(scy[m0] << 16) | scx[m0], i, (int)(j - i)});
+        i = j;
+    }
+    std::stable_sort(runs.begin(), runs.end(), [](const Run& a, const Run& b) { return a.len > b.len; });
+    const int G = 32 / p->J;
+    const size_t nr = (runs.size() + G - 1) / G * G;
+    std::vector<int> cell(nr, 0), start(nr, 0), len(nr, 0);
+    std::vector<Rec> rec(M);
+    int64_t q = 0;
+    for (size_t r = 0; r < runs.size(); ++r) {
+        cell[r] = runs[r].cell;
+        start[r] = (int)q;
+        len[r] = runs[r].len;
+        for (int k = 0; k < runs[r].len; ++k) {
+            const int m = cell_order[runs[r].first + k];
+            int kx0, ky0;
+            Rec e{};
+            split_coord(us[m], p->ax, p->J, kx0, e.phx);
+            split_coord(vs[m], p->ay, p->J, ky0, e.phy);
+            e.m = m;
+            rec[q++] = e;
+        }
+    }
+    p->runs.G = G;
+    p->runs.nruns = (int)nr;
+    p->runs.nsets = (int)(nr / G);
+    upload(p->runs.rec, rec);
+    upload(p->runs.cell, cell);
+    upload(p->runs.start, start);
+    upload(p->runs.len, len);
+    p->workspace_bytes += (int64_t)(p->runs.rec.bytes + p->runs.cell.bytes + p->runs.start.bytes + p->runs.len.bytes);
+}
+
 template <typename T> static void finish_plan(purify_plan* p) {
     using C = typename cplx_of<T>::type;
     const purify_plan_desc& d = p->desc;
@@ -378,12 +427,13 @@ template <typename T> static void finish_plan(purify_plan* p) {
     // workspaces
     const int nw = z;
     p->grid.alloc(sizeof(C) * (size_t)p->Kx * p->Ky);
+    p->gacc.alloc(sizeof(C) * (size_t)p->Kx * p->Ky + 256);
     p->rows.alloc(sizeof(C) * (size_t)p->ny * p->Kx);
     p->ll0.alloc(sizeof(T) * std::max<size_t>(1, (size_t)nw * p->N / 4));
     p->ll1.alloc(sizeof(T) * std::max<size_t>(1, (size_t)nw * p->N / 4));
     p->tmp_img.alloc(sizeof(C) * (size_t)p->N);
     p->tmp_vis.alloc(sizeof(C) * (size_t)p->M);
-    p->workspace_bytes = (int64_t)(p->grid.bytes + p->rows.bytes + p->ll0.bytes + p->ll1.bytes + p->tmp_img.bytes +
+    p->workspace_bytes = (int64_t)(p->grid.bytes + p->gacc.bytes + p->rows.bytes + p->ll0.bytes + p->ll1.bytes + p->tmp_img.bytes +
                                    p->tmp_vis.bytes + p->us.bytes + p->vs.bytes + p->perm.bytes);
     // internal indices ordered by first-tap cell (stable counting sort)
     std::vector<int> cell_order(p->M);
@@ -395,6 +445,7 @@ template <typename T> static void finish_plan(purify_plan* p) {
         for (int64_t i = 0; i < p->M; ++i) cell_order[pos[(int64_t)scy[i] * p->Kx + scx[i]]++] = (int)i;
     }
     autotune<T>(p, cand, bins_for, cell_order, d.tile == 0);
+    build_runwork<T>(p, us, vs, scx, scy, cell_order);
 }
 
 purify_plan* create_plan(const purify_plan_desc* d) {

@@ -576,8 +576,7 @@ template <typename T> struct Solver {
             // p = r + beta p fused into the first FFT pass, then A p
             launch_scale_pad_rows(p, nullptr, inv_nu, s.p.p, s.r.p, scal() + S_BETA, skip);
             launch_cols_fwd(p, skip);
-            launch_degrid(p, p->tmp_vis.p, false, skip);
-            launch_grid(p, p->tmp_vis.p, false, skip);
+            launch_normal_gg(p, skip);
             launch_cols_inv(p, skip);
             // A p = 2 p + Re Phi^H Phi p / nu^2, with p . A p and alpha fused in
             launch_rows_inv_crop(p, s.Ap.p, inv_nu, 1, s.p.p, 2.0, skip, part(), ctr(), scal());
