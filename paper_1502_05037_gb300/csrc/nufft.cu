@@ -495,20 +495,25 @@ k_grid_runs(const typename cplx_of<T>::type* __restrict__ yin, const T* __restri
     }
 }
 
-// G^H (and the fused G^H G) by run sets. Each warp repeatedly takes the
-// next set of G = 32 / J runs from a global counter; lane group g (lanes
-// gJ .. gJ+J-1) walks run g of the set, which holds visibilities sharing one
-// first-tap cell (cx, cy). For each visibility lane b evaluates tap b of both
-// axes (wx[b], wy[b]) and the group exchanges the wx by shuffles; lane b
-// accumulates row b of the cell's J x J patch in registers,
+// G^H (and the fused G^H G) by run sets. Warp w of the grid takes sets
+// w, 2W - 1 - w, 2W + w, ... (W warps in all; sets are sorted by length, so
+// the alternating order balances the warps); lane group g (lanes gJ ..
+// gJ+J-1) walks run g of the set, which holds visibilities sharing one
+// first-tap cell (cx, cy). Lane b of a group loads every J-th record of the
+// run (two batches of J records in flight) and the group reads them by
+// shuffles. For each visibility lane b evaluates tap b of both axes (wx[b],
+// wy[b]) and the group exchanges the wx through a warp-private shared-memory
+// slot (one store, vector loads: lighter on the shuffle pipe than J
+// shuffles, double-buffered by step parity); lane b accumulates row b
+// of the cell's J x J patch in registers,
 //   patch[b][a] += wx[a] * (wy[b] * y),
-// and the set's runs (sorted by length, so a set's runs are about equally
-// long) are flushed together with vector global reductions after the longest
-// run of the set. With FUSED the visibility value is not read but
-// interpolated from the forward grid X: lane b holds row b of X's J x J patch
-// at the run's cell (loaded once per run),
+// and the set's runs (about equally long) are flushed together with vector
+// global reductions after the longest run of the set. With FUSED the
+// visibility value is not read but interpolated from the forward grid X:
+// lane b holds row b of X's J x J patch at the run's cell,
 //   y = sum_b wy[b] sum_a wx[a] X[cy + b][cx + a],
-// summed over the group by shuffles, so G^H G X needs no visibility vector.
+// summed over the group (in b order) through the same kind of shared slot,
+// so G^H G X needs no visibility vector.
 template <int DEG> __device__ __forceinline__ float kb_tap_poly(const float (&c)[DEG + 1], float phi) {
     const float z = fmaf(2.0f, phi, -1.0f);
     float acc = c[DEG];
@@ -528,8 +533,7 @@ k_grid_sets(const typename cplx_of<T>::type* __restrict__ yin, const typename cp
             const typename RunRecOf<T>::type* __restrict__ recs, const int* __restrict__ run_cell,
             const int* __restrict__ run_start, const int* __restrict__ run_len, int nsets,
             const int* __restrict__ perm, KbPoly kp, double beta, double inv_i0beta, int Kx, int Ky,
-            typename cplx_of<T>::type* __restrict__ out, unsigned* __restrict__ next_set,
-            const int* __restrict__ skip) {
+            typename cplx_of<T>::type* __restrict__ out, const int* __restrict__ skip) {
     using C = typename cplx_of<T>::type;
     using Rec = typename RunRecOf<T>::type;
     constexpr int G = 32 / J;
@@ -540,27 +544,48 @@ k_grid_sets(const typename cplx_of<T>::type* __restrict__ yin, const typename cp
     const bool act = g < G;
     const int gg = act ? g : 0;
     const int src = gg * J;
+    const int W = gridDim.x * WARPS, wg = blockIdx.x * WARPS + (threadIdx.x >> 5);
+    // per warp, per step parity, per group: 8 weights and 8 complex terms
+    __shared__ __align__(16) T s_w[WARPS][2][G][8];
+    __shared__ __align__(16) C s_t[WARPS][2][G][8];
+    T (*sw)[G][8] = s_w[threadIdx.x >> 5];
+    C (*st)[G][8] = s_t[threadIdx.x >> 5];
+    auto set_of = [&](int i) { return i * W + ((i & 1) ? W - 1 - wg : wg); };
     float cf[DEG + 1];
 #pragma unroll
     for (int i = 0; i <= DEG; ++i) cf[i] = kp.coef[b][i];
-    for (;;) {
-        int set = 0;
-        if (lane == 0) set = (int)atomicAdd(next_set, 1u);
-        set = __shfl_sync(0xffffffffu, set, 0);
-        if (set >= nsets) break;
-        const int r = set * G + gg;
-        const int len = act ? run_len[r] : 0;
-        const int lmax = run_len[set * G];   // the set's longest run
-        const unsigned cell = (unsigned)run_cell[r];
-        const int start = run_start[r];
-        const int cx = (int)(cell & 0xFFFFu), cy = (int)(cell >> 16);
+    struct Meta { int len, lmax, start; unsigned cell; };
+    auto load_meta = [&](int set, Meta& m) {
+        if (set < nsets) {
+            const int r = set * G + gg;
+            m.len = act ? run_len[r] : 0;
+            m.lmax = run_len[set * G];   // the set's longest run
+            m.start = run_start[r];
+            m.cell = (unsigned)run_cell[r];
+        } else {
+            m.len = m.lmax = m.start = 0;
+            m.cell = 0;
+        }
+    };
+    auto load_rec = [&](const Meta& m, int k, Rec& r) {
+        if (k < m.len) r = recs[m.start + k];
+        else { r.phx = r.phy = T(0); r.m = -1; r.pad = 0; }
+    };
+    int it = 0, set = set_of(0);
+    Meta cur;
+    load_meta(set, cur);
+    while (set < nsets) {
+        const int nset = set_of(it + 1);
+        Meta nxt;
+        load_meta(nset, nxt);
+        const int cx = (int)(cur.cell & 0xFFFFu), cy = (int)(cur.cell >> 16);
         const size_t rowoff = (size_t)((cy + b) & (Ky - 1)) * Kx;
         T xr[J], xi[J];
         if constexpr (FUSED) {
 #pragma unroll
             for (int a = 0; a < J; ++a) {
                 C v = cmake<C>(T(0), T(0));
-                if (len > 0) v = X[rowoff + ((cx + a) & (Kx - 1))];
+                if (cur.len > 0) v = X[rowoff + ((cx + a) & (Kx - 1))];
                 xr[a] = v.x;
                 xi[a] = v.y;
             }
@@ -568,27 +593,46 @@ k_grid_sets(const typename cplx_of<T>::type* __restrict__ yin, const typename cp
         T ar[J], ai[J];
 #pragma unroll
         for (int a = 0; a < J; ++a) ar[a] = ai[a] = T(0);
-        Rec rn{};
-        if (len > 0) rn = recs[start];
-        for (int k = 0; k < lmax; ++k) {
-            const Rec rc = rn;
-            if (k + 1 < len) rn = recs[start + k + 1];
-            const bool valid = k < len;
-            C yv = cmake<C>(T(0), T(0));
+        // this lane's records of the current and the next batch of J
+        Rec bcur, bnext;
+        load_rec(cur, b, bcur);
+        load_rec(cur, J + b, bnext);
+        C ycur = cmake<C>(T(0), T(0));
+        if constexpr (!FUSED) if (bcur.m >= 0) ycur = yin[perm ? perm[bcur.m] : bcur.m];
+        int kk = 0;
+        for (int k = 0; k < cur.lmax; ++k) {
+            const int sl = src + kk;
+            const T phx = __shfl_sync(0xffffffffu, bcur.phx, sl);
+            const T phy = __shfl_sync(0xffffffffu, bcur.phy, sl);
+            const bool valid = k < cur.len;
+            C yv;
             if constexpr (!FUSED) {
-                if (valid) yv = yin[perm ? perm[rc.m] : rc.m];
+                yv.x = __shfl_sync(0xffffffffu, ycur.x, sl);
+                yv.y = __shfl_sync(0xffffffffu, ycur.y, sl);
+            }
+            if (++kk == J) {
+                kk = 0;
+                bcur = bnext;
+                load_rec(cur, k + 1 + J + b, bnext);
+                if constexpr (!FUSED) {
+                    ycur = cmake<C>(T(0), T(0));
+                    if (bcur.m >= 0) ycur = yin[perm ? perm[bcur.m] : bcur.m];
+                }
             }
             T wxb, wyb;
             if constexpr (sizeof(T) == 4) {
-                wxb = kb_tap_poly<DEG>(cf, rc.phx);
-                wyb = kb_tap_poly<DEG>(cf, rc.phy);
+                wxb = kb_tap_poly<DEG>(cf, phx);
+                wyb = kb_tap_poly<DEG>(cf, phy);
             } else {
-                wxb = kb_tap_exact(J, b, beta, inv_i0beta, rc.phx);
-                wyb = kb_tap_exact(J, b, beta, inv_i0beta, rc.phy);
+                wxb = kb_tap_exact(J, b, beta, inv_i0beta, phx);
+                wyb = kb_tap_exact(J, b, beta, inv_i0beta, phy);
             }
+            const int par = k & 1;
+            if (act) sw[par][g][b] = wxb;
+            __syncwarp();
             T wx[J];
 #pragma unroll
-            for (int a = 0; a < J; ++a) wx[a] = __shfl_sync(0xffffffffu, wxb, src + a);
+            for (int a = 0; a < J; ++a) wx[a] = sw[par][gg][a];
             if constexpr (FUSED) {
                 T rx = 0, ry = 0;
 #pragma unroll
@@ -596,12 +640,14 @@ k_grid_sets(const typename cplx_of<T>::type* __restrict__ yin, const typename cp
                     rx = fma(wx[a], xr[a], rx);
                     ry = fma(wx[a], xi[a], ry);
                 }
-                const T tr = wyb * rx, ti = wyb * ry;
+                if (act) st[par][g][b] = cmake<C>(wyb * rx, wyb * ry);
+                __syncwarp();
                 T sr = 0, si = 0;
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
-                    sr += __shfl_sync(0xffffffffu, tr, src + j);
-                    si += __shfl_sync(0xffffffffu, ti, src + j);
+                    const C t = st[par][gg][j];
+                    sr += t.x;
+                    si += t.y;
                 }
                 yv = cmake<C>(sr, si);
             }
@@ -614,11 +660,14 @@ k_grid_sets(const typename cplx_of<T>::type* __restrict__ yin, const typename cp
                 }
             }
         }
-        if (len > 0) {
+        if (cur.len > 0) {
             C* row = out + rowoff;
 #pragma unroll
             for (int a = 0; a < J; ++a) atomic_add_c(row + ((cx + a) & (Kx - 1)), cmake<C>(ar[a], ai[a]));
         }
+        cur = nxt;
+        set = nset;
+        ++it;
     }
 }
 
@@ -857,9 +906,8 @@ template <int J> static void grid_f(purify_plan* p, const void* y, bool c, const
 template <int J> static void grid_d(purify_plan* p, const void* y, bool c, const int* s) { grid_tj<double, J>(p, y, c, s); }
 
 
-// Run-set launches: a persistent grid of 8-warp blocks (four per SM, or
-// fewer when there is less work) taking sets from the counter stored after
-// the gridding output (cleared by the same memset).
+// Run-set launches: a persistent grid of 8-warp blocks (as many as are
+// resident at once, or fewer when there is less work).
 template <typename T, int J, bool FUSED>
 static void grid_sets_tj(purify_plan* p, const void* y, bool caller_order, const int* skip) {
     using C = typename cplx_of<T>::type;
@@ -876,13 +924,11 @@ static void grid_sets_tj(purify_plan* p, const void* y, bool caller_order, const
     PURIFY_CUDA(cudaGetDevice(&dev));
     PURIFY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int blocks = std::max(1, std::min(sms * per_sm, (rw.nsets + W - 1) / W));
-    unsigned* ctr = reinterpret_cast<unsigned*>(static_cast<unsigned char*>(p->gacc.p) +
-                                                sizeof(C) * (size_t)p->Kx * p->Ky);
     Launch L(p, FUSED ? "normal_gg" : "grid");
     k_grid_sets<T, J, W, FUSED><<<blocks, W * 32, 0, p->stream>>>(
         (const C*)y, p->grid.as<C>(), rw.rec.as<typename RunRecOf<T>::type>(), rw.cell.as<int>(),
         rw.start.as<int>(), rw.len.as<int>(), rw.nsets, caller_order ? p->perm.as<int>() : nullptr, p->kbp,
-        p->beta, 1.0 / p->i0beta, p->Kx, p->Ky, p->gacc.as<C>(), ctr, skip);
+        p->beta, 1.0 / p->i0beta, p->Kx, p->Ky, p->gacc.as<C>(), skip);
     L.done();
 }
 template <int J> static void normal_f(purify_plan* p, const int* s) { grid_sets_tj<float, J, true>(p, nullptr, false, s); }
