@@ -72,6 +72,10 @@ typedef struct {
     purify_dtype dtype;            /* operator precision */
     void *stream;                  /* cudaStream_t; NULL = legacy default stream */
     int32_t tile;                  /* gridding tile edge (power of two, 8..64); 0 => autotune */
+    int32_t grid_mode;             /* G^H work decomposition: 0 => autotuned (tile subproblems
+                                      when `tile` is fixed), 1 => tile subproblems (shared-memory
+                                      tile per subproblem), 2 => runs of visibilities sharing
+                                      their first-tap cell, flushed to the grid */
 } purify_plan_desc;
 
 /* Build a plan: validates the description, computes the correction, kernel,
@@ -93,6 +97,7 @@ typedef struct {
     int32_t R, J, levels;
     double beta;
     int64_t workspace_bytes;
+    int32_t grid_mode;             /* the decomposition in use: 1 tile subproblems, 2 runs */
 } purify_plan_info;
 purify_status purify_plan_get_info(const purify_plan *plan, purify_plan_info *info);
 

@@ -50,7 +50,7 @@ class Plan:
     """Owns a purify_plan handle; see purify_plan_create for the fields."""
 
     def __init__(self, nx, ny, u, v, kb_width=6, levels=4, block_offsets=None, oversample=2.0, kb_beta=0.0,
-                 basis_mask=0, dtype=PURIFY_F32, stream=None, tile=0):
+                 basis_mask=0, dtype=PURIFY_F32, stream=None, tile=0, grid_mode=0):
         lib = load()
         M = int(u.numel() if hasattr(u, "numel") else np.asarray(u).size)
         self._keep = [u, v]
@@ -63,7 +63,8 @@ class Plan:
             offs = offs_np.ctypes.data_as(C.POINTER(C.c_int64))
         d = purify_plan_desc(nx=nx, ny=ny, M=M, u=_ptr(u), v=_ptr(v), R=R, block_offsets=offs,
                              kb_width=kb_width, oversample=oversample, kb_beta=kb_beta, levels=levels,
-                             basis_mask=basis_mask, dtype=dtype, stream=_stream_ptr(stream), tile=tile)
+                             basis_mask=basis_mask, dtype=dtype, stream=_stream_ptr(stream), tile=tile,
+                             grid_mode=grid_mode)
         h = C.c_void_p()
         check(lib.purify_plan_create(C.byref(d), C.byref(h)))
         self.handle = h

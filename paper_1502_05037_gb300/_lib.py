@@ -33,6 +33,7 @@ class purify_plan_desc(C.Structure):
         ("dtype", C.c_int32),
         ("stream", C.c_void_p),
         ("tile", C.c_int32),
+        ("grid_mode", C.c_int32),
     ]
 
 
@@ -43,6 +44,7 @@ class purify_plan_info(C.Structure):
         ("R", C.c_int32), ("J", C.c_int32), ("levels", C.c_int32),
         ("beta", C.c_double),
         ("workspace_bytes", C.c_int64),
+        ("grid_mode", C.c_int32),
     ]
 
 

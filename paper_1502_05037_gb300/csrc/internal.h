@@ -159,6 +159,7 @@ struct purify_plan {
     purify::GridWork work;            // gridding work list (tile of the G^H kernel)
     purify::GridWork dwork;           // degridding work list (tile of the G kernel)
     purify::RunWork runs;             // run-ordered work of the fused normal operator
+    bool grid_by_runs = false;        // G^H by run sets (else by tile subproblems); autotuned
     int fft_rb = 0, fft_cb = 0;       // FFT rows / columns per block (0: heuristic)
     // workspaces
     purify::DevBuf grid;              // Ky * Kx complex (forward transform output)

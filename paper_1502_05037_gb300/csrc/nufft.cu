@@ -987,6 +987,10 @@ void launch_degrid(purify_plan* p, void* y, bool caller_order, const int* skip) 
     else { PURIFY_J_DISPATCH(p->J, degrid_d, p, y, caller_order, skip); }
 }
 void launch_grid(purify_plan* p, const void* y, bool caller_order, const int* skip) {
+    if (p->grid_by_runs) {
+        launch_grid_sets(p, y, caller_order, skip);
+        return;
+    }
     if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, grid_f, p, y, caller_order, skip); }
     else { PURIFY_J_DISPATCH(p->J, grid_d, p, y, caller_order, skip); }
 }

@@ -171,12 +171,12 @@ void build_gridlist(purify_plan* p, const std::vector<int>& bins, const std::vec
 // same cell order) and the rows/columns per block of the FFT passes. Results
 // are cached per problem shape.
 struct TuneKey {
-    int nx, ny, J, dtype, mlog, R;
+    int nx, ny, J, dtype, mlog, R, gm;
     bool operator<(const TuneKey& o) const {
-        return std::tie(nx, ny, J, dtype, mlog, R) < std::tie(o.nx, o.ny, o.J, o.dtype, o.mlog, o.R);
+        return std::tie(nx, ny, J, dtype, mlog, R, gm) < std::tie(o.nx, o.ny, o.J, o.dtype, o.mlog, o.R, o.gm);
     }
 };
-struct TuneVal { int tile, dtile, rb, cb, units, dunits; };
+struct TuneVal { int tile, dtile, rb, cb, units, dunits; bool runs; };
 static std::mutex g_tune_mutex;
 static std::map<TuneKey, TuneVal> g_tune_cache;
 
@@ -239,12 +239,12 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
     using C = typename cplx_of<T>::type;
     int mlog = 0;
     while ((int64_t(1) << (mlog + 1)) <= p->M) ++mlog;
-    TuneKey key{p->nx, p->ny, p->J, p->dtype, mlog, std::min(p->R, 64)};
+    TuneKey key{p->nx, p->ny, p->J, p->dtype, mlog, std::min(p->R, 64), p->desc.grid_mode};
     // default subproblem size: about four subproblems per SM's worth of
     // visibilities, in batch units
     const int64_t unit = grid_list_unit(p->dtype, p->J);
     const int u0 = (int)std::max<int64_t>(1, std::min<int64_t>(16, (p->M / (152 * 4) + unit / 2) / unit));
-    TuneVal val{p->work.tile, p->work.tile, 0, 0, u0, u0};
+    TuneVal val{p->work.tile, p->work.tile, 0, 0, u0, u0, false};
     bool cached = false;
     if (tune) {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
@@ -296,12 +296,18 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
                     if (md < bd) { bd = md; val.dtile = t; val.dunits = u; }
                 }
             }
+            // gridding by run sets (independent of the tile)
+            if (p->desc.grid_mode == 0) {
+                const float mr = time_ms(p, [&] { launch_grid_sets(p, yv, false, nullptr); }, 5);
+                val.runs = mr < bg;
+            }
         }
         std::lock_guard<std::mutex> lk(g_tune_mutex);
         g_tune_cache[key] = val;
     }
     p->fft_rb = val.rb;
     p->fft_cb = val.cb;
+    p->grid_by_runs = p->desc.grid_mode == 0 ? val.runs : p->desc.grid_mode == 2;
     build_gridlist(p, bins_for(val.tile), cell_order, val.tile, val.units, p->work);
     build_gridlist(p, bins_for(val.dtile), cell_order, val.dtile, val.dunits, p->dwork);
 }
@@ -444,8 +450,8 @@ template <typename T> static void finish_plan(purify_plan* p) {
         for (int64_t c = 0; c < ncell; ++c) pos[c + 1] += pos[c];
         for (int64_t i = 0; i < p->M; ++i) cell_order[pos[(int64_t)scy[i] * p->Kx + scx[i]]++] = (int)i;
     }
-    autotune<T>(p, cand, bins_for, cell_order, d.tile == 0);
     build_runwork<T>(p, us, vs, scx, scy, cell_order);
+    autotune<T>(p, cand, bins_for, cell_order, d.tile == 0);
 }
 
 purify_plan* create_plan(const purify_plan_desc* d) {
@@ -469,6 +475,7 @@ purify_plan* create_plan(const purify_plan_desc* d) {
                        Ky <= 8192 && Kx > d->nx && Ky > d->ny,
                    "oversample must make K = alpha n a power of two above n (at most 8192)");
     PURIFY_REQUIRE(d->tile == 0 || (is_pow2(d->tile) && d->tile >= 8 && d->tile <= 64), "tile must be 0 or a power of two in [8, 64]");
+    PURIFY_REQUIRE(d->grid_mode >= 0 && d->grid_mode <= 2, "grid_mode must be 0, 1 or 2");
     std::vector<int64_t> offs;
     if (d->block_offsets) {
         offs.assign(d->block_offsets, d->block_offsets + d->R + 1);

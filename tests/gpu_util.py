@@ -35,12 +35,13 @@ def rel(a, b):
 
 
 def make_plan(nx, ny, M, J, levels=3, R=1, dtype=pk.PURIFY_F32, seed=0, sigma=np.pi / 4, mask=0, tile=0,
-              uniform_fraction=0.0):
+              uniform_fraction=0.0, grid_mode=0):
     u, v = synth.uv_coverage(M, 2000 + seed, sigma=sigma, uniform_fraction=uniform_fraction,
                              dtype=np_real(dtype))
     offs = synth.block_offsets(synth.block_sizes(M, R, 4000 + seed)) if R > 1 else None
     plan = pk.Plan(nx, ny, torch.from_numpy(u).to(DEV), torch.from_numpy(v).to(DEV), kb_width=J, levels=levels,
-                   block_offsets=offs, dtype=dtype, basis_mask=mask, tile=tile)
+                   block_offsets=offs, dtype=dtype, basis_mask=mask, tile=tile,
+                   grid_mode=grid_mode)
     return plan, u, v, offs
 
 

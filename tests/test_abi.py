@@ -59,7 +59,8 @@ int main(void) {
   printf("ktime %zu\n", sizeof(purify_kernel_time));
   P(purify_plan_desc, tile) P(purify_plan_desc, stream) P(purify_plan_desc, dtype) P(purify_plan_desc, block_offsets)
   P(purify_sdmm_params, resume) P(purify_sdmm_params, check_every) P(purify_sdmm_params, toeplitz) P(purify_sdmm_stats, status)
-  P(purify_plan_info, workspace_bytes) P(purify_plan_info, beta)
+  P(purify_plan_info, workspace_bytes) P(purify_plan_info, beta) P(purify_plan_info, grid_mode)
+  P(purify_plan_desc, grid_mode)
   return 0;
 }
 """
@@ -78,6 +79,8 @@ int main(void) {
     assert int(got["purify_plan_desc.tile"]) == _lib.purify_plan_desc.tile.offset
     assert int(got["purify_plan_desc.stream"]) == _lib.purify_plan_desc.stream.offset
     assert int(got["purify_plan_desc.dtype"]) == _lib.purify_plan_desc.dtype.offset
+    assert int(got["purify_plan_desc.grid_mode"]) == _lib.purify_plan_desc.grid_mode.offset
+    assert int(got["purify_plan_info.grid_mode"]) == _lib.purify_plan_info.grid_mode.offset
     assert int(got["purify_plan_desc.block_offsets"]) == _lib.purify_plan_desc.block_offsets.offset
     assert int(got["purify_sdmm_params.resume"]) == _lib.purify_sdmm_params.resume.offset
     assert int(got["purify_sdmm_params.check_every"]) == _lib.purify_sdmm_params.check_every.offset

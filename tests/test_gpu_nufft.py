@@ -149,3 +149,44 @@ def test_full_size_sampled_outputs():
     lhs = torch.vdot(yv.to(torch.complex128), y.to(torch.complex128)).real.item()
     rhs = torch.sum(torch.from_numpy(xf).to(DEV).double() * xa.real.double()).item()
     assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+@pytest.mark.parametrize("grid_mode", [1, 2])
+@pytest.mark.parametrize("nx,M,J,R,dtype,tile", [
+    (64, 30011, 6, 3, pk.PURIFY_F32, 0),
+    (64, 30011, 6, 3, pk.PURIFY_F32, 16),
+    (128, 70001, 4, 2, pk.PURIFY_F32, 64),
+    (32, 4099, 7, 2, pk.PURIFY_F64, 0),
+    (16, 5, 5, 1, pk.PURIFY_F32, 0),
+])
+def test_phi_adj_both_decompositions(nx, M, J, R, dtype, tile, grid_mode):
+    # G^H by tile subproblems and by first-tap-cell runs, each against the
+    # oracle in caller order: several tiles, runs cut at their length cap, a
+    # ragged last run set, an odd J and a handful of visibilities
+    plan, u, v, _ = make_plan(nx, nx, M, J, R=R, dtype=dtype, seed=nx + M + grid_mode, tile=tile,
+                              grid_mode=grid_mode)
+    assert plan.info.grid_mode == grid_mode
+    g = np.random.default_rng(M)
+    y = (g.standard_normal(M) + 1j * g.standard_normal(M)).astype(np_cplx(dtype))
+    x = torch.empty((nx, nx), dtype=t_cplx(dtype), device=DEV)
+    pk.purify_phi_adj(plan, torch.from_numpy(y).to(DEV), x)
+    want = onf.phi_adj(oracle_plan(nx, nx, u, v, J), y.astype(np.complex128))
+    assert rel(x.cpu().numpy(), want) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("grid_mode", [1, 2])
+def test_phi_adj_single_cell_runs(grid_mode):
+    # every visibility in a handful of cells: runs longer than the cap are
+    # cut and flushed into the same cells
+    nx = 32
+    M = 20000
+    g = np.random.default_rng(12)
+    u = (np.round(g.uniform(-3, 3, M)) * (2 * np.pi / 64) + 1e-4).astype(np.float32)
+    v = (np.round(g.uniform(-3, 3, M)) * (2 * np.pi / 64) - 1e-4).astype(np.float32)
+    plan = pk.Plan(nx, nx, torch.from_numpy(u).to(DEV), torch.from_numpy(v).to(DEV), kb_width=6, levels=2,
+                   grid_mode=grid_mode)
+    yv = (g.standard_normal(M) + 1j * g.standard_normal(M)).astype(np.complex64)
+    xa = torch.empty((nx, nx), dtype=torch.complex64, device=DEV)
+    pk.purify_phi_adj(plan, torch.from_numpy(yv).to(DEV), xa)
+    want = onf.phi_adj(oracle_plan(nx, nx, u, v, 6), yv.astype(np.complex128))
+    assert rel(xa.cpu().numpy(), want) <= 1e-5
