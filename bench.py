@@ -148,11 +148,11 @@ def algorithmic_bytes(name: str, info, dtype_bytes: int = 4) -> float | None:
 
 def algorithmic_flops(name: str, info) -> float | None:
     """FP32 operations a launch must perform (kernel weights evaluated from
-    J per-tap polynomials of degree J + 5 per axis, J*J taps of a real weight
+    J per-tap polynomials of degree 8-10 per axis, J*J taps of a real weight
     times a complex value; FFT passes 5 n log2 n per length-n transform)."""
     import math
     J, M = info.J, info.M
-    deg = min(14, J + 5)
+    deg = 10 if J <= 3 else (9 if J == 4 else 8)
     weights = 2 * J * (deg + 1) * 2          # Horner: one FMA (2 flops) per coefficient
     taps = J * J * (1 + 4)                    # weight product + complex multiply-accumulate
     ny = int(round(np.sqrt(info.N * info.Ky / info.Kx)))

@@ -545,11 +545,14 @@ k_grid_sets(const typename cplx_of<T>::type* __restrict__ yin, const typename cp
     const int gg = act ? g : 0;
     const int src = gg * J;
     const int W = gridDim.x * WARPS, wg = blockIdx.x * WARPS + (threadIdx.x >> 5);
-    // per warp, per step parity, per group: 8 weights and 8 complex terms
-    __shared__ __align__(16) T s_w[WARPS][2][G][8];
-    __shared__ __align__(16) C s_t[WARPS][2][G][8];
-    T (*sw)[G][8] = s_w[threadIdx.x >> 5];
-    C (*st)[G][8] = s_t[threadIdx.x >> 5];
+    // per warp, per step parity, per group: J weights and J complex terms;
+    // the group strides keep 16-byte alignment and put the groups' vector
+    // reads on distinct banks
+    constexpr int SWS = sizeof(T) == 4 ? 12 : 10, STS = sizeof(T) == 4 ? 10 : 9;
+    __shared__ __align__(16) T s_w[WARPS][2][G][SWS];
+    __shared__ __align__(16) C s_t[WARPS][2][G][STS];
+    T (*sw)[G][SWS] = s_w[threadIdx.x >> 5];
+    C (*st)[G][STS] = s_t[threadIdx.x >> 5];
     auto set_of = [&](int i) { return i * W + ((i & 1) ? W - 1 - wg : wg); };
     float cf[DEG + 1];
 #pragma unroll
