@@ -185,8 +185,9 @@ void launch_phi_adj(purify_plan* p, const void* y, void* out, bool caller_order,
                     int out_mode, const void* add);
 void launch_fft2(purify_plan* p, void* grid, bool inverse);
 // Phi stages used by the solver's fused forms
+// zero_acc: the same launch clears the gridding accumulator (gacc)
 void launch_scale_pad_rows(purify_plan* p, const void* x, double scale, void* pdir, const void* rvec,
-                           const double* beta_dev, const int* skip_flag, bool corr = true);
+                           const double* beta_dev, const int* skip_flag, bool corr = true, bool zero_acc = false);
 void launch_cols_fwd(purify_plan* p, const int* skip_flag);
 void launch_degrid(purify_plan* p, void* y, bool caller_order, const int* skip_flag);
 void launch_grid(purify_plan* p, const void* y, bool caller_order, const int* skip_flag);
@@ -196,7 +197,8 @@ void launch_cols_inv(purify_plan* p, const int* skip_flag, const void* mult = nu
 // G^H G of the grid (the oversampled image after F Z S): for every
 // visibility the J x J interpolation of the forward grid spread back with the
 // same weights, into gacc (the visibility values are never stored)
-void launch_normal_gg(purify_plan* p, const int* skip_flag);
+// (zeroed: gacc was cleared by this step's forward row pass, no memset)
+void launch_normal_gg(purify_plan* p, const int* skip_flag, bool zeroed = false);
 // G^H by runs (same output as launch_grid)
 void launch_grid_sets(purify_plan* p, const void* y, bool caller_order, const int* skip_flag);
 void launch_rows_inv_crop(purify_plan* p, void* out, double scale, int out_mode, const void* add,

@@ -155,16 +155,24 @@ __host__ __device__ inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++
 //
 // S Z and the forward row FFT: rows [i0, i0+rb) of the image to rows[i][0..Kx).
 // When pdir != null the kernel first forms p = r + beta p in place (CG
-// direction update) and transforms the new p.
+// direction update) and transforms the new p. When zero_grid != null block
+// b also clears rows [b Ky/gridDim, (b+1) Ky/gridDim) of that Ky x Kx complex
+// grid (the gridding accumulator of the same CG step).
 template <typename T>
 __global__ void __launch_bounds__(1024) k_rows_fwd(const T* __restrict__ x, typename cplx_of<T>::type* __restrict__ rows,
                            const T* __restrict__ sx, const T* __restrict__ sy,
                            const typename cplx_of<T>::type* __restrict__ tw, int nx, int ny, int Kx,
                            int rb, T scale, T* pdir, const T* __restrict__ rvec,
-                           const double* __restrict__ beta_dev, const int* __restrict__ skip) {
+                           const double* __restrict__ beta_dev, const int* __restrict__ skip,
+                           typename cplx_of<T>::type* __restrict__ zero_grid, int Ky) {
     using C = typename cplx_of<T>::type;
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (zero_grid) {
+        const int per = Ky / gridDim.x;   // whole rows per block (Ky is a multiple of the block count)
+        C* g = zero_grid + (size_t)blockIdx.x * per * Kx;
+        for (int t = threadIdx.x; t < per * Kx; t += blockDim.x) g[t] = cmake<C>(T(0), T(0));
+    }
     const int N8 = Kx >> 3;
     const int f = threadIdx.x / N8, t = threadIdx.x - f * N8;
     C* buf = reinterpret_cast<C*>(smem_raw) + f * fft_padded(Kx);
@@ -777,7 +785,7 @@ template <typename K> static void set_smem(K kernel, size_t bytes) {
 
 template <typename T>
 static void rows_fwd_t(purify_plan* p, const void* x, double scale, void* pdir, const void* rvec,
-                       const double* beta_dev, const int* skip, bool corr) {
+                       const double* beta_dev, const int* skip, bool corr, bool zero_acc) {
     using C = typename cplx_of<T>::type;
     int rb = p->fft_rb > 0 ? p->fft_rb : rows_per_block<T>(p->ny, p->Kx);
     while (p->ny % rb) rb >>= 1;
@@ -787,7 +795,7 @@ static void rows_fwd_t(purify_plan* p, const void* x, double scale, void* pdir, 
     k_rows_fwd<T><<<p->ny / rb, rb * (p->Kx / 8), sm, p->stream>>>(
         (const T*)x, p->rows.as<C>(), corr ? p->sx.as<T>() : p->onesx.as<T>(),
         corr ? p->sy.as<T>() : p->onesy.as<T>(), p->twx.as<C>(), p->nx, p->ny, p->Kx,
-        rb, (T)scale, (T*)pdir, (const T*)rvec, beta_dev, skip);
+        rb, (T)scale, (T*)pdir, (const T*)rvec, beta_dev, skip, zero_acc ? p->gacc.as<C>() : nullptr, p->Ky);
     L.done();
 }
 
@@ -912,10 +920,10 @@ template <int J> static void grid_d(purify_plan* p, const void* y, bool c, const
 // Run-set launches: a persistent grid of 8-warp blocks (as many as are
 // resident at once, or fewer when there is less work).
 template <typename T, int J, bool FUSED>
-static void grid_sets_tj(purify_plan* p, const void* y, bool caller_order, const int* skip) {
+static void grid_sets_tj(purify_plan* p, const void* y, bool caller_order, const int* skip, bool zeroed = false) {
     using C = typename cplx_of<T>::type;
     constexpr int W = 8;
-    PURIFY_CUDA(cudaMemsetAsync(p->gacc.p, 0, p->gacc.bytes, p->stream));
+    if (!zeroed) PURIFY_CUDA(cudaMemsetAsync(p->gacc.p, 0, p->gacc.bytes, p->stream));
     const RunWork& rw = p->runs;
     if (rw.nsets == 0) return;
     static int per_sm = 0;   // resident blocks per SM of this instantiation
@@ -934,14 +942,14 @@ static void grid_sets_tj(purify_plan* p, const void* y, bool caller_order, const
         p->beta, 1.0 / p->i0beta, p->Kx, p->Ky, p->gacc.as<C>(), skip);
     L.done();
 }
-template <int J> static void normal_f(purify_plan* p, const int* s) { grid_sets_tj<float, J, true>(p, nullptr, false, s); }
-template <int J> static void normal_d(purify_plan* p, const int* s) { grid_sets_tj<double, J, true>(p, nullptr, false, s); }
+template <int J> static void normal_f(purify_plan* p, const int* s, bool z) { grid_sets_tj<float, J, true>(p, nullptr, false, s, z); }
+template <int J> static void normal_d(purify_plan* p, const int* s, bool z) { grid_sets_tj<double, J, true>(p, nullptr, false, s, z); }
 template <int J> static void gsets_f(purify_plan* p, const void* y, bool c, const int* s) { grid_sets_tj<float, J, false>(p, y, c, s); }
 template <int J> static void gsets_d(purify_plan* p, const void* y, bool c, const int* s) { grid_sets_tj<double, J, false>(p, y, c, s); }
 
-void launch_normal_gg(purify_plan* p, const int* skip) {
-    if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, normal_f, p, skip); }
-    else { PURIFY_J_DISPATCH(p->J, normal_d, p, skip); }
+void launch_normal_gg(purify_plan* p, const int* skip, bool zeroed) {
+    if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, normal_f, p, skip, zeroed); }
+    else { PURIFY_J_DISPATCH(p->J, normal_d, p, skip, zeroed); }
 }
 void launch_grid_sets(purify_plan* p, const void* y, bool caller_order, const int* skip) {
     if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, gsets_f, p, y, caller_order, skip); }
@@ -968,9 +976,9 @@ int max_grid_tile(int dtype, int J) {
 }
 
 void launch_scale_pad_rows(purify_plan* p, const void* x, double scale, void* pdir, const void* rvec,
-                           const double* beta_dev, const int* skip, bool corr) {
-    if (p->dtype == PURIFY_F32) rows_fwd_t<float>(p, x, scale, pdir, rvec, beta_dev, skip, corr);
-    else rows_fwd_t<double>(p, x, scale, pdir, rvec, beta_dev, skip, corr);
+                           const double* beta_dev, const int* skip, bool corr, bool zero_acc) {
+    if (p->dtype == PURIFY_F32) rows_fwd_t<float>(p, x, scale, pdir, rvec, beta_dev, skip, corr, zero_acc);
+    else rows_fwd_t<double>(p, x, scale, pdir, rvec, beta_dev, skip, corr, zero_acc);
 }
 void launch_cols_fwd(purify_plan* p, const int* skip) {
     if (p->dtype == PURIFY_F32) cols_fwd_t<float>(p, skip); else cols_fwd_t<double>(p, skip);

@@ -144,14 +144,20 @@ __global__ void k_positivity(const T* __restrict__ x, T* __restrict__ z3, const 
     }
 }
 
-// CG start: r holds b - A x. p = 0 and beta = 0 so that the first direction
-// update gives p = r; rs = rs0 = r.r; the done flag is cleared.
+// CG start: r holds b - A x (with `addend` set, r + addend does: the
+// image-space terms are added here so that the adjoint part of r can be
+// formed beside the wavelet branch). p = 0 and beta = 0 so that the first
+// direction update gives p = r; rs = rs0 = r.r; the done flag is cleared.
 template <typename T>
-__global__ void k_cg_init(const T* __restrict__ r, T* __restrict__ p, int64_t N, double* part, unsigned* counters,
-                          double* scal, int* flags) {
+__global__ void k_cg_init(T* __restrict__ r, const T* __restrict__ addend, T* __restrict__ p, int64_t N,
+                          double* part, unsigned* counters, double* scal, int* flags) {
     T acc = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         T v = r[i];
+        if (addend) {
+            v += addend[i];
+            r[i] = v;
+        }
         acc += v * v;
         p[i] = T(0);
     }
@@ -495,10 +501,13 @@ template <typename T> struct Solver {
     void iteration(int cg_iters) {
         T* x = s.x.template as<T>();
         const double inv_nu = 1.0 / s.nu;
-        // The visibility branch (f2: Phi x, block projections) and the
+        // The visibility branch (f2: Phi x, block projections, then the
+        // adjoint part of the CG residual, Re Phi^H (s2 - z2 - Phi x / nu) /
+        // nu, and for the circulant normal operator its correction) and the
         // wavelet branch (f1: Psi^dagger, prox, Psi; then f3) read only x and
-        // their own state, so the visibility branch runs on a side stream
-        // (joined before Phi^dagger). Eager timing runs keep one stream.
+        // their own state, so the visibility branch runs on a side stream,
+        // joined before the CG start adds the image-space terms. Eager timing
+        // runs keep one stream.
         const bool fork = !timing_enabled(p);
         cudaStream_t main_stream = p->stream;
         if (fork) {
@@ -523,6 +532,15 @@ template <typename T> struct Solver {
                                                                  s.eps.template as<double>(), scal(), p->R,
                                                                  s.toeplitz ? 1 : 0);
                 L.done();
+            }
+            // r = Re Phi^H v2 / nu (the image-space terms are added at the CG start)
+            launch_phi_adj(p, s.v2.p, s.r.p, false, inv_nu, 1, nullptr);
+            if (s.toeplitz) {
+                // r -= (normal operator by circulant embedding) x
+                launch_scale_pad_rows(p, x, 1.0, nullptr, nullptr, nullptr, nullptr, false);
+                launch_cols_fwd(p, nullptr);
+                launch_cols_inv(p, nullptr, s.toep.p);
+                launch_rows_inv_crop(p, s.r.p, -1.0, 1, s.r.p, 1.0, nullptr, nullptr, nullptr, nullptr, false);
             }
             if (fork) PURIFY_CUDA(cudaEventRecord(s.ev_join, s.side));
         } catch (...) {
@@ -549,19 +567,11 @@ template <typename T> struct Solver {
             L.done();
         }
         if (fork) PURIFY_CUDA(cudaStreamWaitEvent(p->stream, s.ev_join, 0));
-        // r = b - A x
-        launch_phi_adj(p, s.v2.p, s.r.p, false, inv_nu, 1, s.addend.p);
-        if (s.toeplitz) {
-            // r -= (normal operator by circulant embedding) x
-            launch_scale_pad_rows(p, x, 1.0, nullptr, nullptr, nullptr, nullptr, false);
-            launch_cols_fwd(p, nullptr);
-            launch_cols_inv(p, nullptr, s.toep.p);
-            launch_rows_inv_crop(p, s.r.p, -1.0, 1, s.r.p, 1.0, nullptr, nullptr, nullptr, nullptr, false);
-        }
         {
             Launch L(p, "cg_init");
-            k_cg_init<T><<<red_blocks(p->N), RB, 0, p->stream>>>(s.r.template as<T>(), s.p.template as<T>(), p->N,
-                                                                part(), ctr(), scal(), flags());
+            k_cg_init<T><<<red_blocks(p->N), RB, 0, p->stream>>>(s.r.template as<T>(), s.addend.template as<T>(),
+                                                                s.p.template as<T>(), p->N, part(), ctr(), scal(),
+                                                                flags());
             L.done();
         }
         const int* skip = flags() + F_CGDONE;
@@ -574,9 +584,9 @@ template <typename T> struct Solver {
                 launch_rows_inv_crop(p, s.Ap.p, 1.0, 1, s.p.p, 2.0, skip, part(), ctr(), scal(), false);
             } else {
             // p = r + beta p fused into the first FFT pass, then A p
-            launch_scale_pad_rows(p, nullptr, inv_nu, s.p.p, s.r.p, scal() + S_BETA, skip);
+            launch_scale_pad_rows(p, nullptr, inv_nu, s.p.p, s.r.p, scal() + S_BETA, skip, true, true);
             launch_cols_fwd(p, skip);
-            launch_normal_gg(p, skip);
+            launch_normal_gg(p, skip, true);
             launch_cols_inv(p, skip);
             // A p = 2 p + Re Phi^H Phi p / nu^2, with p . A p and alpha fused in
             launch_rows_inv_crop(p, s.Ap.p, inv_nu, 1, s.p.p, 2.0, skip, part(), ctr(), scal());
