@@ -14,6 +14,12 @@ template <typename T> struct cplx_of;
 template <> struct cplx_of<float> { using type = float2; };
 template <> struct cplx_of<double> { using type = double2; };
 
+// Programmatic dependent launch: wait for the preceding kernel on the stream
+// (no-op when the kernel was launched without the attribute), and allow the
+// next kernel to be scheduled once this block's work is done.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 template <typename C> PURIFY_HD C cmake(decltype(C::x) a, decltype(C::x) b) { C c; c.x = a; c.y = b; return c; }
 template <typename C> PURIFY_HD C cadd(C a, C b) { return cmake<C>(a.x + b.x, a.y + b.y); }
 template <typename C> PURIFY_HD C csub(C a, C b) { return cmake<C>(a.x - b.x, a.y - b.y); }

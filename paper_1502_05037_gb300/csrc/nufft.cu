@@ -166,6 +166,7 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(const T* __restrict__ x, type
                            const double* __restrict__ beta_dev, const int* __restrict__ skip,
                            typename cplx_of<T>::type* __restrict__ zero_grid, int Ky) {
     using C = typename cplx_of<T>::type;
+    pdl_wait();
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (zero_grid) {
@@ -199,6 +200,7 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(const T* __restrict__ x, type
     auto store = [&](int k, C v) { rows[(size_t)i * Kx + k] = v; };
     auto slot = [&](int n) -> C& { return buf[fft_pad(n)]; };
     fft_reg<C, false>(Kx, ilog2(Kx), t, tw, load, store, slot);
+    pdl_trigger();
 }
 
 // Column kernels: a block holds cb adjacent columns, thread
@@ -214,6 +216,7 @@ __global__ void __launch_bounds__(1024) k_cols_fwd(const typename cplx_of<T>::ty
                            const typename cplx_of<T>::type* __restrict__ tw, int ny, int Kx, int Ky,
                            int cb, const int* __restrict__ skip) {
     using C = typename cplx_of<T>::type;
+    pdl_wait();
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
@@ -226,6 +229,7 @@ __global__ void __launch_bounds__(1024) k_cols_fwd(const typename cplx_of<T>::ty
     auto store = [&](int k, C v) { grid[(size_t)k * Kx + c] = v; };
     auto slot = [&](int n) -> C& { return buf[fft_pad(n) * cb + f]; };
     fft_reg<C, false>(Ky, ilog2(Ky), t, tw, load, store, slot);
+    pdl_trigger();
 }
 
 // Inverse column FFT over columns [c0, c0+cb) (grid optionally multiplied
@@ -236,6 +240,7 @@ __global__ void __launch_bounds__(1024) k_cols_inv(const typename cplx_of<T>::ty
                            const typename cplx_of<T>::type* __restrict__ tw, int ny, int Kx, int Ky,
                            int cb, const int* __restrict__ skip, const T* __restrict__ mult) {
     using C = typename cplx_of<T>::type;
+    pdl_wait();
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* buf = reinterpret_cast<C*>(smem_raw);
@@ -253,6 +258,7 @@ __global__ void __launch_bounds__(1024) k_cols_inv(const typename cplx_of<T>::ty
     };
     auto slot = [&](int n) -> C& { return buf[fft_pad(n) * cb + f]; };
     fft_reg<C, true>(Ky, ilog2(Ky), t, tw, load, store, slot);
+    pdl_trigger();
 }
 
 // Inverse row FFT of image rows [i0, i0+rb), then Z^T and S:
@@ -267,6 +273,7 @@ __global__ void __launch_bounds__(MAXT) k_rows_inv(const typename cplx_of<T>::ty
                            int rb, T scale, int out_mode, const T* __restrict__ add, T add_coef,
                            const int* __restrict__ skip, double* dot_part, unsigned* counters, double* scal) {
     using C = typename cplx_of<T>::type;
+    pdl_wait();
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int N8 = Kx >> 3;
@@ -307,6 +314,7 @@ __global__ void __launch_bounds__(MAXT) k_rows_inv(const typename cplx_of<T>::ty
             }
         }
     }
+    pdl_trigger();
 }
 
 // Plain in-place 2-D FFT pieces (purify_fft2): full row pass / column pass.
@@ -546,6 +554,7 @@ k_grid_sets(const typename cplx_of<T>::type* __restrict__ yin, const typename cp
     using Rec = typename RunRecOf<T>::type;
     constexpr int G = 32 / J;
     constexpr int DEG = kb_poly_deg(J);
+    pdl_wait();
     if (skip && *skip) return;
     const int lane = threadIdx.x & 31;
     const int g = lane / J, b = lane - g * J;
@@ -680,6 +689,7 @@ k_grid_sets(const typename cplx_of<T>::type* __restrict__ yin, const typename cp
         set = nset;
         ++it;
     }
+    pdl_trigger();
 }
 
 // G with the tile staged in shared memory: a block owns one subproblem,
@@ -792,7 +802,7 @@ static void rows_fwd_t(purify_plan* p, const void* x, double scale, void* pdir, 
     size_t sm = (size_t)rb * fft_padded(p->Kx) * sizeof(C);
     set_smem(k_rows_fwd<T>, sm);
     Launch L(p, "fft_rows_fwd");
-    k_rows_fwd<T><<<p->ny / rb, rb * (p->Kx / 8), sm, p->stream>>>(
+    launch_dependent(k_rows_fwd<T>, p->ny / rb, rb * (p->Kx / 8), sm, p->stream,
         (const T*)x, p->rows.as<C>(), corr ? p->sx.as<T>() : p->onesx.as<T>(),
         corr ? p->sy.as<T>() : p->onesy.as<T>(), p->twx.as<C>(), p->nx, p->ny, p->Kx,
         rb, (T)scale, (T*)pdir, (const T*)rvec, beta_dev, skip, zero_acc ? p->gacc.as<C>() : nullptr, p->Ky);
@@ -805,8 +815,8 @@ template <typename T> static void cols_fwd_t(purify_plan* p, const int* skip) {
     size_t sm = (size_t)cb * fft_padded(p->Ky) * sizeof(C);
     set_smem(k_cols_fwd<T>, sm);
     Launch L(p, "fft_cols_fwd");
-    k_cols_fwd<T><<<p->Kx / cb, cb * (p->Ky / 8), sm, p->stream>>>(p->rows.as<C>(), p->grid.as<C>(), p->twy.as<C>(),
-                                                      p->ny, p->Kx, p->Ky, cb, skip);
+    launch_dependent(k_cols_fwd<T>, p->Kx / cb, cb * (p->Ky / 8), sm, p->stream, p->rows.as<C>(), p->grid.as<C>(),
+                     p->twy.as<C>(), p->ny, p->Kx, p->Ky, cb, skip);
     L.done();
 }
 
@@ -818,8 +828,8 @@ template <typename T> static void cols_inv_t(purify_plan* p, const int* skip, co
     Launch L(p, "fft_cols_inv");
     // the adjoint reads the gridding output; the circulant path the forward grid
     const C* src = mult ? p->grid.as<C>() : p->gacc.as<C>();
-    k_cols_inv<T><<<p->Kx / cb, cb * (p->Ky / 8), sm, p->stream>>>(src, p->rows.as<C>(), p->twy.as<C>(),
-                                                      p->ny, p->Kx, p->Ky, cb, skip, (const T*)mult);
+    launch_dependent(k_cols_inv<T>, p->Kx / cb, cb * (p->Ky / 8), sm, p->stream, src, p->rows.as<C>(),
+                     p->twy.as<C>(), p->ny, p->Kx, p->Ky, cb, skip, (const T*)mult);
     L.done();
 }
 
@@ -836,7 +846,7 @@ static void rows_inv_t(purify_plan* p, void* out, double scale, int out_mode, co
     auto kern = nt <= 512 ? k_rows_inv<T, 512> : k_rows_inv<T, 1024>;
     set_smem(kern, sm);
     Launch L(p, "fft_rows_inv");
-    kern<<<p->ny / rb, nt, sm, p->stream>>>(p->rows.as<C>(), out, corr ? p->sx.as<T>() : p->onesx.as<T>(),
+    launch_dependent(kern, p->ny / rb, nt, sm, p->stream, p->rows.as<C>(), out, corr ? p->sx.as<T>() : p->onesx.as<T>(),
                                             corr ? p->sy.as<T>() : p->onesy.as<T>(), p->twx.as<C>(), p->nx, p->ny,
                                             p->Kx, rb, (T)scale, out_mode, (const T*)add, (T)add_coef, skip,
                                             dot_part, counters, scal);
@@ -936,7 +946,7 @@ static void grid_sets_tj(purify_plan* p, const void* y, bool caller_order, const
     PURIFY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int blocks = std::max(1, std::min(sms * per_sm, (rw.nsets + W - 1) / W));
     Launch L(p, FUSED ? "normal_gg" : "grid");
-    k_grid_sets<T, J, W, FUSED><<<blocks, W * 32, 0, p->stream>>>(
+    launch_dependent(k_grid_sets<T, J, W, FUSED>, blocks, W * 32, 0, p->stream,
         (const C*)y, p->grid.as<C>(), rw.rec.as<typename RunRecOf<T>::type>(), rw.cell.as<int>(),
         rw.start.as<int>(), rw.len.as<int>(), rw.nsets, caller_order ? p->perm.as<int>() : nullptr, p->kbp,
         p->beta, 1.0 / p->i0beta, p->Kx, p->Ky, p->gacc.as<C>(), skip);

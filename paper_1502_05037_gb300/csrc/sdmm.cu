@@ -180,6 +180,7 @@ __global__ void k_cg_init(T* __restrict__ r, const T* __restrict__ addend, T* __
 template <typename T>
 __global__ void k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ Ap,
                             int64_t N, double* part, unsigned* counters, double* scal, int* flags) {
+    pdl_wait();
     if (flags[F_CGDONE]) return;
     const T alpha = (T)scal[S_ALPHA];
     T acc = 0;
@@ -203,6 +204,7 @@ __global__ void k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __res
             counters[C_UPD] = 0;
         }
     }
+    pdl_trigger();
 }
 
 // ||x||^2 and ||x - xprev||^2 for the relative change.
@@ -593,7 +595,7 @@ template <typename T> struct Solver {
             }
             {
                 Launch L(p, "cg_update");
-                k_cg_update<T><<<red_blocks(p->N), RB, 0, p->stream>>>(x, s.r.template as<T>(), s.p.template as<T>(),
+                launch_dependent(k_cg_update<T>, red_blocks(p->N), RB, 0, p->stream, x, s.r.template as<T>(), s.p.template as<T>(),
                                                                       s.Ap.template as<T>(), p->N, part(), ctr(),
                                                                       scal(), flags());
                 L.done();
