@@ -391,6 +391,7 @@ k_grid_runs(const typename cplx_of<T>::type* __restrict__ yin, const T* __restri
             AxisConst ax, AxisConst ay, KbPoly kp, double beta, double inv_i0beta, const int* __restrict__ perm,
             const int* __restrict__ sub_bin, const int* __restrict__ sub_off, const int* __restrict__ list, int tile,
             int tiles_x, int S, typename cplx_of<T>::type* __restrict__ grid, const int* __restrict__ skip) {
+    pdl_wait();
     using C = typename cplx_of<T>::type;
     using GS = GridStage<J>;
     constexpr int G = GS::G, P = GS::P, NB = GS::NB, F = GS::F;
@@ -509,6 +510,7 @@ k_grid_runs(const typename cplx_of<T>::type* __restrict__ yin, const T* __restri
         if (v.x != T(0) || v.y != T(0))
             atomic_add_c(grid + (size_t)((oy + r) & (Ky - 1)) * Kx + ((ox + c) & (Kx - 1)), v);
     }
+    pdl_trigger();
 }
 
 // G^H (and the fused G^H G) by run sets. Warp w of the grid takes sets
@@ -701,6 +703,7 @@ k_degrid_tile(const typename cplx_of<T>::type* __restrict__ grid, const T* __res
               AxisConst ax, AxisConst ay, KbPoly kp, double beta, double inv_i0beta, const int* __restrict__ perm,
               const int* __restrict__ sub_bin, const int* __restrict__ sub_off, const int* __restrict__ list,
               int tile, int tiles_x, typename cplx_of<T>::type* __restrict__ y, const int* __restrict__ skip) {
+    pdl_wait();
     using C = typename cplx_of<T>::type;
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -763,6 +766,7 @@ k_degrid_tile(const typename cplx_of<T>::type* __restrict__ grid, const T* __res
         }
         y[perm ? perm[m] : m] = cmake<C>(accx, accy);
     }
+    pdl_trigger();
 }
 
 // ------------------------------------------------------------- launchers
@@ -861,7 +865,7 @@ template <typename T, int J> static void degrid_tj(purify_plan* p, void* y, bool
     size_t sm = sizeof(C) * (size_t)PT * PT;
     set_smem(k_degrid_tile<T, J>, sm);
     Launch L(p, "degrid");
-    k_degrid_tile<T, J><<<w.nsub, 128, sm, p->stream>>>(
+    launch_dependent(k_degrid_tile<T, J>, w.nsub, 128, sm, p->stream, 
         p->grid.as<C>(), p->us.as<T>(), p->vs.as<T>(), p->ax, p->ay, p->kbp, p->beta, 1.0 / p->i0beta,
         caller_order ? p->perm.as<int>() : nullptr, w.sub_bin.as<int>(), w.sub_off.as<int>(), w.list.as<int>(),
         tile, w.tiles_x, (C*)y, skip);
@@ -895,7 +899,7 @@ static void grid_tj(purify_plan* p, const void* y, bool caller_order, const int*
     size_t sm = grid_smem_bytes<T, J>(tile);
     set_smem(k_grid_runs<T, J, W>, sm);
     Launch L(p, "grid");
-    k_grid_runs<T, J, W><<<p->work.nsub, W * 32, sm, p->stream>>>(
+    launch_dependent(k_grid_runs<T, J, W>, p->work.nsub, W * 32, sm, p->stream, 
         (const C*)y, p->us.as<T>(), p->vs.as<T>(), p->ax, p->ay, p->kbp, p->beta, 1.0 / p->i0beta,
         caller_order ? p->perm.as<int>() : nullptr, p->work.sub_bin.as<int>(), p->work.sub_off.as<int>(),
         p->work.list.as<int>(), tile, p->work.tiles_x, S, p->gacc.as<C>(), skip);

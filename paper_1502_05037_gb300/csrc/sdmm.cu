@@ -37,6 +37,7 @@ namespace purify {
 template <typename T>
 __global__ void k_prox_l1(T* __restrict__ c, T* __restrict__ z1, const T* __restrict__ w, int64_t D, double gamma,
                           double* part, unsigned* counters, double* scal, int eval_only) {
+    pdl_wait();
     T obj = 0;  // per-thread partial in the plan precision, FP64 across threads
     for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < D; d += (int64_t)gridDim.x * blockDim.x) {
         T v = c[d];
@@ -62,6 +63,7 @@ __global__ void k_prox_l1(T* __restrict__ c, T* __restrict__ z1, const T* __rest
             counters[C_PROX] = 0;
         }
     }
+    pdl_trigger();
 }
 
 // Per-block norms over visibility chunks: ||v2 + z2 - ybar||^2 (z2 may be
@@ -72,6 +74,7 @@ __global__ void k_proj_norms(const typename cplx_of<T>::type* __restrict__ v2,
                              const typename cplx_of<T>::type* __restrict__ ybar, const int* __restrict__ cblk,
                              const int* __restrict__ cbeg, const int* __restrict__ cend, int nchunks, int R,
                              const int* __restrict__ chunk_first, double* part, unsigned* counters, double* scal) {
+    pdl_wait();
     using C = typename cplx_of<T>::type;
     const int ch = blockIdx.x;
     T a = 0, e = 0;  // per-thread partials (at most 16 terms), FP64 across threads
@@ -101,6 +104,7 @@ __global__ void k_proj_norms(const typename cplx_of<T>::type* __restrict__ v2,
         }
         if (threadIdx.x == 0) counters[C_PROJ] = 0;
     }
+    pdl_trigger();
 }
 
 // Projection onto each block's ball plus multiplier update; v2 (= Phi x / nu)
@@ -111,6 +115,7 @@ __global__ void k_proj_apply(typename cplx_of<T>::type* __restrict__ v2, typenam
                              const typename cplx_of<T>::type* __restrict__ ybar, const int* __restrict__ cblk,
                              const int* __restrict__ cbeg, const int* __restrict__ cend,
                              const double* __restrict__ eps, const double* __restrict__ scal, int R, int keep_v) {
+    pdl_wait();
     using C = typename cplx_of<T>::type;
     const int ch = blockIdx.x;
     const int r = cblk[ch];
@@ -126,6 +131,7 @@ __global__ void k_proj_apply(typename cplx_of<T>::type* __restrict__ v2, typenam
         z2[m] = cmake<C>(zx, zy);
         v2[m] = cmake<C>(sx - zx - vk * v.x, sy - zy - vk * v.y);
     }
+    pdl_trigger();
 }
 
 // Positivity step and the image-space part of the CG residual:
@@ -133,6 +139,7 @@ __global__ void k_proj_apply(typename cplx_of<T>::type* __restrict__ v2, typenam
 template <typename T>
 __global__ void k_positivity(const T* __restrict__ x, T* __restrict__ z3, const T* __restrict__ psi_out,
                              T* __restrict__ addend, T* __restrict__ xprev, int64_t N) {
+    pdl_wait();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         T xv = x[i], zz = z3[i];
         T t = xv + zz;
@@ -142,6 +149,7 @@ __global__ void k_positivity(const T* __restrict__ x, T* __restrict__ z3, const 
         addend[i] = psi_out[i] + (s3 - zn) - T(2) * xv;
         xprev[i] = xv;
     }
+    pdl_trigger();
 }
 
 // CG start: r holds b - A x (with `addend` set, r + addend does: the
@@ -151,6 +159,7 @@ __global__ void k_positivity(const T* __restrict__ x, T* __restrict__ z3, const 
 template <typename T>
 __global__ void k_cg_init(T* __restrict__ r, const T* __restrict__ addend, T* __restrict__ p, int64_t N,
                           double* part, unsigned* counters, double* scal, int* flags) {
+    pdl_wait();
     T acc = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         T v = r[i];
@@ -174,6 +183,7 @@ __global__ void k_cg_init(T* __restrict__ r, const T* __restrict__ addend, T* __
             counters[C_CGI] = 0;
         }
     }
+    pdl_trigger();
 }
 
 // x += alpha p; r -= alpha Ap; rs' = r.r; beta = rs'/rs; stop test.
@@ -211,6 +221,7 @@ __global__ void k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __res
 template <typename T>
 __global__ void k_relchange(const T* __restrict__ x, const T* __restrict__ xprev, int64_t N, double* part,
                             unsigned* counters, double* scal) {
+    pdl_wait();
     T a = 0, d = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         T xv = x[i], dv = x[i] - xprev[i];
@@ -229,6 +240,7 @@ __global__ void k_relchange(const T* __restrict__ x, const T* __restrict__ xprev
             counters[C_REL] = 0;
         }
     }
+    pdl_trigger();
 }
 
 // Generic reductions: mode 0 sum of squares, 1 max |.|, 2 sum, 3 sum (v - mean)^2 with mean = scal[S_SUM]/n
@@ -480,7 +492,7 @@ template <typename T> struct Solver {
         launch_psi_adj(p, x, s.c1.p);
         {
             Launch L(p, "prox_l1");
-            k_prox_l1<T><<<red_blocks(p->D), RB, 0, p->stream>>>(s.c1.template as<T>(), nullptr,
+            launch_dependent(k_prox_l1<T>, red_blocks(p->D), RB, 0, p->stream, s.c1.template as<T>(), nullptr,
                                                                s.have_w ? s.w.template as<T>() : nullptr, p->D,
                                                                s.gamma, part(), ctr(), scal(), 1);
             L.done();
@@ -491,7 +503,7 @@ template <typename T> struct Solver {
 
     void proj_norms(bool with_z) {
         Launch L(p, "proj_norms");
-        k_proj_norms<T><<<p->nchunks, RB, 0, p->stream>>>(
+        launch_dependent(k_proj_norms<T>, p->nchunks, RB, 0, p->stream, 
             s.v2.template as<C>(), with_z ? s.z2.template as<C>() : nullptr, s.ybar.template as<C>(),
             p->chunk_blk.as<int>(), p->chunk_beg.as<int>(), p->chunk_end.as<int>(), p->nchunks, p->R,
             s.chunk_first.template as<int>(), proj_part(), ctr(), scal());
@@ -528,7 +540,7 @@ template <typename T> struct Solver {
             proj_norms(true);
             {
                 Launch L(p, "proj_apply");
-                k_proj_apply<T><<<p->nchunks, RB, 0, p->stream>>>(s.v2.template as<C>(), s.z2.template as<C>(),
+                launch_dependent(k_proj_apply<T>, p->nchunks, RB, 0, p->stream, s.v2.template as<C>(), s.z2.template as<C>(),
                                                                  s.ybar.template as<C>(), p->chunk_blk.as<int>(),
                                                                  p->chunk_beg.as<int>(), p->chunk_end.as<int>(),
                                                                  s.eps.template as<double>(), scal(), p->R,
@@ -554,7 +566,7 @@ template <typename T> struct Solver {
         launch_psi_adj(p, x, s.c1.p);
         {
             Launch L(p, "prox_l1");
-            k_prox_l1<T><<<red_blocks(p->D), RB, 0, p->stream>>>(s.c1.template as<T>(), s.z1.template as<T>(),
+            launch_dependent(k_prox_l1<T>, red_blocks(p->D), RB, 0, p->stream, s.c1.template as<T>(), s.z1.template as<T>(),
                                                                s.have_w ? s.w.template as<T>() : nullptr, p->D,
                                                                s.gamma, part(), ctr(), scal(), 0);
             L.done();
@@ -563,7 +575,7 @@ template <typename T> struct Solver {
         // f3 and the image-space terms of the residual
         {
             Launch L(p, "positivity");
-            k_positivity<T><<<ew_blocks(p->N), 256, 0, p->stream>>>(x, s.z3.template as<T>(), s.Ap.template as<T>(),
+            launch_dependent(k_positivity<T>, ew_blocks(p->N), 256, 0, p->stream, x, s.z3.template as<T>(), s.Ap.template as<T>(),
                                                                     s.addend.template as<T>(),
                                                                     s.xprev.template as<T>(), p->N);
             L.done();
@@ -571,7 +583,7 @@ template <typename T> struct Solver {
         if (fork) PURIFY_CUDA(cudaStreamWaitEvent(p->stream, s.ev_join, 0));
         {
             Launch L(p, "cg_init");
-            k_cg_init<T><<<red_blocks(p->N), RB, 0, p->stream>>>(s.r.template as<T>(), s.addend.template as<T>(),
+            launch_dependent(k_cg_init<T>, red_blocks(p->N), RB, 0, p->stream, s.r.template as<T>(), s.addend.template as<T>(),
                                                                 s.p.template as<T>(), p->N, part(), ctr(), scal(),
                                                                 flags());
             L.done();
@@ -603,7 +615,7 @@ template <typename T> struct Solver {
         }
         {
             Launch L(p, "relchange");
-            k_relchange<T><<<red_blocks(p->N), RB, 0, p->stream>>>(x, s.xprev.template as<T>(), p->N, part(), ctr(),
+            launch_dependent(k_relchange<T>, red_blocks(p->N), RB, 0, p->stream, x, s.xprev.template as<T>(), p->N, part(), ctr(),
                                                                   scal());
             L.done();
         }

@@ -129,6 +129,7 @@ __global__ void k_dwt_level(const T* __restrict__ src, int src_basis_stride, int
                             T* __restrict__ coef, const int* __restrict__ planes, int N, int nx,
                             T* __restrict__ ll_out, int ll_basis_stride, int h, int w, int TH, int TW,
                             const int* __restrict__ pids, int nw, int dirac_plane, T inv_sqrt_q) {
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int z = blockIdx.z;
     if (z == nw) {
@@ -148,6 +149,7 @@ __global__ void k_dwt_level(const T* __restrict__ src, int src_basis_stride, int
     T* smem = reinterpret_cast<T*>(smem_raw);
     PURIFY_WITH_LENGTH(fbank<T>().len[pb],
                        (dwt_tile<T, L>(in, src_ld, out, nx, llo, h, w, ky0, kx0, pb, inv_sqrt_q, smem)));
+    pdl_trigger();
 }
 
 // Shared memory of one analysis block (filters up to maxL taps).
@@ -243,6 +245,7 @@ __global__ void __launch_bounds__(SYN_LEVEL_THREADS)
 k_idwt_level(const T* __restrict__ ll_in, int ll_basis_stride, int ll_ld, const T* __restrict__ coef,
              const int* __restrict__ planes, int N, int nx, T* __restrict__ ll_out, int out_basis_stride, int h,
              int w, const int* __restrict__ pids) {
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int PER = (4 * SYN_T * SYN_T + SYN_LEVEL_THREADS - 1) / SYN_LEVEL_THREADS;
     const int z = blockIdx.z;
@@ -268,6 +271,7 @@ k_idwt_level(const T* __restrict__ ll_in, int ll_basis_stride, int ll_ld, const 
             out[(size_t)(oy0 + mr) * w + ox0 + mc] = acc[i];
         }
     }
+    pdl_trigger();
 }
 
 // Finest synthesis level summed over all wavelet bases plus the Dirac plane:
@@ -280,6 +284,7 @@ __global__ void k_idwt_final(const T* __restrict__ ll_in, int ll_basis_stride, c
                              const int* __restrict__ planes, int N, int nx, int ny, int group_elems,
                              const int* __restrict__ pids, int nw, int dirac_plane,
                              T inv_sqrt_q, T* __restrict__ x) {
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int PER = (4 * SYN_T * SYN_T + SYN_GROUP - 1) / SYN_GROUP;
     const int oy0 = blockIdx.y * 2 * SYN_T, ox0 = blockIdx.x * 2 * SYN_T;
@@ -314,6 +319,7 @@ __global__ void k_idwt_final(const T* __restrict__ ll_in, int ll_basis_stride, c
         if (dirac_plane >= 0) v += coef[(size_t)dirac_plane * N + idx];
         x[idx] = v * inv_sqrt_q;
     }
+    pdl_trigger();
 }
 
 // ------------------------------------------------------------- launchers
@@ -375,7 +381,7 @@ template <typename T> static void psi_adj_t(purify_plan* p, const void* xv, void
         // Dirac only
         Launch Lc(p, "dwt_level");
         dim3 g((p->nx + 31) / 32, (p->ny + 31) / 32, 1);
-        k_dwt_level<T><<<g, 256, 0, p->stream>>>(x, 0, p->nx, c, plane_array(p), N, p->nx, nullptr, 0, p->ny,
+        launch_dependent(k_dwt_level<T>, g, 256, 0, p->stream, x, 0, p->nx, c, plane_array(p), N, p->nx, nullptr, 0, p->ny,
                                                  p->nx, 16, 16, pid_array(p), 0, wl.dirac_plane, inv_sqrt_q);
         Lc.done();
         return;
@@ -396,7 +402,7 @@ template <typename T> static void psi_adj_t(purify_plan* p, const void* xv, void
         dim3 g((wsub + TW - 1) / TW, (hs + TH - 1) / TH, zdim);
         T* llo = last ? nullptr : bufs[lev & 1];
         Launch L(p, "dwt_level");
-        k_dwt_level<T><<<g, 256, sm, p->stream>>>(src, src_stride, src_ld, c, plane_array(p), N, p->nx, llo,
+        launch_dependent(k_dwt_level<T>, g, 256, sm, p->stream, src, src_stride, src_ld, c, plane_array(p), N, p->nx, llo,
                                                   llstride, h, w, TH, TW, pid_array(p), wl.nw,
                                                   wl.dirac_plane, inv_sqrt_q);
         L.done();
@@ -429,7 +435,7 @@ template <typename T> static void psi_t(purify_plan* p, const void* cv, void* xv
         T* out = bufs[lev & 1];
         if (sm > 48 * 1024) PURIFY_CUDA(cudaFuncSetAttribute(k_idwt_level<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         Launch L(p, "idwt_level");
-        k_idwt_level<T><<<g, SYN_LEVEL_THREADS, sm, p->stream>>>(ll_in, llstride, ll_ld, c, plane_array(p), N,
+        launch_dependent(k_idwt_level<T>, g, SYN_LEVEL_THREADS, sm, p->stream, ll_in, llstride, ll_ld, c, plane_array(p), N,
                                                                  p->nx, out, llstride, h, w, pid_array(p));
         L.done();
         ll_in = out;
@@ -441,7 +447,7 @@ template <typename T> static void psi_t(purify_plan* p, const void* cv, void* xv
     const int threads = std::max(1, wl.nw) * SYN_GROUP;
     if (sm > 48 * 1024) PURIFY_CUDA(cudaFuncSetAttribute(k_idwt_final<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     Launch L(p, "idwt_final");
-    k_idwt_final<T><<<g, threads, sm, p->stream>>>(ll_in, llstride, c, plane_array(p), N, p->nx, p->ny,
+    launch_dependent(k_idwt_final<T>, g, threads, sm, p->stream, ll_in, llstride, c, plane_array(p), N, p->nx, p->ny,
                                                    (int)group_elems, pid_array(p), wl.nw, wl.dirac_plane,
                                                    inv_sqrt_q, x);
     L.done();
@@ -534,7 +540,7 @@ static void psi_adj_static_t(const T* x, T* c, int nx, int ny, int levels, unsig
     const int* planes = meta + 8;
     if (nw == 0) {
         dim3 g((nx + 31) / 32, (ny + 31) / 32, 1);
-        k_dwt_level<T><<<g, 256, 0, st>>>(x, 0, nx, c, planes, (int)N, nx, nullptr, 0, ny, nx, 16, 16, pids, 0,
+        launch_dependent(k_dwt_level<T>, g, 256, 0, st, x, 0, nx, c, planes, (int)N, nx, nullptr, 0, ny, nx, 16, 16, pids, 0,
                                           dirac_plane, inv_sqrt_q);
         PURIFY_CUDA(cudaGetLastError());
         add_launches(1);
@@ -552,7 +558,7 @@ static void psi_adj_static_t(const T* x, T* c, int nx, int ny, int levels, unsig
         int zdim = nw + ((lev == 0 && dirac_plane >= 0) ? 1 : 0);
         dim3 g((wsub + TW - 1) / TW, (hs + TH - 1) / TH, zdim);
         T* llo = last ? nullptr : bufs[lev & 1];
-        k_dwt_level<T><<<g, 256, sm, st>>>(src, src_stride, src_ld, c, planes, (int)N, nx, llo, llstride, h, w, TH,
+        launch_dependent(k_dwt_level<T>, g, 256, sm, st, src, src_stride, src_ld, c, planes, (int)N, nx, llo, llstride, h, w, TH,
                                            TW, pids, nw, dirac_plane, inv_sqrt_q);
         PURIFY_CUDA(cudaGetLastError());
         add_launches(1);
