@@ -200,6 +200,34 @@ KERNEL_SOURCE = {"degrid": "paper_1502_05037_gb300/csrc/nufft.cu", "grid": "pape
                  "normal_gg": "paper_1502_05037_gb300/csrc/nufft.cu"}
 
 
+# ------------------------------------------------------ ranks (replicas)
+def replica_workload(wl, rank: int):
+    """The workload rank `rank` solves: rank 0 the named one, every other rank
+    an independent problem of the same shape (its seeds shifted by 1000 per
+    rank)."""
+    from paper_1502_05037_gb300 import synth
+    if rank == 0:
+        return wl
+    return synth.Workload(**{**wl.__dict__, "index": wl.index + 1000 * rank})
+
+
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest `value` over all ranks (the value itself without a
+    process group)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, steps: int, total_ms: float) -> float:
+    """Whole-job throughput: every rank runs `steps` steps; the slowest
+    rank's time sets the job's."""
+    return world * steps / (total_ms / 1e3)
+
+
 # -------------------------------------------------------- problem set-up
 def setup_problem(wl_name: str, replica: int, dev):
     import torch
@@ -208,8 +236,7 @@ def setup_problem(wl_name: str, replica: int, dev):
     from paper_1502_05037_gb300 import problem, synth
 
     wl = synth.WORKLOADS[wl_name] if isinstance(wl_name, str) else wl_name
-    if replica:
-        wl = synth.Workload(**{**wl.__dict__, "index": wl.index + 1000 * replica})
+    wl = replica_workload(wl, replica)
     x_true, u, v, offs, nz = wl.draw()
     f64 = wl.dtype == "f64"
     rt, ct = (torch.float64, torch.complex128) if f64 else (torch.float32, torch.complex64)
@@ -280,12 +307,9 @@ def run_ours(args):
     launches = pk.purify_launch_count() - launches0
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
     clocks = clk.summary()
-    value = world * args.steps / (total_ms / 1e3)
+    value = job_rate(world, args.steps, total_ms)
 
     # ---- pass B: per-kernel timing of the same steps (eager launches)
     pk.purify_timing_enable(plan, True)
@@ -343,12 +367,9 @@ def run_ours(args):
         if k >= args.warmup:
             e2e_times.append(t1 - t0)
     e2e_total = sum(e2e_times)
-    if dist is not None:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(e2e_total, dist, dev)
     rb = 8 if wl.dtype == "f64" else 4
-    e2e = {"value": world * args.steps / e2e_total, "unit": "iters/s",
+    e2e = {"value": job_rate(world, args.steps, e2e_total * 1e3), "unit": "iters/s",
            "h2d_bytes_per_step": wl.M * 2 * rb + wl.nx * wl.ny * rb, "d2h_bytes_per_step": wl.nx * wl.ny * rb,
            "call": "purify_sdmm_solve(host y, host x, max_iter=1)"}
 
