@@ -95,7 +95,7 @@ struct SdmmState {
     DevBuf c1;                    // [D] analysis coefficients / prox output
     DevBuf v2;                    // [M] Phi x / nu then fused residual term
     DevBuf addend;                // [N] image-space terms of the CG residual
-    DevBuf r, p, Ap, xprev;       // CG vectors [N]
+    DevBuf r, p, Ap, u, xprev;    // CG vectors [N] (Ap holds s = A p, u = A r)
     DevBuf scal;                  // double scalars (see sdmm.cu)
     DevBuf part;                  // double partial sums
     DevBuf counters;              // unsigned ints for last-block reductions, then int flags
@@ -175,6 +175,28 @@ struct purify_plan {
 
 namespace purify {
 
+// Conjugate gradients in the Chronopoulos-Gear arrangement (equal to the
+// textbook iteration in exact arithmetic; one synchronisation per step): the
+// operator is applied to the residual, u = A r, and the inverse row pass of
+// step k reduces gamma = r.r and delta = r.u directly; its last block sets
+//   beta = gamma / gamma_prev (0 at step 0),
+//   alpha = gamma / (delta - beta gamma / alpha_prev)  (gamma / delta at step 0)
+// and leaves the step's update pending (scal[S_PEND] = k), unless gamma meets
+// the stop test. The forward row pass of step k + 1 (or the finishing kernel
+// after the last step) applies it, p = r + beta p, s = u + beta s (s = A p),
+// x += alpha p, r -= alpha s, and transforms the new r.
+struct CgFold {
+    void* x = nullptr;          // iterate [N]
+    void* r = nullptr;          // residual [N]
+    void* s = nullptr;          // A p [N]
+    const void* u = nullptr;    // A r [N]
+    double* scal = nullptr;
+    int* flags = nullptr;
+    int step = 0;
+};
+// the last step's update if still pending (pdir: the direction p)
+void launch_cg_finish(purify_plan* p, const CgFold& fold, void* pdir);
+
 // ----------------------------------------------------------- operator steps
 // Phi: x real [ny][nx] (internal pointer) -> y complex [M]. If perm != null
 // the output is written in caller order through perm. `scale` multiplies S.
@@ -185,9 +207,11 @@ void launch_phi_adj(purify_plan* p, const void* y, void* out, bool caller_order,
                     int out_mode, const void* add);
 void launch_fft2(purify_plan* p, void* grid, bool inverse);
 // Phi stages used by the solver's fused forms
-// zero_acc: the same launch clears the gridding accumulator (gacc)
+// zero_acc: the same launch clears the gridding accumulator (gacc); fold:
+// apply the pending CG update first (see CgFold)
 void launch_scale_pad_rows(purify_plan* p, const void* x, double scale, void* pdir, const void* rvec,
-                           const double* beta_dev, const int* skip_flag, bool corr = true, bool zero_acc = false);
+                           const double* beta_dev, const int* skip_flag, bool corr = true, bool zero_acc = false,
+                           const CgFold* fold = nullptr);
 void launch_cols_fwd(purify_plan* p, const int* skip_flag);
 void launch_degrid(purify_plan* p, void* y, bool caller_order, const int* skip_flag);
 void launch_grid(purify_plan* p, const void* y, bool caller_order, const int* skip_flag);
@@ -203,7 +227,8 @@ void launch_normal_gg(purify_plan* p, const int* skip_flag, bool zeroed = false)
 void launch_grid_sets(purify_plan* p, const void* y, bool caller_order, const int* skip_flag);
 void launch_rows_inv_crop(purify_plan* p, void* out, double scale, int out_mode, const void* add,
                           double add_coef, const int* skip_flag, double* dot_part = nullptr,
-                          unsigned* counters = nullptr, double* scal = nullptr, bool corr = true);
+                          unsigned* counters = nullptr, double* scal = nullptr, bool corr = true,
+                          const CgFold* fold = nullptr);
 
 // Psi / Psi^dagger
 void launch_psi_adj(purify_plan* p, const void* x, void* c);

@@ -164,10 +164,18 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(const T* __restrict__ x, type
                            const typename cplx_of<T>::type* __restrict__ tw, int nx, int ny, int Kx,
                            int rb, T scale, T* pdir, const T* __restrict__ rvec,
                            const double* __restrict__ beta_dev, const int* __restrict__ skip,
-                           typename cplx_of<T>::type* __restrict__ zero_grid, int Ky) {
+                           typename cplx_of<T>::type* __restrict__ zero_grid, int Ky, CgFold fold) {
     using C = typename cplx_of<T>::type;
     pdl_wait();
-    if (skip && *skip) return;
+    // the previous CG step's update, if pending (see CgFold)
+    const bool pending = fold.x && (int)fold.scal[S_PEND] == fold.step - 1;
+    const T alpha = pending ? (T)fold.scal[S_ALPHA] : T(0);
+    const T cbeta = pending ? (T)fold.scal[S_BETA] : T(0);
+    T* const fx = static_cast<T*>(fold.x);
+    T* const fr = static_cast<T*>(fold.r);
+    T* const fs = static_cast<T*>(fold.s);
+    const T* const fu = static_cast<const T*>(fold.u);
+    if (skip && *skip) return;   // stopped: the last update was not left pending
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (zero_grid) {
         const int per = Ky / gridDim.x;   // whole rows per block (Ky is a multiple of the block count)
@@ -187,7 +195,20 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(const T* __restrict__ x, type
         if (j >= 0 && j < nx) {
             const size_t idx = (size_t)i * nx + j;
             T xv;
-            if (pdir) {
+            if (fold.x) {
+                // Chronopoulos-Gear update, then the transform of the new r
+                T rv = fr[idx];
+                if (pending) {
+                    const T pv = rv + cbeta * pdir[idx];
+                    const T sv = fu[idx] + cbeta * fs[idx];
+                    pdir[idx] = pv;
+                    fs[idx] = sv;
+                    fx[idx] += alpha * pv;
+                    rv = rv - alpha * sv;
+                    fr[idx] = rv;
+                }
+                xv = rv;
+            } else if (pdir) {
                 xv = rvec[idx] + beta * pdir[idx];
                 pdir[idx] = xv;
             } else {
@@ -271,7 +292,8 @@ __global__ void __launch_bounds__(MAXT) k_rows_inv(const typename cplx_of<T>::ty
                            const T* __restrict__ sx, const T* __restrict__ sy,
                            const typename cplx_of<T>::type* __restrict__ tw, int nx, int ny, int Kx,
                            int rb, T scale, int out_mode, const T* __restrict__ add, T add_coef,
-                           const int* __restrict__ skip, double* dot_part, unsigned* counters, double* scal) {
+                           const int* __restrict__ skip, double* dot_part, unsigned* counters, double* scal,
+                           CgFold fold) {
     using C = typename cplx_of<T>::type;
     pdl_wait();
     if (skip && *skip) return;
@@ -281,7 +303,8 @@ __global__ void __launch_bounds__(MAXT) k_rows_inv(const typename cplx_of<T>::ty
     C* buf = reinterpret_cast<C*>(smem_raw) + f * fft_padded(Kx);
     const int i = blockIdx.x * rb + f;
     const T rs = sy[i] * scale;
-    T dacc = 0;
+    T dacc = 0, gacc2 = 0;   // add.out, and with the folded CG add.add (add = r, out = A r)
+    const bool cg = fold.x != nullptr;
     auto load = [&](int k) -> C { return rows[(size_t)i * Kx + k]; };
     auto store = [&](int p1, C v) {
         const int j = (p1 + nx / 2) & (Kx - 1);
@@ -296,13 +319,55 @@ __global__ void __launch_bounds__(MAXT) k_rows_inv(const typename cplx_of<T>::ty
                 const T a = add[idx];
                 r += add_coef * a;
                 dacc += a * r;
+                if (cg) gacc2 += a * a;
             }
             reinterpret_cast<T*>(out)[idx] = r;
         }
     };
     auto slot = [&](int n) -> C& { return buf[fft_pad(n)]; };
     fft_reg<C, true>(Kx, ilog2(Kx), t, tw, load, store, slot);
-    if (dot_part) {
+    if (dot_part && cg) {
+        // Chronopoulos-Gear scalars (see CgFold): gamma = r.r, delta = r.A r
+        const double b0 = block_sum((double)gacc2);
+        const double b1 = block_sum((double)dacc);
+        if (threadIdx.x == 0) {
+            dot_part[2 * blockIdx.x] = b0;
+            dot_part[2 * blockIdx.x + 1] = b1;
+        }
+        if (arrive_last(counters + C_ALPHA)) {
+            double s0 = 0.0, s1 = 0.0;
+            for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
+                s0 += __ldcg(dot_part + 2 * k);
+                s1 += __ldcg(dot_part + 2 * k + 1);
+            }
+            s0 = block_sum(s0);
+            s1 = block_sum(s1);
+            if (threadIdx.x == 0) {
+                const double gam = s0, del = s1;
+                double be = 0.0, al;
+                if (fold.step == 0) {
+                    al = del > 0.0 ? gam / del : 0.0;
+                } else {
+                    const double gprev = scal[S_RS], aprev = scal[S_ALPHA];
+                    be = gprev > 0.0 ? gam / gprev : 0.0;
+                    const double den = del - (aprev > 0.0 ? be * gam / aprev : 0.0);
+                    al = den > 0.0 ? gam / den : 0.0;
+                }
+                scal[S_RS] = gam;
+                scal[S_ALPHA] = al;
+                scal[S_BETA] = be;
+                scal[S_PAP] = del;
+                const bool stop = gam == 0.0 || gam <= scal[S_TOL2] * scal[S_RS0];
+                if (!(gam == gam) || !(al == al)) { fold.flags[F_NAN] = 1; fold.flags[F_CGDONE] = 1; }
+                else if (stop) fold.flags[F_CGDONE] = 1;
+                else {
+                    scal[S_PEND] = (double)fold.step;
+                    scal[S_CGCOUNT] += 1.0;
+                }
+                counters[C_ALPHA] = 0;
+            }
+        }
+    } else if (dot_part) {
         double b = block_sum((double)dacc);
         if (threadIdx.x == 0) dot_part[blockIdx.x] = b;
         if (arrive_last(counters + C_ALPHA)) {
@@ -799,7 +864,7 @@ template <typename K> static void set_smem(K kernel, size_t bytes) {
 
 template <typename T>
 static void rows_fwd_t(purify_plan* p, const void* x, double scale, void* pdir, const void* rvec,
-                       const double* beta_dev, const int* skip, bool corr, bool zero_acc) {
+                       const double* beta_dev, const int* skip, bool corr, bool zero_acc, const CgFold* fold) {
     using C = typename cplx_of<T>::type;
     int rb = p->fft_rb > 0 ? p->fft_rb : rows_per_block<T>(p->ny, p->Kx);
     while (p->ny % rb) rb >>= 1;
@@ -809,7 +874,8 @@ static void rows_fwd_t(purify_plan* p, const void* x, double scale, void* pdir, 
     launch_dependent(k_rows_fwd<T>, p->ny / rb, rb * (p->Kx / 8), sm, p->stream,
         (const T*)x, p->rows.as<C>(), corr ? p->sx.as<T>() : p->onesx.as<T>(),
         corr ? p->sy.as<T>() : p->onesy.as<T>(), p->twx.as<C>(), p->nx, p->ny, p->Kx,
-        rb, (T)scale, (T*)pdir, (const T*)rvec, beta_dev, skip, zero_acc ? p->gacc.as<C>() : nullptr, p->Ky);
+        rb, (T)scale, (T*)pdir, (const T*)rvec, beta_dev, skip, zero_acc ? p->gacc.as<C>() : nullptr, p->Ky,
+        fold ? *fold : CgFold());
     L.done();
 }
 
@@ -839,7 +905,8 @@ template <typename T> static void cols_inv_t(purify_plan* p, const int* skip, co
 
 template <typename T>
 static void rows_inv_t(purify_plan* p, void* out, double scale, int out_mode, const void* add, double add_coef,
-                       const int* skip, double* dot_part, unsigned* counters, double* scal, bool corr) {
+                       const int* skip, double* dot_part, unsigned* counters, double* scal, bool corr,
+                       const CgFold* fold) {
     using C = typename cplx_of<T>::type;
     int rb = p->fft_rb > 0 ? p->fft_rb : rows_per_block<T>(p->ny, p->Kx);
     while (p->ny % rb) rb >>= 1;
@@ -853,7 +920,36 @@ static void rows_inv_t(purify_plan* p, void* out, double scale, int out_mode, co
     launch_dependent(kern, p->ny / rb, nt, sm, p->stream, p->rows.as<C>(), out, corr ? p->sx.as<T>() : p->onesx.as<T>(),
                                             corr ? p->sy.as<T>() : p->onesy.as<T>(), p->twx.as<C>(), p->nx, p->ny,
                                             p->Kx, rb, (T)scale, out_mode, (const T*)add, (T)add_coef, skip,
-                                            dot_part, counters, scal);
+                                            dot_part, counters, scal, fold ? *fold : CgFold());
+    L.done();
+}
+
+// The update of the last CG step (fold.step), when it is still pending (see
+// CgFold): p = r + beta p, s = u + beta s, x += alpha p, r -= alpha s.
+template <typename T>
+__global__ void k_cg_finish(CgFold fold, T* __restrict__ pdir, int64_t N) {
+    pdl_wait();
+    if ((int)fold.scal[S_PEND] != fold.step) return;
+    const T alpha = (T)fold.scal[S_ALPHA], beta = (T)fold.scal[S_BETA];
+    T* x = static_cast<T*>(fold.x);
+    T* r = static_cast<T*>(fold.r);
+    T* sv = static_cast<T*>(fold.s);
+    const T* u = static_cast<const T*>(fold.u);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const T pv = r[i] + beta * pdir[i];
+        const T s2 = u[i] + beta * sv[i];
+        pdir[i] = pv;
+        sv[i] = s2;
+        x[i] += alpha * pv;
+        r[i] = r[i] - alpha * s2;
+    }
+    pdl_trigger();
+}
+
+template <typename T> static void cg_finish_t(purify_plan* p, const CgFold& fold, void* pdir) {
+    Launch L(p, "cg_finish");
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((p->N + 255) / 256, 152 * 8));
+    launch_dependent(k_cg_finish<T>, blocks, 256, 0, p->stream, fold, (T*)pdir, p->N);
     L.done();
 }
 
@@ -990,9 +1086,12 @@ int max_grid_tile(int dtype, int J) {
 }
 
 void launch_scale_pad_rows(purify_plan* p, const void* x, double scale, void* pdir, const void* rvec,
-                           const double* beta_dev, const int* skip, bool corr, bool zero_acc) {
-    if (p->dtype == PURIFY_F32) rows_fwd_t<float>(p, x, scale, pdir, rvec, beta_dev, skip, corr, zero_acc);
-    else rows_fwd_t<double>(p, x, scale, pdir, rvec, beta_dev, skip, corr, zero_acc);
+                           const double* beta_dev, const int* skip, bool corr, bool zero_acc, const CgFold* fold) {
+    if (p->dtype == PURIFY_F32) rows_fwd_t<float>(p, x, scale, pdir, rvec, beta_dev, skip, corr, zero_acc, fold);
+    else rows_fwd_t<double>(p, x, scale, pdir, rvec, beta_dev, skip, corr, zero_acc, fold);
+}
+void launch_cg_finish(purify_plan* p, const CgFold& fold, void* pdir) {
+    if (p->dtype == PURIFY_F32) cg_finish_t<float>(p, fold, pdir); else cg_finish_t<double>(p, fold, pdir);
 }
 void launch_cols_fwd(purify_plan* p, const int* skip) {
     if (p->dtype == PURIFY_F32) cols_fwd_t<float>(p, skip); else cols_fwd_t<double>(p, skip);
@@ -1001,11 +1100,12 @@ void launch_cols_inv(purify_plan* p, const int* skip, const void* mult) {
     if (p->dtype == PURIFY_F32) cols_inv_t<float>(p, skip, mult); else cols_inv_t<double>(p, skip, mult);
 }
 void launch_rows_inv_crop(purify_plan* p, void* out, double scale, int out_mode, const void* add, double add_coef,
-                          const int* skip, double* dot_part, unsigned* counters, double* scal, bool corr) {
+                          const int* skip, double* dot_part, unsigned* counters, double* scal, bool corr,
+                          const CgFold* fold) {
     if (p->dtype == PURIFY_F32)
-        rows_inv_t<float>(p, out, scale, out_mode, add, add_coef, skip, dot_part, counters, scal, corr);
+        rows_inv_t<float>(p, out, scale, out_mode, add, add_coef, skip, dot_part, counters, scal, corr, fold);
     else
-        rows_inv_t<double>(p, out, scale, out_mode, add, add_coef, skip, dot_part, counters, scal, corr);
+        rows_inv_t<double>(p, out, scale, out_mode, add, add_coef, skip, dot_part, counters, scal, corr, fold);
 }
 void launch_degrid(purify_plan* p, void* y, bool caller_order, const int* skip) {
     if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, degrid_f, p, y, caller_order, skip); }

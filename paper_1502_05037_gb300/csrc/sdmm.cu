@@ -157,8 +157,8 @@ __global__ void k_positivity(const T* __restrict__ x, T* __restrict__ z3, const 
 // formed beside the wavelet branch). p = 0 and beta = 0 so that the first
 // direction update gives p = r; rs = rs0 = r.r; the done flag is cleared.
 template <typename T>
-__global__ void k_cg_init(T* __restrict__ r, const T* __restrict__ addend, T* __restrict__ p, int64_t N,
-                          double* part, unsigned* counters, double* scal, int* flags) {
+__global__ void k_cg_init(T* __restrict__ r, const T* __restrict__ addend, T* __restrict__ p, T* __restrict__ s,
+                          int64_t N, double* part, unsigned* counters, double* scal, int* flags) {
     pdl_wait();
     T acc = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
@@ -169,6 +169,7 @@ __global__ void k_cg_init(T* __restrict__ r, const T* __restrict__ addend, T* __
         }
         acc += v * v;
         p[i] = T(0);
+        s[i] = T(0);
     }
     double b = block_sum((double)acc);
     if (threadIdx.x == 0) part[blockIdx.x] = b;
@@ -178,6 +179,7 @@ __global__ void k_cg_init(T* __restrict__ r, const T* __restrict__ addend, T* __
             scal[S_RS] = tot;
             scal[S_RS0] = tot;
             scal[S_BETA] = 0.0;
+            scal[S_PEND] = -1000.0;   // no pending update (never step - 1)
             flags[F_CGDONE] = tot == 0.0 ? 1 : 0;
             if (!(tot == tot)) flags[F_NAN] = 1;
             counters[C_CGI] = 0;
@@ -186,38 +188,6 @@ __global__ void k_cg_init(T* __restrict__ r, const T* __restrict__ addend, T* __
     pdl_trigger();
 }
 
-// x += alpha p; r -= alpha Ap; rs' = r.r; beta = rs'/rs; stop test.
-template <typename T>
-__global__ void k_cg_update(T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p, const T* __restrict__ Ap,
-                            int64_t N, double* part, unsigned* counters, double* scal, int* flags) {
-    pdl_wait();
-    if (flags[F_CGDONE]) return;
-    const T alpha = (T)scal[S_ALPHA];
-    T acc = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        x[i] += alpha * p[i];
-        T rv = r[i] - alpha * Ap[i];
-        r[i] = rv;
-        acc += rv * rv;
-    }
-    double b = block_sum((double)acc);
-    if (threadIdx.x == 0) part[blockIdx.x] = b;
-    if (arrive_last(counters + C_UPD)) {
-        double tot = ordered_sum(part, gridDim.x);
-        if (threadIdx.x == 0) {
-            double rs = scal[S_RS];
-            scal[S_BETA] = rs > 0.0 ? tot / rs : 0.0;
-            scal[S_RS] = tot;
-            scal[S_CGCOUNT] += 1.0;
-            if (tot == 0.0 || tot <= scal[S_TOL2] * scal[S_RS0]) flags[F_CGDONE] = 1;
-            if (!(tot == tot)) { flags[F_NAN] = 1; flags[F_CGDONE] = 1; }
-            counters[C_UPD] = 0;
-        }
-    }
-    pdl_trigger();
-}
-
-// ||x||^2 and ||x - xprev||^2 for the relative change.
 template <typename T>
 __global__ void k_relchange(const T* __restrict__ x, const T* __restrict__ xprev, int64_t N, double* part,
                             unsigned* counters, double* scal) {
@@ -352,7 +322,7 @@ template <typename T> struct Solver {
     double* part() { return s.part.as<double>(); }
     // the projection norms keep their partial sums apart from every other
     // reduction, so that they can run beside the wavelet branch
-    static constexpr size_t kProjPart = 4096;
+    static constexpr size_t kProjPart = 16384;
     double* proj_part() { return s.part.as<double>() + kProjPart; }
     unsigned* ctr() { return s.counters.as<unsigned>(); }
     int* flags() { return reinterpret_cast<int*>(s.counters.as<unsigned>() + 16); }
@@ -373,6 +343,7 @@ template <typename T> struct Solver {
         s.r.alloc(sizeof(T) * N);
         s.p.alloc(sizeof(T) * N);
         s.Ap.alloc(sizeof(T) * N);
+        s.u.alloc(sizeof(T) * N);
         s.xprev.alloc(sizeof(T) * N);
         s.scal.alloc(sizeof(double) * (S_BLOCKS + 2 * (size_t)p->R + 8));
         s.part.alloc(sizeof(double) * (kProjPart + std::max<size_t>(8192, 2 * (size_t)p->nchunks + 64)));
@@ -583,35 +554,45 @@ template <typename T> struct Solver {
         if (fork) PURIFY_CUDA(cudaStreamWaitEvent(p->stream, s.ev_join, 0));
         {
             Launch L(p, "cg_init");
-            launch_dependent(k_cg_init<T>, red_blocks(p->N), RB, 0, p->stream, s.r.template as<T>(), s.addend.template as<T>(),
-                                                                s.p.template as<T>(), p->N, part(), ctr(), scal(),
-                                                                flags());
+            launch_dependent(k_cg_init<T>, red_blocks(p->N), RB, 0, p->stream, s.r.template as<T>(),
+                             s.addend.template as<T>(), s.p.template as<T>(), s.Ap.template as<T>(), p->N, part(),
+                             ctr(), scal(), flags());
             L.done();
         }
         const int* skip = flags() + F_CGDONE;
+        // CG (Chronopoulos-Gear arrangement, see CgFold): step k applies the
+        // operator to r; the update of step k is applied by the forward row
+        // pass of step k + 1 or, after the last step, by the finishing kernel
+        CgFold fold;
+        fold.x = x;
+        fold.r = s.r.p;
+        fold.s = s.Ap.p;
+        fold.u = s.u.p;
+        fold.scal = scal();
+        fold.flags = flags();
         for (int k = 0; k < cg_iters; ++k) {
+            fold.step = k;
             if (s.toeplitz) {
-                // p = r + beta p, then A p = 2 p + (embedded normal operator) p
-                launch_scale_pad_rows(p, nullptr, 1.0, s.p.p, s.r.p, scal() + S_BETA, skip, false);
+                // u = A r = 2 r + (embedded normal operator) r
+                launch_scale_pad_rows(p, nullptr, 1.0, s.p.p, s.r.p, nullptr, skip, false, false, &fold);
                 launch_cols_fwd(p, skip);
                 launch_cols_inv(p, skip, s.toep.p);
-                launch_rows_inv_crop(p, s.Ap.p, 1.0, 1, s.p.p, 2.0, skip, part(), ctr(), scal(), false);
+                launch_rows_inv_crop(p, s.u.p, 1.0, 1, s.r.p, 2.0, skip, part(), ctr(), scal(), false, &fold);
             } else {
-            // p = r + beta p fused into the first FFT pass, then A p
-            launch_scale_pad_rows(p, nullptr, inv_nu, s.p.p, s.r.p, scal() + S_BETA, skip, true, true);
-            launch_cols_fwd(p, skip);
-            launch_normal_gg(p, skip, true);
-            launch_cols_inv(p, skip);
-            // A p = 2 p + Re Phi^H Phi p / nu^2, with p . A p and alpha fused in
-            launch_rows_inv_crop(p, s.Ap.p, inv_nu, 1, s.p.p, 2.0, skip, part(), ctr(), scal());
+                // the pending update and the transform of the new r fused into
+                // the first FFT pass, then u = A r
+                launch_scale_pad_rows(p, nullptr, inv_nu, s.p.p, s.r.p, nullptr, skip, true, true, &fold);
+                launch_cols_fwd(p, skip);
+                launch_normal_gg(p, skip, true);
+                launch_cols_inv(p, skip);
+                // u = 2 r + Re Phi^H Phi r / nu^2, with r.r, r.u and the CG
+                // scalars fused in
+                launch_rows_inv_crop(p, s.u.p, inv_nu, 1, s.r.p, 2.0, skip, part(), ctr(), scal(), true, &fold);
             }
-            {
-                Launch L(p, "cg_update");
-                launch_dependent(k_cg_update<T>, red_blocks(p->N), RB, 0, p->stream, x, s.r.template as<T>(), s.p.template as<T>(),
-                                                                      s.Ap.template as<T>(), p->N, part(), ctr(),
-                                                                      scal(), flags());
-                L.done();
-            }
+        }
+        if (cg_iters > 0) {
+            fold.step = cg_iters - 1;
+            launch_cg_finish(p, fold, s.p.p);
         }
         {
             Launch L(p, "relchange");
