@@ -139,9 +139,8 @@ def algorithmic_bytes(name: str, info, dtype_bytes: int = 4) -> float | None:
         "proj_apply": 5 * c * M,
         "positivity": 5 * dtype_bytes * N,
         "cg_alpha": 2 * dtype_bytes * N,
-        "cg_finish": 6 * dtype_bytes * N,
         "cg_init": 2 * dtype_bytes * N,
-        "relchange": 2 * dtype_bytes * N,
+        "relchange": 10 * dtype_bytes * N,   # with the last CG update: x, xprev, r, p, u, s in; x, p, s, r out
     }
     return float(table[name]) if name in table else None
 
@@ -294,7 +293,8 @@ def run_ours(args):
         pk.purify_sdmm_iterate(plan, 1)
     barrier()
     xs_probe = torch.empty_like(x)
-    cg0 = pk.purify_sdmm_solve(plan, None, None, xs_probe, max_iter=0, resume=True).cg_iters_total
+    cg0 = pk.purify_sdmm_solve(plan, None, None, xs_probe, max_iter=0, resume=True,
+                               cg_iters=args.cg_iters).cg_iters_total
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches0 = pk.purify_launch_count()
     with ClockSampler(dev.index if dev.index is not None else 0) as clk:
@@ -308,8 +308,8 @@ def run_ours(args):
         t_wall = time.perf_counter() - t_wall0
     launches = pk.purify_launch_count() - launches0
     # CG updates actually applied per timed iteration (work is not skipped)
-    cg_per_step = (pk.purify_sdmm_solve(plan, None, None, xs_probe, max_iter=0, resume=True).cg_iters_total
-                   - cg0) / args.steps
+    cg_per_step = (pk.purify_sdmm_solve(plan, None, None, xs_probe, max_iter=0, resume=True,
+                                        cg_iters=args.cg_iters).cg_iters_total - cg0) / args.steps
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = sum(step_ms)
     total_ms = max_over_ranks(total_ms, dist, dev)

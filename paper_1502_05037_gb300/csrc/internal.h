@@ -182,7 +182,7 @@ namespace purify {
 //   beta = gamma / gamma_prev (0 at step 0),
 //   alpha = gamma / (delta - beta gamma / alpha_prev)  (gamma / delta at step 0)
 // and leaves the step's update pending (scal[S_PEND] = k), unless gamma meets
-// the stop test. The forward row pass of step k + 1 (or the finishing kernel
+// the stop test. The forward row pass of step k + 1 (or the relative-change kernel
 // after the last step) applies it, p = r + beta p, s = u + beta s (s = A p),
 // x += alpha p, r -= alpha s, and transforms the new r.
 struct CgFold {
@@ -194,8 +194,6 @@ struct CgFold {
     int* flags = nullptr;
     int step = 0;
 };
-// the last step's update if still pending (pdir: the direction p)
-void launch_cg_finish(purify_plan* p, const CgFold& fold, void* pdir);
 
 // ----------------------------------------------------------- operator steps
 // Phi: x real [ny][nx] (internal pointer) -> y complex [M]. If perm != null

@@ -924,34 +924,6 @@ static void rows_inv_t(purify_plan* p, void* out, double scale, int out_mode, co
     L.done();
 }
 
-// The update of the last CG step (fold.step), when it is still pending (see
-// CgFold): p = r + beta p, s = u + beta s, x += alpha p, r -= alpha s.
-template <typename T>
-__global__ void k_cg_finish(CgFold fold, T* __restrict__ pdir, int64_t N) {
-    pdl_wait();
-    if ((int)fold.scal[S_PEND] != fold.step) return;
-    const T alpha = (T)fold.scal[S_ALPHA], beta = (T)fold.scal[S_BETA];
-    T* x = static_cast<T*>(fold.x);
-    T* r = static_cast<T*>(fold.r);
-    T* sv = static_cast<T*>(fold.s);
-    const T* u = static_cast<const T*>(fold.u);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const T pv = r[i] + beta * pdir[i];
-        const T s2 = u[i] + beta * sv[i];
-        pdir[i] = pv;
-        sv[i] = s2;
-        x[i] += alpha * pv;
-        r[i] = r[i] - alpha * s2;
-    }
-    pdl_trigger();
-}
-
-template <typename T> static void cg_finish_t(purify_plan* p, const CgFold& fold, void* pdir) {
-    Launch L(p, "cg_finish");
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((p->N + 255) / 256, 152 * 8));
-    launch_dependent(k_cg_finish<T>, blocks, 256, 0, p->stream, fold, (T*)pdir, p->N);
-    L.done();
-}
 
 template <typename T, int J> static void degrid_tj(purify_plan* p, void* y, bool caller_order, const int* skip) {
     using C = typename cplx_of<T>::type;
@@ -1090,9 +1062,7 @@ void launch_scale_pad_rows(purify_plan* p, const void* x, double scale, void* pd
     if (p->dtype == PURIFY_F32) rows_fwd_t<float>(p, x, scale, pdir, rvec, beta_dev, skip, corr, zero_acc, fold);
     else rows_fwd_t<double>(p, x, scale, pdir, rvec, beta_dev, skip, corr, zero_acc, fold);
 }
-void launch_cg_finish(purify_plan* p, const CgFold& fold, void* pdir) {
-    if (p->dtype == PURIFY_F32) cg_finish_t<float>(p, fold, pdir); else cg_finish_t<double>(p, fold, pdir);
-}
+
 void launch_cols_fwd(purify_plan* p, const int* skip) {
     if (p->dtype == PURIFY_F32) cols_fwd_t<float>(p, skip); else cols_fwd_t<double>(p, skip);
 }

@@ -189,12 +189,28 @@ __global__ void k_cg_init(T* __restrict__ r, const T* __restrict__ addend, T* __
 }
 
 template <typename T>
-__global__ void k_relchange(const T* __restrict__ x, const T* __restrict__ xprev, int64_t N, double* part,
-                            unsigned* counters, double* scal) {
+__global__ void k_relchange(T* __restrict__ x, const T* __restrict__ xprev, int64_t N, double* part,
+                            unsigned* counters, double* scal, CgFold fold, T* __restrict__ pdir) {
     pdl_wait();
+    // the last CG step's update first, when it is still pending (see CgFold)
+    const bool pending = fold.x && (int)scal[S_PEND] == fold.step;
+    const T alpha = pending ? (T)scal[S_ALPHA] : T(0), beta = pending ? (T)scal[S_BETA] : T(0);
+    T* const r = static_cast<T*>(fold.r);
+    T* const sv = static_cast<T*>(fold.s);
+    const T* const u = static_cast<const T*>(fold.u);
     T a = 0, d = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        T xv = x[i], dv = x[i] - xprev[i];
+        T xv = x[i];
+        if (pending) {
+            const T pv = r[i] + beta * pdir[i];
+            const T s2 = u[i] + beta * sv[i];
+            pdir[i] = pv;
+            sv[i] = s2;
+            xv += alpha * pv;
+            x[i] = xv;
+            r[i] = r[i] - alpha * s2;
+        }
+        const T dv = xv - xprev[i];
         a += xv * xv;
         d += dv * dv;
     }
@@ -562,7 +578,7 @@ template <typename T> struct Solver {
         const int* skip = flags() + F_CGDONE;
         // CG (Chronopoulos-Gear arrangement, see CgFold): step k applies the
         // operator to r; the update of step k is applied by the forward row
-        // pass of step k + 1 or, after the last step, by the finishing kernel
+        // pass of step k + 1 or, after the last step, by the relative-change kernel
         CgFold fold;
         fold.x = x;
         fold.r = s.r.p;
@@ -590,14 +606,12 @@ template <typename T> struct Solver {
                 launch_rows_inv_crop(p, s.u.p, inv_nu, 1, s.r.p, 2.0, skip, part(), ctr(), scal(), true, &fold);
             }
         }
-        if (cg_iters > 0) {
-            fold.step = cg_iters - 1;
-            launch_cg_finish(p, fold, s.p.p);
-        }
+        // the last step's pending update is applied by the relative-change kernel
+        fold.step = cg_iters - 1;
         {
             Launch L(p, "relchange");
-            launch_dependent(k_relchange<T>, red_blocks(p->N), RB, 0, p->stream, x, s.xprev.template as<T>(), p->N, part(), ctr(),
-                                                                  scal());
+            launch_dependent(k_relchange<T>, red_blocks(p->N), RB, 0, p->stream, x, s.xprev.template as<T>(), p->N,
+                             part(), ctr(), scal(), fold, s.p.template as<T>());
             L.done();
         }
     }
