@@ -421,6 +421,38 @@ __device__ __forceinline__ void atomic_add_c(double2* a, double2 v) {
     atomicAdd(&a->y, v.y);
 }
 
+// Adds the J complex values (ar[a], ai[a]) to row[c0 .. c0 + J) of a grid row
+// of Kx cells (periodic): where the segment does not wrap, two cells at a
+// time with 16-byte vector reductions (one L2 operation for two cells), the
+// odd cells at the ends with 8-byte ones.
+template <int J>
+__device__ __forceinline__ void red_row(float2* row, int c0, int Kx, const float (&ar)[J], const float (&ai)[J]) {
+    if (c0 + J <= Kx) {
+        float2* q = row + c0;
+        int a = 0;
+        if (c0 & 1) {
+            atomicAdd(q, make_float2(ar[0], ai[0]));
+            a = 1;
+        }
+#pragma unroll
+        for (int k = 0; k < J; ++k) {
+            if (k < a || k + 1 >= J || ((k - a) & 1)) continue;
+            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(q + k), "f"(ar[k]), "f"(ai[k]),
+                         "f"(ar[k + 1]), "f"(ai[k + 1])
+                         : "memory");
+        }
+        if (((J - a) & 1) != 0) atomicAdd(q + (J - 1), make_float2(ar[J - 1], ai[J - 1]));
+    } else {
+#pragma unroll
+        for (int k = 0; k < J; ++k) atomicAdd(row + ((c0 + k) & (Kx - 1)), make_float2(ar[k], ai[k]));
+    }
+}
+template <int J>
+__device__ __forceinline__ void red_row(double2* row, int c0, int Kx, const double (&ar)[J], const double (&ai)[J]) {
+#pragma unroll
+    for (int k = 0; k < J; ++k) atomic_add_c(row + ((c0 + k) & (Kx - 1)), make_double2(ar[k], ai[k]));
+}
+
 // G^H by cell runs. A block owns one subproblem: a grid tile and an explicit
 // list of its visibilities ordered by first-tap cell across all measurement
 // blocks, so that visibilities sharing their J x J cells are adjacent. The
@@ -747,11 +779,7 @@ k_grid_sets(const typename cplx_of<T>::type* __restrict__ yin, const typename cp
                 }
             }
         }
-        if (cur.len > 0) {
-            C* row = out + rowoff;
-#pragma unroll
-            for (int a = 0; a < J; ++a) atomic_add_c(row + ((cx + a) & (Kx - 1)), cmake<C>(ar[a], ai[a]));
-        }
+        if (cur.len > 0) red_row<J>(out + rowoff, cx, Kx, ar, ai);
         cur = nxt;
         set = nset;
         ++it;
