@@ -42,6 +42,9 @@ solver parameter):
 * SARA reweighting (Sec. 1: weights essentially the inverse of the previous
   solution's coefficients): w = rho / (rho + |Psi^dagger x|), rho_1 =
   std(Psi^dagger x^(0)), rho_{t+1} = rho_t / 2, each pass warm-started.
+* CG stopping (the paper names no rule): a fixed number of steps, or, with a
+  tolerance, the first step at which ||r|| <= tol ||r_0||, r_0 the residual
+  of the warm start of that x-update.
 """
 from __future__ import annotations
 
@@ -87,16 +90,17 @@ def epsilon_chi2(sigma: float, sizes: np.ndarray) -> np.ndarray:
 def cg(apply_A, b: np.ndarray, x0: np.ndarray, iters: int, tol: float = 0.0):
     """Conjugate gradients on a symmetric positive definite system, warm
     started at x0. Runs `iters` iterations, stopping early when the residual
-    norm reaches tol * ||b|| (tol > 0) or becomes exactly zero. Returns
-    (x, iterations done, final residual norm)."""
+    norm reaches tol * ||r_0|| (tol > 0), r_0 = b - A x0 the residual of the
+    warm start, or becomes exactly zero. Returns (x, iterations done, final
+    residual norm)."""
     x = np.array(x0, dtype=np.float64, copy=True)
     r = b - apply_A(x)
     p = r.copy()
     rs = float(np.sum(r * r))
-    bnorm = float(np.sqrt(np.sum(b * b)))
+    r0norm = float(np.sqrt(rs))
     done = 0
     for _ in range(iters):
-        if rs == 0.0 or (tol > 0.0 and np.sqrt(rs) <= tol * bnorm):
+        if rs == 0.0 or (tol > 0.0 and np.sqrt(rs) <= tol * r0norm):
             break
         Ap = apply_A(p)
         alpha = rs / float(np.sum(p * Ap))

@@ -51,6 +51,21 @@ def test_fixed_iteration_trajectory(dtype, tol):
     assert abs(st.max_resid_over_eps - osd.residual_ratios(prob, ref.x).max()) <= 10 * tol
 
 
+def test_cg_tolerance_trajectory():
+    # CG stopped by ||r|| <= tol ||r_0|| inside every x-update: same step
+    # counts and the same iterates as the oracle (FP64, so no stop decision
+    # sits within rounding of the threshold)
+    dtype = pk.PURIFY_F64
+    plan, prob, _ = problem(32, 4096, 6, 3, 3, dtype, seed=9)
+    iters, cap, tol = 12, 40, 1e-3
+    ref = osd.sdmm_solve(prob, np.zeros((32, 32)), iters, cap, tol)
+    counts = [h["cg"] for h in ref.history]
+    assert max(counts) < cap and min(counts) >= 1
+    x, st = gpu_solve(plan, prob, dtype, iters, cap, cg_tol=tol)
+    assert st.iters == iters and st.cg_iters_total == ref.cg_iters
+    assert rel(x.cpu().numpy(), ref.x) <= 1e-9
+
+
 def test_weighted_trajectory_and_reweight():
     dtype = pk.PURIFY_F32
     plan, prob, x_true = problem(32, 3000, 4, 2, 2, dtype, seed=2)

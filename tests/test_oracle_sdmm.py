@@ -124,6 +124,36 @@ def test_cg_fixed_iterations_and_zero_residual():
     assert done == 1 and np.allclose(x, b / 3.0)
 
 
+def test_cg_tolerance_is_relative_to_the_warm_start_residual():
+    # Independent of the recurrences: the k-th CG iterate from x0 is the
+    # Galerkin solution over x0 + K_k(A, r0), computed here from an
+    # orthonormal Krylov basis; the stop is the first k with
+    # ||r_k|| <= tol ||r0||, a different k than ||b|| would give.
+    n = 12
+    d = np.linspace(1.0, 9.0, n)
+    A = np.diag(d)
+    apply = lambda x: d * x
+    rng = np.random.default_rng(21)
+    b = rng.standard_normal(n)
+    x0 = np.linalg.solve(A, b) + 1e-3 * rng.standard_normal(n)   # ||r0|| << ||b||
+    r0 = b - A @ x0
+    tol = 1e-2
+
+    def galerkin(k):
+        K = np.stack([np.linalg.matrix_power(A, j) @ r0 for j in range(k)], axis=1)
+        V, _ = np.linalg.qr(K)
+        c = np.linalg.solve(V.T @ A @ V, V.T @ r0)
+        return x0 + V @ c
+
+    want_k = next(k for k in range(1, n + 1)
+                  if np.linalg.norm(b - A @ galerkin(k)) <= tol * np.linalg.norm(r0))
+    assert np.linalg.norm(r0) <= tol * np.linalg.norm(b)   # a ||b|| rule would stop at 0
+    x, done, res = sdmm.cg(apply, b, x0, 50, tol)
+    assert done == want_k
+    assert np.allclose(x, galerkin(want_k), rtol=0, atol=1e-12 * np.abs(x).max())
+    assert res <= tol * np.linalg.norm(r0) and np.isclose(res, np.linalg.norm(b - A @ x), rtol=1e-8)
+
+
 # ------------------------------------------------------------------ SDMM
 def _dual_certificate(prob, st):
     """Fenchel dual value and feasibility residual from SDMM's multipliers
