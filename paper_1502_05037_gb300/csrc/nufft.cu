@@ -610,25 +610,100 @@ k_grid_runs(const typename cplx_of<T>::type* __restrict__ yin, const T* __restri
     pdl_trigger();
 }
 
+// J consecutive values from a 16-byte aligned shared-memory slot in 16-byte
+// (then 8-, then 4-byte) loads.
+template <int J> __device__ __forceinline__ void lds_vec(const float* s, float (&v)[J]) {
+#pragma unroll
+    for (int i = 0; i + 4 <= J; i += 4) {
+        const float4 t = *reinterpret_cast<const float4*>(s + i);
+        v[i] = t.x;
+        v[i + 1] = t.y;
+        v[i + 2] = t.z;
+        v[i + 3] = t.w;
+    }
+    constexpr int o = J & ~3;
+    if constexpr ((J & 3) >= 2) {
+        const float2 t = *reinterpret_cast<const float2*>(s + o);
+        v[o] = t.x;
+        v[o + 1] = t.y;
+    }
+    if constexpr ((J & 1) != 0) v[J - 1] = s[J - 1];
+}
+template <int J> __device__ __forceinline__ void lds_vec(const double* s, double (&v)[J]) {
+#pragma unroll
+    for (int i = 0; i < J; ++i) v[i] = s[i];
+}
+template <int J> __device__ __forceinline__ void lds_vec(const float2* s, float2 (&v)[J]) {
+    const float4* q = reinterpret_cast<const float4*>(s);
+#pragma unroll
+    for (int i = 0; i < J / 2; ++i) {
+        const float4 t = q[i];
+        v[2 * i] = make_float2(t.x, t.y);
+        v[2 * i + 1] = make_float2(t.z, t.w);
+    }
+    if constexpr ((J & 1) != 0) v[J - 1] = s[J - 1];
+}
+template <int J> __device__ __forceinline__ void lds_vec(const double2* s, double2 (&v)[J]) {
+#pragma unroll
+    for (int i = 0; i < J; ++i) v[i] = s[i];
+}
+
+// J consecutive complex values of a grid row of Kx cells (periodic) from
+// column c0: where the segment does not wrap, two cells per 16-byte load.
+template <int J>
+__device__ __forceinline__ void ldg_row(const float2* __restrict__ row, int c0, int Kx, float2 (&v)[J]) {
+    if (c0 + J <= Kx) {
+        const float2* q = row + c0;
+        int a = 0;
+        if (c0 & 1) {
+            v[0] = q[0];
+            a = 1;
+        }
+#pragma unroll
+        for (int k = 0; k < J; ++k) {
+            if (k < a || k + 1 >= J || ((k - a) & 1)) continue;
+            const float4 t = *reinterpret_cast<const float4*>(q + k);
+            v[k] = make_float2(t.x, t.y);
+            v[k + 1] = make_float2(t.z, t.w);
+        }
+        if (((J - a) & 1) != 0) v[J - 1] = q[J - 1];
+    } else {
+#pragma unroll
+        for (int k = 0; k < J; ++k) v[k] = row[(c0 + k) & (Kx - 1)];
+    }
+}
+template <int J>
+__device__ __forceinline__ void ldg_row(const double2* __restrict__ row, int c0, int Kx, double2 (&v)[J]) {
+#pragma unroll
+    for (int k = 0; k < J; ++k) v[k] = row[(c0 + k) & (Kx - 1)];
+}
+
 // G^H (and the fused G^H G) by run sets. Warp w of the grid takes sets
 // w, 2W - 1 - w, 2W + w, ... (W warps in all; sets are sorted by length, so
 // the alternating order balances the warps); lane group g (lanes gJ ..
 // gJ+J-1) walks run g of the set, which holds visibilities sharing one
-// first-tap cell (cx, cy). Lane b of a group loads every J-th record of the
-// run (two batches of J records in flight) and the group reads them by
-// shuffles. For each visibility lane b evaluates tap b of both axes (wx[b],
-// wy[b]) and the group exchanges the wx through a warp-private shared-memory
-// slot (one store, vector loads: lighter on the shuffle pipe than J
-// shuffles, double-buffered by step parity); lane b accumulates row b
-// of the cell's J x J patch in registers,
+// first-tap cell (cx, cy). For each visibility lane b evaluates tap b of
+// both axes (wx[b], wy[b]) and the group exchanges the wx through a
+// warp-private shared-memory slot (one store, 16-byte loads: lighter on the
+// shuffle pipe than J shuffles); lane b accumulates row b of the cell's
+// J x J patch in registers,
 //   patch[b][a] += wx[a] * (wy[b] * y),
 // and the set's runs (about equally long) are flushed together with vector
-// global reductions after the longest run of the set. With FUSED the
-// visibility value is not read but interpolated from the forward grid X:
-// lane b holds row b of X's J x J patch at the run's cell,
+// global reductions after the longest run of the set. The step has no
+// branch but the loop's: lanes outside every group store to a spare slot,
+// and a step past the end of a lane's run adds zero.
+// Gridding (y given): lane b loads every J-th record of the run (two batches
+// of J records in flight) and the group reads them by shuffles; the weight
+// slot is double-buffered by step parity.
+// Fused (G^H G X): the visibility value is not read but interpolated from
+// the forward grid X. Lane b holds row b of X's J x J patch at the run's
+// cell (read two cells per 16-byte load where the row segment is aligned
+// and does not wrap),
 //   y = sum_b wy[b] sum_a wx[a] X[cy + b][cx + a],
-// summed over the group (in b order) through the same kind of shared slot,
-// so G^H G X needs no visibility vector.
+// summed over the group (in b order) through a second shared slot, so
+// G^H G X needs no visibility vector. All J lanes of a group read the split
+// of the group's next record directly, one step ahead; the two warp
+// barriers of a step order every reuse of the single-buffered slots.
 template <int DEG> __device__ __forceinline__ float kb_tap_poly(const float (&c)[DEG + 1], float phi) {
     const float z = fmaf(2.0f, phi, -1.0f);
     float acc = c[DEG];
@@ -661,14 +736,18 @@ k_grid_sets(const typename cplx_of<T>::type* __restrict__ yin, const typename cp
     const int gg = act ? g : 0;
     const int src = gg * J;
     const int W = gridDim.x * WARPS, wg = blockIdx.x * WARPS + (threadIdx.x >> 5);
-    // per warp, per step parity, per group: J weights and J complex terms;
-    // the group strides keep 16-byte alignment and put the groups' vector
-    // reads on distinct banks
-    constexpr int SWS = sizeof(T) == 4 ? 12 : 10, STS = sizeof(T) == 4 ? 10 : 9;
-    __shared__ __align__(16) T s_w[WARPS][2][G][SWS];
-    __shared__ __align__(16) C s_t[WARPS][2][G][STS];
-    T (*sw)[G][SWS] = s_w[threadIdx.x >> 5];
-    C (*st)[G][STS] = s_t[threadIdx.x >> 5];
+    // per warp, per step parity, per group: J weights and J complex terms,
+    // read back with 16-byte loads; the group strides keep 16-byte alignment
+    // and put the groups' 16-byte reads of one instruction on distinct banks
+    // (the terms' stride of 6 complex values, for J <= 6, also puts each
+    // half-warp's 8-byte stores on distinct banks)
+    constexpr int SWS = sizeof(T) == 4 ? 12 : 10, STS = sizeof(T) == 4 ? (J <= 6 ? 6 : 10) : 9;
+    constexpr int GS = G + (32 % J != 0 ? 1 : 0);   // + a slot the idle lanes write to
+    constexpr int NPAR = FUSED ? 1 : 2;
+    __shared__ __align__(16) T s_w[WARPS][NPAR][GS][SWS];
+    __shared__ __align__(16) C s_t[FUSED ? WARPS : 1][GS][STS];
+    T (*sw)[GS][SWS] = s_w[threadIdx.x >> 5];
+    C (*st)[STS] = s_t[FUSED ? (threadIdx.x >> 5) : 0];
     auto set_of = [&](int i) { return i * W + ((i & 1) ? W - 1 - wg : wg); };
     float cf[DEG + 1];
 #pragma unroll
@@ -701,43 +780,66 @@ k_grid_sets(const typename cplx_of<T>::type* __restrict__ yin, const typename cp
         const size_t rowoff = (size_t)((cy + b) & (Ky - 1)) * Kx;
         T xr[J], xi[J];
         if constexpr (FUSED) {
+            C xv[J];
+            if (cur.len > 0) {
+                ldg_row<J>(X + rowoff, cx, Kx, xv);
+            } else {
+#pragma unroll
+                for (int a = 0; a < J; ++a) xv[a] = cmake<C>(T(0), T(0));
+            }
 #pragma unroll
             for (int a = 0; a < J; ++a) {
-                C v = cmake<C>(T(0), T(0));
-                if (cur.len > 0) v = X[rowoff + ((cx + a) & (Kx - 1))];
-                xr[a] = v.x;
-                xi[a] = v.y;
+                xr[a] = xv[a].x;
+                xi[a] = xv[a].y;
             }
         }
         T ar[J], ai[J];
 #pragma unroll
         for (int a = 0; a < J; ++a) ar[a] = ai[a] = T(0);
-        // this lane's records of the current and the next batch of J
+        // gridding: this lane's records of the current and the next batch
+        // of J, read by the group through shuffles; fused: the split of the
+        // group's record k, read by all J lanes of the group, one step ahead
         Rec bcur, bnext;
-        load_rec(cur, b, bcur);
-        load_rec(cur, J + b, bnext);
-        C ycur = cmake<C>(T(0), T(0));
-        if constexpr (!FUSED) if (bcur.m >= 0) ycur = yin[perm ? perm[bcur.m] : bcur.m];
+        C ycur = cmake<C>(T(0), T(0)), rc = cmake<C>(T(0), T(0));
+        auto split_at = [&](int k) {
+            C v = cmake<C>(T(0), T(0));
+            if (k < cur.len) {
+                const Rec* q = recs + cur.start + k;
+                v = cmake<C>(q->phx, q->phy);
+            }
+            return v;
+        };
+        if constexpr (FUSED) {
+            rc = split_at(0);
+        } else {
+            load_rec(cur, b, bcur);
+            load_rec(cur, J + b, bnext);
+            if (bcur.m >= 0) ycur = yin[perm ? perm[bcur.m] : bcur.m];
+        }
         int kk = 0;
         for (int k = 0; k < cur.lmax; ++k) {
-            const int sl = src + kk;
-            const T phx = __shfl_sync(0xffffffffu, bcur.phx, sl);
-            const T phy = __shfl_sync(0xffffffffu, bcur.phy, sl);
-            const bool valid = k < cur.len;
+            T phx, phy;
             C yv;
-            if constexpr (!FUSED) {
+            if constexpr (FUSED) {
+                const C rn = split_at(k + 1);
+                phx = rc.x;
+                phy = rc.y;
+                rc = rn;
+            } else {
+                const int sl = src + kk;
+                phx = __shfl_sync(0xffffffffu, bcur.phx, sl);
+                phy = __shfl_sync(0xffffffffu, bcur.phy, sl);
                 yv.x = __shfl_sync(0xffffffffu, ycur.x, sl);
                 yv.y = __shfl_sync(0xffffffffu, ycur.y, sl);
-            }
-            if (++kk == J) {
-                kk = 0;
-                bcur = bnext;
-                load_rec(cur, k + 1 + J + b, bnext);
-                if constexpr (!FUSED) {
+                if (++kk == J) {
+                    kk = 0;
+                    bcur = bnext;
+                    load_rec(cur, k + 1 + J + b, bnext);
                     ycur = cmake<C>(T(0), T(0));
                     if (bcur.m >= 0) ycur = yin[perm ? perm[bcur.m] : bcur.m];
                 }
             }
+            const bool valid = k < cur.len;
             T wxb, wyb;
             if constexpr (sizeof(T) == 4) {
                 wxb = kb_tap_poly<DEG>(cf, phx);
@@ -746,12 +848,11 @@ k_grid_sets(const typename cplx_of<T>::type* __restrict__ yin, const typename cp
                 wxb = kb_tap_exact(J, b, beta, inv_i0beta, phx);
                 wyb = kb_tap_exact(J, b, beta, inv_i0beta, phy);
             }
-            const int par = k & 1;
-            if (act) sw[par][g][b] = wxb;
+            const int par = NPAR == 1 ? 0 : (k & 1);
+            sw[par][g][b] = wxb;
             __syncwarp();
             T wx[J];
-#pragma unroll
-            for (int a = 0; a < J; ++a) wx[a] = sw[par][gg][a];
+            lds_vec<J>(sw[par][gg], wx);
             if constexpr (FUSED) {
                 T rx = 0, ry = 0;
 #pragma unroll
@@ -759,19 +860,20 @@ k_grid_sets(const typename cplx_of<T>::type* __restrict__ yin, const typename cp
                     rx = fma(wx[a], xr[a], rx);
                     ry = fma(wx[a], xi[a], ry);
                 }
-                if (act) st[par][g][b] = cmake<C>(wyb * rx, wyb * ry);
+                st[g][b] = cmake<C>(wyb * rx, wyb * ry);
                 __syncwarp();
+                C tv[J];
+                lds_vec<J>(st[gg], tv);
                 T sr = 0, si = 0;
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
-                    const C t = st[par][gg][j];
-                    sr += t.x;
-                    si += t.y;
+                    sr += tv[j].x;
+                    si += tv[j].y;
                 }
                 yv = cmake<C>(sr, si);
             }
-            if (valid) {
-                const T zr = wyb * yv.x, zi = wyb * yv.y;
+            {
+                const T zr = valid ? wyb * yv.x : T(0), zi = valid ? wyb * yv.y : T(0);
 #pragma unroll
                 for (int a = 0; a < J; ++a) {
                     ar[a] = fma(wx[a], zr, ar[a]);
