@@ -101,5 +101,45 @@ def test_invalid_description_is_rejected_before_any_launch(lib):
     assert lib.purify_plan_destroy(None) == _lib.PURIFY_OK
 
 
+@pytest.mark.parametrize("fields,msg", [
+    ({"M": 0}, b"M must be"),                                     # no visibilities
+    ({"R": 5, "M": 4}, b"R must be"),                             # more blocks than visibilities
+    ({"kb_width": 9}, b"kb_width"),
+    ({"kb_width": 1}, b"kb_width"),
+    ({"levels": 6, "nx": 16, "ny": 16}, b"too small"),            # deeper than the image allows
+    ({"tile": 12}, b"tile"),
+    ({"grid_mode": 3}, b"grid_mode"),
+    ({"oversample": 1.5}, b"oversample"),
+    ({"dtype": 7}, b"dtype"),
+    ({"basis_mask": 0x200}, b"basis_mask"),
+])
+def test_degenerate_descriptions_are_rejected_on_the_host(lib, fields, msg):
+    dummy = (ctypes.c_float * 8)()   # never read: validation fails first
+    base = dict(nx=32, ny=32, M=100, u=ctypes.addressof(dummy), v=ctypes.addressof(dummy), R=1, kb_width=6,
+                levels=3)
+    base.update(fields)
+    d = _lib.purify_plan_desc(**base)
+    h = ctypes.c_void_p()
+    assert lib.purify_plan_create(ctypes.byref(d), ctypes.byref(h)) == _lib.PURIFY_EINVAL
+    assert msg in lib.purify_last_error()
+    assert not h.value
+
+
+@pytest.mark.parametrize("offs,msg", [
+    ([0, 50, 50, 100], b"non-empty"),      # an empty block (problem (3) needs a bound per block)
+    ([0, 60, 40, 100], b"non-empty"),      # decreasing offsets
+    ([1, 50, 70, 100], b"start at 0"),
+    ([0, 50, 70, 99], b"end at M"),
+])
+def test_block_partitions_must_cover_the_visibilities(lib, offs, msg):
+    dummy = (ctypes.c_float * 8)()
+    o = (ctypes.c_int64 * len(offs))(*offs)
+    d = _lib.purify_plan_desc(nx=32, ny=32, M=100, u=ctypes.addressof(dummy), v=ctypes.addressof(dummy), R=3,
+                              block_offsets=ctypes.cast(o, ctypes.POINTER(ctypes.c_int64)), kb_width=6, levels=3)
+    h = ctypes.c_void_p()
+    assert lib.purify_plan_create(ctypes.byref(d), ctypes.byref(h)) == _lib.PURIFY_EINVAL
+    assert msg in lib.purify_last_error()
+
+
 def test_launch_counter_starts_finite(lib):
     assert lib.purify_launch_count() >= 0
