@@ -138,8 +138,6 @@ def algorithmic_bytes(name: str, info, dtype_bytes: int = 4) -> float | None:
         "proj_norms": 3 * c * M,
         "proj_apply": 5 * c * M,
         "positivity": 5 * dtype_bytes * N,
-        "cg_alpha": 2 * dtype_bytes * N,
-        "cg_init": 2 * dtype_bytes * N,
         "relchange": 10 * dtype_bytes * N,   # with the last CG update: x, xprev, r, p, u, s in; x, p, s, r out
     }
     return float(table[name]) if name in table else None

@@ -182,14 +182,18 @@ namespace purify {
 //   beta = gamma / gamma_prev (0 at step 0),
 //   alpha = gamma / (delta - beta gamma / alpha_prev)  (gamma / delta at step 0)
 // and leaves the step's update pending (scal[S_PEND] = k), unless gamma meets
-// the stop test. The forward row pass of step k + 1 (or the relative-change kernel
-// after the last step) applies it, p = r + beta p, s = u + beta s (s = A p),
-// x += alpha p, r -= alpha s, and transforms the new r.
+// the stop test (gamma <= tol^2 gamma_0, gamma_0 recorded at step 0). The
+// forward row pass of step k + 1 (or the relative-change kernel after the
+// last step) applies it, p = r + beta p, s = u + beta s (s = A p),
+// x += alpha p, r -= alpha s, and transforms the new r. The forward row pass
+// of step 0 starts the solve: r += add (the residual's terms formed outside
+// the pass), p = s = 0, the stop flag and the pending marker cleared.
 struct CgFold {
     void* x = nullptr;          // iterate [N]
     void* r = nullptr;          // residual [N]
     void* s = nullptr;          // A p [N]
     const void* u = nullptr;    // A r [N]
+    const void* add = nullptr;  // added to r at step 0 (may be null)
     double* scal = nullptr;
     int* flags = nullptr;
     int step = 0;
@@ -198,11 +202,14 @@ struct CgFold {
 // ----------------------------------------------------------- operator steps
 // Phi: x real [ny][nx] (internal pointer) -> y complex [M]. If perm != null
 // the output is written in caller order through perm. `scale` multiplies S.
-void launch_phi(purify_plan* p, const void* x, void* y, bool caller_order, double scale);
+// zero_acc: the forward row pass also clears the gridding accumulator (for a
+// Phi^H launched later with acc_zeroed).
+void launch_phi(purify_plan* p, const void* x, void* y, bool caller_order, double scale, bool zero_acc = false);
 // Phi^H: y complex [M] (caller order if caller_order) -> image.
 //   out_mode 0: complex [ny][nx];  1: real part, out = scale * Re(.) + add (add may be null)
+// acc_zeroed: the gridding accumulator is already clear (no memset).
 void launch_phi_adj(purify_plan* p, const void* y, void* out, bool caller_order, double scale,
-                    int out_mode, const void* add);
+                    int out_mode, const void* add, bool acc_zeroed = false);
 void launch_fft2(purify_plan* p, void* grid, bool inverse);
 // Phi stages used by the solver's fused forms
 // zero_acc: the same launch clears the gridding accumulator (gacc); fold:
@@ -212,7 +219,7 @@ void launch_scale_pad_rows(purify_plan* p, const void* x, double scale, void* pd
                            const CgFold* fold = nullptr);
 void launch_cols_fwd(purify_plan* p, const int* skip_flag);
 void launch_degrid(purify_plan* p, void* y, bool caller_order, const int* skip_flag);
-void launch_grid(purify_plan* p, const void* y, bool caller_order, const int* skip_flag);
+void launch_grid(purify_plan* p, const void* y, bool caller_order, const int* skip_flag, bool zeroed = false);
 // inverse column pass: reads the gridding output (gacc), or with `mult` the
 // forward grid multiplied elementwise by mult
 void launch_cols_inv(purify_plan* p, const int* skip_flag, const void* mult = nullptr);
@@ -222,7 +229,7 @@ void launch_cols_inv(purify_plan* p, const int* skip_flag, const void* mult = nu
 // (zeroed: gacc was cleared by this step's forward row pass, no memset)
 void launch_normal_gg(purify_plan* p, const int* skip_flag, bool zeroed = false);
 // G^H by runs (same output as launch_grid)
-void launch_grid_sets(purify_plan* p, const void* y, bool caller_order, const int* skip_flag);
+void launch_grid_sets(purify_plan* p, const void* y, bool caller_order, const int* skip_flag, bool zeroed = false);
 void launch_rows_inv_crop(purify_plan* p, void* out, double scale, int out_mode, const void* add,
                           double add_coef, const int* skip_flag, double* dot_part = nullptr,
                           unsigned* counters = nullptr, double* scal = nullptr, bool corr = true,

@@ -167,15 +167,23 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(const T* __restrict__ x, type
                            typename cplx_of<T>::type* __restrict__ zero_grid, int Ky, CgFold fold) {
     using C = typename cplx_of<T>::type;
     pdl_wait();
-    // the previous CG step's update, if pending (see CgFold)
-    const bool pending = fold.x && (int)fold.scal[S_PEND] == fold.step - 1;
+    // step 0 starts the solve; later steps apply the previous step's update,
+    // if pending (see CgFold)
+    const bool first = fold.x && fold.step == 0;
+    const bool pending = fold.x && !first && (int)fold.scal[S_PEND] == fold.step - 1;
     const T alpha = pending ? (T)fold.scal[S_ALPHA] : T(0);
     const T cbeta = pending ? (T)fold.scal[S_BETA] : T(0);
     T* const fx = static_cast<T*>(fold.x);
     T* const fr = static_cast<T*>(fold.r);
     T* const fs = static_cast<T*>(fold.s);
     const T* const fu = static_cast<const T*>(fold.u);
-    if (skip && *skip) return;   // stopped: the last update was not left pending
+    const T* const fadd = static_cast<const T*>(fold.add);
+    if (!first && skip && *skip) return;   // stopped: the last update was not left pending
+    if (first && blockIdx.x == 0 && threadIdx.x == 0) {
+        // no other block of this pass reads these; the next kernels do
+        fold.flags[F_CGDONE] = 0;
+        fold.scal[S_PEND] = -1000.0;   // never step - 1
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (zero_grid) {
         const int per = Ky / gridDim.x;   // whole rows per block (Ky is a multiple of the block count)
@@ -198,7 +206,14 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(const T* __restrict__ x, type
             if (fold.x) {
                 // Chronopoulos-Gear update, then the transform of the new r
                 T rv = fr[idx];
-                if (pending) {
+                if (first) {
+                    if (fadd) {
+                        rv += fadd[idx];
+                        fr[idx] = rv;
+                    }
+                    pdir[idx] = T(0);
+                    fs[idx] = T(0);
+                } else if (pending) {
                     const T pv = rv + cbeta * pdir[idx];
                     const T sv = fu[idx] + cbeta * fs[idx];
                     pdir[idx] = pv;
@@ -353,6 +368,7 @@ __global__ void __launch_bounds__(MAXT) k_rows_inv(const typename cplx_of<T>::ty
                     const double den = del - (aprev > 0.0 ? be * gam / aprev : 0.0);
                     al = den > 0.0 ? gam / den : 0.0;
                 }
+                if (fold.step == 0) scal[S_RS0] = gam;
                 scal[S_RS] = gam;
                 scal[S_ALPHA] = al;
                 scal[S_BETA] = be;
@@ -1087,10 +1103,10 @@ static size_t grid_smem_bytes(int tile) {
 }
 
 template <typename T, int J>
-static void grid_tj(purify_plan* p, const void* y, bool caller_order, const int* skip) {
+static void grid_tj(purify_plan* p, const void* y, bool caller_order, const int* skip, bool zeroed) {
     using C = typename cplx_of<T>::type;
     constexpr int W = grid_warps<T>();
-    PURIFY_CUDA(cudaMemsetAsync(p->gacc.p, 0, p->gacc.bytes, p->stream));
+    if (!zeroed) PURIFY_CUDA(cudaMemsetAsync(p->gacc.p, 0, p->gacc.bytes, p->stream));
     if (p->work.nsub == 0) return;
     const int tile = p->work.tile;
     const int S = grid_row_stride(tile, J);
@@ -1125,8 +1141,8 @@ int grid_list_unit(int dtype, int J) {
 
 template <int J> static void degrid_f(purify_plan* p, void* y, bool c, const int* s) { degrid_tj<float, J>(p, y, c, s); }
 template <int J> static void degrid_d(purify_plan* p, void* y, bool c, const int* s) { degrid_tj<double, J>(p, y, c, s); }
-template <int J> static void grid_f(purify_plan* p, const void* y, bool c, const int* s) { grid_tj<float, J>(p, y, c, s); }
-template <int J> static void grid_d(purify_plan* p, const void* y, bool c, const int* s) { grid_tj<double, J>(p, y, c, s); }
+template <int J> static void grid_f(purify_plan* p, const void* y, bool c, const int* s, bool z) { grid_tj<float, J>(p, y, c, s, z); }
+template <int J> static void grid_d(purify_plan* p, const void* y, bool c, const int* s, bool z) { grid_tj<double, J>(p, y, c, s, z); }
 
 
 // Run-set launches: a persistent grid of 8-warp blocks (as many as are
@@ -1156,16 +1172,16 @@ static void grid_sets_tj(purify_plan* p, const void* y, bool caller_order, const
 }
 template <int J> static void normal_f(purify_plan* p, const int* s, bool z) { grid_sets_tj<float, J, true>(p, nullptr, false, s, z); }
 template <int J> static void normal_d(purify_plan* p, const int* s, bool z) { grid_sets_tj<double, J, true>(p, nullptr, false, s, z); }
-template <int J> static void gsets_f(purify_plan* p, const void* y, bool c, const int* s) { grid_sets_tj<float, J, false>(p, y, c, s); }
-template <int J> static void gsets_d(purify_plan* p, const void* y, bool c, const int* s) { grid_sets_tj<double, J, false>(p, y, c, s); }
+template <int J> static void gsets_f(purify_plan* p, const void* y, bool c, const int* s, bool z) { grid_sets_tj<float, J, false>(p, y, c, s, z); }
+template <int J> static void gsets_d(purify_plan* p, const void* y, bool c, const int* s, bool z) { grid_sets_tj<double, J, false>(p, y, c, s, z); }
 
 void launch_normal_gg(purify_plan* p, const int* skip, bool zeroed) {
     if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, normal_f, p, skip, zeroed); }
     else { PURIFY_J_DISPATCH(p->J, normal_d, p, skip, zeroed); }
 }
-void launch_grid_sets(purify_plan* p, const void* y, bool caller_order, const int* skip) {
-    if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, gsets_f, p, y, caller_order, skip); }
-    else { PURIFY_J_DISPATCH(p->J, gsets_d, p, y, caller_order, skip); }
+void launch_grid_sets(purify_plan* p, const void* y, bool caller_order, const int* skip, bool zeroed) {
+    if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, gsets_f, p, y, caller_order, skip, zeroed); }
+    else { PURIFY_J_DISPATCH(p->J, gsets_d, p, y, caller_order, skip, zeroed); }
 }
 
 template <int J> static int max_tile_f() {
@@ -1211,24 +1227,24 @@ void launch_degrid(purify_plan* p, void* y, bool caller_order, const int* skip) 
     if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, degrid_f, p, y, caller_order, skip); }
     else { PURIFY_J_DISPATCH(p->J, degrid_d, p, y, caller_order, skip); }
 }
-void launch_grid(purify_plan* p, const void* y, bool caller_order, const int* skip) {
+void launch_grid(purify_plan* p, const void* y, bool caller_order, const int* skip, bool zeroed) {
     if (p->grid_by_runs) {
-        launch_grid_sets(p, y, caller_order, skip);
+        launch_grid_sets(p, y, caller_order, skip, zeroed);
         return;
     }
-    if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, grid_f, p, y, caller_order, skip); }
-    else { PURIFY_J_DISPATCH(p->J, grid_d, p, y, caller_order, skip); }
+    if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, grid_f, p, y, caller_order, skip, zeroed); }
+    else { PURIFY_J_DISPATCH(p->J, grid_d, p, y, caller_order, skip, zeroed); }
 }
 
-void launch_phi(purify_plan* p, const void* x, void* y, bool caller_order, double scale) {
-    launch_scale_pad_rows(p, x, scale, nullptr, nullptr, nullptr, nullptr);
+void launch_phi(purify_plan* p, const void* x, void* y, bool caller_order, double scale, bool zero_acc) {
+    launch_scale_pad_rows(p, x, scale, nullptr, nullptr, nullptr, nullptr, true, zero_acc);
     launch_cols_fwd(p, nullptr);
     launch_degrid(p, y, caller_order, nullptr);
 }
 
 void launch_phi_adj(purify_plan* p, const void* y, void* out, bool caller_order, double scale, int out_mode,
-                    const void* add) {
-    launch_grid(p, y, caller_order, nullptr);
+                    const void* add, bool acc_zeroed) {
+    launch_grid(p, y, caller_order, nullptr, acc_zeroed);
     launch_cols_inv(p, nullptr);
     launch_rows_inv_crop(p, out, scale, out_mode, add, 1.0, nullptr);
 }

@@ -152,42 +152,6 @@ __global__ void k_positivity(const T* __restrict__ x, T* __restrict__ z3, const 
     pdl_trigger();
 }
 
-// CG start: r holds b - A x (with `addend` set, r + addend does: the
-// image-space terms are added here so that the adjoint part of r can be
-// formed beside the wavelet branch). p = 0 and beta = 0 so that the first
-// direction update gives p = r; rs = rs0 = r.r; the done flag is cleared.
-template <typename T>
-__global__ void k_cg_init(T* __restrict__ r, const T* __restrict__ addend, T* __restrict__ p, T* __restrict__ s,
-                          int64_t N, double* part, unsigned* counters, double* scal, int* flags) {
-    pdl_wait();
-    T acc = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        T v = r[i];
-        if (addend) {
-            v += addend[i];
-            r[i] = v;
-        }
-        acc += v * v;
-        p[i] = T(0);
-        s[i] = T(0);
-    }
-    double b = block_sum((double)acc);
-    if (threadIdx.x == 0) part[blockIdx.x] = b;
-    if (arrive_last(counters + C_CGI)) {
-        double tot = ordered_sum(part, gridDim.x);
-        if (threadIdx.x == 0) {
-            scal[S_RS] = tot;
-            scal[S_RS0] = tot;
-            scal[S_BETA] = 0.0;
-            scal[S_PEND] = -1000.0;   // no pending update (never step - 1)
-            flags[F_CGDONE] = tot == 0.0 ? 1 : 0;
-            if (!(tot == tot)) flags[F_NAN] = 1;
-            counters[C_CGI] = 0;
-        }
-    }
-    pdl_trigger();
-}
-
 template <typename T>
 __global__ void k_relchange(T* __restrict__ x, const T* __restrict__ xprev, int64_t N, double* part,
                             unsigned* counters, double* scal, CgFold fold, T* __restrict__ pdir) {
@@ -522,8 +486,9 @@ template <typename T> struct Solver {
             p->stream = s.side;
         }
         try {
-            // f2
-            launch_phi(p, x, s.v2.p, false, inv_nu);
+            // f2 (the forward row pass also clears the gridding accumulator
+            // of the adjoint below)
+            launch_phi(p, x, s.v2.p, false, inv_nu, true);
             proj_norms(true);
             {
                 Launch L(p, "proj_apply");
@@ -535,7 +500,7 @@ template <typename T> struct Solver {
                 L.done();
             }
             // r = Re Phi^H v2 / nu (the image-space terms are added at the CG start)
-            launch_phi_adj(p, s.v2.p, s.r.p, false, inv_nu, 1, nullptr);
+            launch_phi_adj(p, s.v2.p, s.r.p, false, inv_nu, 1, nullptr, true);
             if (s.toeplitz) {
                 // r -= (normal operator by circulant embedding) x
                 launch_scale_pad_rows(p, x, 1.0, nullptr, nullptr, nullptr, nullptr, false);
@@ -568,22 +533,18 @@ template <typename T> struct Solver {
             L.done();
         }
         if (fork) PURIFY_CUDA(cudaStreamWaitEvent(p->stream, s.ev_join, 0));
-        {
-            Launch L(p, "cg_init");
-            launch_dependent(k_cg_init<T>, red_blocks(p->N), RB, 0, p->stream, s.r.template as<T>(),
-                             s.addend.template as<T>(), s.p.template as<T>(), s.Ap.template as<T>(), p->N, part(),
-                             ctr(), scal(), flags());
-            L.done();
-        }
         const int* skip = flags() + F_CGDONE;
-        // CG (Chronopoulos-Gear arrangement, see CgFold): step k applies the
-        // operator to r; the update of step k is applied by the forward row
-        // pass of step k + 1 or, after the last step, by the relative-change kernel
+        // CG (Chronopoulos-Gear arrangement, see CgFold): the forward row pass
+        // of step 0 adds the image-space terms to r and starts the solve; step
+        // k applies the operator to r; the update of step k is applied by the
+        // forward row pass of step k + 1 or, after the last step, by the
+        // relative-change kernel
         CgFold fold;
         fold.x = x;
         fold.r = s.r.p;
         fold.s = s.Ap.p;
         fold.u = s.u.p;
+        fold.add = s.addend.p;
         fold.scal = scal();
         fold.flags = flags();
         for (int k = 0; k < cg_iters; ++k) {
