@@ -1,0 +1,74 @@
+// The scalars of one Chronopoulos-Gear CG step (see CgFold), reduced from the
+// inverse row pass's per-block partial dot products by the kernel that
+// consumes them: every block of that kernel sums the partials in the same
+// fixed order, so all blocks agree without a last-block pass in the producer.
+#pragma once
+#include "internal.h"
+#include "reduce.cuh"
+
+namespace purify {
+
+// Step k's gamma = r.r and delta = r.A r from f.part[2 i], f.part[2 i + 1]
+// (i < f.nparts), then
+//   beta = gamma / gamma_prev (0 at step 0),
+//   alpha = gamma / (delta - beta gamma / alpha_prev)  (gamma / delta at step 0),
+// with gamma_prev, alpha_prev read from the slots of step k - 1 (slots
+// alternate by step parity, so the block that records step k never
+// overwrites what the other blocks of the same kernel still read). Block 0
+// records the scalars, the stop and non-finite flags and the step count.
+// Returns true when the step's update is to be applied (no stop: gamma > 0
+// and above tol^2 gamma_0, all finite). Every thread of the block must call
+// it.
+__device__ __forceinline__ bool cg_step_scalars(const CgFold& f, int k, double& al, double& be) {
+    __shared__ double sh_gam, sh_del;
+    double s0 = 0.0, s1 = 0.0;
+    for (int i = threadIdx.x; i < f.nparts; i += blockDim.x) {
+        s0 += __ldcg(f.part + 2 * i);
+        s1 += __ldcg(f.part + 2 * i + 1);
+    }
+    s0 = block_sum(s0);
+    s1 = block_sum(s1);
+    if (threadIdx.x == 0) {
+        sh_gam = s0;
+        sh_del = s1;
+    }
+    __syncthreads();
+    const double gam = sh_gam, del = sh_del;
+    be = 0.0;
+    if (k == 0) {
+        al = del > 0.0 ? gam / del : 0.0;
+    } else {
+        const double gprev = f.scal[S_RS_STEP + ((k - 1) & 1)], aprev = f.scal[S_ALPHA_STEP + ((k - 1) & 1)];
+        be = gprev > 0.0 ? gam / gprev : 0.0;
+        const double den = del - (aprev > 0.0 ? be * gam / aprev : 0.0);
+        al = den > 0.0 ? gam / den : 0.0;
+    }
+    const double g0 = k == 0 ? gam : f.scal[S_RS0];
+    const bool bad = !(gam == gam) || !(al == al);
+    const bool stop = bad || gam == 0.0 || gam <= f.scal[S_TOL2] * g0;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (k == 0) f.scal[S_RS0] = gam;
+        f.scal[S_RS_STEP + (k & 1)] = gam;
+        f.scal[S_ALPHA_STEP + (k & 1)] = al;
+        f.scal[S_RS] = gam;
+        f.scal[S_ALPHA] = al;
+        f.scal[S_BETA] = be;
+        f.scal[S_PAP] = del;
+        if (bad) f.flags[F_NAN] = 1;
+        if (stop) f.flags[F_CGDONE] = 1;
+        else f.scal[S_CGCOUNT] += 1.0;
+    }
+    return !stop;
+}
+
+// A flag read once per block (thread 0) and shared, so that every thread of
+// the block takes the same branch even while another block of the same
+// kernel may be setting it.
+__device__ __forceinline__ int block_flag(const int* flag) {
+    __shared__ int sh;
+    if (threadIdx.x == 0) sh = flag ? *reinterpret_cast<const volatile int*>(flag) : 0;
+    __syncthreads();
+    return sh;
+}
+
+}  // namespace purify

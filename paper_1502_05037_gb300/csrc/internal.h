@@ -178,26 +178,30 @@ namespace purify {
 // Conjugate gradients in the Chronopoulos-Gear arrangement (equal to the
 // textbook iteration in exact arithmetic; one synchronisation per step): the
 // operator is applied to the residual, u = A r, and the inverse row pass of
-// step k reduces gamma = r.r and delta = r.u directly; its last block sets
-//   beta = gamma / gamma_prev (0 at step 0),
-//   alpha = gamma / (delta - beta gamma / alpha_prev)  (gamma / delta at step 0)
-// and leaves the step's update pending (scal[S_PEND] = k), unless gamma meets
-// the stop test (gamma <= tol^2 gamma_0, gamma_0 recorded at step 0). The
+// step k writes per-block partials of gamma = r.r and delta = r.u. The
 // forward row pass of step k + 1 (or the relative-change kernel after the
-// last step) applies it, p = r + beta p, s = u + beta s (s = A p),
-// x += alpha p, r -= alpha s, and transforms the new r. The forward row pass
+// last step) reduces them in every block (cg_step_scalars), to
+//   beta = gamma / gamma_prev (0 at step 0),
+//   alpha = gamma / (delta - beta gamma / alpha_prev)  (gamma / delta at step 0),
+// and unless gamma meets the stop test (gamma <= tol^2 gamma_0, gamma_0 of
+// step 0) applies the update p = r + beta p, s = u + beta s (s = A p),
+// x += alpha p, r -= alpha s, then transforms the new r. The forward row pass
 // of step 0 starts the solve: r += add (the residual's terms formed outside
-// the pass), p = s = 0, the stop flag and the pending marker cleared.
+// the pass), p = s = 0, the stop flag cleared.
 struct CgFold {
-    void* x = nullptr;          // iterate [N]
-    void* r = nullptr;          // residual [N]
-    void* s = nullptr;          // A p [N]
-    const void* u = nullptr;    // A r [N]
-    const void* add = nullptr;  // added to r at step 0 (may be null)
+    void* x = nullptr;           // iterate [N]
+    void* r = nullptr;           // residual [N]
+    void* s = nullptr;           // A p [N]
+    const void* u = nullptr;     // A r [N]
+    const void* add = nullptr;   // added to r at step 0 (may be null)
+    const double* part = nullptr;   // the inverse row pass's partials, 2 per block
+    int nparts = 0;              // blocks of the inverse row pass
     double* scal = nullptr;
     int* flags = nullptr;
     int step = 0;
 };
+// blocks of the inverse row pass (the number of CG partials it writes)
+int rows_inv_blocks(purify_plan* p);
 
 // ----------------------------------------------------------- operator steps
 // Phi: x real [ny][nx] (internal pointer) -> y complex [M]. If perm != null

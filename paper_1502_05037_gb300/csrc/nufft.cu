@@ -16,6 +16,7 @@
 
 #include <algorithm>
 
+#include "cg.cuh"
 #include "internal.h"
 #include "launch.h"
 #include "reduce.cuh"
@@ -167,23 +168,27 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(const T* __restrict__ x, type
                            typename cplx_of<T>::type* __restrict__ zero_grid, int Ky, CgFold fold) {
     using C = typename cplx_of<T>::type;
     pdl_wait();
-    // step 0 starts the solve; later steps apply the previous step's update,
-    // if pending (see CgFold)
+    // step 0 starts the solve; later steps first apply the previous step's
+    // update unless it met the stop test (see CgFold)
     const bool first = fold.x && fold.step == 0;
-    const bool pending = fold.x && !first && (int)fold.scal[S_PEND] == fold.step - 1;
-    const T alpha = pending ? (T)fold.scal[S_ALPHA] : T(0);
-    const T cbeta = pending ? (T)fold.scal[S_BETA] : T(0);
     T* const fx = static_cast<T*>(fold.x);
     T* const fr = static_cast<T*>(fold.r);
     T* const fs = static_cast<T*>(fold.s);
     const T* const fu = static_cast<const T*>(fold.u);
     const T* const fadd = static_cast<const T*>(fold.add);
-    if (!first && skip && *skip) return;   // stopped: the last update was not left pending
-    if (first && blockIdx.x == 0 && threadIdx.x == 0) {
-        // no other block of this pass reads these; the next kernels do
-        fold.flags[F_CGDONE] = 0;
-        fold.scal[S_PEND] = -1000.0;   // never step - 1
+    // stopped at an earlier step (block 0 of this pass may set the flag
+    // meanwhile: each block reads it once)
+    if (block_flag(first ? nullptr : skip)) return;
+    bool pending = false;
+    T alpha = T(0), cbeta = T(0);
+    if (fold.x && !first) {
+        double al, be;
+        if (!cg_step_scalars(fold, fold.step - 1, al, be)) return;   // stopped at the previous step
+        pending = true;
+        alpha = (T)al;
+        cbeta = (T)be;
     }
+    if (first && blockIdx.x == 0 && threadIdx.x == 0) fold.flags[F_CGDONE] = 0;   // the next kernels read it
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (zero_grid) {
         const int per = Ky / gridDim.x;   // whole rows per block (Ky is a multiple of the block count)
@@ -342,46 +347,13 @@ __global__ void __launch_bounds__(MAXT) k_rows_inv(const typename cplx_of<T>::ty
     auto slot = [&](int n) -> C& { return buf[fft_pad(n)]; };
     fft_reg<C, true>(Kx, ilog2(Kx), t, tw, load, store, slot);
     if (dot_part && cg) {
-        // Chronopoulos-Gear scalars (see CgFold): gamma = r.r, delta = r.A r
+        // Chronopoulos-Gear partials (see CgFold): gamma = r.r, delta = r.A r;
+        // the consumer of this step's scalars reduces them
         const double b0 = block_sum((double)gacc2);
         const double b1 = block_sum((double)dacc);
         if (threadIdx.x == 0) {
             dot_part[2 * blockIdx.x] = b0;
             dot_part[2 * blockIdx.x + 1] = b1;
-        }
-        if (arrive_last(counters + C_ALPHA)) {
-            double s0 = 0.0, s1 = 0.0;
-            for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) {
-                s0 += __ldcg(dot_part + 2 * k);
-                s1 += __ldcg(dot_part + 2 * k + 1);
-            }
-            s0 = block_sum(s0);
-            s1 = block_sum(s1);
-            if (threadIdx.x == 0) {
-                const double gam = s0, del = s1;
-                double be = 0.0, al;
-                if (fold.step == 0) {
-                    al = del > 0.0 ? gam / del : 0.0;
-                } else {
-                    const double gprev = scal[S_RS], aprev = scal[S_ALPHA];
-                    be = gprev > 0.0 ? gam / gprev : 0.0;
-                    const double den = del - (aprev > 0.0 ? be * gam / aprev : 0.0);
-                    al = den > 0.0 ? gam / den : 0.0;
-                }
-                if (fold.step == 0) scal[S_RS0] = gam;
-                scal[S_RS] = gam;
-                scal[S_ALPHA] = al;
-                scal[S_BETA] = be;
-                scal[S_PAP] = del;
-                const bool stop = gam == 0.0 || gam <= scal[S_TOL2] * scal[S_RS0];
-                if (!(gam == gam) || !(al == al)) { fold.flags[F_NAN] = 1; fold.flags[F_CGDONE] = 1; }
-                else if (stop) fold.flags[F_CGDONE] = 1;
-                else {
-                    scal[S_PEND] = (double)fold.step;
-                    scal[S_CGCOUNT] += 1.0;
-                }
-                counters[C_ALPHA] = 0;
-            }
         }
     } else if (dot_part) {
         double b = block_sum((double)dacc);
@@ -1070,6 +1042,14 @@ static void rows_inv_t(purify_plan* p, void* out, double scale, int out_mode, co
     L.done();
 }
 
+
+int rows_inv_blocks(purify_plan* p) {
+    int rb = p->fft_rb > 0 ? p->fft_rb
+                           : (p->dtype == PURIFY_F32 ? rows_per_block<float>(p->ny, p->Kx)
+                                                     : rows_per_block<double>(p->ny, p->Kx));
+    while (p->ny % rb) rb >>= 1;
+    return p->ny / rb;
+}
 
 template <typename T, int J> static void degrid_tj(purify_plan* p, void* y, bool caller_order, const int* skip) {
     using C = typename cplx_of<T>::type;

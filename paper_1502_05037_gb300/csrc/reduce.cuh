@@ -24,7 +24,8 @@ enum Slot {
     S_GMAX = 11,     // max |.| reduction result
     S_NORM2 = 12,    // generic norm^2 result
     S_SUM = 13,      // generic sum result
-    S_PEND = 14,     // CG step whose update (x += alpha p, r -= alpha Ap) is still to be applied (-1000: none)
+    S_RS_STEP = 15,      // r.r of CG steps of even / odd index (15, 16)
+    S_ALPHA_STEP = 17,   // alpha of CG steps of even / odd index (17, 18)
     S_BLOCKS = 32    // then R entries of ||r_i||^2, then R of ||Phi_i x/nu - ybar_i||^2
 };
 enum Counter { C_PROX = 0, C_PROJ, C_CGI, C_ALPHA, C_UPD, C_REL, C_GEN, C_COUNT };

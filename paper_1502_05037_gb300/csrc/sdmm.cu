@@ -25,6 +25,7 @@
 #include <cstring>
 #include <vector>
 
+#include "cg.cuh"
 #include "internal.h"
 #include "launch.h"
 #include "reduce.cuh"
@@ -156,9 +157,17 @@ template <typename T>
 __global__ void k_relchange(T* __restrict__ x, const T* __restrict__ xprev, int64_t N, double* part,
                             unsigned* counters, double* scal, CgFold fold, T* __restrict__ pdir) {
     pdl_wait();
-    // the last CG step's update first, when it is still pending (see CgFold)
-    const bool pending = fold.x && (int)scal[S_PEND] == fold.step;
-    const T alpha = pending ? (T)scal[S_ALPHA] : T(0), beta = pending ? (T)scal[S_BETA] : T(0);
+    // the last CG step's update first, unless the solve stopped (see CgFold)
+    bool pending = false;
+    T alpha = T(0), beta = T(0);
+    if (fold.x && !block_flag(fold.flags + F_CGDONE)) {
+        double al, be;
+        if (cg_step_scalars(fold, fold.step, al, be)) {
+            pending = true;
+            alpha = (T)al;
+            beta = (T)be;
+        }
+    }
     T* const r = static_cast<T*>(fold.r);
     T* const sv = static_cast<T*>(fold.s);
     const T* const u = static_cast<const T*>(fold.u);
@@ -303,7 +312,11 @@ template <typename T> struct Solver {
     // the projection norms keep their partial sums apart from every other
     // reduction, so that they can run beside the wavelet branch
     static constexpr size_t kProjPart = 16384;
+    static constexpr size_t kCgPart = 8192;   // [kCgPart, kProjPart): the CG partials
     double* proj_part() { return s.part.as<double>() + kProjPart; }
+    // the CG partials (2 per inverse-row-pass block, at most 2 * 4096), apart
+    // from the partials the relative-change kernel writes while it reads them
+    double* cg_part() { return s.part.as<double>() + kCgPart; }
     unsigned* ctr() { return s.counters.as<unsigned>(); }
     int* flags() { return reinterpret_cast<int*>(s.counters.as<unsigned>() + 16); }
 
@@ -545,6 +558,8 @@ template <typename T> struct Solver {
         fold.s = s.Ap.p;
         fold.u = s.u.p;
         fold.add = s.addend.p;
+        fold.part = cg_part();
+        fold.nparts = rows_inv_blocks(p);
         fold.scal = scal();
         fold.flags = flags();
         for (int k = 0; k < cg_iters; ++k) {
@@ -554,7 +569,7 @@ template <typename T> struct Solver {
                 launch_scale_pad_rows(p, nullptr, 1.0, s.p.p, s.r.p, nullptr, skip, false, false, &fold);
                 launch_cols_fwd(p, skip);
                 launch_cols_inv(p, skip, s.toep.p);
-                launch_rows_inv_crop(p, s.u.p, 1.0, 1, s.r.p, 2.0, skip, part(), ctr(), scal(), false, &fold);
+                launch_rows_inv_crop(p, s.u.p, 1.0, 1, s.r.p, 2.0, skip, cg_part(), ctr(), scal(), false, &fold);
             } else {
                 // the pending update and the transform of the new r fused into
                 // the first FFT pass, then u = A r
@@ -564,7 +579,7 @@ template <typename T> struct Solver {
                 launch_cols_inv(p, skip);
                 // u = 2 r + Re Phi^H Phi r / nu^2, with r.r, r.u and the CG
                 // scalars fused in
-                launch_rows_inv_crop(p, s.u.p, inv_nu, 1, s.r.p, 2.0, skip, part(), ctr(), scal(), true, &fold);
+                launch_rows_inv_crop(p, s.u.p, inv_nu, 1, s.r.p, 2.0, skip, cg_part(), ctr(), scal(), true, &fold);
             }
         }
         // the last step's pending update is applied by the relative-change kernel
