@@ -396,6 +396,27 @@ def run_ours(args):
         toep = {"value": args.steps / (tms / 1e3), "unit": "iters/s", "ms_per_step": tms / args.steps,
                 "note": "CG normal operator by circulant embedding of the exact model (separate parity class)"}
 
+    # ---- pass A'': primal-dual (Chambolle-Pock) iterations on the same problem,
+    # timed as the difference of two synchronous solves (setup and statistics
+    # cancel)
+    pdl = None
+    if args.pd_pass:
+        xp = torch.zeros((wl.ny, wl.nx), dtype=rdt, device=dev)
+        pk.purify_pd_solve(plan, y, eps, xp, iters=5, nu=nu)   # captures the iteration graph
+        reps = 4 * args.steps
+        walls = []
+        for n_it in (5, 5 + reps):
+            xp.zero_()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            pk.purify_pd_solve(plan, y, eps, xp, iters=n_it, nu=nu)
+            walls.append(time.perf_counter() - t0)
+        per = (walls[1] - walls[0]) / reps
+        pdl = {"value": 1.0 / per, "unit": "iters/s", "ms_per_step": per * 1e3,
+               "note": "Chambolle-Pock primal-dual iterations (no inner CG; a different solver of problem (3), "
+                       "parity-tested against its FP64 oracle), back to back without an L2 flush, from the "
+                       "wall-clock difference of two synchronous solves"}
+
     # ---- pass D: Phi + Phi^dagger Gvis/s (caller order, device buffers)
     xin = torch.from_numpy(x_true).to(rdt).to(dev)
     yv = torch.empty(wl.M, dtype=cdt, device=dev)
@@ -436,6 +457,7 @@ def run_ours(args):
             "e2e": e2e, "gpu_launches": int(launches), "gpu_launches_per_step": launches / args.steps,
             "wall_s_timed": t_wall, "clocks": clocks, "roofline": roofline, "cpu_baseline": cpu,
             "toeplitz_cg": toep,
+            "primal_dual": pdl,
             "kernels": kernel_table,
         }
         print(json.dumps(line), flush=True)
@@ -729,6 +751,8 @@ def main():
     ap.add_argument("--cg-iters", type=int, default=CG_ITERS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-pd-pass", dest="pd_pass", action="store_false",
+                    help="skip timing the primal-dual solver")
     ap.add_argument("--no-toeplitz-pass", dest="toeplitz_pass", action="store_false",
                     help="skip the extra timed pass with the circulant-embedded CG normal operator")
     ap.add_argument("--channels32", action="store_true",

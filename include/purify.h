@@ -186,6 +186,32 @@ purify_status purify_sdmm_solve(purify_plan *plan, const void *y, const double *
  * started on the plan. */
 purify_status purify_sdmm_iterate(purify_plan *plan, int32_t iters);
 
+/* Primal-dual solver for problem (3) without an inner CG (the paper's SDMM
+ * family; Chambolle & Pock 2011, Algorithm 1 with theta = 1) on
+ *   min_x  i_{R_+^N}(x) + ||W v||_1 + sum_i i_{B(y_i/nu, eps_i/nu)}(s_i),
+ *   (v, s) = K x,  K = [Psi^dagger; Phi/nu],
+ * with complex blocks taken as real vectors, so K^*(v, s) = Psi v + Re Phi^H s/nu
+ * and ||K||^2 <= 2. From x_0 = x (input), xbar = x, p1 = 0, p2 = 0, each
+ * iteration does
+ *   p1 = clip(p1 + sigma Psi^dagger xbar, -w, w);
+ *   q = p2 + sigma Phi xbar/nu,  p2_i = q_i - sigma proj_{B(y_i/nu, eps_i/nu)}(q_i/sigma);
+ *   x_new = max(x - tau (Psi p1 + Re Phi^H p2/nu), 0);  xbar = 2 x_new - x;  x = x_new.
+ * The iterations run as replays of a captured CUDA graph. It uses the plan's
+ * solver state, so a previously started purify_sdmm_solve can no longer be
+ * resumed afterwards. stats (HOST, may be NULL) are evaluated at the returned
+ * x (cg_iters_total = 0, gamma = 0, rel_change = 0). Synchronous.
+ * Errors: EINVAL (null y, eps or x; eps not positive; tau or sigma not finite),
+ * ENAN (non-finite visibilities), ECUDA. */
+typedef struct {
+    int32_t iters;      /* primal-dual iterations (exact count, >= 0) */
+    double tau;         /* primal step; <= 0 => 0.05 */
+    double sigma;       /* dual step; <= 0 => 9.8 (tau sigma ||K||^2 < 1 for the defaults) */
+    double nu;          /* data-term scale ||Phi||_2; <= 0 => 100 power iterations */
+} purify_pd_params;
+
+purify_status purify_pd_solve(purify_plan *plan, const void *y, const double *eps, const void *w,
+                              void *x, const purify_pd_params *params, purify_sdmm_stats *stats);
+
 /* Batched channels: independent problems (one plan each, e.g. the spectral
  * channels of one observation) advanced together. Every plan must already
  * hold a started solve (purify_sdmm_solve). purify_batch_iterate runs

@@ -13,7 +13,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (PURIFY_F32, PURIFY_F64, PurifyError, check, load, purify_kernel_time, purify_plan_desc,
-                   purify_plan_info, purify_sdmm_params, purify_sdmm_stats)
+                   purify_pd_params, purify_plan_info, purify_sdmm_params, purify_sdmm_stats)
 
 __all__ = [
     "Plan", "purify_plan_create", "purify_plan_destroy", "purify_phi", "purify_phi_adj", "purify_fft2",
@@ -140,6 +140,17 @@ def purify_sdmm_solve(plan: Plan, y, eps, x, w=None, max_iter=200, cg_iters=10, 
     status = load().purify_sdmm_solve(plan.handle, _ptr(y), eps_ptr, _ptr(w), _ptr(x), C.byref(prm), C.byref(st))
     if raise_on_error:
         check(status)
+    return st
+
+
+def purify_pd_solve(plan: Plan, y, eps, x, w=None, iters=200, tau=0.0, sigma=0.0, nu=0.0):
+    """Primal-dual (Chambolle-Pock) iterations for problem (3); x is updated
+    in place. Returns purify_sdmm_stats."""
+    eps_np = np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
+    prm = purify_pd_params(iters=iters, tau=tau, sigma=sigma, nu=nu)
+    st = purify_sdmm_stats()
+    check(load().purify_pd_solve(plan.handle, _ptr(y), eps_np.ctypes.data_as(C.POINTER(C.c_double)), _ptr(w),
+                                 _ptr(x), C.byref(prm), C.byref(st)))
     return st
 
 

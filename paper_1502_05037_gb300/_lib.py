@@ -63,6 +63,15 @@ class purify_sdmm_params(C.Structure):
     ]
 
 
+class purify_pd_params(C.Structure):
+    _fields_ = [
+        ("iters", C.c_int32),
+        ("tau", C.c_double),
+        ("sigma", C.c_double),
+        ("nu", C.c_double),
+    ]
+
+
 class purify_sdmm_stats(C.Structure):
     _fields_ = [
         ("iters", C.c_int32),
@@ -95,6 +104,8 @@ _SIGS = {
     "purify_sdmm_solve": (C.c_int, [_P, _P, C.POINTER(C.c_double), _P, _P,
                                     C.POINTER(purify_sdmm_params), C.POINTER(purify_sdmm_stats)]),
     "purify_sdmm_iterate": (C.c_int, [_P, C.c_int32]),
+    "purify_pd_solve": (C.c_int, [_P, _P, C.POINTER(C.c_double), _P, _P,
+                                  C.POINTER(purify_pd_params), C.POINTER(purify_sdmm_stats)]),
     "purify_batch_create": (C.c_int, [C.POINTER(_P), C.c_int32, _P, C.POINTER(_P)]),
     "purify_batch_iterate": (C.c_int, [_P, C.c_int32]),
     "purify_batch_destroy": (C.c_int, [_P]),

@@ -243,6 +243,18 @@ purify_status purify_sdmm_solve(purify_plan* p, const void* y, const double* eps
     });
 }
 
+purify_status purify_pd_solve(purify_plan* p, const void* y, const double* eps, const void* w, void* x,
+                              const purify_pd_params* params, purify_sdmm_stats* stats) {
+    return guarded([&] {
+        PURIFY_REQUIRE(p && params && x && y && eps, "null argument");
+        PURIFY_REQUIRE(params->iters >= 0, "negative iteration count");
+        PURIFY_REQUIRE(std::isfinite(params->tau) && std::isfinite(params->sigma) && std::isfinite(params->nu),
+                       "tau, sigma and nu must be finite");
+        if (stats) std::memset(stats, 0, sizeof(*stats));
+        pd_solve(p, y, eps, w, x, *params, stats);
+    });
+}
+
 purify_status purify_sdmm_iterate(purify_plan* p, int32_t iters) {
     return guarded([&] {
         PURIFY_REQUIRE(p != nullptr && iters >= 0, "bad argument");

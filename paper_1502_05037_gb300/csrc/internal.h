@@ -115,6 +115,9 @@ struct SdmmState {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaGraphExec_t gexec = nullptr;
+    cudaGraphExec_t pd_gexec = nullptr;   // one primal-dual iteration
+    double pd_key[4] = {0, 0, 0, 0};      // tau, sigma, nu, weights of pd_gexec
+    int64_t pd_kernels = 0;
     int g_cg = -1;
     double g_gamma = 0, g_nu = 0;
     bool g_have_w = false;
@@ -122,6 +125,7 @@ struct SdmmState {
     int64_t g_kernels = 0;
     ~SdmmState() {
         if (gexec) cudaGraphExecDestroy(gexec);
+        if (pd_gexec) cudaGraphExecDestroy(pd_gexec);
         if (ev_in) cudaEventDestroy(ev_in);
         if (ev_out) cudaEventDestroy(ev_out);
         if (gstream) cudaStreamDestroy(gstream);
@@ -279,6 +283,8 @@ struct BatchState {
 void batch_iterate(BatchState* b, int iters);
 void batch_destroy(BatchState* b);
 void sdmm_iterate(purify_plan* p, int iters);
+void pd_solve(purify_plan* p, const void* y, const double* eps, const void* w, void* x,
+              const purify_pd_params& prm, purify_sdmm_stats* st);
 void add_launches(int64_t n);
 bool timing_enabled(const purify_plan* p);
 void reweight(purify_plan* p, const void* x, double rho, void* w);

@@ -108,14 +108,17 @@ __global__ void k_proj_norms(const typename cplx_of<T>::type* __restrict__ v2,
     pdl_trigger();
 }
 
-// Projection onto each block's ball plus multiplier update; v2 (= Phi x / nu)
-// is replaced by s2 - z2 - v2 for the fused CG residual (by s2 - z2 when
-// keep_v: the embedded normal operator forms A x separately).
+// Projection onto each block's ball plus multiplier update, s2 = proj(v2 + z2),
+// z2 += v2 - s2, with v2 (= Phi x / nu) replaced by
+//   out_mode 0: s2 - z2 - v2 (the fused CG residual),
+//   out_mode 1: s2 - z2 (the embedded normal operator forms A x separately),
+//   out_mode 2: z2 (the primal-dual solver: z2 = p2 / sigma, the dual
+//               variable of the balls; see pd_solve).
 template <typename T>
 __global__ void k_proj_apply(typename cplx_of<T>::type* __restrict__ v2, typename cplx_of<T>::type* __restrict__ z2,
                              const typename cplx_of<T>::type* __restrict__ ybar, const int* __restrict__ cblk,
                              const int* __restrict__ cbeg, const int* __restrict__ cend,
-                             const double* __restrict__ eps, const double* __restrict__ scal, int R, int keep_v) {
+                             const double* __restrict__ eps, const double* __restrict__ scal, int R, int out_mode) {
     pdl_wait();
     using C = typename cplx_of<T>::type;
     const int ch = blockIdx.x;
@@ -123,14 +126,43 @@ __global__ void k_proj_apply(typename cplx_of<T>::type* __restrict__ v2, typenam
     const double nr = sqrt(scal[S_BLOCKS + r]);
     const double e = eps[r];
     const T f = nr > e ? (T)(e / nr) : T(1);
-    const T vk = keep_v ? T(0) : T(1);
+    const T vk = out_mode == 0 ? T(1) : T(0);
+    const T sk = out_mode == 2 ? T(0) : T(1);
     for (int m = cbeg[ch] + threadIdx.x; m < cend[ch]; m += blockDim.x) {
         C v = v2[m], z = z2[m], y = ybar[m];
         T rx = v.x + z.x - y.x, ry = v.y + z.y - y.y;
         T sx = y.x + rx * f, sy = y.y + ry * f;
         T zx = z.x + v.x - sx, zy = z.y + v.y - sy;
         z2[m] = cmake<C>(zx, zy);
-        v2[m] = cmake<C>(sx - zx - vk * v.x, sy - zy - vk * v.y);
+        v2[m] = out_mode == 2 ? cmake<C>(zx, zy) : cmake<C>(sk * sx - zx - vk * v.x, sk * sy - zy - vk * v.y);
+    }
+    pdl_trigger();
+}
+
+// Primal-dual dual step on the l1 term: p1 = clip(p1 + sigma c, -w, w), c =
+// Psi^dagger xbar (w = 1 without weights).
+template <typename T>
+__global__ void k_pd_dual_l1(const T* __restrict__ c, T* __restrict__ p1, const T* __restrict__ w, int64_t D,
+                             T sigma) {
+    pdl_wait();
+    for (int64_t d = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; d < D; d += (int64_t)gridDim.x * blockDim.x) {
+        const T wd = w ? w[d] : T(1);
+        const T t = p1[d] + sigma * c[d];
+        p1[d] = t > wd ? wd : (t < -wd ? -wd : t);
+    }
+    pdl_trigger();
+}
+
+// Primal-dual primal step: x_new = max(x - tau g, 0), xbar = 2 x_new - x.
+template <typename T>
+__global__ void k_pd_primal(T* __restrict__ x, const T* __restrict__ g, T* __restrict__ xbar, int64_t N, T tau) {
+    pdl_wait();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const T xv = x[i];
+        T xn = xv - tau * g[i];
+        xn = xn > T(0) ? xn : T(0);
+        xbar[i] = T(2) * xn - xv;
+        x[i] = xn;
     }
     pdl_trigger();
 }
@@ -593,6 +625,136 @@ template <typename T> struct Solver {
     }
 };
 
+// One primal-dual iteration (see pd_solve): state x, xbar (in r), p1 (in
+// z1), z = p2 / sigma (in z2). The ball branch (Phi xbar, the projections, the
+// adjoint of the new p2 up to its inverse row pass) runs on the side stream
+// beside the l1 branch (Psi^dagger xbar, the clip, Psi p1); the inverse row
+// pass then forms g = Psi p1 + Re Phi^H p2 / nu and the primal step follows.
+template <typename T> static void pd_iteration(Solver<T>& S, double tau, double sigma) {
+    using C = typename cplx_of<T>::type;
+    purify_plan* p = S.p;
+    SdmmState& s = S.s;
+    T* x = s.x.template as<T>();
+    T* xbar = s.r.template as<T>();
+    const double inv_nu = 1.0 / s.nu;
+    const bool fork = !timing_enabled(p);
+    cudaStream_t main_stream = p->stream;
+    if (fork) {
+        if (!s.side) {
+            PURIFY_CUDA(cudaStreamCreateWithFlags(&s.side, cudaStreamNonBlocking));
+            PURIFY_CUDA(cudaEventCreateWithFlags(&s.ev_fork, cudaEventDisableTiming));
+            PURIFY_CUDA(cudaEventCreateWithFlags(&s.ev_join, cudaEventDisableTiming));
+        }
+        PURIFY_CUDA(cudaEventRecord(s.ev_fork, main_stream));
+        PURIFY_CUDA(cudaStreamWaitEvent(s.side, s.ev_fork, 0));
+        p->stream = s.side;
+    }
+    try {
+        // q / sigma = z + Phi xbar / nu; z += Phi xbar / nu - proj(q / sigma)
+        launch_phi(p, xbar, s.v2.p, false, inv_nu, true);
+        S.proj_norms(true);
+        {
+            Launch L(p, "proj_apply");
+            launch_dependent(k_proj_apply<T>, p->nchunks, RB, 0, p->stream, s.v2.template as<C>(),
+                             s.z2.template as<C>(), s.ybar.template as<C>(), p->chunk_blk.as<int>(),
+                             p->chunk_beg.as<int>(), p->chunk_end.as<int>(), s.eps.template as<double>(),
+                             S.scal(), p->R, 2);
+            L.done();
+        }
+        launch_grid(p, s.v2.p, false, nullptr, true);
+        launch_cols_inv(p, nullptr);
+        if (fork) PURIFY_CUDA(cudaEventRecord(s.ev_join, s.side));
+    } catch (...) {
+        p->stream = main_stream;
+        throw;
+    }
+    p->stream = main_stream;
+    launch_psi_adj(p, xbar, s.c1.p);
+    {
+        Launch L(p, "pd_dual_l1");
+        launch_dependent(k_pd_dual_l1<T>, ew_blocks(p->D), 256, 0, p->stream, s.c1.template as<T>(),
+                         s.z1.template as<T>(), s.have_w ? s.w.template as<T>() : nullptr, p->D, (T)sigma);
+        L.done();
+    }
+    launch_psi(p, s.z1.p, s.p.p);
+    if (fork) PURIFY_CUDA(cudaStreamWaitEvent(p->stream, s.ev_join, 0));
+    // g = Psi p1 + Re Phi^H (sigma z) / nu
+    launch_rows_inv_crop(p, s.u.p, sigma * inv_nu, 1, s.p.p, 1.0, nullptr);
+    {
+        Launch L(p, "pd_primal");
+        launch_dependent(k_pd_primal<T>, ew_blocks(p->N), 256, 0, p->stream, x, s.u.template as<T>(), xbar,
+                         (int64_t)p->N, (T)tau);
+        L.done();
+    }
+}
+
+// Run `n` primal-dual iterations as replays of a captured one-iteration graph
+// (eager with kernel timing), ordered after and before the caller's stream.
+template <typename T> static void run_pd_iterations(purify_plan* p, int n, double tau, double sigma) {
+    SdmmState& s = p->sd;
+    Solver<T> S(p);
+    if (n <= 0) return;
+    if (timing_enabled(p)) {
+        for (int i = 0; i < n; ++i) pd_iteration<T>(S, tau, sigma);
+        return;
+    }
+    if (!s.gstream) {
+        PURIFY_CUDA(cudaStreamCreateWithFlags(&s.gstream, cudaStreamNonBlocking));
+        PURIFY_CUDA(cudaEventCreateWithFlags(&s.ev_in, cudaEventDisableTiming));
+        PURIFY_CUDA(cudaEventCreateWithFlags(&s.ev_out, cudaEventDisableTiming));
+    }
+    cudaStream_t user = p->stream;
+    PURIFY_CUDA(cudaEventRecord(s.ev_in, user));
+    PURIFY_CUDA(cudaStreamWaitEvent(s.gstream, s.ev_in, 0));
+    int start = 0;
+    const double key[4] = {tau, sigma, s.nu, s.have_w ? 1.0 : 0.0};
+    if (!s.pd_gexec || !std::equal(key, key + 4, s.pd_key)) {
+        if (s.pd_gexec) { cudaGraphExecDestroy(s.pd_gexec); s.pd_gexec = nullptr; }
+        p->stream = s.gstream;
+        try {
+            // one eager iteration first (sets kernel attributes outside capture)
+            pd_iteration<T>(S, tau, sigma);
+            start = 1;
+            cudaGraph_t g = nullptr;
+            PURIFY_CUDA(cudaStreamBeginCapture(s.gstream, cudaStreamCaptureModeThreadLocal));
+            try {
+                pd_iteration<T>(S, tau, sigma);
+            } catch (...) {
+                cudaStreamEndCapture(s.gstream, &g);
+                if (g) cudaGraphDestroy(g);
+                throw;
+            }
+            PURIFY_CUDA(cudaStreamEndCapture(s.gstream, &g));
+            size_t nn = 0;
+            PURIFY_CUDA(cudaGraphGetNodes(g, nullptr, &nn));
+            std::vector<cudaGraphNode_t> nodes(nn);
+            PURIFY_CUDA(cudaGraphGetNodes(g, nodes.data(), &nn));
+            int64_t kn = 0;
+            for (auto nd : nodes) {
+                cudaGraphNodeType t;
+                PURIFY_CUDA(cudaGraphNodeGetType(nd, &t));
+                if (t == cudaGraphNodeTypeKernel) ++kn;
+            }
+            cudaError_t ie = cudaGraphInstantiate(&s.pd_gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) { s.pd_gexec = nullptr; PURIFY_CUDA(ie); }
+            s.pd_kernels = kn;
+            std::copy(key, key + 4, s.pd_key);
+            add_launches(-kn);
+        } catch (...) {
+            p->stream = user;
+            throw;
+        }
+        p->stream = user;
+    }
+    for (int i = start; i < n; ++i) {
+        PURIFY_CUDA(cudaGraphLaunch(s.pd_gexec, s.gstream));
+        add_launches(s.pd_kernels);
+    }
+    PURIFY_CUDA(cudaEventRecord(s.ev_out, s.gstream));
+    PURIFY_CUDA(cudaStreamWaitEvent(user, s.ev_out, 0));
+}
+
 // Run `n` iterations: eager when kernel timing is on, otherwise as replays of
 // a captured one-iteration graph on the plan's private stream, ordered after
 // and before the caller's stream with events.
@@ -914,6 +1076,72 @@ void sdmm_solve(purify_plan* p, const void* y, const double* eps, const void* w,
                 const purify_sdmm_params& prm, purify_sdmm_stats* st) {
     if (p->dtype == PURIFY_F32) sdmm_solve_t<float>(p, y, eps, w, x, prm, st);
     else sdmm_solve_t<double>(p, y, eps, w, x, prm, st);
+}
+
+template <typename T>
+static void pd_solve_t(purify_plan* p, const void* y, const double* eps, const void* w, void* x_io,
+                       const purify_pd_params& prm, purify_sdmm_stats* st) {
+    using C = typename cplx_of<T>::type;
+    Solver<T> S(p);
+    S.ensure();
+    SdmmState& s = p->sd;
+    for (int r = 0; r < p->R; ++r)
+        PURIFY_REQUIRE(std::isfinite(eps[r]) && eps[r] > 0.0, "eps must be positive and finite");
+    const double tau = prm.tau > 0 ? prm.tau : 0.05, sigma = prm.sigma > 0 ? prm.sigma : 9.8;
+    s.started = false;   // the SDMM state is overwritten
+    s.nu = prm.nu > 0 ? prm.nu : std::sqrt(S.op_norm_sq(100));
+    if (is_host_pointer(y)) {
+        PURIFY_CUDA(cudaMemcpyAsync(p->tmp_vis.p, y, sizeof(C) * p->M, cudaMemcpyDefault, p->stream));
+        y = p->tmp_vis.p;
+    }
+    PURIFY_CUDA(cudaMemsetAsync(S.flags(), 0, sizeof(int) * F_COUNT, p->stream));
+    {
+        Launch L(p, "check_finite");
+        k_check_finite<T><<<ew_blocks(2 * p->M), 256, 0, p->stream>>>((const T*)y, 2 * p->M, S.flags());
+        L.done();
+    }
+    {
+        Launch L(p, "gather_scale");
+        k_gather_scale<T><<<ew_blocks(p->M), 256, 0, p->stream>>>((const C*)y, p->perm.as<int>(),
+                                                                  s.ybar.template as<C>(), p->M, (T)(1.0 / s.nu));
+        L.done();
+    }
+    std::vector<double> en(p->R);
+    for (int r = 0; r < p->R; ++r) en[r] = eps[r] / s.nu;
+    PURIFY_CUDA(cudaMemcpyAsync(s.eps.p, en.data(), sizeof(double) * p->R, cudaMemcpyHostToDevice, p->stream));
+    s.eps_host.assign(eps, eps + p->R);
+    s.have_w = w != nullptr;
+    if (w) PURIFY_CUDA(cudaMemcpyAsync(s.w.p, w, sizeof(T) * p->D, cudaMemcpyDefault, p->stream));
+    PURIFY_CUDA(cudaMemcpyAsync(s.x.p, x_io, sizeof(T) * p->N, cudaMemcpyDefault, p->stream));
+    PURIFY_CUDA(cudaMemcpyAsync(s.r.p, s.x.p, sizeof(T) * p->N, cudaMemcpyDeviceToDevice, p->stream));   // xbar = x
+    PURIFY_CUDA(cudaMemsetAsync(s.z1.p, 0, s.z1.bytes, p->stream));   // p1 = 0
+    PURIFY_CUDA(cudaMemsetAsync(s.z2.p, 0, s.z2.bytes, p->stream));   // p2 = 0
+    PURIFY_CUDA(cudaStreamSynchronize(p->stream));
+    int fl[F_COUNT];
+    PURIFY_CUDA(cudaMemcpy(fl, S.flags(), sizeof(fl), cudaMemcpyDeviceToHost));
+    if (fl[F_NAN]) throw Error{PURIFY_ENAN, "non-finite visibility"};
+    run_pd_iterations<T>(p, prm.iters, tau, sigma);
+    // statistics at the returned x
+    S.evaluate(s.x.template as<T>());
+    std::vector<double> sc(S_BLOCKS + 2 * p->R);
+    PURIFY_CUDA(cudaMemcpyAsync(sc.data(), S.scal(), sizeof(double) * sc.size(), cudaMemcpyDeviceToHost, p->stream));
+    PURIFY_CUDA(cudaMemcpyAsync(x_io, s.x.p, sizeof(T) * p->N, cudaMemcpyDefault, p->stream));
+    PURIFY_CUDA(cudaStreamSynchronize(p->stream));
+    if (st) {
+        st->iters = prm.iters;
+        st->objective = sc[S_OBJ];
+        double worst = 0.0;
+        for (int r = 0; r < p->R; ++r) worst = std::max(worst, std::sqrt(sc[S_BLOCKS + p->R + r]) * s.nu / s.eps_host[r]);
+        st->max_resid_over_eps = worst;
+        st->nu = s.nu;
+        st->status = PURIFY_OK;
+    }
+}
+
+void pd_solve(purify_plan* p, const void* y, const double* eps, const void* w, void* x,
+              const purify_pd_params& prm, purify_sdmm_stats* st) {
+    if (p->dtype == PURIFY_F32) pd_solve_t<float>(p, y, eps, w, x, prm, st);
+    else pd_solve_t<double>(p, y, eps, w, x, prm, st);
 }
 
 double op_norm_sq(purify_plan* p, int iters) {

@@ -57,6 +57,8 @@ int main(void) {
   printf("params %zu\n", sizeof(purify_sdmm_params));
   printf("stats %zu\n", sizeof(purify_sdmm_stats));
   printf("ktime %zu\n", sizeof(purify_kernel_time));
+  printf("pd %zu\n", sizeof(purify_pd_params));
+  P(purify_pd_params, tau) P(purify_pd_params, nu)
   P(purify_plan_desc, tile) P(purify_plan_desc, stream) P(purify_plan_desc, dtype) P(purify_plan_desc, block_offsets)
   P(purify_sdmm_params, resume) P(purify_sdmm_params, check_every) P(purify_sdmm_params, toeplitz) P(purify_sdmm_stats, status)
   P(purify_plan_info, workspace_bytes) P(purify_plan_info, beta) P(purify_plan_info, grid_mode)
@@ -76,6 +78,9 @@ int main(void) {
     assert int(got["params"]) == ctypes.sizeof(_lib.purify_sdmm_params)
     assert int(got["stats"]) == ctypes.sizeof(_lib.purify_sdmm_stats)
     assert int(got["ktime"]) == ctypes.sizeof(_lib.purify_kernel_time)
+    assert int(got["pd"]) == ctypes.sizeof(_lib.purify_pd_params)
+    assert int(got["purify_pd_params.tau"]) == _lib.purify_pd_params.tau.offset
+    assert int(got["purify_pd_params.nu"]) == _lib.purify_pd_params.nu.offset
     assert int(got["purify_plan_desc.tile"]) == _lib.purify_plan_desc.tile.offset
     assert int(got["purify_plan_desc.stream"]) == _lib.purify_plan_desc.stream.offset
     assert int(got["purify_plan_desc.dtype"]) == _lib.purify_plan_desc.dtype.offset

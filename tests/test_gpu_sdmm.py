@@ -7,6 +7,7 @@ import torch
 import paper_1502_05037_gb300 as pk
 from gpu_util import DEV, make_plan, np_cplx, np_real, rel, snr_db, t_real
 from oracle import nufft as onf
+from oracle import primal_dual as opd
 from oracle import sdmm as osd
 from paper_1502_05037_gb300 import synth
 
@@ -64,6 +65,32 @@ def test_cg_tolerance_trajectory():
     x, st = gpu_solve(plan, prob, dtype, iters, cap, cg_tol=tol)
     assert st.iters == iters and st.cg_iters_total == ref.cg_iters
     assert rel(x.cpu().numpy(), ref.x) <= 1e-9
+
+
+@pytest.mark.parametrize("dtype,tol,weighted", [(pk.PURIFY_F64, 1e-9, False), (pk.PURIFY_F32, 1e-3, False),
+                                                (pk.PURIFY_F32, 1e-3, True)])
+def test_primal_dual_trajectory(dtype, tol, weighted):
+    # Chambolle-Pock iterations for problem (3) against the FP64 oracle's
+    # (the same steps, sigma z kept as the ball dual on the GPU)
+    plan, prob, x_true = problem(32, 4096, 6, 3, 3, dtype, seed=11)
+    if weighted:
+        prob.weights = 0.5 + np.random.default_rng(12).random((plan.info.q, 32, 32))
+    iters, tau, sigma = 40, 0.05, 9.8
+    ref = opd.chambolle_pock(prob, iters, tau=tau, sigma=sigma, x0=np.zeros((32, 32)))
+    x = torch.zeros((32, 32), dtype=t_real(dtype), device=DEV)
+    y = torch.from_numpy(prob.y.astype(np_cplx(dtype))).to(DEV)
+    w = None if prob.weights is None else torch.from_numpy(prob.weights.astype(np_real(dtype))).to(DEV)
+    st = pk.purify_pd_solve(plan, y, prob.eps, x, w=w, iters=iters, tau=tau, sigma=sigma, nu=prob.nu)
+    xg = x.cpu().numpy().astype(np.float64)
+    assert rel(xg, ref) <= tol
+    assert st.iters == iters and st.cg_iters_total == 0 and st.status == 0
+    assert abs(st.objective - osd.objective(prob, ref)) <= 10 * tol * osd.objective(prob, ref)
+    assert abs(st.max_resid_over_eps - osd.residual_ratios(prob, ref).max()) <= 10 * tol
+    # a second call starts over from its x (here the result): the step from
+    # the oracle's result agrees as well
+    ref2 = opd.chambolle_pock(prob, 5, tau=tau, sigma=sigma, x0=ref)
+    pk.purify_pd_solve(plan, y, prob.eps, x, w=w, iters=5, tau=tau, sigma=sigma, nu=prob.nu)
+    assert rel(x.cpu().numpy().astype(np.float64), ref2) <= 2 * tol
 
 
 def test_weighted_trajectory_and_reweight():
