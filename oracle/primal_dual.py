@@ -1,5 +1,8 @@
-"""Oracle: an independent primal-dual solver for problem (3), used only to
-pin the SDMM oracle's converged objective value.
+"""Oracle: an independent primal-dual solver for problem (3). It pins the
+SDMM oracle's converged objective value, and it is the reference of the GPU
+primal-dual solver (purify_pd_solve), whose iterations follow these steps.
+It is pinned by its first two iterations written out with the dense
+measurement matrix and by its converged objective matching SDMM's.
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 

@@ -200,6 +200,36 @@ def test_sdmm_objective_matches_chambolle_pock(converged):
     assert np.linalg.norm(xc - st.x) <= 1e-2 * np.linalg.norm(st.x)
 
 
+def test_chambolle_pock_first_two_iterations_by_hand():
+    # Algorithm 1 of Chambolle & Pock with theta = 1, written out with the
+    # dense measurement matrix: iteration 1 from x = 0 and iteration 2 from the
+    # extrapolated point 2 x_1 (this pins the extrapolation, the signs of the
+    # Moreau steps and the clip)
+    prob, _ = _tiny_problem(R=1)
+    tau, sigma = 0.05, 9.8
+    A = nf.phi_matrix(prob.plan) / prob.nu
+    yn, en = prob.y / prob.nu, prob.eps[0] / prob.nu
+
+    def ball(t):
+        d = t - yn
+        nd = np.linalg.norm(d)
+        return t if nd <= en else yn + d * (en / nd)
+
+    def adj_re(s):
+        return np.real(A.conj().T @ s).reshape(prob.plan.ny, prob.plan.nx)
+
+    p2 = -sigma * ball(np.zeros(prob.plan.M, dtype=complex))
+    x1 = np.maximum(-tau * adj_re(p2), 0.0)
+    xb = 2.0 * x1
+    p1 = np.clip(sigma * prob.psi_adj(xb), -1.0, 1.0)
+    q = p2 + sigma * (A @ xb.ravel())
+    p2 = q - sigma * ball(q / sigma)
+    x2 = np.maximum(x1 - tau * (prob.psi(p1) + adj_re(p2)), 0.0)
+    got = primal_dual.chambolle_pock(prob, 2, tau=tau, sigma=sigma)
+    assert np.abs(x1).max() > 0 and np.abs(x2 - x1).max() > 0
+    assert np.allclose(got, x2, rtol=0, atol=1e-12 * np.abs(x2).max())
+
+
 def test_sdmm_first_iteration_from_zero_by_hand():
     # from x = 0, z = 0: s1 = 0, s3 = 0 and s2 = projection of 0 onto each
     # ball, z2 = -s2, so the CG right-hand side is Re Phi^H (s2 - z2) / nu
