@@ -195,6 +195,7 @@ namespace purify {
 struct CgFold {
     void* x = nullptr;           // iterate [N]
     void* r = nullptr;           // residual [N]
+    void* p = nullptr;           // direction [N]
     void* s = nullptr;           // A p [N]
     const void* u = nullptr;     // A r [N]
     const void* add = nullptr;   // added to r at step 0 (may be null)
@@ -222,9 +223,8 @@ void launch_fft2(purify_plan* p, void* grid, bool inverse);
 // Phi stages used by the solver's fused forms
 // zero_acc: the same launch clears the gridding accumulator (gacc); fold:
 // apply the pending CG update first (see CgFold)
-void launch_scale_pad_rows(purify_plan* p, const void* x, double scale, void* pdir, const void* rvec,
-                           const double* beta_dev, const int* skip_flag, bool corr = true, bool zero_acc = false,
-                           const CgFold* fold = nullptr);
+void launch_scale_pad_rows(purify_plan* p, const void* x, double scale, const int* skip_flag, bool corr = true,
+                           bool zero_acc = false, const CgFold* fold = nullptr);
 void launch_cols_fwd(purify_plan* p, const int* skip_flag);
 void launch_degrid(purify_plan* p, void* y, bool caller_order, const int* skip_flag);
 void launch_grid(purify_plan* p, const void* y, bool caller_order, const int* skip_flag, bool zeroed = false);
@@ -238,10 +238,10 @@ void launch_cols_inv(purify_plan* p, const int* skip_flag, const void* mult = nu
 void launch_normal_gg(purify_plan* p, const int* skip_flag, bool zeroed = false);
 // G^H by runs (same output as launch_grid)
 void launch_grid_sets(purify_plan* p, const void* y, bool caller_order, const int* skip_flag, bool zeroed = false);
+// dot_part: a CG step (out = A r, add = r): per-block partials of r.r and
+// r.A r, 2 per block (see CgFold)
 void launch_rows_inv_crop(purify_plan* p, void* out, double scale, int out_mode, const void* add,
-                          double add_coef, const int* skip_flag, double* dot_part = nullptr,
-                          unsigned* counters = nullptr, double* scal = nullptr, bool corr = true,
-                          const CgFold* fold = nullptr);
+                          double add_coef, const int* skip_flag, double* dot_part = nullptr, bool corr = true);
 
 // Psi / Psi^dagger
 void launch_psi_adj(purify_plan* p, const void* x, void* c);

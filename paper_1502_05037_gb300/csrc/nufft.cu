@@ -155,16 +155,15 @@ __host__ __device__ inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++
 // [f * pad(Kx), (f + 1) * pad(Kx)).
 //
 // S Z and the forward row FFT: rows [i0, i0+rb) of the image to rows[i][0..Kx).
-// When pdir != null the kernel first forms p = r + beta p in place (CG
-// direction update) and transforms the new p. When zero_grid != null block
-// b also clears rows [b Ky/gridDim, (b+1) Ky/gridDim) of that Ky x Kx complex
-// grid (the gridding accumulator of the same CG step).
+// With a CG fold (fold.x set) the input is the residual r after the step's
+// update (see CgFold), not x. When zero_grid != null block b also clears rows
+// [b Ky/gridDim, (b+1) Ky/gridDim) of that Ky x Kx complex grid (the gridding
+// accumulator of the same CG step, or of the adjoint that follows Phi).
 template <typename T>
 __global__ void __launch_bounds__(1024) k_rows_fwd(const T* __restrict__ x, typename cplx_of<T>::type* __restrict__ rows,
                            const T* __restrict__ sx, const T* __restrict__ sy,
                            const typename cplx_of<T>::type* __restrict__ tw, int nx, int ny, int Kx,
-                           int rb, T scale, T* pdir, const T* __restrict__ rvec,
-                           const double* __restrict__ beta_dev, const int* __restrict__ skip,
+                           int rb, T scale, const int* __restrict__ skip,
                            typename cplx_of<T>::type* __restrict__ zero_grid, int Ky, CgFold fold) {
     using C = typename cplx_of<T>::type;
     pdl_wait();
@@ -174,6 +173,7 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(const T* __restrict__ x, type
     T* const fx = static_cast<T*>(fold.x);
     T* const fr = static_cast<T*>(fold.r);
     T* const fs = static_cast<T*>(fold.s);
+    T* const pdir = static_cast<T*>(fold.p);
     const T* const fu = static_cast<const T*>(fold.u);
     const T* const fadd = static_cast<const T*>(fold.add);
     // stopped at an earlier step (block 0 of this pass may set the flag
@@ -199,7 +199,6 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(const T* __restrict__ x, type
     const int f = threadIdx.x / N8, t = threadIdx.x - f * N8;
     C* buf = reinterpret_cast<C*>(smem_raw) + f * fft_padded(Kx);
     const int i = blockIdx.x * rb + f;
-    const T beta = beta_dev ? (T)(*beta_dev) : T(0);
     const T rs = sy[i] * scale;
     auto load = [&](int p1) -> C {
         // pixel column j with (j - nx/2) mod Kx == p1
@@ -228,9 +227,6 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(const T* __restrict__ x, type
                     fr[idx] = rv;
                 }
                 xv = rv;
-            } else if (pdir) {
-                xv = rvec[idx] + beta * pdir[idx];
-                pdir[idx] = xv;
             } else {
                 xv = x[idx];
             }
@@ -305,15 +301,14 @@ __global__ void __launch_bounds__(1024) k_cols_inv(const typename cplx_of<T>::ty
 // Inverse row FFT of image rows [i0, i0+rb), then Z^T and S:
 //   out_mode 0: complex out[i][j] = scale * s * v
 //   out_mode 1: real    out[i][j] = scale * s * Re v + add_coef * (add ? add[i][j] : 0)
-// With dot_part set (CG, out = A p, add = p) the kernel also forms p . A p
-// and, in the last block to finish, alpha = (r . r) / (p . A p).
+// With dot_part set (a CG step: out = A r, add = r, see CgFold) the kernel
+// also writes per-block partials of r . r and r . A r to dot_part.
 template <typename T, int MAXT>
 __global__ void __launch_bounds__(MAXT) k_rows_inv(const typename cplx_of<T>::type* __restrict__ rows, void* out,
                            const T* __restrict__ sx, const T* __restrict__ sy,
                            const typename cplx_of<T>::type* __restrict__ tw, int nx, int ny, int Kx,
                            int rb, T scale, int out_mode, const T* __restrict__ add, T add_coef,
-                           const int* __restrict__ skip, double* dot_part, unsigned* counters, double* scal,
-                           CgFold fold) {
+                           const int* __restrict__ skip, double* dot_part) {
     using C = typename cplx_of<T>::type;
     pdl_wait();
     if (skip && *skip) return;
@@ -324,7 +319,7 @@ __global__ void __launch_bounds__(MAXT) k_rows_inv(const typename cplx_of<T>::ty
     const int i = blockIdx.x * rb + f;
     const T rs = sy[i] * scale;
     T dacc = 0, gacc2 = 0;   // add.out, and with the folded CG add.add (add = r, out = A r)
-    const bool cg = fold.x != nullptr;
+    const bool cg = dot_part != nullptr;
     auto load = [&](int k) -> C { return rows[(size_t)i * Kx + k]; };
     auto store = [&](int p1, C v) {
         const int j = (p1 + nx / 2) & (Kx - 1);
@@ -346,7 +341,7 @@ __global__ void __launch_bounds__(MAXT) k_rows_inv(const typename cplx_of<T>::ty
     };
     auto slot = [&](int n) -> C& { return buf[fft_pad(n)]; };
     fft_reg<C, true>(Kx, ilog2(Kx), t, tw, load, store, slot);
-    if (dot_part && cg) {
+    if (cg) {
         // Chronopoulos-Gear partials (see CgFold): gamma = r.r, delta = r.A r;
         // the consumer of this step's scalars reduces them
         const double b0 = block_sum((double)gacc2);
@@ -354,17 +349,6 @@ __global__ void __launch_bounds__(MAXT) k_rows_inv(const typename cplx_of<T>::ty
         if (threadIdx.x == 0) {
             dot_part[2 * blockIdx.x] = b0;
             dot_part[2 * blockIdx.x + 1] = b1;
-        }
-    } else if (dot_part) {
-        double b = block_sum((double)dacc);
-        if (threadIdx.x == 0) dot_part[blockIdx.x] = b;
-        if (arrive_last(counters + C_ALPHA)) {
-            double tot = ordered_sum(dot_part, gridDim.x);
-            if (threadIdx.x == 0) {
-                scal[S_PAP] = tot;
-                scal[S_ALPHA] = tot > 0.0 ? scal[S_RS] / tot : 0.0;
-                counters[C_ALPHA] = 0;
-            }
         }
     }
     pdl_trigger();
@@ -981,8 +965,8 @@ template <typename K> static void set_smem(K kernel, size_t bytes) {
 }
 
 template <typename T>
-static void rows_fwd_t(purify_plan* p, const void* x, double scale, void* pdir, const void* rvec,
-                       const double* beta_dev, const int* skip, bool corr, bool zero_acc, const CgFold* fold) {
+static void rows_fwd_t(purify_plan* p, const void* x, double scale, const int* skip, bool corr, bool zero_acc,
+                       const CgFold* fold) {
     using C = typename cplx_of<T>::type;
     int rb = p->fft_rb > 0 ? p->fft_rb : rows_per_block<T>(p->ny, p->Kx);
     while (p->ny % rb) rb >>= 1;
@@ -992,7 +976,7 @@ static void rows_fwd_t(purify_plan* p, const void* x, double scale, void* pdir, 
     launch_dependent(k_rows_fwd<T>, p->ny / rb, rb * (p->Kx / 8), sm, p->stream,
         (const T*)x, p->rows.as<C>(), corr ? p->sx.as<T>() : p->onesx.as<T>(),
         corr ? p->sy.as<T>() : p->onesy.as<T>(), p->twx.as<C>(), p->nx, p->ny, p->Kx,
-        rb, (T)scale, (T*)pdir, (const T*)rvec, beta_dev, skip, zero_acc ? p->gacc.as<C>() : nullptr, p->Ky,
+        rb, (T)scale, skip, zero_acc ? p->gacc.as<C>() : nullptr, p->Ky,
         fold ? *fold : CgFold());
     L.done();
 }
@@ -1023,8 +1007,7 @@ template <typename T> static void cols_inv_t(purify_plan* p, const int* skip, co
 
 template <typename T>
 static void rows_inv_t(purify_plan* p, void* out, double scale, int out_mode, const void* add, double add_coef,
-                       const int* skip, double* dot_part, unsigned* counters, double* scal, bool corr,
-                       const CgFold* fold) {
+                       const int* skip, double* dot_part, bool corr) {
     using C = typename cplx_of<T>::type;
     int rb = p->fft_rb > 0 ? p->fft_rb : rows_per_block<T>(p->ny, p->Kx);
     while (p->ny % rb) rb >>= 1;
@@ -1038,7 +1021,7 @@ static void rows_inv_t(purify_plan* p, void* out, double scale, int out_mode, co
     launch_dependent(kern, p->ny / rb, nt, sm, p->stream, p->rows.as<C>(), out, corr ? p->sx.as<T>() : p->onesx.as<T>(),
                                             corr ? p->sy.as<T>() : p->onesy.as<T>(), p->twx.as<C>(), p->nx, p->ny,
                                             p->Kx, rb, (T)scale, out_mode, (const T*)add, (T)add_coef, skip,
-                                            dot_part, counters, scal, fold ? *fold : CgFold());
+                                            dot_part);
     L.done();
 }
 
@@ -1183,10 +1166,10 @@ int max_grid_tile(int dtype, int J) {
     return t;
 }
 
-void launch_scale_pad_rows(purify_plan* p, const void* x, double scale, void* pdir, const void* rvec,
-                           const double* beta_dev, const int* skip, bool corr, bool zero_acc, const CgFold* fold) {
-    if (p->dtype == PURIFY_F32) rows_fwd_t<float>(p, x, scale, pdir, rvec, beta_dev, skip, corr, zero_acc, fold);
-    else rows_fwd_t<double>(p, x, scale, pdir, rvec, beta_dev, skip, corr, zero_acc, fold);
+void launch_scale_pad_rows(purify_plan* p, const void* x, double scale, const int* skip, bool corr, bool zero_acc,
+                           const CgFold* fold) {
+    if (p->dtype == PURIFY_F32) rows_fwd_t<float>(p, x, scale, skip, corr, zero_acc, fold);
+    else rows_fwd_t<double>(p, x, scale, skip, corr, zero_acc, fold);
 }
 
 void launch_cols_fwd(purify_plan* p, const int* skip) {
@@ -1196,12 +1179,9 @@ void launch_cols_inv(purify_plan* p, const int* skip, const void* mult) {
     if (p->dtype == PURIFY_F32) cols_inv_t<float>(p, skip, mult); else cols_inv_t<double>(p, skip, mult);
 }
 void launch_rows_inv_crop(purify_plan* p, void* out, double scale, int out_mode, const void* add, double add_coef,
-                          const int* skip, double* dot_part, unsigned* counters, double* scal, bool corr,
-                          const CgFold* fold) {
-    if (p->dtype == PURIFY_F32)
-        rows_inv_t<float>(p, out, scale, out_mode, add, add_coef, skip, dot_part, counters, scal, corr, fold);
-    else
-        rows_inv_t<double>(p, out, scale, out_mode, add, add_coef, skip, dot_part, counters, scal, corr, fold);
+                          const int* skip, double* dot_part, bool corr) {
+    if (p->dtype == PURIFY_F32) rows_inv_t<float>(p, out, scale, out_mode, add, add_coef, skip, dot_part, corr);
+    else rows_inv_t<double>(p, out, scale, out_mode, add, add_coef, skip, dot_part, corr);
 }
 void launch_degrid(purify_plan* p, void* y, bool caller_order, const int* skip) {
     if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, degrid_f, p, y, caller_order, skip); }
@@ -1217,7 +1197,7 @@ void launch_grid(purify_plan* p, const void* y, bool caller_order, const int* sk
 }
 
 void launch_phi(purify_plan* p, const void* x, void* y, bool caller_order, double scale, bool zero_acc) {
-    launch_scale_pad_rows(p, x, scale, nullptr, nullptr, nullptr, nullptr, true, zero_acc);
+    launch_scale_pad_rows(p, x, scale, nullptr, true, zero_acc);
     launch_cols_fwd(p, nullptr);
     launch_degrid(p, y, caller_order, nullptr);
 }

@@ -270,7 +270,7 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
         for (int rb = 1; rb <= 8; rb *= 2) {
             if (p->ny % rb || !fft_shape_ok(rb, p->Kx, p->dtype)) continue;
             p->fft_rb = rb;
-            float ms = time_ms(p, [&] { launch_scale_pad_rows(p, ximg, 1.0, nullptr, nullptr, nullptr, nullptr); }, 10);
+            float ms = time_ms(p, [&] { launch_scale_pad_rows(p, ximg, 1.0, nullptr); }, 10);
             if (ms < best) { best = ms; val.rb = rb; }
         }
         best = 1e30f;

@@ -187,7 +187,7 @@ __global__ void k_positivity(const T* __restrict__ x, T* __restrict__ z3, const 
 
 template <typename T>
 __global__ void k_relchange(T* __restrict__ x, const T* __restrict__ xprev, int64_t N, double* part,
-                            unsigned* counters, double* scal, CgFold fold, T* __restrict__ pdir) {
+                            unsigned* counters, double* scal, CgFold fold) {
     pdl_wait();
     // the last CG step's update first, unless the solve stopped (see CgFold)
     bool pending = false;
@@ -203,6 +203,7 @@ __global__ void k_relchange(T* __restrict__ x, const T* __restrict__ xprev, int6
     T* const r = static_cast<T*>(fold.r);
     T* const sv = static_cast<T*>(fold.s);
     const T* const u = static_cast<const T*>(fold.u);
+    T* const pdir = static_cast<T*>(fold.p);
     T a = 0, d = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         T xv = x[i];
@@ -548,10 +549,10 @@ template <typename T> struct Solver {
             launch_phi_adj(p, s.v2.p, s.r.p, false, inv_nu, 1, nullptr, true);
             if (s.toeplitz) {
                 // r -= (normal operator by circulant embedding) x
-                launch_scale_pad_rows(p, x, 1.0, nullptr, nullptr, nullptr, nullptr, false);
+                launch_scale_pad_rows(p, x, 1.0, nullptr, false);
                 launch_cols_fwd(p, nullptr);
                 launch_cols_inv(p, nullptr, s.toep.p);
-                launch_rows_inv_crop(p, s.r.p, -1.0, 1, s.r.p, 1.0, nullptr, nullptr, nullptr, nullptr, false);
+                launch_rows_inv_crop(p, s.r.p, -1.0, 1, s.r.p, 1.0, nullptr, nullptr, false);
             }
             if (fork) PURIFY_CUDA(cudaEventRecord(s.ev_join, s.side));
         } catch (...) {
@@ -587,6 +588,7 @@ template <typename T> struct Solver {
         CgFold fold;
         fold.x = x;
         fold.r = s.r.p;
+        fold.p = s.p.p;
         fold.s = s.Ap.p;
         fold.u = s.u.p;
         fold.add = s.addend.p;
@@ -598,20 +600,20 @@ template <typename T> struct Solver {
             fold.step = k;
             if (s.toeplitz) {
                 // u = A r = 2 r + (embedded normal operator) r
-                launch_scale_pad_rows(p, nullptr, 1.0, s.p.p, s.r.p, nullptr, skip, false, false, &fold);
+                launch_scale_pad_rows(p, nullptr, 1.0, skip, false, false, &fold);
                 launch_cols_fwd(p, skip);
                 launch_cols_inv(p, skip, s.toep.p);
-                launch_rows_inv_crop(p, s.u.p, 1.0, 1, s.r.p, 2.0, skip, cg_part(), ctr(), scal(), false, &fold);
+                launch_rows_inv_crop(p, s.u.p, 1.0, 1, s.r.p, 2.0, skip, cg_part(), false);
             } else {
                 // the pending update and the transform of the new r fused into
                 // the first FFT pass, then u = A r
-                launch_scale_pad_rows(p, nullptr, inv_nu, s.p.p, s.r.p, nullptr, skip, true, true, &fold);
+                launch_scale_pad_rows(p, nullptr, inv_nu, skip, true, true, &fold);
                 launch_cols_fwd(p, skip);
                 launch_normal_gg(p, skip, true);
                 launch_cols_inv(p, skip);
                 // u = 2 r + Re Phi^H Phi r / nu^2, with r.r, r.u and the CG
                 // scalars fused in
-                launch_rows_inv_crop(p, s.u.p, inv_nu, 1, s.r.p, 2.0, skip, cg_part(), ctr(), scal(), true, &fold);
+                launch_rows_inv_crop(p, s.u.p, inv_nu, 1, s.r.p, 2.0, skip, cg_part(), true);
             }
         }
         // the last step's pending update is applied by the relative-change kernel
@@ -619,7 +621,7 @@ template <typename T> struct Solver {
         {
             Launch L(p, "relchange");
             launch_dependent(k_relchange<T>, red_blocks(p->N), RB, 0, p->stream, x, s.xprev.template as<T>(), p->N,
-                             part(), ctr(), scal(), fold, s.p.template as<T>());
+                             part(), ctr(), scal(), fold);
             L.done();
         }
     }
