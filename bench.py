@@ -1,25 +1,32 @@
 #!/usr/bin/env python
 """Benchmark of the SARA/SDMM imaging hot path on GB300.
 
-Workload (default): 256 x 256 sky, M = 655,360 visibilities (Gaussian (u, v)
-density), Kaiser-Bessel width J = 6, oversampling 2, Psi = Dirac + db1..db8 at
-4 levels (q = 9), R = 8 uneven blocks, FP32 operators with FP64 reductions,
-30 dB input SNR, synthetic seeded data. One step = one SDMM iteration
-(Psi^dagger + prox, Phi + block projections, positivity, Psi, Phi^dagger and
-CG_ITERS conjugate-gradient steps of Phi^dagger Phi) on the plan's resident
-state, launched as one captured CUDA graph.
+Workload (default): the largest single-GPU configuration, a 1024 x 1024 sky
+(500 point sources, 40 blobs, diffuse component), M = 10,485,760
+visibilities (Gaussian (u, v) density plus 10% uniform), Kaiser-Bessel width
+J = 6, oversampling 2, Psi = Dirac + db1..db8 at 5 levels (q = 9), R = 64
+uneven blocks, FP32 operators with FP64 reductions, 20 dB input SNR,
+synthetic seeded data. One step = one SDMM iteration (Psi^dagger + prox,
+Phi + block projections, positivity, Psi, Phi^dagger and CG_ITERS
+conjugate-gradient steps of Phi^dagger Phi) on the plan's resident state,
+launched as one captured CUDA graph.
 
 Passes (all in one run):
   A  timed pass: W warm-up steps, then K steps each bracketed by CUDA events
      on the launching stream; a 512 MiB buffer is rewritten between steps to
      flush L2 (outside the events).                      -> value, ms_per_step
   B  roofline pass: the same K steps launched eagerly with per-kernel CUDA
-     events; the dominant kernel's algorithmic bytes / mean duration.
+     events; the dominant kernel's algorithmic flops (or bytes) / mean
+     duration.                                            -> roofline
   C  end-to-end pass: K calls of purify_sdmm_solve with pinned host buffers
      (y in, x in/out), one iteration each, wall-clock timed.  -> e2e
-  D  Phi + Phi^dagger through the C ABI (caller order).      -> Gvis/s
-  E  CPU baseline: the FP64 oracle, one SDMM iteration on a visibility
-     sample, scaled to the full workload (rank 0, N = 1 only).
+  D  Phi, Phi^dagger, Psi, Psi^dagger through the C ABI: algorithmic GB/s
+     and the fraction of the HBM peak; Phi + Phi^dagger Gvis/s.
+                                             -> roofline.operators, Gvis/s
+  E  the 256 x 256 (M = 655,360, R = 8) and 64 x 64 FP64 workloads by the
+     same rules (rank 0, N = 1).                         -> other_workloads
+  F  CPU baseline: the FP64 oracle, one SDMM iteration on the host cores
+     (whole, or on a stated visibility sample; rank 0, N = 1 only).
 
 With torchrun (N > 1) every rank solves its own independent problem (replicas,
 weak scaling); the max over ranks of the timed region sets the time.
@@ -175,15 +182,15 @@ def source_sha1(relpath: str) -> str:
     return hashlib.sha1(open(os.path.join(ROOT, relpath), "rb").read()).hexdigest()
 
 
-def ncu_traffic(kernel: str):
+def ncu_traffic(kernel: str, workload: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current source of that kernel; else None."""
+    the current source of that kernel and for this workload; else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(path):
         return None
     try:
         d = json.load(open(path))
-        e = d.get(kernel)
+        e = d.get(f"{kernel}@{workload}")
         if not e:
             return None
         if e.get("source_sha1") != source_sha1(e["source"]):
@@ -251,6 +258,103 @@ def setup_problem(wl_name: str, replica: int, dev):
 
 
 # ------------------------------------------------------------------ ours
+def operator_bytes(wl, info) -> dict:
+    """Algorithmic bytes of one application of each operator (FP32, the
+    minimum traffic with the Kaiser-Bessel weights computed on the fly):
+    Phi and Phi^dagger move the image (4 B per pixel), the oversampled grid
+    written once and read once after F (16 B per cell), the coordinates and
+    the visibilities (8 + 8 B each): 4N + 16 K^2 + 16 M; Psi^dagger and Psi
+    read or write the image once and every coefficient once: 4N + 4qN."""
+    N, M, K2, q = info.N, info.M, info.Kx * info.Ky, info.q
+    vis = 4 * N + 16 * K2 + 16 * M
+    wav = 4 * N + 4 * q * N
+    return {"phi": vis, "phi_adj": vis, "psi": wav, "psi_adj": wav}
+
+
+def time_operators(pk, plan, wl, dev, stream, flush, reps, peak):
+    """Each operator through the C ABI (caller order for the visibilities),
+    `reps` timed calls after 3 untimed ones, L2 flushed before each call;
+    mean milliseconds, algorithmic GB/s and the fraction of the HBM peak."""
+    import torch
+    rdt = torch.float64 if wl.dtype == "f64" else torch.float32
+    cdt = torch.complex128 if wl.dtype == "f64" else torch.complex64
+    info = plan.info
+    x_true = synth_sky(wl)
+    xin = torch.from_numpy(x_true).to(rdt).to(dev)
+    yv = torch.empty(wl.M, dtype=cdt, device=dev)
+    xa = torch.empty((wl.ny, wl.nx), dtype=cdt, device=dev)
+    c = torch.empty((info.q, wl.ny, wl.nx), dtype=rdt, device=dev)
+    xo = torch.empty_like(xin)
+    calls = {"phi": lambda: pk.purify_phi(plan, xin, yv), "phi_adj": lambda: pk.purify_phi_adj(plan, yv, xa),
+             "psi_adj": lambda: pk.purify_psi_adj(plan, xin, c), "psi": lambda: pk.purify_psi(plan, c, xo)}
+    ab = operator_bytes(wl, info)
+    out = {}
+    for name, fn in calls.items():
+        for _ in range(3):
+            fn()
+        evs = []
+        for k in range(reps):
+            flush.fill_(k & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize(dev)
+        ms = sum(a.elapsed_time(b) for a, b in evs) / reps
+        gbs = ab[name] / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "algorithmic_bytes": ab[name], "gbs": gbs, "frac_of_hbm": gbs / peak}
+    return out
+
+
+def synth_sky(wl):
+    return wl.draw()[0]
+
+
+def timed_iterations(pk, plan, dev, stream, flush, steps, warmup, clocks=None):
+    """`warmup` untimed then `steps` timed SDMM iterations (graph replays),
+    each bracketed by CUDA events on the launching stream, the L2 flushed
+    before each (outside the events). Returns the per-step milliseconds."""
+    import torch
+    for i in range(warmup):
+        flush.fill_(i & 0xFF)
+        pk.purify_sdmm_iterate(plan, 1)
+    torch.cuda.synchronize(dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_((k + 7) & 0xFF)
+        evs[k][0].record(stream)
+        pk.purify_sdmm_iterate(plan, 1)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def other_workload(pk, name, dev, steps, warmup, cg_iters, flush):
+    """SDMM iterations/s and Phi + Phi^dagger Gvis/s on another workload
+    (same timing rules as the headline; reported beside it)."""
+    import torch
+    wl, plan, y, eps, x_true = setup_problem(name, 0, dev)
+    stream = torch.cuda.current_stream(dev)
+    rdt = torch.float64 if wl.dtype == "f64" else torch.float32
+    x = torch.zeros((wl.ny, wl.nx), dtype=rdt, device=dev)
+    pk.purify_sdmm_solve(plan, y, eps, x, max_iter=0, cg_iters=cg_iters)
+    ms = timed_iterations(pk, plan, dev, stream, flush, steps, warmup)
+    peak, _ = peaks()
+    ops = time_operators(pk, plan, wl, dev, stream, flush, max(5, steps // 2), peak)
+    out = {"workload": describe(wl), "value": steps / (sum(ms) / 1e3), "unit": "iters/s",
+           "ms_per_step": sum(ms) / steps, "steps": steps, "dtype": wl.dtype,
+           "phi_phiadj_gvis_s": wl.M / ((ops["phi"]["ms"] + ops["phi_adj"]["ms"]) * 1e-3) / 1e9,
+           "operators": ops}
+    plan.close()
+    return out
+
+
+def describe(wl) -> str:
+    return (f"{wl.name}: {wl.nx}x{wl.ny} sky, M={wl.M}, J={wl.J}, alpha=2, q=9, L={wl.levels}, R={wl.R}, "
+            f"{wl.snr_db:g} dB, {wl.dtype}")
+
+
 def run_ours(args):
     import torch
 
@@ -325,13 +429,14 @@ def run_ours(args):
     pk.purify_timing_enable(plan, False)
     dom = max(ktimes.items(), key=lambda kv: kv[1][1]) if ktimes else None
     peak, peak_src = peaks()
+    dtb = 8 if wl.dtype == "f64" else 4
     roofline = None
     if dom:
         name, (nl, tms) = dom
         per = tms / nl
-        ab = algorithmic_bytes(name, plan.info, 8 if wl.dtype == "f64" else 4)
+        ab = algorithmic_bytes(name, plan.info, dtb)
         af = algorithmic_flops(name, plan.info)
-        tr = ncu_traffic(name)
+        tr = ncu_traffic(name, wl.name)
         alu_peak = fp32_peak_tflops(clocks.get("sm_max_mhz"))
         # the binding resource by arithmetic intensity against the ridge point
         ai = (af / ab) if (af and ab) else 0.0
@@ -350,10 +455,7 @@ def run_ours(args):
             achieved = ab / (per * 1e-3) / 1e9 if ab else None
             roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": (achieved / peak if achieved else None), "peak_source": peak_src, **common}
-    kernel_table = {k: {"launches_per_step": n / args.steps, "ms_per_step": t / args.steps,
-                        "gbs": (algorithmic_bytes(k, plan.info, 8 if wl.dtype == "f64" else 4) / (t / n * 1e-3) / 1e9
-                                if algorithmic_bytes(k, plan.info) else None)}
-                    for k, (n, t) in sorted(ktimes.items(), key=lambda kv: -kv[1][1])}
+    kernel_table = kernel_rates(ktimes, plan.info, args.steps, dtb, wl.levels)
 
     # ---- pass C: end to end through the public API with pinned host buffers
     y_host = torch.empty(wl.M, dtype=cdt, pin_memory=True)
@@ -371,7 +473,7 @@ def run_ours(args):
             e2e_times.append(t1 - t0)
     e2e_total = sum(e2e_times)
     e2e_total = max_over_ranks(e2e_total, dist, dev)
-    rb = 8 if wl.dtype == "f64" else 4
+    rb = dtb
     e2e = {"value": job_rate(world, args.steps, e2e_total * 1e3), "unit": "iters/s",
            "h2d_bytes_per_step": wl.M * 2 * rb + wl.nx * wl.ny * rb, "d2h_bytes_per_step": wl.nx * wl.ny * rb,
            "call": "purify_sdmm_solve(host y, host x, max_iter=1)"}
@@ -381,18 +483,8 @@ def run_ours(args):
     if args.toeplitz_pass:
         xt0 = torch.zeros((wl.ny, wl.nx), dtype=rdt, device=dev)
         pk.purify_sdmm_solve(plan, y, eps, xt0, max_iter=0, cg_iters=args.cg_iters, gamma=gamma, nu=nu, toeplitz=True)
-        for i in range(args.warmup):
-            flush.fill_(i & 0xFF)
-            pk.purify_sdmm_iterate(plan, 1)
-        torch.cuda.synchronize(dev)
-        tev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-        for k in range(args.steps):
-            flush.fill_((k + 11) & 0xFF)
-            tev[k][0].record(stream)
-            pk.purify_sdmm_iterate(plan, 1)
-            tev[k][1].record(stream)
-        torch.cuda.synchronize(dev)
-        tms = sum(a.elapsed_time(b) for a, b in tev)
+        tms_l = timed_iterations(pk, plan, dev, stream, flush, args.steps, args.warmup)
+        tms = sum(tms_l)
         toep = {"value": args.steps / (tms / 1e3), "unit": "iters/s", "ms_per_step": tms / args.steps,
                 "note": "CG normal operator by circulant embedding of the exact model (separate parity class)"}
 
@@ -417,47 +509,44 @@ def run_ours(args):
                        "parity-tested against its FP64 oracle), back to back without an L2 flush, from the "
                        "wall-clock difference of two synchronous solves"}
 
-    # ---- pass D: Phi + Phi^dagger Gvis/s (caller order, device buffers)
-    xin = torch.from_numpy(x_true).to(rdt).to(dev)
-    yv = torch.empty(wl.M, dtype=cdt, device=dev)
-    xa = torch.empty((wl.ny, wl.nx), dtype=cdt, device=dev)
-    for _ in range(3):
-        pk.purify_phi(plan, xin, yv)
-        pk.purify_phi_adj(plan, yv, xa)
-    ph = []
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)
-        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
-        a.record(stream)
-        pk.purify_phi(plan, xin, yv)
-        b.record(stream)
-        pk.purify_phi_adj(plan, yv, xa)
-        c.record(stream)
-        ph.append((a, b, c))
-    torch.cuda.synchronize(dev)
-    t_phi = sum(a.elapsed_time(b) for a, b, _ in ph) / args.steps
-    t_adj = sum(b.elapsed_time(c) for _, b, c in ph) / args.steps
-    gvis = wl.M / ((t_phi + t_adj) * 1e-3) / 1e9
+    # ---- pass D: each operator through the C ABI (caller order), Phi + Phi^dagger Gvis/s
+    ops = time_operators(pk, plan, wl, dev, stream, flush, args.steps, peak)
+    gvis = wl.M / ((ops["phi"]["ms"] + ops["phi_adj"]["ms"]) * 1e-3) / 1e9
+    if roofline is not None:
+        roofline["operators"] = {k: {**v, "target_frac": 0.6} for k, v in ops.items()}
+        roofline["operators_note"] = ("whole operators through the C ABI, algorithmic bytes (4N + 16K^2 + 16M for "
+                                      "Phi and Phi^dagger, 4N + 4qN for Psi and Psi^dagger) over CUDA-event "
+                                      "time, against the measured HBM copy bandwidth")
+    plan.close()
+    del y
+
+    # ---- pass E: the other single-GPU workloads, reported beside the headline
+    others = {}
+    if rank == 0 and world == 1 and not args.no_other_workloads:
+        for name in ("sara256_r8", "sara64_fp64"):
+            if name != wl.name:
+                others[name] = other_workload(pk, name, dev, max(args.steps, 20), args.warmup, args.cg_iters,
+                                              flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(wl, args.cg_iters, budget_s=args.cpu_budget)
+        cpu = cpu_baseline(wl, args.cg_iters, args.cpu_vis_fraction)
 
     if rank == 0:
         line = {
             "metric": "SDMM iters/s", "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": wl.dtype, "data": "synthetic",
-            "config": {"workload": f"{wl.name}: {wl.nx}x{wl.ny} sky, M={wl.M}, J={wl.J}, alpha=2, q=9, "
-                                   f"L={wl.levels}, R={wl.R}, {wl.snr_db:g} dB",
+            "config": {"workload": describe(wl),
                        "cg_iters": args.cg_iters, "cg_steps_applied_per_iteration": cg_per_step,
                        "parallelism": f"replicas x{world}",
-                       "l2": "512 MiB buffer rewritten between timed steps"},
-            "phi_phiadj_gvis_s": gvis, "phi_ms": t_phi, "phi_adj_ms": t_adj,
+                       "l2": "inputs larger than L2, and a 512 MiB buffer rewritten between timed steps"},
+            "phi_phiadj_gvis_s": gvis, "phi_ms": ops["phi"]["ms"], "phi_adj_ms": ops["phi_adj"]["ms"],
             "e2e": e2e, "gpu_launches": int(launches), "gpu_launches_per_step": launches / args.steps,
             "wall_s_timed": t_wall, "clocks": clocks, "roofline": roofline, "cpu_baseline": cpu,
             "toeplitz_cg": toep,
             "primal_dual": pdl,
+            "other_workloads": others,
             "kernels": kernel_table,
         }
         print(json.dumps(line), flush=True)
@@ -466,44 +555,196 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-# ------------------------------------------------------------- oracle arm
-def oracle_iteration_seconds(wl_name: str, cg_iters: int, vis_sample: int, seed=0):
-    """Seconds of one FP64 oracle SDMM iteration on the workload, measured on
-    a visibility sample and scaled: the sampled iteration is timed whole,
-    then the visibility-proportional steps (gridding and degridding, once per
-    Phi and Phi^dagger: cg_iters + 1 of each) are timed alone on the sample and
-    extrapolated linearly to all M visibilities."""
-    from oracle import nufft as onf
-    from oracle import sdmm as osd
-    from paper_1502_05037_gb300 import problem, synth
+def kernel_rates(ktimes, info, steps, dtb, levels):
+    """Per-kernel-kind launches and milliseconds per step, with the
+    algorithmic GB/s where the kind has a fixed per-launch byte count; the
+    wavelet kinds are rated per transform (all levels of one Psi^dagger are
+    dwt_level launches, all levels of one Psi are idwt_level launches plus
+    one idwt_final), at 4N + 4qN bytes per transform."""
+    table = {}
+    for k, (n, t) in sorted(ktimes.items(), key=lambda kv: -kv[1][1]):
+        ab = algorithmic_bytes(k, info, dtb)
+        table[k] = {"launches_per_step": n / steps, "ms_per_step": t / steps,
+                    "gbs": ab / (t / n * 1e-3) / 1e9 if ab else None}
+    wav = dtb * (info.N + info.q * info.N)
+    if "dwt_level" in ktimes:
+        n, t = ktimes["dwt_level"]
+        table["dwt_level"]["gbs_per_transform"] = (n / levels) * wav / (t * 1e-3) / 1e9
+    if "idwt_final" in ktimes:
+        nf_, tf = ktimes["idwt_final"]
+        tl = ktimes.get("idwt_level", (0, 0.0))[1]
+        table["idwt_final"]["gbs_per_transform_with_idwt_level"] = nf_ * wav / ((tf + tl) * 1e-3) / 1e9
+    return table
 
-    wl = synth.WORKLOADS[wl_name]
-    x_true, u, v, offs, nz = wl.draw()
-    g = np.random.default_rng(seed)
-    Ms = int(min(wl.M, max(1024, vis_sample)))
-    idx = np.sort(g.choice(wl.M, Ms, replace=False))
-    blk = np.searchsorted(offs, idx, side="right") - 1
-    offs_s = np.concatenate([[0], np.cumsum(np.bincount(blk, minlength=wl.R))])
-    keep = np.diff(offs_s) > 0
-    offs_s = np.concatenate([[0], np.cumsum(np.diff(offs_s)[keep])])
-    op = onf.NufftPlan(wl.nx, wl.ny, u[idx].astype(np.float64), v[idx].astype(np.float64), wl.J)
-    y0 = onf.phi(op, x_true)
-    sig = problem.noise_sigma_from_norm(float(np.linalg.norm(y0)), Ms, wl.snr_db)
-    y = y0 + sig * nz[idx]
-    eps = problem.chi2_epsilon(sig, np.diff(offs_s))
-    # fixed constants: nu and gamma change no step count of the oracle's work
-    prob = osd.Problem(op, wl.levels, y, offs_s, eps, nu=1.0, gamma=1e-4)
-    st = osd.init_state(prob, np.zeros((wl.ny, wl.nx)))
-    t0 = time.perf_counter()
-    osd.sdmm_iteration(prob, st, cg_iters)
-    t_iter = time.perf_counter() - t0
-    X = onf.fft2(onf.scale_pad(op, x_true))
-    t0 = time.perf_counter()
-    onf.degrid(op, X)
-    onf.grid(op, y)
-    t_vis = time.perf_counter() - t0
-    total = t_iter + (cg_iters + 1) * t_vis * (wl.M / Ms - 1.0)
-    return total, Ms, t_iter, t_vis
+
+# ------------------------------------------------------------- oracle arm
+# The FP64 oracle timed on the host cores. Its gridding and degridding are
+# sums and maps over visibilities, so they run in spawned worker processes
+# on contiguous visibility chunks (each worker calls the oracle's own
+# degrid/grid on its chunk; the chunk grids are added in chunk order), and
+# its FFTs use scipy.fft with one worker thread per core. Nothing of the
+# oracle's arithmetic changes.
+_W = {}
+
+
+def _pool_init(spec):
+    from multiprocessing import shared_memory
+    _W["shm"] = []
+    for key, (name, shape, dt) in spec["arrays"].items():
+        h = shared_memory.SharedMemory(name=name)
+        _W["shm"].append(h)
+        _W[key] = np.ndarray(shape, dtype=dt, buffer=h.buf)
+    _W["spec"] = spec
+    _W["plans"] = {}
+
+
+def _pool_plan(k):
+    from oracle import nufft as onf
+    if k not in _W["plans"]:
+        sp = _W["spec"]
+        a, b = sp["chunks"][k]
+        _W["plans"][k] = onf.NufftPlan(sp["nx"], sp["ny"], _W["u"][a:b], _W["v"][a:b], sp["J"])
+    return _W["plans"][k]
+
+
+def _pool_degrid(k):
+    from oracle import nufft as onf
+    a, b = _W["spec"]["chunks"][k]
+    _W["y_out"][a:b] = onf.degrid(_pool_plan(k), _W["X"])
+    return k
+
+
+def _pool_grid(k):
+    from oracle import nufft as onf
+    a, b = _W["spec"]["chunks"][k]
+    _W["grids"][k] = onf.grid(_pool_plan(k), _W["y_in"][a:b])
+    return k
+
+
+class OracleVisPool:
+    """G and G^H of the oracle over `workers` visibility chunks in spawned
+    processes, the arrays in shared memory."""
+
+    def __init__(self, nx, ny, J, u, v, workers):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        from multiprocessing import shared_memory
+        M = u.size
+        Kx, Ky = 2 * nx, 2 * ny
+        self.P = max(1, min(workers, M))
+        edges = np.linspace(0, M, self.P + 1).astype(np.int64)
+        shapes = {"u": ((M,), np.float64), "v": ((M,), np.float64), "X": ((Ky, Kx), np.complex128),
+                  "y_in": ((M,), np.complex128), "y_out": ((M,), np.complex128),
+                  "grids": ((self.P, Ky, Kx), np.complex128)}
+        self.shm, self.a, arrays = [], {}, {}
+        for key, (shape, dt) in shapes.items():
+            nbytes = int(np.prod(shape)) * np.dtype(dt).itemsize
+            h = shared_memory.SharedMemory(create=True, size=max(nbytes, 1))
+            self.shm.append(h)
+            self.a[key] = np.ndarray(shape, dtype=dt, buffer=h.buf)
+            arrays[key] = (h.name, shape, np.dtype(dt).str)
+        self.a["u"][:] = u
+        self.a["v"][:] = v
+        spec = {"arrays": arrays, "chunks": [(int(edges[k]), int(edges[k + 1])) for k in range(self.P)],
+                "nx": nx, "ny": ny, "J": J}
+        self.ex = cf.ProcessPoolExecutor(max_workers=self.P, mp_context=mp.get_context("spawn"),
+                                         initializer=_pool_init, initargs=(spec,))
+
+    def degrid(self, X):
+        self.a["X"][:] = X
+        list(self.ex.map(_pool_degrid, range(self.P)))
+        return self.a["y_out"].copy()
+
+    def grid(self, y):
+        self.a["y_in"][:] = y
+        list(self.ex.map(_pool_grid, range(self.P)))
+        g = self.a["grids"]
+        out = g[0].copy()
+        for k in range(1, self.P):
+            out += g[k]
+        return out
+
+    def close(self):
+        self.ex.shutdown(wait=True)
+        for h in self.shm:
+            h.close()
+            h.unlink()
+
+
+class OracleRun:
+    """The FP64 oracle's SDMM iterations (k_CG = cg_iters) on the workload, or
+    on a random visibility sample of it (vis_fraction < 1: the same blocks,
+    each cut to its sampled visibilities), with the visibility pool above.
+    step() runs one iteration and returns its wall seconds and the seconds of
+    it spent in gridding and degridding."""
+
+    def __init__(self, wl_name: str, cg_iters: int, vis_fraction: float, cores: int, seed: int = 0):
+        import scipy.fft
+
+        from oracle import nufft as onf
+        from oracle import sdmm as osd
+        from paper_1502_05037_gb300 import synth
+
+        self.osd, self.cg_iters, self.cores = osd, cg_iters, cores
+        self.wl = wl = synth.WORKLOADS[wl_name]
+        x_true, u, v, offs, nz = wl.draw()
+        if vis_fraction < 1.0:
+            g = np.random.default_rng(seed)
+            Ms = int(max(1024, min(wl.M, round(vis_fraction * wl.M))))
+            idx = np.sort(g.choice(wl.M, Ms, replace=False))
+            blk = np.searchsorted(offs, idx, side="right") - 1
+            counts = np.bincount(blk, minlength=wl.R)
+            counts = counts[counts > 0]
+            offs = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+            u, v, nz = u[idx], v[idx], nz[idx]
+        self.Ms = u.size
+        self.pool = OracleVisPool(wl.nx, wl.ny, wl.J, u.astype(np.float64), v.astype(np.float64), cores)
+        self.t_vis = 0.0
+        run = self
+
+        def degrid(X):
+            t0 = time.perf_counter()
+            r = run.pool.degrid(X)
+            run.t_vis += time.perf_counter() - t0
+            return r
+
+        def grid(y):
+            t0 = time.perf_counter()
+            r = run.pool.grid(y)
+            run.t_vis += time.perf_counter() - t0
+            return r
+
+        class PooledProblem(osd.Problem):
+            def phi_n(self, x):
+                return degrid(onf.fft2(onf.scale_pad(self.plan, x))) / self.nu
+
+            def phi_n_adj_re(self, y):
+                return np.real(onf.crop_scale(self.plan, onf.ifft2_unnormalised(grid(y)))) / self.nu
+
+        with scipy.fft.set_workers(cores):
+            op = onf.NufftPlan(wl.nx, wl.ny, u.astype(np.float64), v.astype(np.float64), wl.J)
+            y0 = degrid(onf.fft2(onf.scale_pad(op, x_true)))
+            sig = osd.noise_sigma(y0, wl.snr_db)
+            eps = osd.epsilon_chi2(sig, np.diff(offs))
+            # fixed constants: nu and gamma change no step count of the oracle's work
+            self.prob = PooledProblem(op, wl.levels, y0 + sig * nz, offs, eps, nu=1.0, gamma=1e-4)
+            self.state = osd.init_state(self.prob, np.zeros((wl.ny, wl.nx)))
+
+    def step(self):
+        import scipy.fft
+        self.t_vis = 0.0
+        with scipy.fft.set_workers(self.cores):
+            t0 = time.perf_counter()
+            self.osd.sdmm_iteration(self.prob, self.state, self.cg_iters)
+            wall = time.perf_counter() - t0
+        return wall, self.t_vis
+
+    def scaled(self, wall, t_vis):
+        """The iteration's seconds with its visibility work scaled to all M."""
+        return wall + t_vis * (self.wl.M / self.Ms - 1.0)
+
+    def close(self):
+        self.pool.close()
 
 
 def cpu_threads() -> int:
@@ -513,14 +754,24 @@ def cpu_threads() -> int:
         return os.cpu_count() or 1
 
 
-def cpu_baseline(wl, cg_iters, budget_s=20.0):
-    Ms = int(65536 * max(0.25, budget_s / 20.0))
-    total, Ms, t_iter, t_vis = oracle_iteration_seconds(wl.name, cg_iters, Ms)
-    return {"value": 1.0 / total, "unit": "iters/s", "cores": 1, "kind": "oracle",
-            "threads_available": cpu_threads(),
-            "sample": f"one FP64 oracle SDMM iteration (k_CG={cg_iters}) on {Ms} of {wl.M} visibilities "
-                      f"({t_iter:.1f} s), gridding+degridding timed alone on the sample ({t_vis:.2f} s) "
-                      f"and scaled to all visibilities; NumPy/SciPy single-threaded"}
+def cpu_baseline(wl, cg_iters, vis_fraction=0.0):
+    cores = cpu_threads()
+    if vis_fraction <= 0.0:
+        vis_fraction = min(1.0, 1.5e6 / wl.M)
+    run = OracleRun(wl.name, cg_iters, vis_fraction, cores)
+    try:
+        wall, t_vis = run.step()
+    finally:
+        run.close()
+    if run.Ms == wl.M:
+        value, how = 1.0 / wall, "one whole FP64 oracle SDMM iteration on the full workload"
+    else:
+        value = 1.0 / run.scaled(wall, t_vis)
+        how = (f"one FP64 oracle SDMM iteration on {run.Ms} of {wl.M} visibilities, its gridding time scaled "
+               f"to all M")
+    return {"value": value, "unit": "iters/s", "cores": cores, "kind": "oracle",
+            "sample": f"{how} (k_CG={cg_iters}; {wall:.1f} s wall, {t_vis:.1f} s of it gridding and degridding "
+                      f"in {cores} spawned processes over visibility chunks; scipy.fft with {cores} workers)"}
 
 
 def run_reference(args):
@@ -528,25 +779,33 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from paper_1502_05037_gb300 import synth
-    wl = synth.WORKLOADS[args.workload]
-    per_step_budget = max(1.0, 150.0 / max(1, args.steps + args.warmup))
-    Ms = int(65536 * per_step_budget / 6.0)
-    secs = []
-    for k in range(args.warmup + args.steps):
-        total, Ms_used, t_iter, t_vis = oracle_iteration_seconds(args.workload, args.cg_iters, Ms, seed=k)
-        if k >= args.warmup:
-            secs.append(total)
-    value = args.steps / sum(secs)
+    cores = cpu_threads()
+    run = OracleRun(args.workload, args.cg_iters, args.ref_vis_fraction, cores)
+    wl = run.wl
+    walls, scaled = [], []
+    try:
+        for k in range(args.warmup + args.steps):
+            wall, t_vis = run.step()
+            if k >= args.warmup:
+                walls.append(wall)
+                scaled.append(run.scaled(wall, t_vis))
+    finally:
+        run.close()
+    value = args.steps / sum(scaled)
+    whole = run.Ms == wl.M
     line = {
         "impl": "reference", "metric": "SDMM iters/s", "value": value, "unit": "iters/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{wl.name}: {wl.nx}x{wl.ny} sky, M={wl.M}, J={wl.J}, alpha=2, q=9, "
-                               f"L={wl.levels}, R={wl.R}, {wl.snr_db:g} dB", "cg_iters": args.cg_iters},
-        "cpu_baseline": {"value": value, "unit": "iters/s", "kind": "oracle", "cores": 1,
-                         "sample": f"each step: one oracle SDMM iteration on {Ms_used} of {wl.M} visibilities, "
-                                   f"visibility-proportional steps scaled to all M"},
+        "config": {"workload": describe(wl), "cg_iters": args.cg_iters},
+        "value_scaled_from_sample": not whole,
+        "cpu_baseline": {"value": value, "unit": "iters/s", "kind": "oracle", "cores": cores,
+                         "sample": (f"each step: one FP64 oracle SDMM iteration (k_CG={args.cg_iters}) on a fixed "
+                                    f"random sample of {run.Ms} of {wl.M} visibilities (ms_per_step is its wall "
+                                    f"time); value scales the gridding and degridding time to all M"
+                                    if not whole else
+                                    f"each step: one whole FP64 oracle SDMM iteration (k_CG={args.cg_iters})")
+                         + f"; gridding in {cores} spawned processes, scipy.fft with {cores} workers"},
         "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -747,10 +1006,16 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="sara256_r8")
+    ap.add_argument("--workload", default="sara1024_r64")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the extra timed passes on the 256x256 and 64x64 workloads")
     ap.add_argument("--cg-iters", type=int, default=CG_ITERS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--cpu-vis-fraction", type=float, default=0.0,
+                    help="visibility fraction of the timed oracle iteration of cpu_baseline (1 = whole iteration; "
+                         "0 = whole up to 1.5 M visibilities, else a 1.5 M sample)")
+    ap.add_argument("--ref-vis-fraction", type=float, default=1.0 / 64,
+                    help="visibility sample of each oracle step of --impl reference")
     ap.add_argument("--no-pd-pass", dest="pd_pass", action="store_false",
                     help="skip timing the primal-dual solver")
     ap.add_argument("--no-toeplitz-pass", dest="toeplitz_pass", action="store_false",

@@ -109,6 +109,14 @@ purify_status purify_phi(purify_plan *plan, const void *x, void *y);
  * images: y complex [M] caller order, x complex [ny][nx]. */
 purify_status purify_phi_adj(purify_plan *plan, const void *y, void *x);
 
+/* out = Re Phi^H Phi x, the data-fidelity normal operator of the SDMM
+ * x-update (Sec. 1: the CG system (2 I + Re Phi^H Phi / nu^2) x = b of the
+ * solve of problem (3)), applied as the solver applies it: S Z and F, then
+ * G^H G fused (each visibility's J x J interpolation spread straight back,
+ * no visibility vector), then F^H, Z^T and S. x real [ny][nx], out real
+ * [ny][nx] (host or device; may not alias). Errors: EINVAL, ECUDA. */
+purify_status purify_phi_normal(purify_plan *plan, const void *x, void *out);
+
 /* F of Phi = G F Z S alone: in-place unnormalised 2-D DFT of a complex
  * [Ky][Kx] grid; inverse != 0 applies F^H (the +i sign, no 1/K^2 factor). */
 purify_status purify_fft2(purify_plan *plan, void *grid, int32_t inverse);
@@ -228,6 +236,20 @@ purify_status purify_batch_destroy(purify_batch *batch);
 /* SARA weights (Sec. 1, reweighted l1): w = rho / (rho + |Psi^dagger x|),
  * x real [ny][nx], w real [q][ny][nx]; rho > 0. */
 purify_status purify_reweight(purify_plan *plan, const void *x, double rho, void *w);
+
+/* Problem set-up on the host (Sec. 1, Eq. 3: eps_i bounds the norm of block
+ * i's noise; the paper only asks for an appropriate bound). Reading used:
+ * complex noise n_m = sigma (a + i b) / sqrt 2 with a, b ~ N(0, 1), so
+ * (2 / sigma^2) ||n_i||^2 is chi^2 with 2 M_i degrees of freedom, and eps_i is
+ * its mean plus two standard deviations:
+ *   eps_i = (sigma / sqrt 2) sqrt(2 M_i + 4 sqrt(M_i)),  M_i = offsets[i+1] - offsets[i].
+ * purify_noise_sigma gives sigma = y_norm / sqrt(M) * 10^(-snr_db / 20) for a
+ * noiseless ||Phi x|| = y_norm and an input SNR in dB.
+ * block_offsets: HOST int64 [R + 1] (0 = first < ... < last), eps: HOST double [R].
+ * Errors: EINVAL (null pointers, R < 1, offsets not increasing, sigma <= 0 or
+ * not finite, M < 1). Synchronous, no GPU work. */
+purify_status purify_noise_sigma(double y_norm, int64_t M, double snr_db, double *sigma);
+purify_status purify_chi2_epsilon(double sigma, const int64_t *block_offsets, int32_t R, double *eps);
 
 /* Standard deviation of Psi^dagger x over all D coefficients (FP64 reduction),
  * the first SARA reweighting scale. Synchronous. */

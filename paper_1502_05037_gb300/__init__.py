@@ -16,7 +16,8 @@ from ._lib import (PURIFY_F32, PURIFY_F64, PurifyError, check, load, purify_kern
                    purify_pd_params, purify_plan_info, purify_sdmm_params, purify_sdmm_stats)
 
 __all__ = [
-    "Plan", "purify_plan_create", "purify_plan_destroy", "purify_phi", "purify_phi_adj", "purify_fft2",
+    "Plan", "purify_plan_create", "purify_plan_destroy", "purify_phi", "purify_phi_adj", "purify_phi_normal",
+    "purify_fft2",
     "purify_psi", "purify_psi_adj", "purify_op_norm_sq", "purify_sdmm_solve", "purify_sdmm_iterate",
     "purify_reweight",
     "purify_coef_std", "purify_launch_count", "PurifyError", "PURIFY_F32", "PURIFY_F64",
@@ -104,6 +105,11 @@ def purify_phi(plan: Plan, x, y):
 
 def purify_phi_adj(plan: Plan, y, x):
     check(load().purify_phi_adj(plan.handle, _ptr(y), _ptr(x)))
+
+
+def purify_phi_normal(plan: Plan, x, out):
+    """out = Re Phi^H Phi x (real images), the solver's normal operator."""
+    check(load().purify_phi_normal(plan.handle, _ptr(x), _ptr(out)))
 
 
 def purify_fft2(plan: Plan, grid, inverse: bool = False):

@@ -97,6 +97,7 @@ _SIGS = {
     "purify_plan_get_info": (C.c_int, [_P, C.POINTER(purify_plan_info)]),
     "purify_phi": (C.c_int, [_P, _P, _P]),
     "purify_phi_adj": (C.c_int, [_P, _P, _P]),
+    "purify_phi_normal": (C.c_int, [_P, _P, _P]),
     "purify_fft2": (C.c_int, [_P, _P, C.c_int32]),
     "purify_psi": (C.c_int, [_P, _P, _P]),
     "purify_psi_adj": (C.c_int, [_P, _P, _P]),
@@ -111,6 +112,8 @@ _SIGS = {
     "purify_batch_destroy": (C.c_int, [_P]),
     "purify_reweight": (C.c_int, [_P, _P, C.c_double, _P]),
     "purify_coef_std": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
+    "purify_noise_sigma": (C.c_int, [C.c_double, C.c_int64, C.c_double, C.POINTER(C.c_double)]),
+    "purify_chi2_epsilon": (C.c_int, [C.c_double, C.POINTER(C.c_int64), C.c_int32, C.POINTER(C.c_double)]),
     "purify_psi_adj_static": (C.c_int, [_P, _P, C.c_int32, C.c_int32, C.c_int32, C.c_uint32, C.c_int32, _P]),
     "purify_conv2d": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.c_int32, _P, _P, C.c_int32, C.c_int32,
                                 C.c_int32, _P, _P]),

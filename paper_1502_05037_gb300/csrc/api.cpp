@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <string>
@@ -192,6 +193,22 @@ purify_status purify_phi_adj(purify_plan* p, const void* y, void* x) {
     });
 }
 
+purify_status purify_phi_normal(purify_plan* p, const void* x, void* out) {
+    return guarded([&] {
+        PURIFY_REQUIRE(p && x && out, "null argument");
+        const size_t rb = real_bytes(p);
+        Staged xs = stage_in(p, x, rb * p->N, p->stage_in);
+        Staged os = stage_out(p, out, rb * p->N, p->stage_out);
+        // the forward row pass clears the accumulator that G^H G adds into
+        launch_scale_pad_rows(p, xs.dev, 1.0, nullptr, true, true);
+        launch_cols_fwd(p, nullptr);
+        launch_normal_gg(p, nullptr, true);
+        launch_cols_inv(p, nullptr);
+        launch_rows_inv_crop(p, os.dev, 1.0, 1, nullptr, 0.0, nullptr);
+        finish_out(p, os, out, rb * p->N);
+    });
+}
+
 purify_status purify_fft2(purify_plan* p, void* grid, int32_t inverse) {
     return guarded([&] {
         PURIFY_REQUIRE(p && grid, "null argument");
@@ -307,6 +324,29 @@ purify_status purify_reweight(purify_plan* p, const void* x, double rho, void* w
         Staged ws = stage_out(p, w, rb * p->D, p->stage_out);
         reweight(p, xs.dev, rho, ws.dev);
         finish_out(p, ws, w, rb * p->D);
+    });
+}
+
+purify_status purify_noise_sigma(double y_norm, int64_t M, double snr_db, double* sigma) {
+    return guarded([&] {
+        PURIFY_REQUIRE(sigma != nullptr, "null argument");
+        PURIFY_REQUIRE(M >= 1 && std::isfinite(y_norm) && y_norm >= 0 && std::isfinite(snr_db),
+                       "need M >= 1, a finite non-negative norm and a finite SNR");
+        *sigma = y_norm / std::sqrt((double)M) * std::pow(10.0, -snr_db / 20.0);
+    });
+}
+
+purify_status purify_chi2_epsilon(double sigma, const int64_t* offs, int32_t R, double* eps) {
+    return guarded([&] {
+        PURIFY_REQUIRE(offs && eps && R >= 1, "null argument or R < 1");
+        PURIFY_REQUIRE(std::isfinite(sigma) && sigma > 0, "sigma must be positive and finite");
+        PURIFY_REQUIRE(offs[0] == 0, "block_offsets[0] must be 0");
+        for (int i = 0; i < R; ++i) PURIFY_REQUIRE(offs[i + 1] > offs[i], "block_offsets must increase");
+        for (int i = 0; i < R; ++i) {
+            // chi^2 with 2 M_i degrees of freedom, scaled by sigma^2 / 2: mean + 2 std
+            const double m = (double)(offs[i + 1] - offs[i]);
+            eps[i] = sigma / std::sqrt(2.0) * std::sqrt(2.0 * m + 4.0 * std::sqrt(m));
+        }
     });
 }
 

@@ -1,22 +1,30 @@
-"""Host-side set-up of an imaging problem for the GPU library: noise level
-and per-block l2 bounds (problem (3) of the paper, Sec. 1: each eps_i bounds
-the norm of the block's noise).
-
-Reading of "an appropriate bound": complex noise n_m = sigma (a + i b)/sqrt 2
-with a, b ~ N(0, 1), so (2/sigma^2) ||n_i||^2 ~ chi^2 with 2 M_i degrees of
-freedom; eps_i is the chi^2 mean plus two standard deviations,
-    eps_i = (sigma / sqrt 2) sqrt(2 M_i + 4 sqrt(M_i)),
-and sigma = ||Phi x|| / sqrt(M) * 10^(-SNR/20) for an input SNR in dB.
+"""Host-side set-up of an imaging problem: the noise level and the per-block
+l2 bounds of problem (3) (Sec. 1, Eq. 3: eps_i bounds the norm of block i's
+noise). Argument marshalling only: both values are computed by the library
+(purify_noise_sigma, purify_chi2_epsilon in include/purify.h), which states
+the chi^2 reading of "an appropriate bound" it uses.
 """
 from __future__ import annotations
 
+import ctypes as C
+
 import numpy as np
+
+from ._lib import check, load
 
 
 def noise_sigma_from_norm(y_clean_norm: float, M: int, snr_db: float) -> float:
-    return float(y_clean_norm / np.sqrt(M) * 10.0 ** (-snr_db / 20.0))
+    """sigma for a noiseless ||Phi x|| and an input SNR in dB."""
+    out = C.c_double()
+    check(load().purify_noise_sigma(float(y_clean_norm), int(M), float(snr_db), C.byref(out)))
+    return out.value
 
 
 def chi2_epsilon(sigma: float, block_sizes) -> np.ndarray:
-    m = np.asarray(block_sizes, dtype=np.float64)
-    return sigma / np.sqrt(2.0) * np.sqrt(2.0 * m + 4.0 * np.sqrt(m))
+    """eps_i for blocks of the given sizes (the contiguous partition of Eq. 2)."""
+    sizes = np.asarray(block_sizes, dtype=np.int64).ravel()
+    offs = np.ascontiguousarray(np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64))
+    eps = np.empty(sizes.size, dtype=np.float64)
+    check(load().purify_chi2_epsilon(float(sigma), offs.ctypes.data_as(C.POINTER(C.c_int64)), int(sizes.size),
+                                     eps.ctypes.data_as(C.POINTER(C.c_double))))
+    return eps

@@ -148,3 +148,29 @@ def test_block_partitions_must_cover_the_visibilities(lib, offs, msg):
 
 def test_launch_counter_starts_finite(lib):
     assert lib.purify_launch_count() >= 0
+
+
+def test_problem_setup_matches_the_oracle_reading(lib):
+    # sigma and the chi^2 bounds of Eq. 3 are host calls of the library (no
+    # GPU work); they follow the oracle's reading of "an appropriate bound"
+    import numpy as np
+
+    from oracle import sdmm as osd
+    from paper_1502_05037_gb300 import problem, synth
+
+    g = np.random.default_rng(3)
+    y = g.standard_normal(5000) + 1j * g.standard_normal(5000)
+    assert abs(problem.noise_sigma_from_norm(np.linalg.norm(y), y.size, 27.5) - osd.noise_sigma(y, 27.5)) \
+        <= 1e-14 * osd.noise_sigma(y, 27.5)
+    sizes = synth.block_sizes(100000, 13, 4)
+    got = problem.chi2_epsilon(0.37, sizes)
+    want = osd.epsilon_chi2(0.37, sizes)
+    assert np.max(np.abs(got - want) / want) <= 1e-14
+    # a single visibility block of size 1: sqrt(2 + 4) sigma / sqrt 2
+    assert abs(problem.chi2_epsilon(2.0, [1])[0] - np.sqrt(6.0) * 2.0 / np.sqrt(2.0)) <= 1e-14 * 4
+    for bad in (lambda: problem.chi2_epsilon(0.0, sizes), lambda: problem.chi2_epsilon(-1.0, sizes),
+                lambda: problem.chi2_epsilon(1.0, [3, 0, 2]), lambda: problem.noise_sigma_from_norm(1.0, 0, 30.0),
+                lambda: problem.noise_sigma_from_norm(float("nan"), 10, 30.0)):
+        with pytest.raises(_lib.PurifyError) as e:
+            bad()
+        assert e.value.status == _lib.PURIFY_EINVAL

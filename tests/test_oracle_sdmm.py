@@ -246,13 +246,68 @@ def test_sdmm_first_iteration_from_zero_by_hand():
     assert np.allclose(st.z2, -s2, atol=1e-14)
 
 
-def test_reweight_formula():
+def _log_sum(c, rho):
+    """The log-sum sparsity penalty rho sum_d log(rho + c_d) of magnitudes
+    c_d = |coefficient| (evaluated as given, also slightly below 0), whose
+    majorise-minimise steps are reweighted l1 problems (Candes, Wakin & Boyd
+    2008); the paper (Sec. 1) describes the weights as essentially the
+    inverse of the previous solution's coefficients."""
+    return rho * float(np.sum(np.log(rho + np.asarray(c))))
+
+
+def test_reweight_is_the_log_sum_slope():
+    # the weights are the derivative of the log-sum penalty in |c_d| at the
+    # previous solution's coefficients: a central difference in each
+    # coefficient magnitude (a dropped rho, a square or a missing |.| fails)
     prob, x = _tiny_problem()
     c = prob.psi_adj(x)
-    w = sdmm.reweight(prob, x, 0.1)
-    assert w.shape == c.shape
-    assert np.all(w > 0) and np.all(w <= 1)
-    assert np.allclose(w * (0.1 + np.abs(c)), 0.1)
+    for rho in (0.03, 0.1, 0.7):
+        w = sdmm.reweight(prob, x, rho)
+        assert w.shape == c.shape
+        # the penalty's term rho log(rho + a) is analytic in a > -rho, so a
+        # symmetric difference also holds at a = 0
+        h = 1e-5 * rho
+        a = np.abs(c).ravel()
+        term = lambda t: rho * np.log(rho + t)
+        slope = (term(a + h) - term(a - h)) / (2 * h)
+        assert np.max(np.abs(w.ravel() - slope)) <= 1e-8
+        # and the whole penalty's change for one coefficient moved by +-h
+        for d in np.random.default_rng(5).choice(a.size, 20, replace=False):
+            up, dn = a.copy(), a.copy()
+            up[d] += h
+            dn[d] -= h
+            fd = (_log_sum(up, rho) - _log_sum(dn, rho)) / (2 * h)
+            assert abs(w.ravel()[d] - fd) <= 1e-5
+    # x = 0: every coefficient is zero and every weight one
+    assert np.array_equal(sdmm.reweight(prob, np.zeros_like(x), 0.2), np.ones_like(c))
+
+
+def test_reweight_majorises_the_log_sum_penalty():
+    # concavity: for every c, penalty(c) <= penalty(c_t) + sum w_t (|c| - |c_t|)
+    # with w_t the weights at c_t, so the weighted l1 problem majorises it
+    prob, x = _tiny_problem(seed=4)
+    ct = prob.psi_adj(x)
+    rho = 0.05
+    wt = sdmm.reweight(prob, x, rho)
+    g = np.random.default_rng(6)
+    for _ in range(50):
+        c = ct + g.standard_normal(ct.shape) * g.choice([1e-3, 0.1, 1.0])
+        bound = _log_sum(np.abs(ct), rho) + float(np.sum(wt * (np.abs(c) - np.abs(ct))))
+        assert _log_sum(np.abs(c), rho) <= bound + 1e-12
+
+
+def test_reweighted_pass_does_not_increase_the_log_sum_penalty():
+    # majorise-minimise descent: solving the problem weighted at x_0 from x_0
+    # lowers the log-sum penalty of the analysis coefficients (x_0 is
+    # feasible, so the weighted l1 minimiser is at most its value)
+    prob, _ = _tiny_problem(seed=21)
+    x0 = sdmm.sdmm_solve(prob, np.zeros((8, 8)), 400, 20).x
+    assert np.all(sdmm.residual_ratios(prob, x0) <= 1.0 + 1e-3)
+    rho = float(np.std(prob.psi_adj(x0)))
+    prob.weights = sdmm.reweight(prob, x0, rho)
+    x1 = sdmm.sdmm_solve(prob, x0, 400, 20).x
+    assert np.all(sdmm.residual_ratios(prob, x1) <= 1.0 + 1e-3)
+    assert _log_sum(np.abs(prob.psi_adj(x1)), rho) < _log_sum(np.abs(prob.psi_adj(x0)), rho)
 
 
 def test_sara_reweighting_keeps_feasibility():
