@@ -456,6 +456,9 @@ def run_ours(args):
             roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                         "frac": (achieved / peak if achieved else None), "peak_source": peak_src, **common}
     kernel_table = kernel_rates(ktimes, plan.info, args.steps, dtb, wl.levels)
+    inf = plan.info
+    decomposition = {"grid": inf.grid_mode, "degrid": inf.degrid_mode, "normal": inf.normal_mode,
+                     "lane_tile": inf.lane_tile, "legend": "1 tile subproblems, 2 run sets, 3 lanes, 4 lanes by tiles"}
 
     # ---- pass C: end to end through the public API with pinned host buffers
     y_host = torch.empty(wl.M, dtype=cdt, pin_memory=True)
@@ -539,6 +542,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": wl.dtype, "data": "synthetic",
             "config": {"workload": describe(wl),
                        "cg_iters": args.cg_iters, "cg_steps_applied_per_iteration": cg_per_step,
+                       "decomposition": decomposition,
                        "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2, and a 512 MiB buffer rewritten between timed steps"},
             "phi_phiadj_gvis_s": gvis, "phi_ms": ops["phi"]["ms"], "phi_adj_ms": ops["phi_adj"]["ms"],
@@ -824,6 +828,7 @@ def run_profile_op(args):
     yv = torch.empty(wl.M, dtype=torch.complex64, device=dev)
     xa = torch.empty((wl.ny, wl.nx), dtype=torch.complex64, device=dev)
     c = torch.empty((plan.info.q, wl.ny, wl.nx), dtype=torch.float32, device=dev)
+    xo = torch.empty_like(x)
     if args.profile_op == "iteration":
         xs = torch.zeros_like(x)
         pk.purify_sdmm_solve(plan, y, eps, xs, max_iter=0, cg_iters=args.cg_iters, nu=1.0, gamma=1e-4)
@@ -837,6 +842,8 @@ def run_profile_op(args):
             pk.purify_psi_adj(plan, x, c)
         elif args.profile_op == "psi":
             pk.purify_psi(plan, c, x)
+        elif args.profile_op == "normal":
+            pk.purify_phi_normal(plan, x, xo)
         else:
             pk.purify_sdmm_iterate(plan, 1)
     torch.cuda.synchronize(dev)
@@ -1032,7 +1039,7 @@ def main():
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
-    ap.add_argument("--profile-op", choices=["phi", "phi_adj", "psi", "psi_adj", "iteration"], default=None,
+    ap.add_argument("--profile-op", choices=["phi", "phi_adj", "psi", "psi_adj", "normal", "iteration"], default=None,
                     help="only launch this operator W + K times (for ncu captures); prints no bench line")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -72,10 +72,12 @@ typedef struct {
     purify_dtype dtype;            /* operator precision */
     void *stream;                  /* cudaStream_t; NULL = legacy default stream */
     int32_t tile;                  /* gridding tile edge (power of two, 8..64); 0 => autotune */
-    int32_t grid_mode;             /* G^H work decomposition: 0 => autotuned (tile subproblems
-                                      when `tile` is fixed), 1 => tile subproblems (shared-memory
-                                      tile per subproblem), 2 => runs of visibilities sharing
-                                      their first-tap cell, flushed to the grid */
+    int32_t grid_mode;             /* G^H / G work decomposition: 0 => autotuned (tile
+                                      subproblems when `tile` is fixed), 1 => tile subproblems
+                                      (shared-memory tile per subproblem), 2 => G^H by runs of
+                                      visibilities sharing their first-tap cell, flushed to the
+                                      grid (G by tiles), 3 => both by lanes: one run per lane, its
+                                      patch and accumulator in registers (FP32, J <= 6 only) */
 } purify_plan_desc;
 
 /* Build a plan: validates the description, computes the correction, kernel,
@@ -97,7 +99,13 @@ typedef struct {
     int32_t R, J, levels;
     double beta;
     int64_t workspace_bytes;
-    int32_t grid_mode;             /* the decomposition in use: 1 tile subproblems, 2 runs */
+    int32_t grid_mode;             /* the G^H decomposition in use: 1 tile subproblems, 2 runs,
+                                      3 lanes, 4 lanes by tiles */
+    int32_t degrid_mode;           /* the G decomposition in use: 1 tile subproblems, 3 lanes,
+                                      4 lanes by tiles */
+    int32_t normal_mode;           /* the fused G^H G of the CG normal operator: 2 runs, 3 lanes,
+                                      4 lanes by tiles */
+    int32_t lane_tile;             /* grid tile edge of the lanes-by-tiles work (0: none) */
 } purify_plan_info;
 purify_status purify_plan_get_info(const purify_plan *plan, purify_plan_info *info);
 

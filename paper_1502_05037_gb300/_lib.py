@@ -45,6 +45,9 @@ class purify_plan_info(C.Structure):
         ("beta", C.c_double),
         ("workspace_bytes", C.c_int64),
         ("grid_mode", C.c_int32),
+        ("degrid_mode", C.c_int32),
+        ("normal_mode", C.c_int32),
+        ("lane_tile", C.c_int32),
     ]
 
 

@@ -167,7 +167,10 @@ purify_status purify_plan_get_info(const purify_plan* plan, purify_plan_info* in
         info->levels = plan->levels;
         info->beta = plan->beta;
         info->workspace_bytes = plan->workspace_bytes;
-        info->grid_mode = plan->grid_by_runs ? 2 : 1;
+        info->grid_mode = plan->grid_kind;
+        info->degrid_mode = plan->degrid_kind;
+        info->normal_mode = plan->normal_kind;
+        info->lane_tile = plan->lanet.tile;
     });
 }
 

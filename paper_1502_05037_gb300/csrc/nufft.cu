@@ -861,6 +861,268 @@ k_grid_sets(const typename cplx_of<T>::type* __restrict__ yin, const typename cp
     pdl_trigger();
 }
 
+// Lane-per-run forms of G^H G, G^H and G (FP32, J <= 6; see LaneWork). A
+// warp takes a set of 32 runs (sets w, 2W - 1 - w, 2W + w, ... for warp w of
+// W, which balances the length-sorted sets), lane l owns run l of the set:
+// it holds the run's J x J patch of the forward grid X (G^H G, G) and/or its
+// J x J accumulator (G^H G, G^H) in registers and walks the run's
+// visibilities alone, evaluating all 2J tap weights itself (Horner in the
+// per-tap polynomials, whose coefficients are kernel-parameter constants):
+//   G^H G: y = sum_b wy[b] sum_a wx[a] X[b][a];  acc[b][a] += wx[a] wy[b] y
+//   G^H  : y = yin[idx];                          acc[b][a] += wx[a] wy[b] y
+//   G    : yout[idx] = sum_b wy[b] sum_a wx[a] X[b][a]
+// with no exchange between lanes. One step of the warp reads 32 consecutive
+// records; padding records (past a lane's run) get zero weights. The
+// accumulators are flushed with vector reductions after the set.
+enum { LANE_GG = 0, LANE_GRID = 1, LANE_DEGRID = 2 };
+
+template <int J, int MODE>
+__global__ void __launch_bounds__(128)
+k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __restrict__ yout,
+       const int2* __restrict__ set_info, const int2* __restrict__ run_cl, const float2* __restrict__ recs,
+       const int* __restrict__ idx, int nsets, KbPoly kp, int Kx, int Ky, float2* __restrict__ out,
+       const int* __restrict__ skip) {
+    constexpr int DEG = kb_poly_deg(J);
+    constexpr bool HAS_X = MODE != LANE_GRID, HAS_ACC = MODE != LANE_DEGRID;
+    pdl_wait();
+    if (skip && *skip) return;
+    const int lane = threadIdx.x & 31;
+    const int W = gridDim.x * (blockDim.x >> 5), wg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    for (int it = 0;; ++it) {
+        const int set = it * W + ((it & 1) ? W - 1 - wg : wg);
+        if (set >= nsets) break;
+        const int2 si = set_info[set];
+        const int2 rc = run_cl[(size_t)set * 32 + lane];
+        const int cx = rc.x & 0xFFFF, cy = (int)((unsigned)rc.x >> 16), len = rc.y;
+        float xr[HAS_X ? J : 1][HAS_X ? J : 1], xi[HAS_X ? J : 1][HAS_X ? J : 1];
+        float ar[HAS_ACC ? J : 1][HAS_ACC ? J : 1], ai[HAS_ACC ? J : 1][HAS_ACC ? J : 1];
+        if constexpr (HAS_X) {
+#pragma unroll
+            for (int b = 0; b < J; ++b) {
+                float2 v[J];
+                if (len > 0) {
+                    ldg_row<J>(X + (size_t)((cy + b) & (Ky - 1)) * Kx, cx, Kx, v);
+                } else {
+#pragma unroll
+                    for (int a = 0; a < J; ++a) v[a] = make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int a = 0; a < J; ++a) {
+                    xr[b][a] = v[a].x;
+                    xi[b][a] = v[a].y;
+                }
+            }
+        }
+        if constexpr (HAS_ACC) {
+#pragma unroll
+            for (int b = 0; b < J; ++b)
+#pragma unroll
+                for (int a = 0; a < J; ++a) ar[b][a] = ai[b][a] = 0.f;
+        }
+        const size_t base = (size_t)si.x * 32 + lane;
+        const int lmax = si.y;
+        float2 rcur = lmax > 0 ? recs[base] : make_float2(0.f, 0.f);
+        int icur = (MODE != LANE_GG && lmax > 0) ? idx[base] : -1;
+        for (int k = 0; k < lmax; ++k) {
+            // the next step's record, one step ahead
+            float2 rnx = make_float2(0.f, 0.f);
+            int inx = -1;
+            if (k + 1 < lmax) {
+                rnx = recs[base + (size_t)(k + 1) * 32];
+                if (MODE != LANE_GG) inx = idx[base + (size_t)(k + 1) * 32];
+            }
+            const bool valid = k < len;
+            float wx[J], wy[J];
+            kb_weights<J>(kp, rcur.x, wx);
+            kb_weights<J>(kp, rcur.y, wy);
+            if (!valid) {
+#pragma unroll
+                for (int a = 0; a < J; ++a) wx[a] = 0.f;
+            }
+            float yr = 0.f, yi = 0.f;
+            if constexpr (HAS_X) {
+#pragma unroll
+                for (int b = 0; b < J; ++b) {
+                    float tr = 0.f, ti = 0.f;
+#pragma unroll
+                    for (int a = 0; a < J; ++a) {
+                        tr = fmaf(wx[a], xr[b][a], tr);
+                        ti = fmaf(wx[a], xi[b][a], ti);
+                    }
+                    yr = fmaf(wy[b], tr, yr);
+                    yi = fmaf(wy[b], ti, yi);
+                }
+            }
+            if constexpr (MODE == LANE_GRID) {
+                if (icur >= 0) {
+                    const float2 v = yin[icur];
+                    yr = v.x;
+                    yi = v.y;
+                }
+            }
+            if constexpr (MODE == LANE_DEGRID) {
+                if (valid && icur >= 0) yout[icur] = make_float2(yr, yi);
+            }
+            if constexpr (HAS_ACC) {
+#pragma unroll
+                for (int b = 0; b < J; ++b) {
+                    const float ur = wy[b] * yr, ui = wy[b] * yi;
+#pragma unroll
+                    for (int a = 0; a < J; ++a) {
+                        ar[b][a] = fmaf(wx[a], ur, ar[b][a]);
+                        ai[b][a] = fmaf(wx[a], ui, ai[b][a]);
+                    }
+                }
+            }
+            rcur = rnx;
+            icur = inx;
+        }
+        if constexpr (HAS_ACC) {
+            if (len > 0) {
+#pragma unroll
+                for (int b = 0; b < J; ++b) red_row<J>(out + (size_t)((cy + b) & (Ky - 1)) * Kx, cx, Kx, ar[b], ai[b]);
+            }
+        }
+    }
+    pdl_trigger();
+}
+
+// The lane-per-run kernels by grid tiles: a block owns one subproblem (a
+// grid tile and some of its runs). The tile plus its (J - 1) halo of the
+// forward grid X is copied to shared memory (G^H G, G) and an accumulator
+// tile of the same shape is cleared (G^H G, G^H); warp w takes the
+// subproblem's sets w, w + 4, ...; lane l reads its run's patch from the
+// shared X tile, walks the run as in k_lane, and adds its patch accumulator
+// to the shared tile with shared-memory atomics. The accumulator tile is
+// then added to the grid once, with coalesced reductions of its non-zero
+// cells.
+template <int J, int MODE>
+__global__ void __launch_bounds__(128)
+k_lane_tile(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __restrict__ yout,
+            const int4* __restrict__ sub_info, const int2* __restrict__ set_info, const int2* __restrict__ run_cl,
+            const float2* __restrict__ recs, const int* __restrict__ idx, int tile, int tiles_x, int S, KbPoly kp,
+            int Kx, int Ky, float2* __restrict__ out, const int* __restrict__ skip) {
+    constexpr bool HAS_X = MODE != LANE_GRID, HAS_ACC = MODE != LANE_DEGRID;
+    pdl_wait();
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int PT = tile + J - 1;
+    float2* sX = reinterpret_cast<float2*>(smem_raw);                 // [PT][S] (G^H G, G)
+    float2* sA = sX + (HAS_X ? (size_t)PT * S : 0);                  // [PT][S] (G^H G, G^H)
+    const int4 si4 = sub_info[blockIdx.x];
+    const int oy = (si4.x / tiles_x) * tile, ox = (si4.x % tiles_x) * tile;
+    for (int t = threadIdx.x; t < PT * PT; t += blockDim.x) {
+        const int r = t / PT, c = t - r * PT;
+        if (HAS_X) sX[r * S + c] = X[(size_t)((oy + r) & (Ky - 1)) * Kx + ((ox + c) & (Kx - 1))];
+        if (HAS_ACC) sA[r * S + c] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int set = si4.y + warp; set < si4.z; set += nwarps) {
+        const int2 si = set_info[set];
+        const int2 rc = run_cl[(size_t)set * 32 + lane];
+        const int len = rc.y;
+        const int lx = (rc.x & 0xFFFF) - ox, ly = (int)((unsigned)rc.x >> 16) - oy;
+        const int o0 = len > 0 ? ly * S + lx : 0;
+        float xr[HAS_X ? J : 1][HAS_X ? J : 1], xi[HAS_X ? J : 1][HAS_X ? J : 1];
+        float ar[HAS_ACC ? J : 1][HAS_ACC ? J : 1], ai[HAS_ACC ? J : 1][HAS_ACC ? J : 1];
+        if constexpr (HAS_X) {
+#pragma unroll
+            for (int b = 0; b < J; ++b)
+#pragma unroll
+                for (int a = 0; a < J; ++a) {
+                    const float2 v = sX[o0 + b * S + a];
+                    xr[b][a] = v.x;
+                    xi[b][a] = v.y;
+                }
+        }
+        if constexpr (HAS_ACC) {
+#pragma unroll
+            for (int b = 0; b < J; ++b)
+#pragma unroll
+                for (int a = 0; a < J; ++a) ar[b][a] = ai[b][a] = 0.f;
+        }
+        const size_t base = (size_t)si.x * 32 + lane;
+        const int lmax = si.y;
+        float2 rcur = lmax > 0 ? recs[base] : make_float2(0.f, 0.f);
+        int icur = (MODE != LANE_GG && lmax > 0) ? idx[base] : -1;
+        for (int k = 0; k < lmax; ++k) {
+            float2 rnx = make_float2(0.f, 0.f);
+            int inx = -1;
+            if (k + 1 < lmax) {
+                rnx = recs[base + (size_t)(k + 1) * 32];
+                if (MODE != LANE_GG) inx = idx[base + (size_t)(k + 1) * 32];
+            }
+            const bool valid = k < len;
+            float wx[J], wy[J];
+            kb_weights<J>(kp, rcur.x, wx);
+            kb_weights<J>(kp, rcur.y, wy);
+            if (!valid) {
+#pragma unroll
+                for (int a = 0; a < J; ++a) wx[a] = 0.f;
+            }
+            float yr = 0.f, yi = 0.f;
+            if constexpr (HAS_X) {
+#pragma unroll
+                for (int b = 0; b < J; ++b) {
+                    float tr = 0.f, ti = 0.f;
+#pragma unroll
+                    for (int a = 0; a < J; ++a) {
+                        tr = fmaf(wx[a], xr[b][a], tr);
+                        ti = fmaf(wx[a], xi[b][a], ti);
+                    }
+                    yr = fmaf(wy[b], tr, yr);
+                    yi = fmaf(wy[b], ti, yi);
+                }
+            }
+            if constexpr (MODE == LANE_GRID) {
+                if (icur >= 0) {
+                    const float2 v = yin[icur];
+                    yr = v.x;
+                    yi = v.y;
+                }
+            }
+            if constexpr (MODE == LANE_DEGRID) {
+                if (valid && icur >= 0) yout[icur] = make_float2(yr, yi);
+            }
+            if constexpr (HAS_ACC) {
+#pragma unroll
+                for (int b = 0; b < J; ++b) {
+                    const float ur = wy[b] * yr, ui = wy[b] * yi;
+#pragma unroll
+                    for (int a = 0; a < J; ++a) {
+                        ar[b][a] = fmaf(wx[a], ur, ar[b][a]);
+                        ai[b][a] = fmaf(wx[a], ui, ai[b][a]);
+                    }
+                }
+            }
+            rcur = rnx;
+            icur = inx;
+        }
+        if constexpr (HAS_ACC) {
+            if (len > 0) {
+#pragma unroll
+                for (int b = 0; b < J; ++b)
+#pragma unroll
+                    for (int a = 0; a < J; ++a) {
+                        atomicAdd(&sA[o0 + b * S + a].x, ar[b][a]);
+                        atomicAdd(&sA[o0 + b * S + a].y, ai[b][a]);
+                    }
+            }
+        }
+    }
+    if constexpr (HAS_ACC) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < PT * PT; t += blockDim.x) {
+            const int r = t / PT, c = t - r * PT;
+            const float2 v = sA[r * S + c];
+            if (v.x != 0.f || v.y != 0.f)
+                atomicAdd(out + (size_t)((oy + r) & (Ky - 1)) * Kx + ((ox + c) & (Kx - 1)), v);
+        }
+    }
+    pdl_trigger();
+}
+
 // G with the tile staged in shared memory: a block owns one subproblem,
 // copies the tile plus its (J-1) halo from the grid, then every thread
 // interpolates visibilities of the subproblem from the shared copy.
@@ -1133,14 +1395,90 @@ static void grid_sets_tj(purify_plan* p, const void* y, bool caller_order, const
         p->beta, 1.0 / p->i0beta, p->Kx, p->Ky, p->gacc.as<C>(), skip);
     L.done();
 }
+// Lane-per-run launches: a persistent grid of 4-warp blocks (as many as are
+// resident at once, or fewer when there is less work).
+template <int J, int MODE>
+static void lane_tj(purify_plan* p, const void* yin, void* yout, bool caller_order, const int* skip, bool zeroed) {
+    if (MODE != LANE_DEGRID && !zeroed) PURIFY_CUDA(cudaMemsetAsync(p->gacc.p, 0, p->gacc.bytes, p->stream));
+    const LaneWork& lw = p->lanes;
+    if (lw.nsets == 0) return;
+    static int per_sm = 0;   // resident blocks per SM of this instantiation
+    if (per_sm == 0) {
+        PURIFY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lane<J, MODE>, 128, 0));
+        per_sm = std::max(1, per_sm);
+    }
+    int sms = 0, dev = 0;
+    PURIFY_CUDA(cudaGetDevice(&dev));
+    PURIFY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = std::max(1, std::min(sms * per_sm, (lw.nsets + 3) / 4));
+    Launch L(p, MODE == LANE_GG ? "normal_gg" : (MODE == LANE_GRID ? "grid" : "degrid"));
+    launch_dependent(k_lane<J, MODE>, blocks, 128, 0, p->stream, p->grid.as<float2>(), (const float2*)yin,
+                     (float2*)yout, lw.set_info.as<int2>(), lw.run_cl.as<int2>(), lw.rec.as<float2>(),
+                     caller_order ? lw.idx_caller.as<int>() : lw.idx.as<int>(), lw.nsets, p->kbp, p->Kx, p->Ky,
+                     p->gacc.as<float2>(), skip);
+    L.done();
+}
+// By tiles: one block per subproblem.
+template <int J, int MODE>
+static void lane_tile_tj(purify_plan* p, const void* yin, void* yout, bool caller_order, const int* skip,
+                         bool zeroed) {
+    if (MODE != LANE_DEGRID && !zeroed) PURIFY_CUDA(cudaMemsetAsync(p->gacc.p, 0, p->gacc.bytes, p->stream));
+    const LaneWork& lw = p->lanet;
+    if (lw.nsub == 0) return;
+    const int PT = lw.tile + J - 1, S = PT | 1;
+    const size_t sm = sizeof(float2) * (size_t)PT * S * (MODE == LANE_GG ? 2 : 1);
+    set_smem(k_lane_tile<J, MODE>, sm);
+    Launch L(p, MODE == LANE_GG ? "normal_gg" : (MODE == LANE_GRID ? "grid" : "degrid"));
+    launch_dependent(k_lane_tile<J, MODE>, lw.nsub, 128, sm, p->stream, p->grid.as<float2>(), (const float2*)yin,
+                     (float2*)yout, lw.sub_info.as<int4>(), lw.set_info.as<int2>(), lw.run_cl.as<int2>(),
+                     lw.rec.as<float2>(), caller_order ? lw.idx_caller.as<int>() : lw.idx.as<int>(), lw.tile,
+                     lw.tiles_x, S, p->kbp, p->Kx, p->Ky, p->gacc.as<float2>(), skip);
+    L.done();
+}
+template <int J, int MODE>
+static void lane_any(purify_plan* p, int kind, const void* yin, void* yout, bool c, const int* s, bool z) {
+    if constexpr (J <= kLaneMaxJ) {
+        if (kind == 4) lane_tile_tj<J, MODE>(p, yin, yout, c, s, z);
+        else lane_tj<J, MODE>(p, yin, yout, c, s, z);
+    }
+}
+template <int J> static void lane_gg(purify_plan* p, int kind, const int* s, bool z) {
+    lane_any<J, LANE_GG>(p, kind, nullptr, nullptr, false, s, z);
+}
+template <int J> static void lane_grid(purify_plan* p, int kind, const void* y, bool c, const int* s, bool z) {
+    lane_any<J, LANE_GRID>(p, kind, y, nullptr, c, s, z);
+}
+template <int J> static void lane_degrid(purify_plan* p, int kind, void* y, bool c, const int* s) {
+    lane_any<J, LANE_DEGRID>(p, kind, nullptr, y, c, s, true);
+}
+
 template <int J> static void normal_f(purify_plan* p, const int* s, bool z) { grid_sets_tj<float, J, true>(p, nullptr, false, s, z); }
 template <int J> static void normal_d(purify_plan* p, const int* s, bool z) { grid_sets_tj<double, J, true>(p, nullptr, false, s, z); }
 template <int J> static void gsets_f(purify_plan* p, const void* y, bool c, const int* s, bool z) { grid_sets_tj<float, J, false>(p, y, c, s, z); }
 template <int J> static void gsets_d(purify_plan* p, const void* y, bool c, const int* s, bool z) { grid_sets_tj<double, J, false>(p, y, c, s, z); }
 
+bool lane_work_ok(const purify_plan* p) { return p->dtype == PURIFY_F32 && p->J <= kLaneMaxJ && p->lanes.nsets > 0; }
+
 void launch_normal_gg(purify_plan* p, const int* skip, bool zeroed) {
-    if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, normal_f, p, skip, zeroed); }
+    if (p->normal_kind >= 3 && lane_work_ok(p)) { PURIFY_J_DISPATCH(p->J, lane_gg, p, p->normal_kind, skip, zeroed); }
+    else if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, normal_f, p, skip, zeroed); }
     else { PURIFY_J_DISPATCH(p->J, normal_d, p, skip, zeroed); }
+}
+void launch_grid_lanes(purify_plan* p, int kind, const void* y, bool caller_order, const int* skip, bool zeroed) {
+    if (!lane_work_ok(p)) throw Error{PURIFY_EINVAL, "lane-per-run gridding needs an FP32 plan with J <= 6"};
+    PURIFY_J_DISPATCH(p->J, lane_grid, p, kind, y, caller_order, skip, zeroed);
+}
+void launch_degrid_lanes(purify_plan* p, int kind, void* y, bool caller_order, const int* skip) {
+    if (!lane_work_ok(p)) throw Error{PURIFY_EINVAL, "lane-per-run degridding needs an FP32 plan with J <= 6"};
+    PURIFY_J_DISPATCH(p->J, lane_degrid, p, kind, y, caller_order, skip);
+}
+void launch_normal_lanes(purify_plan* p, int kind, const int* skip, bool zeroed) {
+    if (kind == 2 || !lane_work_ok(p)) {
+        if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, normal_f, p, skip, zeroed); }
+        else { PURIFY_J_DISPATCH(p->J, normal_d, p, skip, zeroed); }
+        return;
+    }
+    PURIFY_J_DISPATCH(p->J, lane_gg, p, kind, skip, zeroed);
 }
 void launch_grid_sets(purify_plan* p, const void* y, bool caller_order, const int* skip, bool zeroed) {
     if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, gsets_f, p, y, caller_order, skip, zeroed); }
@@ -1184,12 +1522,20 @@ void launch_rows_inv_crop(purify_plan* p, void* out, double scale, int out_mode,
     else rows_inv_t<double>(p, out, scale, out_mode, add, add_coef, skip, dot_part, corr);
 }
 void launch_degrid(purify_plan* p, void* y, bool caller_order, const int* skip) {
+    if (p->degrid_kind >= 3) {
+        launch_degrid_lanes(p, p->degrid_kind, y, caller_order, skip);
+        return;
+    }
     if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, degrid_f, p, y, caller_order, skip); }
     else { PURIFY_J_DISPATCH(p->J, degrid_d, p, y, caller_order, skip); }
 }
 void launch_grid(purify_plan* p, const void* y, bool caller_order, const int* skip, bool zeroed) {
-    if (p->grid_by_runs) {
+    if (p->grid_kind == 2) {
         launch_grid_sets(p, y, caller_order, skip, zeroed);
+        return;
+    }
+    if (p->grid_kind >= 3) {
+        launch_grid_lanes(p, p->grid_kind, y, caller_order, skip, zeroed);
         return;
     }
     if (p->dtype == PURIFY_F32) { PURIFY_J_DISPATCH(p->J, grid_f, p, y, caller_order, skip, zeroed); }

@@ -62,6 +62,7 @@ int main(void) {
   P(purify_plan_desc, tile) P(purify_plan_desc, stream) P(purify_plan_desc, dtype) P(purify_plan_desc, block_offsets)
   P(purify_sdmm_params, resume) P(purify_sdmm_params, check_every) P(purify_sdmm_params, toeplitz) P(purify_sdmm_stats, status)
   P(purify_plan_info, workspace_bytes) P(purify_plan_info, beta) P(purify_plan_info, grid_mode)
+  P(purify_plan_info, lane_tile)
   P(purify_plan_desc, grid_mode)
   return 0;
 }
@@ -86,6 +87,7 @@ int main(void) {
     assert int(got["purify_plan_desc.dtype"]) == _lib.purify_plan_desc.dtype.offset
     assert int(got["purify_plan_desc.grid_mode"]) == _lib.purify_plan_desc.grid_mode.offset
     assert int(got["purify_plan_info.grid_mode"]) == _lib.purify_plan_info.grid_mode.offset
+    assert int(got["purify_plan_info.lane_tile"]) == _lib.purify_plan_info.lane_tile.offset
     assert int(got["purify_plan_desc.block_offsets"]) == _lib.purify_plan_desc.block_offsets.offset
     assert int(got["purify_sdmm_params.resume"]) == _lib.purify_sdmm_params.resume.offset
     assert int(got["purify_sdmm_params.check_every"]) == _lib.purify_sdmm_params.check_every.offset
@@ -113,7 +115,10 @@ def test_invalid_description_is_rejected_before_any_launch(lib):
     ({"kb_width": 1}, b"kb_width"),
     ({"levels": 6, "nx": 16, "ny": 16}, b"too small"),            # deeper than the image allows
     ({"tile": 12}, b"tile"),
-    ({"grid_mode": 3}, b"grid_mode"),
+    ({"grid_mode": 5}, b"grid_mode"),
+    ({"grid_mode": 4, "dtype": 1}, b"grid_mode 3 or 4"),
+    ({"grid_mode": 3, "dtype": 1}, b"grid_mode 3 or 4"),               # lanes are FP32 only
+    ({"grid_mode": 3, "kb_width": 7}, b"grid_mode 3 or 4"),
     ({"oversample": 1.5}, b"oversample"),
     ({"dtype": 7}, b"dtype"),
     ({"basis_mask": 0x200}, b"basis_mask"),

@@ -151,7 +151,7 @@ def test_full_size_sampled_outputs():
     assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
 
 
-@pytest.mark.parametrize("grid_mode", [1, 2])
+@pytest.mark.parametrize("grid_mode", [1, 2, 3, 4])
 @pytest.mark.parametrize("nx,M,J,R,dtype,tile", [
     (64, 30011, 6, 3, pk.PURIFY_F32, 0),
     (64, 30011, 6, 3, pk.PURIFY_F32, 16),
@@ -160,9 +160,13 @@ def test_full_size_sampled_outputs():
     (16, 5, 5, 1, pk.PURIFY_F32, 0),
 ])
 def test_phi_adj_both_decompositions(nx, M, J, R, dtype, tile, grid_mode):
-    # G^H by tile subproblems and by first-tap-cell runs, each against the
+    # G^H by tile subproblems, by first-tap-cell runs and by lanes (one run
+    # per lane; 3: one pool of runs, 4: by grid tiles), each against the
     # oracle in caller order: several tiles, runs cut at their length cap, a
-    # ragged last run set, an odd J and a handful of visibilities
+    # ragged last run set, an odd J and a handful of visibilities; also G
+    # (Phi) and the normal operator of each decomposition
+    if grid_mode >= 3 and (dtype != pk.PURIFY_F32 or J > 6):
+        pytest.skip("lanes are FP32 with J <= 6 only")
     plan, u, v, _ = make_plan(nx, nx, M, J, R=R, dtype=dtype, seed=nx + M + grid_mode, tile=tile,
                               grid_mode=grid_mode)
     assert plan.info.grid_mode == grid_mode
@@ -170,11 +174,20 @@ def test_phi_adj_both_decompositions(nx, M, J, R, dtype, tile, grid_mode):
     y = (g.standard_normal(M) + 1j * g.standard_normal(M)).astype(np_cplx(dtype))
     x = torch.empty((nx, nx), dtype=t_cplx(dtype), device=DEV)
     pk.purify_phi_adj(plan, torch.from_numpy(y).to(DEV), x)
-    want = onf.phi_adj(oracle_plan(nx, nx, u, v, J), y.astype(np.complex128))
+    op = oracle_plan(nx, nx, u, v, J)
+    want = onf.phi_adj(op, y.astype(np.complex128))
     assert rel(x.cpu().numpy(), want) <= TOL[dtype]
+    xr = np.random.default_rng(M + 1).standard_normal((nx, nx)).astype(np_real(dtype))
+    yg = torch.empty(M, dtype=t_cplx(dtype), device=DEV)
+    pk.purify_phi(plan, torch.from_numpy(xr).to(DEV), yg)
+    assert rel(yg.cpu().numpy(), onf.phi(op, xr.astype(np.float64))) <= TOL[dtype]
+    out = torch.empty((nx, nx), dtype=t_real(dtype), device=DEV)
+    pk.purify_phi_normal(plan, torch.from_numpy(xr).to(DEV), out)
+    want_n = np.real(onf.phi_adj(op, onf.phi(op, xr.astype(np.float64))))
+    assert rel(out.cpu().numpy(), want_n) <= TOL[dtype]
 
 
-@pytest.mark.parametrize("grid_mode", [1, 2])
+@pytest.mark.parametrize("grid_mode", [1, 2, 3, 4])
 def test_phi_adj_single_cell_runs(grid_mode):
     # every visibility in a handful of cells: runs longer than the cap are
     # cut and flushed into the same cells
