@@ -76,8 +76,11 @@ typedef struct {
                                       subproblems when `tile` is fixed), 1 => tile subproblems
                                       (shared-memory tile per subproblem), 2 => G^H by runs of
                                       visibilities sharing their first-tap cell, flushed to the
-                                      grid (G by tiles), 3 => both by lanes: one run per lane, its
-                                      patch and accumulator in registers (FP32, J <= 6 only) */
+                                      grid (G by tiles), 3..5 => G^H, G and the solver's G^H G
+                                      by lanes: each run of visibilities sharing a first-tap cell
+                                      owned by one lane (3) or a lane pair (4; 5: runs grouped by
+                                      grid tile), its patch and accumulator in registers (FP32,
+                                      J <= 6 only) */
 } purify_plan_desc;
 
 /* Build a plan: validates the description, computes the correction, kernel,
@@ -100,12 +103,10 @@ typedef struct {
     double beta;
     int64_t workspace_bytes;
     int32_t grid_mode;             /* the G^H decomposition in use: 1 tile subproblems, 2 runs,
-                                      3 lanes, 4 lanes by tiles */
-    int32_t degrid_mode;           /* the G decomposition in use: 1 tile subproblems, 3 lanes,
-                                      4 lanes by tiles */
-    int32_t normal_mode;           /* the fused G^H G of the CG normal operator: 2 runs, 3 lanes,
-                                      4 lanes by tiles */
-    int32_t lane_tile;             /* grid tile edge of the lanes-by-tiles work (0: none) */
+                                      3..5 lanes (as grid_mode of the description) */
+    int32_t degrid_mode;           /* the G decomposition in use: 1 tile subproblems, 3..5 lanes */
+    int32_t normal_mode;           /* the fused G^H G of the CG normal operator: 2 runs, 3..5 lanes */
+    int32_t lane_tile;             /* grid tile edge grouping the runs of normal_mode 5 (else 0) */
 } purify_plan_info;
 purify_status purify_plan_get_info(const purify_plan *plan, purify_plan_info *info);
 

@@ -170,7 +170,7 @@ purify_status purify_plan_get_info(const purify_plan* plan, purify_plan_info* in
         info->grid_mode = plan->grid_kind;
         info->degrid_mode = plan->degrid_kind;
         info->normal_mode = plan->normal_kind;
-        info->lane_tile = plan->lanet.tile;
+        info->lane_tile = plan->normal_kind == 5 ? plan->lanes[2].tile : 0;
     });
 }
 

@@ -84,27 +84,33 @@ struct RunWork {
     DevBuf rec, cell, start, len;
 };
 
-// Lane-per-run work (FP32 plans, J <= 6): the same runs, 32 per warp set,
-// one run per lane. Set s holds record rows [row0, row0 + lmax) with lmax
-// its longest run; the record of run 32 s + lane at step k is
-// rec[(row0 + k) * 32 + lane], so one step of a warp reads 32 consecutive
-// records. Records past a run's end are padding (zero offsets, index -1).
-// run_cl[32 s + lane] = (cell, len), the cell packed as (cy << 16) | cx;
-// idx / idx_caller give each record's visibility in internal / caller order.
-// tile == 0: one pool of sets, runs sorted by length (longest first).
-// tile > 0: subproblems, each a grid tile (bin = ty * tiles_x + tx) and a
-// range of sets holding some of the tile's runs (sorted by length within
-// the tile); sub_info[s] = (bin, first set, end set, visibilities), the
-// subproblems sorted by visibility count (largest first).
+// Lane-per-run work (FP32 plans, J <= 6): the same runs, `width` per warp
+// set (32 / lanes per run). Set s holds record rows [row0, row0 + lmax) with
+// lmax its longest run; the record of run width s + r at step k is
+// rec[(row0 + k) * width + r], so one step of a warp reads `width`
+// consecutive records. Records past a run's end are padding (zero offsets,
+// index -1). run_cl[width s + r] = (cell, len), the cell packed as
+// (cy << 16) | cx; idx / idx_caller give each record's visibility in
+// internal / caller order. Set order: runs sorted by length (longest
+// first), or with tile > 0 grouped by grid tile of that edge (tiles in
+// raster order, runs by length within a tile).
 static constexpr int kLaneMaxJ = 6;
 struct LaneWork {
-    int nsets = 0, nsub = 0, tile = 0, tiles_x = 0;
+    int nsets = 0, width = 32, tile = 0;
     int64_t rows = 0;
-    DevBuf sub_info;              // int4 per subproblem (tile > 0)
     DevBuf set_info;              // int2 (row0, lmax) per set
     DevBuf run_cl;                // int2 (cell, len) per run
     DevBuf rec;                   // float2 (phx, phy) per record
     DevBuf idx, idx_caller;       // int per record
+    void release() {
+        nsets = 0;
+        rows = 0;
+        set_info.release();
+        run_cl.release();
+        rec.release();
+        idx.release();
+        idx_caller.release();
+    }
 };
 
 // SDMM device state (allocated on first solve).
@@ -186,11 +192,11 @@ struct purify_plan {
     purify::GridWork work;            // gridding work list (tile of the G^H kernel)
     purify::GridWork dwork;           // degridding work list (tile of the G kernel)
     purify::RunWork runs;             // run-ordered work of the fused normal operator
-    purify::LaneWork lanes;           // lane-per-run form of the same runs (FP32, J <= 6), one pool
-    purify::LaneWork lanet;           // the same by grid tiles (shared-memory tile per subproblem)
-    int normal_kind = 2;              // G^H G: 2 run sets, 3 lanes, 4 lanes by tiles; autotuned
-    int grid_kind = 1;                // G^H: 1 tile subproblems, 2 run sets, 3 lanes, 4 lanes by tiles; autotuned
-    int degrid_kind = 1;              // G: 1 tile subproblems, 3 lanes, 4 lanes by tiles; autotuned
+    purify::LaneWork lanes[3];        // lane-per-run forms of the same runs (FP32, J <= 6): one lane
+                                      // per run; two lanes per run; two, sets grouped by tile
+    int normal_kind = 2;              // G^H G: 2 run sets, 3..5 lanes (as lanes[kind - 3]); autotuned
+    int grid_kind = 1;                // G^H: 1 tile subproblems, 2 run sets, 3..5 lanes; autotuned
+    int degrid_kind = 1;              // G: 1 tile subproblems, 3..5 lanes; autotuned
     int fft_rb = 0, fft_cb = 0;       // FFT rows / columns per block (0: heuristic)
     // workspaces
     purify::DevBuf grid;              // Ky * Kx complex (forward transform output)
@@ -321,7 +327,8 @@ int max_grid_tile(int dtype, int J);
 // the lane-per-run kernels apply to this plan (FP32, J <= kLaneMaxJ)
 bool lane_work_ok(const purify_plan* p);
 // G^H / G by the lane-per-run kernels (same outputs as launch_grid / launch_degrid)
-// (kind 3: one pool of sets, kind 4: by tiles)
+// (kind 3: one lane per run, 4: two lanes per run, 5: two lanes per run
+// with the sets grouped by grid tile)
 void launch_grid_lanes(purify_plan* p, int kind, const void* y, bool caller_order, const int* skip,
                        bool zeroed = false);
 void launch_degrid_lanes(purify_plan* p, int kind, void* y, bool caller_order, const int* skip);

@@ -862,201 +862,158 @@ k_grid_sets(const typename cplx_of<T>::type* __restrict__ yin, const typename cp
 }
 
 // Lane-per-run forms of G^H G, G^H and G (FP32, J <= 6; see LaneWork). A
-// warp takes a set of 32 runs (sets w, 2W - 1 - w, 2W + w, ... for warp w of
-// W, which balances the length-sorted sets), lane l owns run l of the set:
-// it holds the run's J x J patch of the forward grid X (G^H G, G) and/or its
-// J x J accumulator (G^H G, G^H) in registers and walks the run's
-// visibilities alone, evaluating all 2J tap weights itself (Horner in the
-// per-tap polynomials, whose coefficients are kernel-parameter constants):
+// warp takes a set of 32 / H runs (sets w, 2W - 1 - w, 2W + w, ... for warp
+// w of W, which balances the length-sorted sets); the H lanes r, r + 32 / H,
+// ... own run r of the set, lane h of them rows [h RH, (h + 1) RH) of the
+// run's J x J patch (RH = ceil(J / H)): it holds those rows of the forward
+// grid X (G^H G, G) and/or of the accumulator (G^H G, G^H) in registers and
+// walks the run's visibilities. With H = 1 a lane evaluates all 2J tap
+// weights itself; with H = 2 the lane pair evaluates the J weights of one
+// axis each and swaps them with one shuffle per tap, and adds its partial
+// interpolation to its partner's with one more. Per visibility (Horner in
+// the per-tap polynomials, coefficients taken from the kernel parameters):
 //   G^H G: y = sum_b wy[b] sum_a wx[a] X[b][a];  acc[b][a] += wx[a] wy[b] y
 //   G^H  : y = yin[idx];                          acc[b][a] += wx[a] wy[b] y
 //   G    : yout[idx] = sum_b wy[b] sum_a wx[a] X[b][a]
-// with no exchange between lanes. One step of the warp reads 32 consecutive
-// records; padding records (past a lane's run) get zero weights. The
-// accumulators are flushed with vector reductions after the set.
+// One step of the warp reads 32 / H consecutive records, two steps ahead;
+// padding records (past a run's end) get zero weights. The accumulators are
+// flushed with vector reductions after the set.
 enum { LANE_GG = 0, LANE_GRID = 1, LANE_DEGRID = 2 };
 
-template <int J, int MODE>
-__global__ void __launch_bounds__(128)
+// Shared staging of the lane kernels: per warp two buffers (current and next
+// set) of each lane's RH x J patch of X, lane stride RH J + 1 complex values
+// (odd, so the 8-byte accesses of a half-warp fall on distinct banks).
+template <int J, int H> struct LaneStage {
+    static constexpr int RH = (J + H - 1) / H;
+    static constexpr int LS = RH * J + 1;
+    static constexpr size_t bytes_per_warp = 2 * 32 * LS * sizeof(float2);
+};
+
+__device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <int J, int MODE, int H>
+__global__ void __launch_bounds__(128, H == 2 ? 4 : 1)
 k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __restrict__ yout,
        const int2* __restrict__ set_info, const int2* __restrict__ run_cl, const float2* __restrict__ recs,
        const int* __restrict__ idx, int nsets, KbPoly kp, int Kx, int Ky, float2* __restrict__ out,
        const int* __restrict__ skip) {
-    constexpr int DEG = kb_poly_deg(J);
     constexpr bool HAS_X = MODE != LANE_GRID, HAS_ACC = MODE != LANE_DEGRID;
-    pdl_wait();
-    if (skip && *skip) return;
-    const int lane = threadIdx.x & 31;
-    const int W = gridDim.x * (blockDim.x >> 5), wg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    for (int it = 0;; ++it) {
-        const int set = it * W + ((it & 1) ? W - 1 - wg : wg);
-        if (set >= nsets) break;
-        const int2 si = set_info[set];
-        const int2 rc = run_cl[(size_t)set * 32 + lane];
-        const int cx = rc.x & 0xFFFF, cy = (int)((unsigned)rc.x >> 16), len = rc.y;
-        float xr[HAS_X ? J : 1][HAS_X ? J : 1], xi[HAS_X ? J : 1][HAS_X ? J : 1];
-        float ar[HAS_ACC ? J : 1][HAS_ACC ? J : 1], ai[HAS_ACC ? J : 1][HAS_ACC ? J : 1];
-        if constexpr (HAS_X) {
-#pragma unroll
-            for (int b = 0; b < J; ++b) {
-                float2 v[J];
-                if (len > 0) {
-                    ldg_row<J>(X + (size_t)((cy + b) & (Ky - 1)) * Kx, cx, Kx, v);
-                } else {
-#pragma unroll
-                    for (int a = 0; a < J; ++a) v[a] = make_float2(0.f, 0.f);
-                }
-#pragma unroll
-                for (int a = 0; a < J; ++a) {
-                    xr[b][a] = v[a].x;
-                    xi[b][a] = v[a].y;
-                }
-            }
-        }
-        if constexpr (HAS_ACC) {
-#pragma unroll
-            for (int b = 0; b < J; ++b)
-#pragma unroll
-                for (int a = 0; a < J; ++a) ar[b][a] = ai[b][a] = 0.f;
-        }
-        const size_t base = (size_t)si.x * 32 + lane;
-        const int lmax = si.y;
-        float2 rcur = lmax > 0 ? recs[base] : make_float2(0.f, 0.f);
-        int icur = (MODE != LANE_GG && lmax > 0) ? idx[base] : -1;
-        for (int k = 0; k < lmax; ++k) {
-            // the next step's record, one step ahead
-            float2 rnx = make_float2(0.f, 0.f);
-            int inx = -1;
-            if (k + 1 < lmax) {
-                rnx = recs[base + (size_t)(k + 1) * 32];
-                if (MODE != LANE_GG) inx = idx[base + (size_t)(k + 1) * 32];
-            }
-            const bool valid = k < len;
-            float wx[J], wy[J];
-            kb_weights<J>(kp, rcur.x, wx);
-            kb_weights<J>(kp, rcur.y, wy);
-            if (!valid) {
-#pragma unroll
-                for (int a = 0; a < J; ++a) wx[a] = 0.f;
-            }
-            float yr = 0.f, yi = 0.f;
-            if constexpr (HAS_X) {
-#pragma unroll
-                for (int b = 0; b < J; ++b) {
-                    float tr = 0.f, ti = 0.f;
-#pragma unroll
-                    for (int a = 0; a < J; ++a) {
-                        tr = fmaf(wx[a], xr[b][a], tr);
-                        ti = fmaf(wx[a], xi[b][a], ti);
-                    }
-                    yr = fmaf(wy[b], tr, yr);
-                    yi = fmaf(wy[b], ti, yi);
-                }
-            }
-            if constexpr (MODE == LANE_GRID) {
-                if (icur >= 0) {
-                    const float2 v = yin[icur];
-                    yr = v.x;
-                    yi = v.y;
-                }
-            }
-            if constexpr (MODE == LANE_DEGRID) {
-                if (valid && icur >= 0) yout[icur] = make_float2(yr, yi);
-            }
-            if constexpr (HAS_ACC) {
-#pragma unroll
-                for (int b = 0; b < J; ++b) {
-                    const float ur = wy[b] * yr, ui = wy[b] * yi;
-#pragma unroll
-                    for (int a = 0; a < J; ++a) {
-                        ar[b][a] = fmaf(wx[a], ur, ar[b][a]);
-                        ai[b][a] = fmaf(wx[a], ui, ai[b][a]);
-                    }
-                }
-            }
-            rcur = rnx;
-            icur = inx;
-        }
-        if constexpr (HAS_ACC) {
-            if (len > 0) {
-#pragma unroll
-                for (int b = 0; b < J; ++b) red_row<J>(out + (size_t)((cy + b) & (Ky - 1)) * Kx, cx, Kx, ar[b], ai[b]);
-            }
-        }
-    }
-    pdl_trigger();
-}
-
-// The lane-per-run kernels by grid tiles: a block owns one subproblem (a
-// grid tile and some of its runs). The tile plus its (J - 1) halo of the
-// forward grid X is copied to shared memory (G^H G, G) and an accumulator
-// tile of the same shape is cleared (G^H G, G^H); warp w takes the
-// subproblem's sets w, w + 4, ...; lane l reads its run's patch from the
-// shared X tile, walks the run as in k_lane, and adds its patch accumulator
-// to the shared tile with shared-memory atomics. The accumulator tile is
-// then added to the grid once, with coalesced reductions of its non-zero
-// cells.
-template <int J, int MODE>
-__global__ void __launch_bounds__(128)
-k_lane_tile(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __restrict__ yout,
-            const int4* __restrict__ sub_info, const int2* __restrict__ set_info, const int2* __restrict__ run_cl,
-            const float2* __restrict__ recs, const int* __restrict__ idx, int tile, int tiles_x, int S, KbPoly kp,
-            int Kx, int Ky, float2* __restrict__ out, const int* __restrict__ skip) {
-    constexpr bool HAS_X = MODE != LANE_GRID, HAS_ACC = MODE != LANE_DEGRID;
+    constexpr int WID = 32 / H, RH = LaneStage<J, H>::RH, LS = LaneStage<J, H>::LS;
     pdl_wait();
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int PT = tile + J - 1;
-    float2* sX = reinterpret_cast<float2*>(smem_raw);                 // [PT][S] (G^H G, G)
-    float2* sA = sX + (HAS_X ? (size_t)PT * S : 0);                  // [PT][S] (G^H G, G^H)
-    const int4 si4 = sub_info[blockIdx.x];
-    const int oy = (si4.x / tiles_x) * tile, ox = (si4.x % tiles_x) * tile;
-    for (int t = threadIdx.x; t < PT * PT; t += blockDim.x) {
-        const int r = t / PT, c = t - r * PT;
-        if (HAS_X) sX[r * S + c] = X[(size_t)((oy + r) & (Ky - 1)) * Kx + ((ox + c) & (Kx - 1))];
-        if (HAS_ACC) sA[r * S + c] = make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int set = si4.y + warp; set < si4.z; set += nwarps) {
-        const int2 si = set_info[set];
-        const int2 rc = run_cl[(size_t)set * 32 + lane];
-        const int len = rc.y;
-        const int lx = (rc.x & 0xFFFF) - ox, ly = (int)((unsigned)rc.x >> 16) - oy;
-        const int o0 = len > 0 ? ly * S + lx : 0;
-        float xr[HAS_X ? J : 1][HAS_X ? J : 1], xi[HAS_X ? J : 1][HAS_X ? J : 1];
-        float ar[HAS_ACC ? J : 1][HAS_ACC ? J : 1], ai[HAS_ACC ? J : 1][HAS_ACC ? J : 1];
-        if constexpr (HAS_X) {
+    const int lane = threadIdx.x & 31, r = lane % WID, h = lane / WID;
+    const int W = gridDim.x * (blockDim.x >> 5), wg = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    // this lane's two staging buffers
+    float2* stage = reinterpret_cast<float2*>(smem_raw) + ((size_t)(threadIdx.x >> 5) * 64 + lane) * LS;
+    auto buf = [&](int i) { return stage + (size_t)(i & 1) * 32 * LS; };
+    auto set_of = [&](int i) { return i * W + ((i & 1) ? W - 1 - wg : wg); };
+    // this lane's rows of a run's X patch into a staging buffer
+    auto patch_async = [&](int2 rcn, float2* dst) {
+        const int cx = rcn.x & 0xFFFF, cy = (int)((unsigned)rcn.x >> 16);
+        if (rcn.y <= 0) return;
 #pragma unroll
-            for (int b = 0; b < J; ++b)
+        for (int i = 0; i < RH; ++i) {
+            const int b = h * RH + i;
+            if (b < J) {
+                const float2* row = X + (size_t)((cy + b) & (Ky - 1)) * Kx;
+#pragma unroll
+                for (int a = 0; a < J; ++a) cp_async8(dst + i * J + a, row + ((cx + a) & (Kx - 1)));
+            }
+        }
+    };
+    int set = set_of(0);
+    int2 si = make_int2(0, 0), rc = make_int2(0, 0);
+    float2 f0 = make_float2(0.f, 0.f), f1 = make_float2(0.f, 0.f);
+    int i0 = -1, i1 = -1;
+    if (set < nsets) {
+        si = set_info[set];
+        rc = run_cl[(size_t)set * WID + r];
+        const size_t b0 = (size_t)si.x * WID + r;
+        f0 = recs[b0];
+        if (si.y > 1) f1 = recs[b0 + WID];
+        if (MODE != LANE_GG) {
+            i0 = idx[b0];
+            if (si.y > 1) i1 = idx[b0 + WID];
+        }
+        if constexpr (HAS_X) patch_async(rc, buf(0));
+    }
+    cp_async_commit();
+    for (int it = 0; set < nsets; ++it) {
+        const int nset = set_of(it + 1);
+        const bool has_next = nset < nsets;
+        int2 nsi = make_int2(0, 0), nrc = make_int2(0, 0);
+        if (has_next) {
+            nsi = set_info[nset];
+            nrc = run_cl[(size_t)nset * WID + r];
+        }
+        const int cx = rc.x & 0xFFFF, cy = (int)((unsigned)rc.x >> 16), len = rc.y;
+        float xr[HAS_X ? RH : 1][HAS_X ? J : 1], xi[HAS_X ? RH : 1][HAS_X ? J : 1];
+        float ar[HAS_ACC ? RH : 1][HAS_ACC ? J : 1], ai[HAS_ACC ? RH : 1][HAS_ACC ? J : 1];
+        if constexpr (HAS_X) {
+            cp_async_wait_all();
+            const float2* cur = buf(it);
+#pragma unroll
+            for (int i = 0; i < RH; ++i) {
+                const bool rowok = len > 0 && h * RH + i < J;
 #pragma unroll
                 for (int a = 0; a < J; ++a) {
-                    const float2 v = sX[o0 + b * S + a];
-                    xr[b][a] = v.x;
-                    xi[b][a] = v.y;
+                    const float2 v = rowok ? cur[i * J + a] : make_float2(0.f, 0.f);
+                    xr[i][a] = v.x;
+                    xi[i][a] = v.y;
                 }
+            }
         }
         if constexpr (HAS_ACC) {
 #pragma unroll
-            for (int b = 0; b < J; ++b)
+            for (int i = 0; i < RH; ++i)
 #pragma unroll
-                for (int a = 0; a < J; ++a) ar[b][a] = ai[b][a] = 0.f;
+                for (int a = 0; a < J; ++a) ar[i][a] = ai[i][a] = 0.f;
         }
-        const size_t base = (size_t)si.x * 32 + lane;
+        const size_t base = (size_t)si.x * WID + r;
         const int lmax = si.y;
-        float2 rcur = lmax > 0 ? recs[base] : make_float2(0.f, 0.f);
-        int icur = (MODE != LANE_GG && lmax > 0) ? idx[base] : -1;
+        float2 rc0 = f0, rc1 = f1;
+        int ic0 = i0, ic1 = i1;
+        float2 yv0 = make_float2(0.f, 0.f);   // gridding: this step's value, one step ahead
+        if (MODE == LANE_GRID && ic0 >= 0) yv0 = yin[ic0];
+        float2 nf0 = make_float2(0.f, 0.f), nf1 = make_float2(0.f, 0.f);
+        int ni0 = -1, ni1 = -1;
+        bool issued = false;
         for (int k = 0; k < lmax; ++k) {
-            float2 rnx = make_float2(0.f, 0.f);
-            int inx = -1;
-            if (k + 1 < lmax) {
-                rnx = recs[base + (size_t)(k + 1) * 32];
-                if (MODE != LANE_GG) inx = idx[base + (size_t)(k + 1) * 32];
+            // records two steps ahead, the gridding value one step ahead
+            float2 rc2 = make_float2(0.f, 0.f);
+            int ic2 = -1;
+            if (k + 2 < lmax) {
+                rc2 = recs[base + (size_t)(k + 2) * WID];
+                if (MODE != LANE_GG) ic2 = idx[base + (size_t)(k + 2) * WID];
             }
+            float2 yv1 = make_float2(0.f, 0.f);
+            if (MODE == LANE_GRID && ic1 >= 0) yv1 = yin[ic1];
             const bool valid = k < len;
-            float wx[J], wy[J];
-            kb_weights<J>(kp, rcur.x, wx);
-            kb_weights<J>(kp, rcur.y, wy);
+            float wx[J], wy[RH];
+            if constexpr (H == 1) {
+                kb_weights<J>(kp, rc0.x, wx);
+                kb_weights<J>(kp, rc0.y, wy);
+            } else {
+                // this lane's axis, then the partner's by shuffle
+                float own[J], oth[J];
+                kb_weights<J>(kp, h ? rc0.y : rc0.x, own);
+#pragma unroll
+                for (int a = 0; a < J; ++a) oth[a] = __shfl_xor_sync(0xffffffffu, own[a], WID);
+#pragma unroll
+                for (int a = 0; a < J; ++a) wx[a] = h ? oth[a] : own[a];
+#pragma unroll
+                for (int i = 0; i < RH; ++i) {
+                    const float w0 = oth[i];                                              // row i (h = 0)
+                    const float w1 = RH + i < J ? own[RH + i < J ? RH + i : 0] : 0.f;   // row RH + i (h = 1)
+                    wy[i] = h ? w1 : w0;
+                }
+            }
             if (!valid) {
 #pragma unroll
                 for (int a = 0; a < J; ++a) wx[a] = 0.f;
@@ -1064,62 +1021,90 @@ k_lane_tile(const float2* __restrict__ X, const float2* __restrict__ yin, float2
             float yr = 0.f, yi = 0.f;
             if constexpr (HAS_X) {
 #pragma unroll
-                for (int b = 0; b < J; ++b) {
+                for (int i = 0; i < RH; ++i) {
                     float tr = 0.f, ti = 0.f;
 #pragma unroll
                     for (int a = 0; a < J; ++a) {
-                        tr = fmaf(wx[a], xr[b][a], tr);
-                        ti = fmaf(wx[a], xi[b][a], ti);
+                        tr = fmaf(wx[a], xr[i][a], tr);
+                        ti = fmaf(wx[a], xi[i][a], ti);
                     }
-                    yr = fmaf(wy[b], tr, yr);
-                    yi = fmaf(wy[b], ti, yi);
+                    yr = fmaf(wy[i], tr, yr);
+                    yi = fmaf(wy[i], ti, yi);
+                }
+                if constexpr (H == 2) {
+                    // rows of the pair in order: the h = 0 half first
+                    const float pr = __shfl_xor_sync(0xffffffffu, yr, WID);
+                    const float pi = __shfl_xor_sync(0xffffffffu, yi, WID);
+                    yr = h ? pr + yr : yr + pr;
+                    yi = h ? pi + yi : yi + pi;
                 }
             }
             if constexpr (MODE == LANE_GRID) {
-                if (icur >= 0) {
-                    const float2 v = yin[icur];
-                    yr = v.x;
-                    yi = v.y;
-                }
+                yr = yv0.x;
+                yi = yv0.y;
             }
             if constexpr (MODE == LANE_DEGRID) {
-                if (valid && icur >= 0) yout[icur] = make_float2(yr, yi);
+                if (valid && ic0 >= 0 && h == 0) yout[ic0] = make_float2(yr, yi);
             }
             if constexpr (HAS_ACC) {
 #pragma unroll
-                for (int b = 0; b < J; ++b) {
-                    const float ur = wy[b] * yr, ui = wy[b] * yi;
+                for (int i = 0; i < RH; ++i) {
+                    const float ur = wy[i] * yr, ui = wy[i] * yi;
 #pragma unroll
                     for (int a = 0; a < J; ++a) {
-                        ar[b][a] = fmaf(wx[a], ur, ar[b][a]);
-                        ai[b][a] = fmaf(wx[a], ui, ai[b][a]);
+                        ar[i][a] = fmaf(wx[a], ur, ar[i][a]);
+                        ai[i][a] = fmaf(wx[a], ui, ai[i][a]);
                     }
                 }
             }
-            rcur = rnx;
-            icur = inx;
+            if (k == 0 && has_next) {
+                // the next set's patch and first records, behind this set's work
+                if constexpr (HAS_X) patch_async(nrc, buf(it + 1));
+                cp_async_commit();
+                const size_t nb = (size_t)nsi.x * WID + r;
+                nf0 = recs[nb];
+                if (nsi.y > 1) nf1 = recs[nb + WID];
+                if (MODE != LANE_GG) {
+                    ni0 = idx[nb];
+                    if (nsi.y > 1) ni1 = idx[nb + WID];
+                }
+                issued = true;
+            }
+            rc0 = rc1;
+            rc1 = rc2;
+            ic0 = ic1;
+            ic1 = ic2;
+            yv0 = yv1;
+        }
+        if (has_next && !issued) {
+            if constexpr (HAS_X) patch_async(nrc, buf(it + 1));
+            cp_async_commit();
+            const size_t nb = (size_t)nsi.x * WID + r;
+            nf0 = recs[nb];
+            if (nsi.y > 1) nf1 = recs[nb + WID];
+            if (MODE != LANE_GG) {
+                ni0 = idx[nb];
+                if (nsi.y > 1) ni1 = idx[nb + WID];
+            }
         }
         if constexpr (HAS_ACC) {
             if (len > 0) {
 #pragma unroll
-                for (int b = 0; b < J; ++b)
-#pragma unroll
-                    for (int a = 0; a < J; ++a) {
-                        atomicAdd(&sA[o0 + b * S + a].x, ar[b][a]);
-                        atomicAdd(&sA[o0 + b * S + a].y, ai[b][a]);
-                    }
+                for (int i = 0; i < RH; ++i) {
+                    const int b = h * RH + i;
+                    if (b < J) red_row<J>(out + (size_t)((cy + b) & (Ky - 1)) * Kx, cx, Kx, ar[i], ai[i]);
+                }
             }
         }
+        set = nset;
+        si = nsi;
+        rc = nrc;
+        f0 = nf0;
+        f1 = nf1;
+        i0 = ni0;
+        i1 = ni1;
     }
-    if constexpr (HAS_ACC) {
-        __syncthreads();
-        for (int t = threadIdx.x; t < PT * PT; t += blockDim.x) {
-            const int r = t / PT, c = t - r * PT;
-            const float2 v = sA[r * S + c];
-            if (v.x != 0.f || v.y != 0.f)
-                atomicAdd(out + (size_t)((oy + r) & (Ky - 1)) * Kx + ((ox + c) & (Kx - 1)), v);
-        }
-    }
+    cp_async_wait_all();
     pdl_trigger();
 }
 
@@ -1395,16 +1380,22 @@ static void grid_sets_tj(purify_plan* p, const void* y, bool caller_order, const
         p->beta, 1.0 / p->i0beta, p->Kx, p->Ky, p->gacc.as<C>(), skip);
     L.done();
 }
-// Lane-per-run launches: a persistent grid of 4-warp blocks (as many as are
-// resident at once, or fewer when there is less work).
-template <int J, int MODE>
-static void lane_tj(purify_plan* p, const void* yin, void* yout, bool caller_order, const int* skip, bool zeroed) {
+// Lane-per-run launches (kind 3: one lane per run, 4: two lanes per run,
+// 5: two lanes per run with the sets grouped by grid tile): a persistent
+// grid of 4-warp blocks (as many as are resident at once, or fewer when
+// there is less work).
+static const LaneWork& lane_work(const purify_plan* p, int kind) { return p->lanes[kind - 3]; }
+template <int J, int MODE, int H>
+static void lane_tj(purify_plan* p, int kind, const void* yin, void* yout, bool caller_order, const int* skip,
+                    bool zeroed) {
     if (MODE != LANE_DEGRID && !zeroed) PURIFY_CUDA(cudaMemsetAsync(p->gacc.p, 0, p->gacc.bytes, p->stream));
-    const LaneWork& lw = p->lanes;
+    const LaneWork& lw = lane_work(p, kind);
     if (lw.nsets == 0) return;
+    const size_t lane_smem = 4 * LaneStage<J, H>::bytes_per_warp;
     static int per_sm = 0;   // resident blocks per SM of this instantiation
     if (per_sm == 0) {
-        PURIFY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lane<J, MODE>, 128, 0));
+        set_smem(k_lane<J, MODE, H>, lane_smem);
+        PURIFY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lane<J, MODE, H>, 128, lane_smem));
         per_sm = std::max(1, per_sm);
     }
     int sms = 0, dev = 0;
@@ -1412,34 +1403,17 @@ static void lane_tj(purify_plan* p, const void* yin, void* yout, bool caller_ord
     PURIFY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int blocks = std::max(1, std::min(sms * per_sm, (lw.nsets + 3) / 4));
     Launch L(p, MODE == LANE_GG ? "normal_gg" : (MODE == LANE_GRID ? "grid" : "degrid"));
-    launch_dependent(k_lane<J, MODE>, blocks, 128, 0, p->stream, p->grid.as<float2>(), (const float2*)yin,
+    launch_dependent(k_lane<J, MODE, H>, blocks, 128, lane_smem, p->stream, p->grid.as<float2>(), (const float2*)yin,
                      (float2*)yout, lw.set_info.as<int2>(), lw.run_cl.as<int2>(), lw.rec.as<float2>(),
                      caller_order ? lw.idx_caller.as<int>() : lw.idx.as<int>(), lw.nsets, p->kbp, p->Kx, p->Ky,
                      p->gacc.as<float2>(), skip);
     L.done();
 }
-// By tiles: one block per subproblem.
-template <int J, int MODE>
-static void lane_tile_tj(purify_plan* p, const void* yin, void* yout, bool caller_order, const int* skip,
-                         bool zeroed) {
-    if (MODE != LANE_DEGRID && !zeroed) PURIFY_CUDA(cudaMemsetAsync(p->gacc.p, 0, p->gacc.bytes, p->stream));
-    const LaneWork& lw = p->lanet;
-    if (lw.nsub == 0) return;
-    const int PT = lw.tile + J - 1, S = PT | 1;
-    const size_t sm = sizeof(float2) * (size_t)PT * S * (MODE == LANE_GG ? 2 : 1);
-    set_smem(k_lane_tile<J, MODE>, sm);
-    Launch L(p, MODE == LANE_GG ? "normal_gg" : (MODE == LANE_GRID ? "grid" : "degrid"));
-    launch_dependent(k_lane_tile<J, MODE>, lw.nsub, 128, sm, p->stream, p->grid.as<float2>(), (const float2*)yin,
-                     (float2*)yout, lw.sub_info.as<int4>(), lw.set_info.as<int2>(), lw.run_cl.as<int2>(),
-                     lw.rec.as<float2>(), caller_order ? lw.idx_caller.as<int>() : lw.idx.as<int>(), lw.tile,
-                     lw.tiles_x, S, p->kbp, p->Kx, p->Ky, p->gacc.as<float2>(), skip);
-    L.done();
-}
 template <int J, int MODE>
 static void lane_any(purify_plan* p, int kind, const void* yin, void* yout, bool c, const int* s, bool z) {
     if constexpr (J <= kLaneMaxJ) {
-        if (kind == 4) lane_tile_tj<J, MODE>(p, yin, yout, c, s, z);
-        else lane_tj<J, MODE>(p, yin, yout, c, s, z);
+        if (kind == 3) lane_tj<J, MODE, 1>(p, kind, yin, yout, c, s, z);
+        else lane_tj<J, MODE, 2>(p, kind, yin, yout, c, s, z);
     }
 }
 template <int J> static void lane_gg(purify_plan* p, int kind, const int* s, bool z) {
@@ -1457,7 +1431,11 @@ template <int J> static void normal_d(purify_plan* p, const int* s, bool z) { gr
 template <int J> static void gsets_f(purify_plan* p, const void* y, bool c, const int* s, bool z) { grid_sets_tj<float, J, false>(p, y, c, s, z); }
 template <int J> static void gsets_d(purify_plan* p, const void* y, bool c, const int* s, bool z) { grid_sets_tj<double, J, false>(p, y, c, s, z); }
 
-bool lane_work_ok(const purify_plan* p) { return p->dtype == PURIFY_F32 && p->J <= kLaneMaxJ && p->lanes.nsets > 0; }
+bool lane_work_ok(const purify_plan* p) { return p->dtype == PURIFY_F32 && p->J <= kLaneMaxJ; }
+static void require_lane_work(const purify_plan* p, int kind) {
+    if (!lane_work_ok(p) || kind < 3 || kind > 5 || lane_work(p, kind).nsets == 0)
+        throw Error{PURIFY_EINVAL, "lane-per-run kernels need an FP32 plan with J <= 6 built for that form"};
+}
 
 void launch_normal_gg(purify_plan* p, const int* skip, bool zeroed) {
     if (p->normal_kind >= 3 && lane_work_ok(p)) { PURIFY_J_DISPATCH(p->J, lane_gg, p, p->normal_kind, skip, zeroed); }
@@ -1465,11 +1443,11 @@ void launch_normal_gg(purify_plan* p, const int* skip, bool zeroed) {
     else { PURIFY_J_DISPATCH(p->J, normal_d, p, skip, zeroed); }
 }
 void launch_grid_lanes(purify_plan* p, int kind, const void* y, bool caller_order, const int* skip, bool zeroed) {
-    if (!lane_work_ok(p)) throw Error{PURIFY_EINVAL, "lane-per-run gridding needs an FP32 plan with J <= 6"};
+    require_lane_work(p, kind);
     PURIFY_J_DISPATCH(p->J, lane_grid, p, kind, y, caller_order, skip, zeroed);
 }
 void launch_degrid_lanes(purify_plan* p, int kind, void* y, bool caller_order, const int* skip) {
-    if (!lane_work_ok(p)) throw Error{PURIFY_EINVAL, "lane-per-run degridding needs an FP32 plan with J <= 6"};
+    require_lane_work(p, kind);
     PURIFY_J_DISPATCH(p->J, lane_degrid, p, kind, y, caller_order, skip);
 }
 void launch_normal_lanes(purify_plan* p, int kind, const int* skip, bool zeroed) {
@@ -1478,6 +1456,7 @@ void launch_normal_lanes(purify_plan* p, int kind, const int* skip, bool zeroed)
         else { PURIFY_J_DISPATCH(p->J, normal_d, p, skip, zeroed); }
         return;
     }
+    require_lane_work(p, kind);
     PURIFY_J_DISPATCH(p->J, lane_gg, p, kind, skip, zeroed);
 }
 void launch_grid_sets(purify_plan* p, const void* y, bool caller_order, const int* skip, bool zeroed) {

@@ -176,7 +176,7 @@ struct TuneKey {
         return std::tie(nx, ny, J, dtype, mlog, R, gm) < std::tie(o.nx, o.ny, o.J, o.dtype, o.mlog, o.R, o.gm);
     }
 };
-struct TuneVal { int tile, dtile, rb, cb, units, dunits, gkind, dkind, nkind, ltile; };
+struct TuneVal { int tile, dtile, rb, cb, units, dunits, gkind, dkind, nkind; };
 static std::mutex g_tune_mutex;
 static std::map<TuneKey, TuneVal> g_tune_cache;
 
@@ -233,9 +233,9 @@ static float time_ms(purify_plan* p, const std::function<void()>& f, int reps) {
     return best;
 }
 
-template <typename T, typename BinsFor, typename LaneTiles>
+template <typename T, typename BinsFor>
 static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_for,
-                     const std::vector<int>& cell_order, bool tune, LaneTiles lane_tiles) {
+                     const std::vector<int>& cell_order, bool tune) {
     using C = typename cplx_of<T>::type;
     int mlog = 0;
     while ((int64_t(1) << (mlog + 1)) <= p->M) ++mlog;
@@ -244,7 +244,7 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
     // visibilities, in batch units
     const int64_t unit = grid_list_unit(p->dtype, p->J);
     const int u0 = (int)std::max<int64_t>(1, std::min<int64_t>(16, (p->M / (152 * 4) + unit / 2) / unit));
-    TuneVal val{p->work.tile, p->work.tile, 0, 0, u0, u0, 1, 1, 2, 32};
+    TuneVal val{p->work.tile, p->work.tile, 0, 0, u0, u0, 1, 1, 2};
     bool cached = false;
     if (tune) {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
@@ -304,27 +304,14 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
                 if (mr < bg) { bg = mr; val.gkind = 2; }
                 float bn = time_ms(p, [&] { launch_normal_lanes(p, 2, nullptr); }, 5);
                 if (lane_work_ok(p)) {
-                    auto try_kind = [&](int kind) {
+                    for (int kind = 3; kind <= 5; ++kind) {
                         const float mn = time_ms(p, [&] { launch_normal_lanes(p, kind, nullptr); }, 5);
                         const float ml = time_ms(p, [&] { launch_grid_lanes(p, kind, yv, false, nullptr); }, 5);
                         const float mdl = time_ms(p, [&] { launch_degrid_lanes(p, kind, yv, false, nullptr); }, 5);
-                        const bool better = mn < bn;
-                        if (better) { bn = mn; val.nkind = kind; }
+                        if (mn < bn) { bn = mn; val.nkind = kind; }
                         if (ml < bg) { bg = ml; val.gkind = kind; }
                         if (mdl < bd) { bd = mdl; val.dkind = kind; }
-                        return better;
-                    };
-                    try_kind(3);
-                    // the lane tile is the normal operator's best (it dominates the solver)
-                    float bt = 1e30f;
-                    for (int t : {16, 32, 64}) {
-                        if (t > std::min(p->Kx, p->Ky)) continue;
-                        lane_tiles(t);
-                        const float mn = time_ms(p, [&] { launch_normal_lanes(p, 4, nullptr); }, 5);
-                        if (mn < bt) { bt = mn; val.ltile = t; }
                     }
-                    lane_tiles(val.ltile);
-                    try_kind(4);
                 }
             }
         }
@@ -334,107 +321,70 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
     p->fft_rb = val.rb;
     p->fft_cb = val.cb;
     // a forced decomposition: grid_mode 1 and 2 degrid by tiles and apply
-    // G^H G by run sets, 3 and 4 do all three by lanes (4: by tiles)
+    // G^H G by run sets, 3..5 do all three by that lane form
     const int gm = p->desc.grid_mode;
     p->grid_kind = gm == 0 ? val.gkind : gm;
     p->degrid_kind = gm == 0 ? val.dkind : (gm >= 3 ? gm : 1);
     p->normal_kind = gm == 0 ? val.nkind : (gm >= 3 ? gm : 2);
-    if (lane_work_ok(p))
-        lane_tiles(std::min(gm == 4 && p->desc.tile > 0 ? p->desc.tile : val.ltile, std::min(p->Kx, p->Ky)));
     build_gridlist(p, bins_for(val.tile), cell_order, val.tile, val.units, p->work);
     build_gridlist(p, bins_for(val.dtile), cell_order, val.dtile, val.dunits, p->dwork);
 }
 
-// Lane-per-run work (see LaneWork) from the length-sorted runs: 32 runs per
-// set, each set padded to its longest run; with tile > 0 the runs of each
-// grid tile (in length order) are cut into subproblems of at most
-// kLaneSubSets sets or kLaneSubVis visibilities.
-static const int kLaneSubSets = 8, kLaneSubVis = 4096;
+// Lane-per-run work (see LaneWork) from the length-sorted runs: `width`
+// runs per set, each set padded to its longest run; with tile > 0 the runs
+// are grouped by grid tile first (stable, so by length within a tile).
 struct HostRun { int cell; int64_t first; int len; };
 template <typename Rec>
 static void build_lanework(purify_plan* p, const std::vector<HostRun>& runs, const std::vector<Rec>& rec,
-                           const std::vector<int>& start, const std::vector<int>& perm, int tile, LaneWork& w) {
+                           const std::vector<int>& start, const std::vector<int>& perm, int width, int tile,
+                           LaneWork& w) {
     const size_t nr = runs.size();
-    // run groups: the whole list, or one list per subproblem
-    std::vector<std::vector<int>> groups;
-    std::vector<int> gbin;
-    if (tile == 0) {
-        groups.emplace_back(nr);
-        std::iota(groups[0].begin(), groups[0].end(), 0);
-        gbin.push_back(0);
-    } else {
-        const int tx = p->Kx / tile, ty = p->Ky / tile;
-        std::vector<std::vector<int>> per_bin((size_t)tx * ty);
-        for (size_t r = 0; r < nr; ++r) {
+    std::vector<int> order(nr);
+    std::iota(order.begin(), order.end(), 0);
+    if (tile > 0) {
+        const int tx = p->Kx / tile;
+        auto bin = [&](int r) {
             const int cx = runs[r].cell & 0xFFFF, cy = runs[r].cell >> 16;
-            per_bin[(size_t)(cy / tile) * tx + cx / tile].push_back((int)r);
-        }
-        struct G { int bin; std::vector<int> r; int64_t vis; };
-        std::vector<G> gs;
-        for (size_t b = 0; b < per_bin.size(); ++b) {
-            const std::vector<int>& lst = per_bin[b];
-            size_t i = 0;
-            while (i < lst.size()) {
-                G g{(int)b, {}, 0};
-                while (i < lst.size() && (int)g.r.size() < 32 * kLaneSubSets &&
-                       (g.r.empty() || g.vis + runs[lst[i]].len <= kLaneSubVis)) {
-                    g.vis += runs[lst[i]].len;
-                    g.r.push_back(lst[i++]);
-                }
-                gs.push_back(std::move(g));
-            }
-        }
-        std::stable_sort(gs.begin(), gs.end(), [](const G& a, const G& b) { return a.vis > b.vis; });
-        for (G& g : gs) {
-            gbin.push_back(g.bin);
-            groups.push_back(std::move(g.r));
-        }
+            return (cy / tile) * tx + cx / tile;
+        };
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return bin(a) < bin(b); });
     }
-    std::vector<int4> sub_info;
-    std::vector<int2> set_info, run_cl;
-    std::vector<int> set_run;   // run of each (set, lane) slot, -1 padding
+    const int nsets = (int)((nr + width - 1) / width);
+    std::vector<int2> set_info(nsets), run_cl((size_t)nsets * width, make_int2(0, 0));
     int64_t rows = 0;
-    for (size_t gi = 0; gi < groups.size(); ++gi) {
-        const std::vector<int>& g = groups[gi];
-        const int set0 = (int)set_info.size();
-        int64_t vis = 0;
-        for (size_t i = 0; i < g.size(); i += 32) {
-            int lmax = 0;
-            for (size_t l = 0; l < 32; ++l) {
-                const int r = i + l < g.size() ? g[i + l] : -1;
-                set_run.push_back(r);
-                run_cl.push_back(r >= 0 ? make_int2(runs[r].cell, runs[r].len) : make_int2(0, 0));
-                if (r >= 0) {
-                    lmax = std::max(lmax, runs[r].len);
-                    vis += runs[r].len;
-                }
+    for (int s = 0; s < nsets; ++s) {
+        int lmax = 0;
+        for (int l = 0; l < width; ++l) {
+            const size_t q = (size_t)s * width + l;
+            if (q < nr) {
+                const HostRun& hr = runs[order[q]];
+                run_cl[q] = make_int2(hr.cell, hr.len);
+                lmax = std::max(lmax, hr.len);
             }
-            set_info.push_back(make_int2((int)rows, lmax));
-            rows += lmax;
         }
-        sub_info.push_back(make_int4(gbin[gi], set0, (int)set_info.size(), (int)vis));
+        set_info[s] = make_int2((int)rows, lmax);
+        rows += lmax;
     }
-    PURIFY_REQUIRE(rows * 32 < ((int64_t)1 << 31), "too many visibility records for the lane work");
-    std::vector<float2> lrec((size_t)rows * 32, make_float2(0.f, 0.f));
-    std::vector<int> lidx((size_t)rows * 32, -1), lcal((size_t)rows * 32, -1);
-    for (size_t s = 0; s < set_info.size(); ++s)
-        for (int l = 0; l < 32; ++l) {
-            const int r = set_run[s * 32 + l];
-            if (r < 0) continue;
+    PURIFY_REQUIRE(rows * width < ((int64_t)1 << 31), "too many visibility records for the lane work");
+    std::vector<float2> lrec((size_t)rows * width, make_float2(0.f, 0.f));
+    std::vector<int> lidx((size_t)rows * width, -1), lcal((size_t)rows * width, -1);
+    for (int s = 0; s < nsets; ++s)
+        for (int l = 0; l < width; ++l) {
+            const size_t q0 = (size_t)s * width + l;
+            if (q0 >= nr) continue;
+            const int r = order[q0];
             for (int k = 0; k < runs[r].len; ++k) {
                 const Rec& e = rec[start[r] + k];
-                const size_t q = ((size_t)set_info[s].x + k) * 32 + l;
+                const size_t q = ((size_t)set_info[s].x + k) * width + l;
                 lrec[q] = make_float2((float)e.phx, (float)e.phy);
                 lidx[q] = e.m;
                 lcal[q] = perm[e.m];
             }
         }
-    w.nsets = (int)set_info.size();
-    w.nsub = tile > 0 ? (int)sub_info.size() : 0;
+    w.nsets = nsets;
+    w.width = width;
     w.tile = tile;
-    w.tiles_x = tile > 0 ? p->Kx / tile : 0;
     w.rows = rows;
-    if (tile > 0) upload(w.sub_info, sub_info);
     upload(w.set_info, set_info);
     upload(w.run_cl, run_cl);
     upload(w.rec, lrec);
@@ -446,13 +396,8 @@ static void build_lanework(purify_plan* p, const std::vector<HostRun>& runs, con
 // order, cut at kRunMax visibilities, sorted by length (longest first,
 // stable), padded to a multiple of G; records in run order.
 static const int kRunMax = 48;
-template <typename T> struct RunHost {
-    std::vector<HostRun> runs;
-    std::vector<typename RunRecOf<T>::type> rec;
-    std::vector<int> start;
-};
 template <typename T>
-static RunHost<T> build_runwork(purify_plan* p, const std::vector<T>& us, const std::vector<T>& vs,
+static void build_runwork(purify_plan* p, const std::vector<T>& us, const std::vector<T>& vs,
                                 const std::vector<int>& scx, const std::vector<int>& scy,
                                 const std::vector<int>& cell_order, const std::vector<int>& perm) {
     using Rec = typename RunRecOf<T>::type;
@@ -487,7 +432,11 @@ static RunHost<T> build_runwork(purify_plan* p, const std::vector<T>& us, const 
             rec[q++] = e;
         }
     }
-    if (sizeof(T) == 4 && p->J <= kLaneMaxJ) build_lanework(p, runs, rec, start, perm, 0, p->lanes);
+    if (sizeof(T) == 4 && p->J <= kLaneMaxJ) {
+        build_lanework(p, runs, rec, start, perm, 32, 0, p->lanes[0]);
+        build_lanework(p, runs, rec, start, perm, 16, 0, p->lanes[1]);
+        build_lanework(p, runs, rec, start, perm, 16, std::min(32, std::min(p->Kx, p->Ky)), p->lanes[2]);
+    }
     p->runs.G = G;
     p->runs.nruns = (int)nr;
     p->runs.nsets = (int)(nr / G);
@@ -496,16 +445,10 @@ static RunHost<T> build_runwork(purify_plan* p, const std::vector<T>& us, const 
     upload(p->runs.start, start);
     upload(p->runs.len, len);
     p->workspace_bytes += (int64_t)(p->runs.rec.bytes + p->runs.cell.bytes + p->runs.start.bytes + p->runs.len.bytes);
-    RunHost<T> h;
-    h.runs = std::move(runs);
-    h.rec = std::move(rec);
-    h.start = std::move(start);
-    return h;
 }
 
 static int64_t lane_bytes(const LaneWork& w) {
-    return (int64_t)(w.sub_info.bytes + w.set_info.bytes + w.run_cl.bytes + w.rec.bytes + w.idx.bytes +
-                     w.idx_caller.bytes);
+    return (int64_t)(w.set_info.bytes + w.run_cl.bytes + w.rec.bytes + w.idx.bytes + w.idx_caller.bytes);
 }
 
 template <typename T> static void finish_plan(purify_plan* p) {
@@ -597,13 +540,12 @@ template <typename T> static void finish_plan(purify_plan* p) {
         for (int64_t c = 0; c < ncell; ++c) pos[c + 1] += pos[c];
         for (int64_t i = 0; i < p->M; ++i) cell_order[pos[(int64_t)scy[i] * p->Kx + scx[i]]++] = (int)i;
     }
-    RunHost<T> rh = build_runwork<T>(p, us, vs, scx, scy, cell_order, perm);
-    auto lane_tiles = [&](int t) {
-        if (sizeof(T) == 4 && p->J <= kLaneMaxJ && p->lanet.tile != t)
-            build_lanework(p, rh.runs, rh.rec, rh.start, perm, t, p->lanet);
-    };
-    autotune<T>(p, cand, bins_for, cell_order, d.tile == 0, lane_tiles);
-    p->workspace_bytes += lane_bytes(p->lanes) + lane_bytes(p->lanet);
+    build_runwork<T>(p, us, vs, scx, scy, cell_order, perm);
+    autotune<T>(p, cand, bins_for, cell_order, d.tile == 0);
+    // keep only the lane work in use
+    for (int k = 3; k <= 5; ++k)
+        if (p->grid_kind != k && p->degrid_kind != k && p->normal_kind != k) p->lanes[k - 3].release();
+    for (int k = 0; k < 3; ++k) p->workspace_bytes += lane_bytes(p->lanes[k]);
 }
 
 purify_plan* create_plan(const purify_plan_desc* d) {
@@ -627,9 +569,9 @@ purify_plan* create_plan(const purify_plan_desc* d) {
                        Ky <= 8192 && Kx > d->nx && Ky > d->ny,
                    "oversample must make K = alpha n a power of two above n (at most 8192)");
     PURIFY_REQUIRE(d->tile == 0 || (is_pow2(d->tile) && d->tile >= 8 && d->tile <= 64), "tile must be 0 or a power of two in [8, 64]");
-    PURIFY_REQUIRE(d->grid_mode >= 0 && d->grid_mode <= 4, "grid_mode must be 0, 1, 2, 3 or 4");
+    PURIFY_REQUIRE(d->grid_mode >= 0 && d->grid_mode <= 5, "grid_mode must be in 0..5");
     PURIFY_REQUIRE(d->grid_mode < 3 || (d->dtype == PURIFY_F32 && d->kb_width <= kLaneMaxJ),
-                   "grid_mode 3 or 4 (lanes) needs an FP32 plan with kb_width <= 6");
+                   "grid_mode 3..5 (lanes) needs an FP32 plan with kb_width <= 6");
     std::vector<int64_t> offs;
     if (d->block_offsets) {
         offs.assign(d->block_offsets, d->block_offsets + d->R + 1);
