@@ -832,6 +832,10 @@ def run_profile_op(args):
     if args.profile_op == "iteration":
         xs = torch.zeros_like(x)
         pk.purify_sdmm_solve(plan, y, eps, xs, max_iter=0, cg_iters=args.cg_iters, nu=1.0, gamma=1e-4)
+    torch.cuda.synchronize(dev)
+    # the profiled range (ncu --profile-from-start off): the W + K calls only,
+    # not the plan's autotuning or the solver's set-up
+    torch.cuda.profiler.start()
     t0 = time.perf_counter()
     for k in range(args.warmup + args.steps):
         if args.profile_op == "phi":
@@ -847,6 +851,7 @@ def run_profile_op(args):
         else:
             pk.purify_sdmm_iterate(plan, 1)
     torch.cuda.synchronize(dev)
+    torch.cuda.profiler.stop()
     print(json.dumps({"profile_op": args.profile_op, "calls": args.warmup + args.steps,
                       "wall_s": time.perf_counter() - t0, "launches": pk.purify_launch_count()}))
 

@@ -215,16 +215,16 @@ namespace purify {
 // Conjugate gradients in the Chronopoulos-Gear arrangement (equal to the
 // textbook iteration in exact arithmetic; one synchronisation per step): the
 // operator is applied to the residual, u = A r, and the inverse row pass of
-// step k writes per-block partials of gamma = r.r and delta = r.u. The
-// forward row pass of step k + 1 (or the relative-change kernel after the
-// last step) reduces them in every block (cg_step_scalars), to
+// step k writes per-block partials of gamma = r.r and delta = r.u; its last
+// block to finish reduces them (cg_decide) to
 //   beta = gamma / gamma_prev (0 at step 0),
 //   alpha = gamma / (delta - beta gamma / alpha_prev)  (gamma / delta at step 0),
-// and unless gamma meets the stop test (gamma <= tol^2 gamma_0, gamma_0 of
-// step 0) applies the update p = r + beta p, s = u + beta s (s = A p),
-// x += alpha p, r -= alpha s, then transforms the new r. The forward row pass
-// of step 0 starts the solve: r += add (the residual's terms formed outside
-// the pass), p = s = 0, the stop flag cleared.
+// and the stop test (gamma <= tol^2 gamma_0, gamma_0 of step 0). Unless the
+// step stopped the solve, the forward row pass of step k + 1 (or the
+// relative-change kernel after the last step) applies the update p = r + beta p,
+// s = u + beta s (s = A p), x += alpha p, r -= alpha s, then transforms the
+// new r. The forward row pass of step 0 starts the solve: r += add (the
+// residual's terms formed outside the pass), p = s = 0, the stop flag cleared.
 struct CgFold {
     void* x = nullptr;           // iterate [N]
     void* r = nullptr;           // residual [N]
@@ -232,8 +232,8 @@ struct CgFold {
     void* s = nullptr;           // A p [N]
     const void* u = nullptr;     // A r [N]
     const void* add = nullptr;   // added to r at step 0 (may be null)
-    const double* part = nullptr;   // the inverse row pass's partials, 2 per block
-    int nparts = 0;              // blocks of the inverse row pass
+    double* part = nullptr;      // the inverse row pass's partials, 2 per block
+    unsigned* counter = nullptr; // arrival counter of the inverse row pass
     double* scal = nullptr;
     int* flags = nullptr;
     int step = 0;
@@ -271,10 +271,11 @@ void launch_cols_inv(purify_plan* p, const int* skip_flag, const void* mult = nu
 void launch_normal_gg(purify_plan* p, const int* skip_flag, bool zeroed = false);
 // G^H by runs (same output as launch_grid)
 void launch_grid_sets(purify_plan* p, const void* y, bool caller_order, const int* skip_flag, bool zeroed = false);
-// dot_part: a CG step (out = A r, add = r): per-block partials of r.r and
-// r.A r, 2 per block (see CgFold)
+// cg: a CG step (out = A r, add = r): per-block partials of r.r and r.A r
+// (2 per block, in cg->part), reduced and decided by the last block (see
+// CgFold); cg->step is the step
 void launch_rows_inv_crop(purify_plan* p, void* out, double scale, int out_mode, const void* add,
-                          double add_coef, const int* skip_flag, double* dot_part = nullptr, bool corr = true);
+                          double add_coef, const int* skip_flag, const CgFold* cg = nullptr, bool corr = true);
 
 // Psi / Psi^dagger
 void launch_psi_adj(purify_plan* p, const void* x, void* c);

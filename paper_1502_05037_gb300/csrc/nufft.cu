@@ -128,12 +128,19 @@ __device__ __forceinline__ void fft_reg(int N, int logN, int t, const C* __restr
         const int kk = t & (Ns - 1);
 #pragma unroll
         for (int k = 0; k < 8; ++k) v[k] = slot(t + k * N8);
+        // W^{k ts} for k = 1..7 from three table entries (k = 1, 2, 4) and
+        // four products
         const int ts = kk * (N8 / Ns);
+        C w[8];
+        w[1] = tw[ts];
+        w[2] = tw[2 * ts];
+        w[4] = tw[4 * ts];
+        w[3] = cmul(w[1], w[2]);
+        w[5] = cmul(w[1], w[4]);
+        w[6] = cmul(w[2], w[4]);
+        w[7] = cmul(w[3], w[4]);
 #pragma unroll
-        for (int k = 1; k < 8; ++k) {
-            const C w = tw[k * ts];
-            v[k] = INV ? cmulconj(v[k], w) : cmul(v[k], w);
-        }
+        for (int k = 1; k < 8; ++k) v[k] = INV ? cmulconj(v[k], w[k]) : cmul(v[k], w[k]);
         dft8<C, INV>(v);
         if (Ns == N8) {
 #pragma unroll
@@ -182,8 +189,9 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(const T* __restrict__ x, type
     bool pending = false;
     T alpha = T(0), cbeta = T(0);
     if (fold.x && !first) {
+        // the previous step's update (it did not stop the solve: checked above)
         double al, be;
-        if (!cg_step_scalars(fold, fold.step - 1, al, be)) return;   // stopped at the previous step
+        if (!cg_pending(fold, al, be)) return;
         pending = true;
         alpha = (T)al;
         cbeta = (T)be;
@@ -301,14 +309,15 @@ __global__ void __launch_bounds__(1024) k_cols_inv(const typename cplx_of<T>::ty
 // Inverse row FFT of image rows [i0, i0+rb), then Z^T and S:
 //   out_mode 0: complex out[i][j] = scale * s * v
 //   out_mode 1: real    out[i][j] = scale * s * Re v + add_coef * (add ? add[i][j] : 0)
-// With dot_part set (a CG step: out = A r, add = r, see CgFold) the kernel
-// also writes per-block partials of r . r and r . A r to dot_part.
+// With cg.part set (a CG step: out = A r, add = r, see CgFold) the kernel
+// also writes per-block partials of r . r and r . A r, and its last block
+// reduces them and decides the step (cg_decide).
 template <typename T, int MAXT>
 __global__ void __launch_bounds__(MAXT) k_rows_inv(const typename cplx_of<T>::type* __restrict__ rows, void* out,
                            const T* __restrict__ sx, const T* __restrict__ sy,
                            const typename cplx_of<T>::type* __restrict__ tw, int nx, int ny, int Kx,
                            int rb, T scale, int out_mode, const T* __restrict__ add, T add_coef,
-                           const int* __restrict__ skip, double* dot_part) {
+                           const int* __restrict__ skip, CgFold cgf) {
     using C = typename cplx_of<T>::type;
     pdl_wait();
     if (skip && *skip) return;
@@ -319,7 +328,7 @@ __global__ void __launch_bounds__(MAXT) k_rows_inv(const typename cplx_of<T>::ty
     const int i = blockIdx.x * rb + f;
     const T rs = sy[i] * scale;
     T dacc = 0, gacc2 = 0;   // add.out, and with the folded CG add.add (add = r, out = A r)
-    const bool cg = dot_part != nullptr;
+    const bool cg = cgf.part != nullptr;
     auto load = [&](int k) -> C { return rows[(size_t)i * Kx + k]; };
     auto store = [&](int p1, C v) {
         const int j = (p1 + nx / 2) & (Kx - 1);
@@ -344,11 +353,15 @@ __global__ void __launch_bounds__(MAXT) k_rows_inv(const typename cplx_of<T>::ty
     if (cg) {
         // Chronopoulos-Gear partials (see CgFold): gamma = r.r, delta = r.A r;
         // the consumer of this step's scalars reduces them
-        const double b0 = block_sum((double)gacc2);
-        const double b1 = block_sum((double)dacc);
+        const double b0 = block_sum_t(gacc2);
+        const double b1 = block_sum_t(dacc);
         if (threadIdx.x == 0) {
-            dot_part[2 * blockIdx.x] = b0;
-            dot_part[2 * blockIdx.x + 1] = b1;
+            cgf.part[2 * blockIdx.x] = b0;
+            cgf.part[2 * blockIdx.x + 1] = b1;
+        }
+        if (arrive_last(cgf.counter)) {
+            cg_decide(cgf, cgf.step, gridDim.x);
+            if (threadIdx.x == 0) *cgf.counter = 0;
         }
     }
     pdl_trigger();
@@ -1254,7 +1267,7 @@ template <typename T> static void cols_inv_t(purify_plan* p, const int* skip, co
 
 template <typename T>
 static void rows_inv_t(purify_plan* p, void* out, double scale, int out_mode, const void* add, double add_coef,
-                       const int* skip, double* dot_part, bool corr) {
+                       const int* skip, const CgFold* cg, bool corr) {
     using C = typename cplx_of<T>::type;
     int rb = p->fft_rb > 0 ? p->fft_rb : rows_per_block<T>(p->ny, p->Kx);
     while (p->ny % rb) rb >>= 1;
@@ -1268,7 +1281,7 @@ static void rows_inv_t(purify_plan* p, void* out, double scale, int out_mode, co
     launch_dependent(kern, p->ny / rb, nt, sm, p->stream, p->rows.as<C>(), out, corr ? p->sx.as<T>() : p->onesx.as<T>(),
                                             corr ? p->sy.as<T>() : p->onesy.as<T>(), p->twx.as<C>(), p->nx, p->ny,
                                             p->Kx, rb, (T)scale, out_mode, (const T*)add, (T)add_coef, skip,
-                                            dot_part);
+                                            cg ? *cg : CgFold());
     L.done();
 }
 
@@ -1496,9 +1509,9 @@ void launch_cols_inv(purify_plan* p, const int* skip, const void* mult) {
     if (p->dtype == PURIFY_F32) cols_inv_t<float>(p, skip, mult); else cols_inv_t<double>(p, skip, mult);
 }
 void launch_rows_inv_crop(purify_plan* p, void* out, double scale, int out_mode, const void* add, double add_coef,
-                          const int* skip, double* dot_part, bool corr) {
-    if (p->dtype == PURIFY_F32) rows_inv_t<float>(p, out, scale, out_mode, add, add_coef, skip, dot_part, corr);
-    else rows_inv_t<double>(p, out, scale, out_mode, add, add_coef, skip, dot_part, corr);
+                          const int* skip, const CgFold* cg, bool corr) {
+    if (p->dtype == PURIFY_F32) rows_inv_t<float>(p, out, scale, out_mode, add, add_coef, skip, cg, corr);
+    else rows_inv_t<double>(p, out, scale, out_mode, add, add_coef, skip, cg, corr);
 }
 void launch_degrid(purify_plan* p, void* y, bool caller_order, const int* skip) {
     if (p->degrid_kind >= 3) {

@@ -70,6 +70,53 @@ __device__ __forceinline__ double block_sum(double v) {
     return v;
 }
 
+// Error-free transformation of a float sum (Knuth's TwoSum): s + e == a + b
+// exactly, s = fl(a + b).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Sum over the thread block of per-thread float values (result valid in
+// thread 0). Within a warp the running sum is an unevaluated pair hi + lo
+// of floats, each step adding the partner's pair with TwoSum, so the warp sum
+// carries about twice the float precision; the warp sums are then added in
+// FP64 by warp 0 (in warp order). This keeps the block-level arithmetic off
+// the slow FP64 pipe while the result matches an FP64 sum of the thread
+// values to about 2^-44 relative.
+__device__ __forceinline__ double block_sum_f(float v) {
+    __shared__ double shf[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+    const int n = min(32, (int)blockDim.x - wid * 32);
+    const unsigned mask = n == 32 ? 0xffffffffu : ((1u << n) - 1u);
+    float hi = v, lo = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_down_sync(mask, hi, o), l2 = __shfl_down_sync(mask, lo, o);
+        if (lane + o < n) {
+            float s, e;
+            two_sum(hi, h2, s, e);
+            hi = s;
+            lo = __fadd_rn(__fadd_rn(lo, l2), e);
+        }
+    }
+    __syncthreads();
+    if (lane == 0) shf[wid] = (double)hi + (double)lo;
+    __syncthreads();
+    double t = 0.0;
+    if (wid == 0) {
+        t = lane < nw ? shf[lane] : 0.0;
+        t = warp_sum_n(t, blockDim.x >= 32 ? 0xffffffffu : ((1u << blockDim.x) - 1u), nw);
+    }
+    return t;
+}
+// Block sum in the plan precision's reduction form: compensated float pairs
+// for float values, FP64 for double values.
+__device__ __forceinline__ double block_sum_t(float v) { return block_sum_f(v); }
+__device__ __forceinline__ double block_sum_t(double v) { return block_sum(v); }
+
 // True in every thread of the last block to arrive; partials written before
 // the call by other blocks are then visible.
 __device__ __forceinline__ bool arrive_last(unsigned* counter) {

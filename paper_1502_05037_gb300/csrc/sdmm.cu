@@ -54,7 +54,7 @@ __global__ void k_prox_l1(T* __restrict__ c, T* __restrict__ z1, const T* __rest
         z1[d] = zn;
         c[d] = s - zn;
     }
-    double b = block_sum((double)obj);
+    double b = block_sum_t(obj);
     if (threadIdx.x == 0) part[blockIdx.x] = b;
     if (arrive_last(counters + C_PROX)) {
         double tot = ordered_sum(part, gridDim.x);
@@ -89,8 +89,8 @@ __global__ void k_proj_norms(const typename cplx_of<T>::type* __restrict__ v2,
             a += tx * tx + ty * ty;
         }
     }
-    double sa = block_sum((double)a);
-    double se = block_sum((double)e);
+    double sa = block_sum_t(a);
+    double se = block_sum_t(e);
     if (threadIdx.x == 0) { part[2 * ch] = sa; part[2 * ch + 1] = se; }
     if (arrive_last(counters + C_PROJ)) {
         // chunk_first[r] .. chunk_first[r+1] are block r's chunks
@@ -192,9 +192,9 @@ __global__ void k_relchange(T* __restrict__ x, const T* __restrict__ xprev, int6
     // the last CG step's update first, unless the solve stopped (see CgFold)
     bool pending = false;
     T alpha = T(0), beta = T(0);
-    if (fold.x && !block_flag(fold.flags + F_CGDONE)) {
+    if (fold.x) {
         double al, be;
-        if (cg_step_scalars(fold, fold.step, al, be)) {
+        if (cg_pending(fold, al, be)) {
             pending = true;
             alpha = (T)al;
             beta = (T)be;
@@ -220,13 +220,19 @@ __global__ void k_relchange(T* __restrict__ x, const T* __restrict__ xprev, int6
         a += xv * xv;
         d += dv * dv;
     }
-    double ba = block_sum((double)a);
-    double bd = block_sum((double)d);
+    double ba = block_sum_t(a);
+    double bd = block_sum_t(d);
     if (threadIdx.x == 0) { part[2 * blockIdx.x] = ba; part[2 * blockIdx.x + 1] = bd; }
     if (arrive_last(counters + C_REL)) {
+        // fixed-order block-parallel sum of the block partials
         double sa = 0.0, sd = 0.0;
+        for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) {
+            sa += __ldcg(part + 2 * k);
+            sd += __ldcg(part + 2 * k + 1);
+        }
+        sa = block_sum(sa);
+        sd = block_sum(sd);
         if (threadIdx.x == 0) {
-            for (unsigned k = 0; k < gridDim.x; ++k) { sa += __ldcg(part + 2 * k); sd += __ldcg(part + 2 * k + 1); }
             scal[S_XN2] = sa;
             scal[S_DXN2] = sd;
             counters[C_REL] = 0;
@@ -262,15 +268,24 @@ __global__ void k_reduce(const T* __restrict__ v, int64_t n, int mode, double* p
     }
     if (threadIdx.x == 0) part[blockIdx.x] = acc;
     if (arrive_last(counters + C_GEN)) {
-        if (threadIdx.x == 0) {
+        // fixed-order block-parallel combination of the block partials
+        if (mode == 1) {
             double t = 0.0;
-            for (unsigned k = 0; k < gridDim.x; ++k) {
-                double pk = __ldcg(part + k);
-                t = mode == 1 ? fmax(t, pk) : t + pk;
+            for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) t = fmax(t, __ldcg(part + k));
+            __shared__ double shm[32];
+            for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_down_sync(0xffffffffu, t, o));
+            if ((threadIdx.x & 31) == 0) shm[threadIdx.x >> 5] = t;
+            __syncthreads();
+            if (threadIdx.x < 32) {
+                t = threadIdx.x < (blockDim.x >> 5) ? shm[threadIdx.x] : 0.0;
+                for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_down_sync(0xffffffffu, t, o));
             }
-            scal[slot] = t;
-            counters[C_GEN] = 0;
+            if (threadIdx.x == 0) scal[slot] = t;
+        } else {
+            const double t = ordered_sum(part, gridDim.x);
+            if (threadIdx.x == 0) scal[slot] = t;
         }
+        if (threadIdx.x == 0) counters[C_GEN] = 0;
     }
 }
 
@@ -593,7 +608,7 @@ template <typename T> struct Solver {
         fold.u = s.u.p;
         fold.add = s.addend.p;
         fold.part = cg_part();
-        fold.nparts = rows_inv_blocks(p);
+        fold.counter = ctr() + C_CGI;
         fold.scal = scal();
         fold.flags = flags();
         for (int k = 0; k < cg_iters; ++k) {
@@ -603,7 +618,7 @@ template <typename T> struct Solver {
                 launch_scale_pad_rows(p, nullptr, 1.0, skip, false, false, &fold);
                 launch_cols_fwd(p, skip);
                 launch_cols_inv(p, skip, s.toep.p);
-                launch_rows_inv_crop(p, s.u.p, 1.0, 1, s.r.p, 2.0, skip, cg_part(), false);
+                launch_rows_inv_crop(p, s.u.p, 1.0, 1, s.r.p, 2.0, skip, &fold, false);
             } else {
                 // the pending update and the transform of the new r fused into
                 // the first FFT pass, then u = A r
@@ -613,11 +628,12 @@ template <typename T> struct Solver {
                 launch_cols_inv(p, skip);
                 // u = 2 r + Re Phi^H Phi r / nu^2, with r.r, r.u and the CG
                 // scalars fused in
-                launch_rows_inv_crop(p, s.u.p, inv_nu, 1, s.r.p, 2.0, skip, cg_part(), true);
+                launch_rows_inv_crop(p, s.u.p, inv_nu, 1, s.r.p, 2.0, skip, &fold, true);
             }
         }
         // the last step's pending update is applied by the relative-change kernel
         fold.step = cg_iters - 1;
+        if (cg_iters == 0) fold = CgFold();   // no CG step ran: nothing pending
         {
             Launch L(p, "relchange");
             launch_dependent(k_relchange<T>, red_blocks(p->N), RB, 0, p->stream, x, s.xprev.template as<T>(), p->N,
