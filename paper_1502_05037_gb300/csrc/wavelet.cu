@@ -279,8 +279,12 @@ k_idwt_level(const T* __restrict__ ll_in, int ll_basis_stride, int ll_ld, const 
 // threads) synthesises basis z's contribution to the block's output tile;
 // the partial tiles are then added in basis order. When `ll_in` is null
 // (L == 1) the low-pass bands come from the coefficient planes.
-template <typename T>
-__global__ void k_idwt_final(const T* __restrict__ ll_in, int ll_basis_stride, const T* __restrict__ coef,
+// Every group runs the same code: filters zero-padded to the plan's longest
+// length L (the padded taps add exact zeros), so the block has one instruction
+// stream and one barrier sequence whatever the bases.
+template <typename T, int L>
+__global__ void __launch_bounds__(512, 2)
+k_idwt_final(const T* __restrict__ ll_in, int ll_basis_stride, const T* __restrict__ coef,
                              const int* __restrict__ planes, int N, int nx, int ny, int group_elems,
                              const int* __restrict__ pids, int nw, int dirac_plane,
                              T inv_sqrt_q, T* __restrict__ x) {
@@ -301,9 +305,7 @@ __global__ void k_idwt_final(const T* __restrict__ ll_in, int ll_basis_stride, c
         const T* det = coef + (size_t)planes[z] * N;
         const T* ll = ll_in ? ll_in + (size_t)z * ll_basis_stride : det;
         const int ld = ll_in ? (nx >> 1) : nx;
-        PURIFY_WITH_LENGTH(fbank<T>().len[pb],
-                           (synth_tile<T, L, PER>(ll, ld, det, nx, ny, nx, oy0, ox0, th2, tw2, pb, gsm, gt,
-                                                  SYN_GROUP, acc)));
+        synth_tile<T, L, PER>(ll, ld, det, nx, ny, nx, oy0, ox0, th2, tw2, pb, gsm, gt, SYN_GROUP, acc);
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
             const int t = gt + i * SYN_GROUP;
@@ -414,6 +416,15 @@ template <typename T> static void psi_adj_t(purify_plan* p, const void* xv, void
     }
 }
 
+template <typename T, int L>
+static void launch_idwt_final(purify_plan* p, dim3 g, int threads, size_t sm, const T* ll_in, int llstride,
+                              const T* c, int N, int group_elems, const WaveletLayout& wl, T inv_sqrt_q, T* x) {
+    if (sm > 48 * 1024)
+        PURIFY_CUDA(cudaFuncSetAttribute(k_idwt_final<T, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    launch_dependent(k_idwt_final<T, L>, g, threads, sm, p->stream, ll_in, llstride, c, plane_array(p), N, p->nx,
+                     p->ny, group_elems, pid_array(p), wl.nw, wl.dirac_plane, inv_sqrt_q, x);
+}
+
 template <typename T> static void psi_t(purify_plan* p, const void* cv, void* xv) {
     const T* c = (const T*)cv;
     T* x = (T*)xv;
@@ -445,12 +456,10 @@ template <typename T> static void psi_t(purify_plan* p, const void* cv, void* xv
     const size_t sm = sizeof(T) * ((size_t)wl.nw * 4 * SYN_T * SYN_T + (size_t)wl.nw * group_elems);
     dim3 g((p->nx + 2 * SYN_T - 1) / (2 * SYN_T), (p->ny + 2 * SYN_T - 1) / (2 * SYN_T), 1);
     const int threads = std::max(1, wl.nw) * SYN_GROUP;
-    if (sm > 48 * 1024) PURIFY_CUDA(cudaFuncSetAttribute(k_idwt_final<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    Launch L(p, "idwt_final");
-    launch_dependent(k_idwt_final<T>, g, threads, sm, p->stream, ll_in, llstride, c, plane_array(p), N, p->nx, p->ny,
-                                                   (int)group_elems, pid_array(p), wl.nw, wl.dirac_plane,
-                                                   inv_sqrt_q, x);
-    L.done();
+    Launch Lf(p, "idwt_final");
+    PURIFY_WITH_LENGTH(maxL, (launch_idwt_final<T, L>(p, g, threads, sm, ll_in, llstride, c, N, (int)group_elems, wl,
+                                                       inv_sqrt_q, x)));
+    Lf.done();
 }
 
 void launch_psi_adj(purify_plan* p, const void* x, void* c) {
