@@ -42,6 +42,11 @@ solver parameter):
 * SARA reweighting (Sec. 1: weights essentially the inverse of the previous
   solution's coefficients): w = rho / (rho + |Psi^dagger x|), rho_1 =
   std(Psi^dagger x^(0)), rho_{t+1} = rho_t / 2, each pass warm-started.
+* Stochastic block-subset iterations (the paper's closing paragraph names
+  using one data block or a subset of blocks per iteration as a way to lower
+  the cost of an iteration): sdmm_iteration_groups, the blocks dealt
+  round-robin into G groups, one group per iteration, its data term scaled
+  by G in the x-update (see there).
 * CG stopping (the paper names no rule): a fixed number of steps, or, with a
   tolerance, the first step at which ||r|| <= tol ||r_0||, r_0 the residual
   of the warm start of that x-update.
@@ -212,6 +217,61 @@ def sdmm_iteration(prob: Problem, st: State, cg_iters: int, cg_tol: float = 0.0)
     st.cg_iters += done
     rel = float(np.linalg.norm(x_new - x) / max(np.linalg.norm(x_new), 1e-300))
     st.history.append({"rel_change": rel, "cg": done})
+    st.x = x_new
+    return st
+
+
+def block_group(prob: Problem, g: int, G: int) -> list:
+    """Blocks of group g when the R blocks are dealt round-robin into G
+    groups: block i belongs to group i mod G."""
+    return [i for i in range(prob.R) if i % G == g]
+
+
+def sdmm_iteration_groups(prob: Problem, st: State, cg_iters: int, g: int, G: int,
+                          cg_tol: float = 0.0) -> State:
+    """One stochastic block-subset SDMM iteration (the paper's closing
+    paragraph: use one data block, or a subset of blocks, per iteration).
+    Reading: only the blocks i of group g (i mod G == g) take part; their
+    data term, scaled by G so that its expectation over a uniformly drawn
+    group is the full data term, replaces the full one in the x-update, and
+    only their multipliers move:
+        s1, z1 and s3, z3 as in sdmm_iteration;
+        for i in the group: v2_i = Phi_i x / nu, s2_i = proj(v2_i + z2_i), z2_i += v2_i - s2_i;
+        x = CG solution of (2 I + G Re sum_{i in group} Phi_i^H Phi_i / nu^2) x
+            = Psi (s1 - z1) + (s3 - z3) + G sum_{i in group} Re Phi_i^H (s2_i - z2_i) / nu.
+    With G = 1 (one group holding every block) this is sdmm_iteration."""
+    x = st.x
+    blocks = block_group(prob, g, G)
+    mask = np.zeros(prob.plan.M)
+    for i in blocks:
+        mask[prob.offsets[i]:prob.offsets[i + 1]] = 1.0
+    # f_1
+    v1 = prob.psi_adj(x)
+    s1 = soft_threshold(v1 + st.z1, prob.gamma * prob.w())
+    st.z1 = st.z1 + v1 - s1
+    # f_2 on the group's blocks
+    v2 = prob.phi_n(x)
+    yn = prob.y / prob.nu
+    s2 = np.array(st.z2, copy=True)   # placeholder values outside the group (not used)
+    z2 = np.array(st.z2, copy=True)
+    for i in blocks:
+        a, b = prob.offsets[i], prob.offsets[i + 1]
+        s2[a:b] = proj_l2_ball(v2[a:b] + st.z2[a:b], yn[a:b], prob.eps[i] / prob.nu)
+        z2[a:b] = st.z2[a:b] + v2[a:b] - s2[a:b]
+    st.z2 = z2
+    # f_3
+    s3 = proj_positive(x + st.z3)
+    st.z3 = st.z3 + x - s3
+    # x-update with the group's data term, scaled by G
+    b = prob.psi(s1 - st.z1) + G * prob.phi_n_adj_re(mask * (s2 - st.z2)) + (s3 - st.z3)
+
+    def apply_group(v):
+        return 2.0 * v + G * prob.phi_n_adj_re(mask * prob.phi_n(v))
+
+    x_new, done, _ = cg(apply_group, b, x, cg_iters, cg_tol)
+    st.cg_iters += done
+    rel = float(np.linalg.norm(x_new - x) / max(np.linalg.norm(x_new), 1e-300))
+    st.history.append({"rel_change": rel, "cg": done, "group": g})
     st.x = x_new
     return st
 

@@ -322,3 +322,71 @@ def test_block_offsets_partition():
     for M, R, seed in ((100, 7, 1), (655360, 8, 4001), (50, 50, 2)):
         s = synth.block_sizes(M, R, seed)
         assert s.sum() == M and s.min() >= 1 and s.size == R
+
+
+# ---------------------------------------------- block-subset iterations
+def test_one_group_is_plain_sdmm():
+    # G = 1: one group holding every block, the data term unscaled: the same
+    # iterates as plain SDMM, bit for bit
+    prob, _ = _tiny_problem(R=3, seed=31)
+    a = sdmm.init_state(prob, np.zeros((8, 8)))
+    b = sdmm.init_state(prob, np.zeros((8, 8)))
+    for _ in range(4):
+        sdmm.sdmm_iteration(prob, a, 12)
+        sdmm.sdmm_iteration_groups(prob, b, 12, 0, 1)
+    assert np.array_equal(a.x, b.x) and np.array_equal(a.z2, b.z2) and np.array_equal(a.z1, b.z1)
+
+
+def test_group_iteration_against_dense_restricted_system():
+    # the x-update of a group iteration solves (2 I + G Re Phi_g^H Phi_g / nu^2) x = b
+    # with the group's rows of the dense measurement matrix; blocks outside the
+    # group keep their multipliers
+    prob, _ = _tiny_problem(R=4, M=120, seed=32)
+    G, g = 2, 1
+    st = sdmm.init_state(prob, np.zeros((8, 8)))
+    sdmm.sdmm_iteration(prob, st, 30, 1e-14)            # a non-trivial state
+    x0, z1, z2, z3 = st.x.copy(), st.z1.copy(), st.z2.copy(), st.z3.copy()
+    sdmm.sdmm_iteration_groups(prob, st, 200, g, G, 1e-14)
+    A = nf.phi_matrix(prob.plan) / prob.nu
+    rows = np.zeros(prob.plan.M, dtype=bool)
+    for i in sdmm.block_group(prob, g, G):
+        rows[prob.offsets[i]:prob.offsets[i + 1]] = True
+    Ag = A[rows]
+    n = 64
+    # s and z of the iteration, written out from the definitions
+    v1 = prob.psi_adj(x0)
+    s1 = sdmm.soft_threshold(v1 + z1, prob.gamma)
+    z1n = z1 + v1 - s1
+    v2 = A @ x0.ravel()
+    yn = prob.y / prob.nu
+    z2n = z2.copy()
+    s2 = np.zeros_like(z2)
+    for i in sdmm.block_group(prob, g, G):
+        a, b_ = prob.offsets[i], prob.offsets[i + 1]
+        s2[a:b_] = sdmm.proj_l2_ball(v2[a:b_] + z2[a:b_], yn[a:b_], prob.eps[i] / prob.nu)
+        z2n[a:b_] = z2[a:b_] + v2[a:b_] - s2[a:b_]
+    s3 = np.maximum(x0 + z3, 0.0)
+    z3n = z3 + x0 - s3
+    rhs = prob.psi(s1 - z1n).ravel() + G * np.real(Ag.conj().T @ (s2 - z2n)[rows]) + (s3 - z3n).ravel()
+    Ad = 2 * np.eye(n) + G * np.real(Ag.conj().T @ Ag)
+    want = np.linalg.solve(Ad, rhs).reshape(8, 8)
+    assert np.allclose(st.x, want, atol=1e-9 * np.abs(want).max())
+    out = ~rows
+    assert np.array_equal(st.z2[out], z2[out])
+    assert np.allclose(st.z2[rows], z2n[rows], atol=1e-13)
+
+
+def test_group_data_term_is_unbiased():
+    # averaged over the G groups, the scaled group data terms are the full
+    # data term: sum_g G Phi_g^H Phi_g / G = Phi^H Phi
+    prob, _ = _tiny_problem(R=5, M=150, seed=33)
+    A = nf.phi_matrix(prob.plan)
+    G = 3
+    acc = np.zeros((64, 64))
+    for g in range(G):
+        rows = np.zeros(prob.plan.M, dtype=bool)
+        for i in sdmm.block_group(prob, g, G):
+            rows[prob.offsets[i]:prob.offsets[i + 1]] = True
+        acc += G * np.real(A[rows].conj().T @ A[rows]) / G
+    assert np.allclose(acc, np.real(A.conj().T @ A), atol=1e-10 * np.abs(acc).max())
+    assert sorted(i for g in range(G) for i in sdmm.block_group(prob, g, G)) == list(range(5))
