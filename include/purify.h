@@ -163,6 +163,20 @@ typedef struct {
                              adjoint NUFFT), instead of a gridding / degridding pair per
                              CG step; the operator then differs from the NUFFT one by the
                              NUFFT error. Needs oversample 2. */
+    int32_t block_groups; /* G >= 1: stochastic block-subset iterations (Sec. 1, closing
+                             paragraph: one data block or a subset of blocks per
+                             iteration). Block i belongs to group i mod G; iteration t
+                             uses group g_t only: Phi_g x, the projections and multiplier
+                             updates of the group's blocks, and an x-update whose data
+                             term is G times the group's (an unbiased estimate of the full
+                             one):  (2 I + G Re Phi_g^H Phi_g / nu^2) x = Psi (s1 - z1)
+                             + (s3 - z3) + G Re Phi_g^H (s2_g - z2_g) / nu. G = 1 is plain
+                             SDMM (on the group code path); 0 = plain SDMM. FP32 plans
+                             with kb_width <= 6, no toeplitz; G <= R. In tolerance mode the
+                             test evaluates every block at x and compares the objective
+                             with that of the previous check. */
+    const int32_t *group_seq; /* HOST, max_iter entries in [0, G): g_t of this call's
+                             iterations; NULL => (iterations done) mod G */
 } purify_sdmm_params;
 
 /* Statistics of a solve, evaluated at the returned x. */
@@ -202,6 +216,13 @@ purify_status purify_sdmm_solve(purify_plan *plan, const void *y, const double *
  * max_iter = 0 returns it with statistics. Errors: EINVAL if no solve was
  * started on the plan. */
 purify_status purify_sdmm_iterate(purify_plan *plan, int32_t iters);
+
+/* purify_sdmm_iterate for a solve started with block_groups = G: iteration i
+ * uses group groups[i] (HOST, iters entries in [0, G); NULL => round-robin
+ * from the iterations done), each group's iteration a replay of its own
+ * captured graph. On a solve without groups it is purify_sdmm_iterate.
+ * Errors: EINVAL (no started solve, group out of range). */
+purify_status purify_sdmm_iterate_groups(purify_plan *plan, int32_t iters, const int32_t *groups);
 
 /* Primal-dual solver for problem (3) without an inner CG (the paper's SDMM
  * family; Chambolle & Pock 2011, Algorithm 1 with theta = 1) on

@@ -130,18 +130,31 @@ def purify_op_norm_sq(plan: Plan, iters: int = 100) -> float:
     return out.value
 
 
+def _int32_seq(seq):
+    if seq is None:
+        return None, None
+    a = np.ascontiguousarray(np.asarray(seq, dtype=np.int32))
+    return a, a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
 def purify_sdmm_solve(plan: Plan, y, eps, x, w=None, max_iter=200, cg_iters=10, cg_tol=0.0, gamma=0.0, nu=0.0,
                       rel_obj_tol=0.0, eps_tol=0.0, check_every=0, resume=False, toeplitz=False,
-                      raise_on_error=True):
-    """Solve problem (3); x is updated in place. Returns purify_sdmm_stats."""
+                      block_groups=0, group_seq=None, raise_on_error=True):
+    """Solve problem (3); x is updated in place. Returns purify_sdmm_stats.
+    block_groups / group_seq: stochastic block-subset iterations (group_seq
+    holds max_iter group indices)."""
     eps_np = None
     eps_ptr = None
     if eps is not None:
         eps_np = np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
         eps_ptr = eps_np.ctypes.data_as(C.POINTER(C.c_double))
+    seq_np, seq_ptr = _int32_seq(group_seq)
+    if seq_np is not None and seq_np.size < max_iter:
+        raise ValueError("group_seq needs max_iter entries")
     prm = purify_sdmm_params(max_iter=max_iter, cg_iters=cg_iters, cg_tol=cg_tol, gamma=gamma, nu=nu,
                              rel_obj_tol=rel_obj_tol, eps_tol=eps_tol, check_every=check_every,
-                             resume=int(bool(resume)), toeplitz=int(bool(toeplitz)))
+                             resume=int(bool(resume)), toeplitz=int(bool(toeplitz)), block_groups=block_groups,
+                             group_seq=seq_ptr)
     st = purify_sdmm_stats()
     status = load().purify_sdmm_solve(plan.handle, _ptr(y), eps_ptr, _ptr(w), _ptr(x), C.byref(prm), C.byref(st))
     if raise_on_error:
@@ -163,6 +176,15 @@ def purify_pd_solve(plan: Plan, y, eps, x, w=None, iters=200, tau=0.0, sigma=0.0
 def purify_sdmm_iterate(plan: Plan, iters: int):
     """Advance the plan's current SDMM state by `iters` iterations (async)."""
     check(load().purify_sdmm_iterate(plan.handle, int(iters)))
+
+
+def purify_sdmm_iterate_groups(plan: Plan, iters: int, groups=None):
+    """Advance a block-group solve by `iters` iterations, iteration i on group
+    groups[i] (None: round-robin); asynchronous."""
+    seq_np, seq_ptr = _int32_seq(groups)
+    if seq_np is not None and seq_np.size < iters:
+        raise ValueError("groups needs iters entries")
+    check(load().purify_sdmm_iterate_groups(plan.handle, int(iters), seq_ptr))
 
 
 class Batch:

@@ -63,6 +63,8 @@ class purify_sdmm_params(C.Structure):
         ("check_every", C.c_int32),
         ("resume", C.c_int32),
         ("toeplitz", C.c_int32),
+        ("block_groups", C.c_int32),
+        ("group_seq", C.POINTER(C.c_int32)),
     ]
 
 
@@ -108,6 +110,7 @@ _SIGS = {
     "purify_sdmm_solve": (C.c_int, [_P, _P, C.POINTER(C.c_double), _P, _P,
                                     C.POINTER(purify_sdmm_params), C.POINTER(purify_sdmm_stats)]),
     "purify_sdmm_iterate": (C.c_int, [_P, C.c_int32]),
+    "purify_sdmm_iterate_groups": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int32)]),
     "purify_pd_solve": (C.c_int, [_P, _P, C.POINTER(C.c_double), _P, _P,
                                   C.POINTER(purify_pd_params), C.POINTER(purify_sdmm_stats)]),
     "purify_batch_create": (C.c_int, [C.POINTER(_P), C.c_int32, _P, C.POINTER(_P)]),

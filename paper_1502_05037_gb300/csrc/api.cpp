@@ -258,6 +258,11 @@ purify_status purify_sdmm_solve(purify_plan* p, const void* y, const double* eps
         PURIFY_REQUIRE(params->max_iter >= 0 && params->cg_iters >= 0, "negative iteration count");
         PURIFY_REQUIRE(params->resume || (y && eps), "y and eps are required unless resuming");
         PURIFY_REQUIRE(!params->resume || p->sd.started, "resume without a previous solve on this plan");
+        PURIFY_REQUIRE(params->block_groups >= 0 && params->block_groups <= p->R, "block_groups must be in [0, R]");
+        if (params->block_groups > 0 && params->group_seq)
+            for (int i = 0; i < params->max_iter; ++i)
+                PURIFY_REQUIRE(params->group_seq[i] >= 0 && params->group_seq[i] < params->block_groups,
+                               "group_seq entry out of range");
         if (stats) std::memset(stats, 0, sizeof(*stats));
         sdmm_solve(p, y, eps, w, x, *params, stats);
     });
@@ -280,6 +285,14 @@ purify_status purify_sdmm_iterate(purify_plan* p, int32_t iters) {
         PURIFY_REQUIRE(p != nullptr && iters >= 0, "bad argument");
         PURIFY_REQUIRE(p->sd.started, "no SDMM solve started on this plan");
         sdmm_iterate(p, iters);
+    });
+}
+
+purify_status purify_sdmm_iterate_groups(purify_plan* p, int32_t iters, const int32_t* groups) {
+    return guarded([&] {
+        PURIFY_REQUIRE(p != nullptr && iters >= 0, "bad argument");
+        PURIFY_REQUIRE(p->sd.started, "no SDMM solve started on this plan");
+        sdmm_iterate(p, iters, groups);
     });
 }
 

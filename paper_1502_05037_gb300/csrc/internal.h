@@ -113,6 +113,15 @@ struct LaneWork {
     }
 };
 
+// Block groups of the stochastic block-subset iterations: block i belongs to
+// group i mod G; per group the lane work of its visibilities (two lanes per
+// run) and the visibility chunks of its blocks (chunk_first indexes the
+// group's own chunk list; blocks outside the group have empty ranges).
+struct GroupChunks {
+    int n = 0;
+    DevBuf cblk, cbeg, cend, chunk_first;
+};
+
 // SDMM device state (allocated on first solve).
 struct SdmmState {
     bool ready = false;
@@ -153,6 +162,8 @@ struct SdmmState {
     bool g_toep = false;
     int64_t g_kernels = 0;
     ~SdmmState() {
+        for (auto& e : gexec_group)
+            if (e) cudaGraphExecDestroy(e);
         if (gexec) cudaGraphExecDestroy(gexec);
         if (pd_gexec) cudaGraphExecDestroy(pd_gexec);
         if (ev_in) cudaEventDestroy(ev_in);
@@ -164,6 +175,21 @@ struct SdmmState {
     }
     int64_t iters_done = 0;
     int64_t cg_total = 0;
+    // block-subset iterations: groups of the current solve (0: all blocks
+    // every iteration) and one captured graph per group
+    int groups = 0;
+    std::vector<cudaGraphExec_t> gexec_group;
+    std::vector<int64_t> kernels_group;
+    int gg_cg = -1;
+    double gg_gamma = 0, gg_nu = 0;
+    bool gg_have_w = false;
+    int gg_groups = 0;
+    void drop_group_graphs() {
+        for (auto& e : gexec_group)
+            if (e) cudaGraphExecDestroy(e);
+        gexec_group.clear();
+        kernels_group.clear();
+    }
 };
 
 }  // namespace purify
@@ -195,6 +221,9 @@ struct purify_plan {
     purify::LaneWork lanes[3];        // lane-per-run forms of the same runs (FP32, J <= 6): one lane
                                       // per run; two lanes per run; two, sets grouped by tile
     int normal_kind = 2;              // G^H G: 2 run sets, 3..5 lanes (as lanes[kind - 3]); autotuned
+    int group_count = 0;              // G of group_lanes / group_chunks (0: not built)
+    std::vector<purify::LaneWork> group_lanes;
+    std::vector<purify::GroupChunks> group_chunks;
     int grid_kind = 1;                // G^H: 1 tile subproblems, 2 run sets, 3..5 lanes; autotuned
     int degrid_kind = 1;              // G: 1 tile subproblems, 3..5 lanes; autotuned
     int fft_rb = 0, fft_cb = 0;       // FFT rows / columns per block (0: heuristic)
@@ -316,7 +345,7 @@ struct BatchState {
 };
 void batch_iterate(BatchState* b, int iters);
 void batch_destroy(BatchState* b);
-void sdmm_iterate(purify_plan* p, int iters);
+void sdmm_iterate(purify_plan* p, int iters, const int32_t* groups = nullptr);
 void pd_solve(purify_plan* p, const void* y, const double* eps, const void* w, void* x,
               const purify_pd_params& prm, purify_sdmm_stats* st);
 void add_launches(int64_t n);
@@ -334,6 +363,12 @@ void launch_grid_lanes(purify_plan* p, int kind, const void* y, bool caller_orde
                        bool zeroed = false);
 void launch_degrid_lanes(purify_plan* p, int kind, void* y, bool caller_order, const int* skip);
 void launch_normal_lanes(purify_plan* p, int kind, const int* skip, bool zeroed = false);
+// the lane kernels on an explicit lane work (mode 0 G^H G into gacc, 1 G^H of
+// yin into gacc, 2 G into yout; internal or caller order)
+void launch_lanes_on(purify_plan* p, const LaneWork& lw, int mode, const void* yin, void* yout, bool caller_order,
+                     const int* skip, bool zeroed);
+// lane work and chunk lists of G block groups (FP32 plans with J <= kLaneMaxJ)
+void build_group_lanes(purify_plan* p, int G);
 int grid_list_unit(int dtype, int J);
 bool fft_shape_ok(int nb, int K, int dtype);
 

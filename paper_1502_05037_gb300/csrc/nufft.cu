@@ -1399,10 +1399,9 @@ static void grid_sets_tj(purify_plan* p, const void* y, bool caller_order, const
 // there is less work).
 static const LaneWork& lane_work(const purify_plan* p, int kind) { return p->lanes[kind - 3]; }
 template <int J, int MODE, int H>
-static void lane_tj(purify_plan* p, int kind, const void* yin, void* yout, bool caller_order, const int* skip,
-                    bool zeroed) {
+static void lane_tw(purify_plan* p, const LaneWork& lw, const void* yin, void* yout, bool caller_order,
+                    const int* skip, bool zeroed) {
     if (MODE != LANE_DEGRID && !zeroed) PURIFY_CUDA(cudaMemsetAsync(p->gacc.p, 0, p->gacc.bytes, p->stream));
-    const LaneWork& lw = lane_work(p, kind);
     if (lw.nsets == 0) return;
     const size_t lane_smem = 4 * LaneStage<J, H>::bytes_per_warp;
     static int per_sm = 0;   // resident blocks per SM of this instantiation
@@ -1423,11 +1422,22 @@ static void lane_tj(purify_plan* p, int kind, const void* yin, void* yout, bool 
     L.done();
 }
 template <int J, int MODE>
-static void lane_any(purify_plan* p, int kind, const void* yin, void* yout, bool c, const int* s, bool z) {
+static void lane_on(purify_plan* p, const LaneWork& lw, const void* yin, void* yout, bool c, const int* s, bool z) {
     if constexpr (J <= kLaneMaxJ) {
-        if (kind == 3) lane_tj<J, MODE, 1>(p, kind, yin, yout, c, s, z);
-        else lane_tj<J, MODE, 2>(p, kind, yin, yout, c, s, z);
+        if (lw.width == 32) lane_tw<J, MODE, 1>(p, lw, yin, yout, c, s, z);
+        else lane_tw<J, MODE, 2>(p, lw, yin, yout, c, s, z);
     }
+}
+template <int J, int MODE>
+static void lane_any(purify_plan* p, int kind, const void* yin, void* yout, bool c, const int* s, bool z) {
+    lane_on<J, MODE>(p, lane_work(p, kind), yin, yout, c, s, z);
+}
+template <int J>
+static void lane_mode(purify_plan* p, const LaneWork& lw, int mode, const void* yin, void* yout, bool c, const int* s,
+                      bool z) {
+    if (mode == LANE_GG) lane_on<J, LANE_GG>(p, lw, nullptr, nullptr, false, s, z);
+    else if (mode == LANE_GRID) lane_on<J, LANE_GRID>(p, lw, yin, nullptr, c, s, z);
+    else lane_on<J, LANE_DEGRID>(p, lw, nullptr, yout, c, s, true);
 }
 template <int J> static void lane_gg(purify_plan* p, int kind, const int* s, bool z) {
     lane_any<J, LANE_GG>(p, kind, nullptr, nullptr, false, s, z);
@@ -1462,6 +1472,12 @@ void launch_grid_lanes(purify_plan* p, int kind, const void* y, bool caller_orde
 void launch_degrid_lanes(purify_plan* p, int kind, void* y, bool caller_order, const int* skip) {
     require_lane_work(p, kind);
     PURIFY_J_DISPATCH(p->J, lane_degrid, p, kind, y, caller_order, skip);
+}
+void launch_lanes_on(purify_plan* p, const LaneWork& lw, int mode, const void* yin, void* yout, bool caller_order,
+                     const int* skip, bool zeroed) {
+    if (!lane_work_ok(p) || lw.nsets == 0 || (lw.width != 32 && lw.width != 16))
+        throw Error{PURIFY_EINVAL, "lane-per-run kernels need an FP32 plan with J <= 6"};
+    PURIFY_J_DISPATCH(p->J, lane_mode, p, lw, mode, yin, yout, caller_order, skip, zeroed);
 }
 void launch_normal_lanes(purify_plan* p, int kind, const int* skip, bool zeroed) {
     if (kind == 2 || !lane_work_ok(p)) {

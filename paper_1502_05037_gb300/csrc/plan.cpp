@@ -447,6 +447,86 @@ static void build_runwork(purify_plan* p, const std::vector<T>& us, const std::v
     p->workspace_bytes += (int64_t)(p->runs.rec.bytes + p->runs.cell.bytes + p->runs.start.bytes + p->runs.len.bytes);
 }
 
+// Lane work and visibility chunks of G block groups (block i in group
+// i mod G), from the plan's sorted coordinates: per group, its visibilities
+// in first-tap-cell order are cut into runs as for the whole plan (at most
+// kRunMax, sorted by length), two lanes per run.
+void build_group_lanes(purify_plan* p, int G) {
+    PURIFY_REQUIRE(lane_work_ok(p), "block groups need an FP32 plan with kb_width <= 6");
+    PURIFY_REQUIRE(G >= 1 && G <= p->R, "block_groups must be in [1, R]");
+    if (p->group_count == G) return;
+    p->group_lanes.clear();
+    p->group_chunks.clear();
+    p->group_count = 0;
+    const int64_t M = p->M;
+    std::vector<float> us(M), vs(M);
+    std::vector<int> perm(M);
+    PURIFY_CUDA(cudaMemcpy(us.data(), p->us.p, sizeof(float) * M, cudaMemcpyDeviceToHost));
+    PURIFY_CUDA(cudaMemcpy(vs.data(), p->vs.p, sizeof(float) * M, cudaMemcpyDeviceToHost));
+    PURIFY_CUDA(cudaMemcpy(perm.data(), p->perm.p, sizeof(int) * M, cudaMemcpyDeviceToHost));
+    std::vector<int> cx(M), cy(M);
+    std::vector<RunRecF> rec_of(M);
+    for (int64_t m = 0; m < M; ++m) {
+        int kx0, ky0;
+        RunRecF e{};
+        split_coord(us[m], p->ax, p->J, kx0, e.phx);
+        split_coord(vs[m], p->ay, p->J, ky0, e.phy);
+        e.m = (int)m;
+        rec_of[m] = e;
+        cx[m] = kx0 & (p->Kx - 1);
+        cy[m] = ky0 & (p->Ky - 1);
+    }
+    p->group_lanes.resize(G);
+    p->group_chunks.resize(G);
+    for (int g = 0; g < G; ++g) {
+        // the group's internal indices (blocks are contiguous internal ranges), by cell
+        std::vector<int> idx;
+        for (int r = g; r < p->R; r += G)
+            for (int64_t m = p->offsets[r]; m < p->offsets[r + 1]; ++m) idx.push_back((int)m);
+        std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+            return std::make_pair(cy[a], cx[a]) < std::make_pair(cy[b], cx[b]);
+        });
+        std::vector<HostRun> runs;
+        const int64_t n = (int64_t)idx.size();
+        for (int64_t i = 0; i < n;) {
+            const int m0 = idx[i];
+            int64_t j = i + 1;
+            while (j < n && j - i < kRunMax && cx[idx[j]] == cx[m0] && cy[idx[j]] == cy[m0]) ++j;
+            runs.push_back({(cy[m0] << 16) | cx[m0], i, (int)(j - i)});
+            i = j;
+        }
+        std::stable_sort(runs.begin(), runs.end(), [](const HostRun& a, const HostRun& b) { return a.len > b.len; });
+        std::vector<RunRecF> rec((size_t)n);
+        std::vector<int> start(runs.size());
+        int64_t q = 0;
+        for (size_t r = 0; r < runs.size(); ++r) {
+            start[r] = (int)q;
+            for (int k = 0; k < runs[r].len; ++k) rec[q++] = rec_of[idx[runs[r].first + k]];
+        }
+        build_lanework(p, runs, rec, start, perm, 16, 0, p->group_lanes[g]);
+        // the group's visibility chunks (the plan's chunking, blocks of the group only)
+        const int64_t CH = 4096;
+        std::vector<int> cb, cs, ce, cf(p->R + 1, 0);
+        for (int r = 0; r < p->R; ++r) {
+            cf[r] = (int)cb.size();
+            if (r % G != g) continue;
+            for (int64_t a = p->offsets[r]; a < p->offsets[r + 1]; a += CH) {
+                cb.push_back(r);
+                cs.push_back((int)a);
+                ce.push_back((int)std::min(a + CH, p->offsets[r + 1]));
+            }
+        }
+        cf[p->R] = (int)cb.size();
+        GroupChunks& gc = p->group_chunks[g];
+        gc.n = (int)cb.size();
+        upload(gc.cblk, cb);
+        upload(gc.cbeg, cs);
+        upload(gc.cend, ce);
+        upload(gc.chunk_first, cf);
+    }
+    p->group_count = G;
+}
+
 static int64_t lane_bytes(const LaneWork& w) {
     return (int64_t)(w.set_info.bytes + w.run_cl.bytes + w.rec.bytes + w.idx.bytes + w.idx_caller.bytes);
 }

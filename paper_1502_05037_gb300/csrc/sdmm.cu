@@ -513,18 +513,39 @@ template <typename T> struct Solver {
         proj_norms(false);
     }
 
-    void proj_norms(bool with_z) {
+    void proj_norms(bool with_z, const GroupChunks* gc = nullptr) {
         Launch L(p, "proj_norms");
-        launch_dependent(k_proj_norms<T>, p->nchunks, RB, 0, p->stream, 
-            s.v2.template as<C>(), with_z ? s.z2.template as<C>() : nullptr, s.ybar.template as<C>(),
-            p->chunk_blk.as<int>(), p->chunk_beg.as<int>(), p->chunk_end.as<int>(), p->nchunks, p->R,
-            s.chunk_first.template as<int>(), proj_part(), ctr(), scal());
+        if (gc) {
+            launch_dependent(k_proj_norms<T>, gc->n, RB, 0, p->stream, s.v2.template as<C>(),
+                             with_z ? s.z2.template as<C>() : nullptr, s.ybar.template as<C>(), gc->cblk.as<int>(),
+                             gc->cbeg.as<int>(), gc->cend.as<int>(), gc->n, p->R, gc->chunk_first.as<int>(),
+                             proj_part(), ctr(), scal());
+        } else {
+            launch_dependent(k_proj_norms<T>, p->nchunks, RB, 0, p->stream,
+                s.v2.template as<C>(), with_z ? s.z2.template as<C>() : nullptr, s.ybar.template as<C>(),
+                p->chunk_blk.as<int>(), p->chunk_beg.as<int>(), p->chunk_end.as<int>(), p->nchunks, p->R,
+                s.chunk_first.template as<int>(), proj_part(), ctr(), scal());
+        }
+        L.done();
+    }
+
+    void proj_apply(int out_mode, const GroupChunks* gc = nullptr) {
+        Launch L(p, "proj_apply");
+        launch_dependent(k_proj_apply<T>, gc ? gc->n : p->nchunks, RB, 0, p->stream, s.v2.template as<C>(),
+                         s.z2.template as<C>(), s.ybar.template as<C>(),
+                         gc ? gc->cblk.as<int>() : p->chunk_blk.as<int>(),
+                         gc ? gc->cbeg.as<int>() : p->chunk_beg.as<int>(),
+                         gc ? gc->cend.as<int>() : p->chunk_end.as<int>(), s.eps.template as<double>(), scal(), p->R,
+                         out_mode);
         L.done();
     }
 
     // one SDMM iteration with exactly cg_iters CG steps (fewer only if the
-    // stop test fires, in which case the remaining kernels return at once)
-    void iteration(int cg_iters) {
+    // stop test fires, in which case the remaining kernels return at once);
+    // group >= 0: a block-subset iteration on that group of the s.groups
+    // groups (see sdmm_iteration_groups of the reading: the group's
+    // visibilities only, its data term scaled by the group count)
+    void iteration(int cg_iters, int group = -1) {
         T* x = s.x.template as<T>();
         const double inv_nu = 1.0 / s.nu;
         // The visibility branch (f2: Phi x, block projections, then the
@@ -547,19 +568,25 @@ template <typename T> struct Solver {
             p->stream = s.side;
         }
         try {
+            if (group >= 0) {
+                // the group's blocks: Phi_g x / nu, their projections, and
+                // r = G Re Phi_g^H v2 / nu
+                const LaneWork& lw = p->group_lanes[group];
+                const GroupChunks* gc = &p->group_chunks[group];
+                launch_scale_pad_rows(p, x, inv_nu, nullptr, true, true);
+                launch_cols_fwd(p, nullptr);
+                launch_lanes_on(p, lw, 2, nullptr, s.v2.p, false, nullptr, true);
+                proj_norms(true, gc);
+                proj_apply(0, gc);
+                launch_lanes_on(p, lw, 1, s.v2.p, nullptr, false, nullptr, true);
+                launch_cols_inv(p, nullptr);
+                launch_rows_inv_crop(p, s.r.p, inv_nu * s.groups, 1, nullptr, 1.0, nullptr);
+            } else {
             // f2 (the forward row pass also clears the gridding accumulator
             // of the adjoint below)
             launch_phi(p, x, s.v2.p, false, inv_nu, true);
             proj_norms(true);
-            {
-                Launch L(p, "proj_apply");
-                launch_dependent(k_proj_apply<T>, p->nchunks, RB, 0, p->stream, s.v2.template as<C>(), s.z2.template as<C>(),
-                                                                 s.ybar.template as<C>(), p->chunk_blk.as<int>(),
-                                                                 p->chunk_beg.as<int>(), p->chunk_end.as<int>(),
-                                                                 s.eps.template as<double>(), scal(), p->R,
-                                                                 s.toeplitz ? 1 : 0);
-                L.done();
-            }
+            proj_apply(s.toeplitz ? 1 : 0);
             // r = Re Phi^H v2 / nu (the image-space terms are added at the CG start)
             launch_phi_adj(p, s.v2.p, s.r.p, false, inv_nu, 1, nullptr, true);
             if (s.toeplitz) {
@@ -568,6 +595,7 @@ template <typename T> struct Solver {
                 launch_cols_fwd(p, nullptr);
                 launch_cols_inv(p, nullptr, s.toep.p);
                 launch_rows_inv_crop(p, s.r.p, -1.0, 1, s.r.p, 1.0, nullptr, nullptr, false);
+            }
             }
             if (fork) PURIFY_CUDA(cudaEventRecord(s.ev_join, s.side));
         } catch (...) {
@@ -624,11 +652,13 @@ template <typename T> struct Solver {
                 // the first FFT pass, then u = A r
                 launch_scale_pad_rows(p, nullptr, inv_nu, skip, true, true, &fold);
                 launch_cols_fwd(p, skip);
-                launch_normal_gg(p, skip, true);
+                if (group >= 0) launch_lanes_on(p, p->group_lanes[group], 0, nullptr, nullptr, false, skip, true);
+                else launch_normal_gg(p, skip, true);
                 launch_cols_inv(p, skip);
-                // u = 2 r + Re Phi^H Phi r / nu^2, with r.r, r.u and the CG
-                // scalars fused in
-                launch_rows_inv_crop(p, s.u.p, inv_nu, 1, s.r.p, 2.0, skip, &fold, true);
+                // u = 2 r + Re Phi^H Phi r / nu^2 (G Re Phi_g^H Phi_g r / nu^2
+                // for a group), with r.r, r.u and the CG scalars fused in
+                launch_rows_inv_crop(p, s.u.p, group >= 0 ? inv_nu * s.groups : inv_nu, 1, s.r.p, 2.0, skip, &fold,
+                                     true);
             }
         }
         // the last step's pending update is applied by the relative-change kernel
@@ -846,6 +876,91 @@ template <typename T> static void run_iterations(purify_plan* p, int n) {
     PURIFY_CUDA(cudaStreamWaitEvent(user, s.ev_out, 0));
 }
 
+// Block-subset iterations: iteration i runs group groups[i] (round-robin
+// from the iteration count when groups is null), each group's iteration a
+// replay of its own captured graph (captured on first use and whenever
+// gamma, nu, the weights, the CG count or the group count change); eager
+// when kernel timing is on.
+template <typename T> static void run_group_iterations(purify_plan* p, int n, const int32_t* groups) {
+    SdmmState& s = p->sd;
+    Solver<T> S(p);
+    if (n <= 0) return;
+    const int G = s.groups;
+    auto group_of = [&](int i) {
+        const int g = groups ? groups[i] : (int)((s.iters_done + i) % G);
+        if (g < 0 || g >= G) throw Error{PURIFY_EINVAL, "group index out of range"};
+        return g;
+    };
+    for (int i = 0; i < n; ++i) group_of(i);   // validate before any launch
+    if (timing_enabled(p)) {
+        for (int i = 0; i < n; ++i) S.iteration(s.cg_iters, group_of(i));
+        return;
+    }
+    if (!s.gstream) {
+        PURIFY_CUDA(cudaStreamCreateWithFlags(&s.gstream, cudaStreamNonBlocking));
+        PURIFY_CUDA(cudaEventCreateWithFlags(&s.ev_in, cudaEventDisableTiming));
+        PURIFY_CUDA(cudaEventCreateWithFlags(&s.ev_out, cudaEventDisableTiming));
+    }
+    if (s.gg_cg != s.cg_iters || s.gg_gamma != s.gamma || s.gg_nu != s.nu || s.gg_have_w != s.have_w ||
+        s.gg_groups != G || (int)s.gexec_group.size() != G) {
+        s.drop_group_graphs();
+        s.gexec_group.assign(G, nullptr);
+        s.kernels_group.assign(G, 0);
+        s.gg_cg = s.cg_iters;
+        s.gg_gamma = s.gamma;
+        s.gg_nu = s.nu;
+        s.gg_have_w = s.have_w;
+        s.gg_groups = G;
+    }
+    cudaStream_t user = p->stream;
+    PURIFY_CUDA(cudaEventRecord(s.ev_in, user));
+    PURIFY_CUDA(cudaStreamWaitEvent(s.gstream, s.ev_in, 0));
+    for (int i = 0; i < n; ++i) {
+        const int g = group_of(i);
+        if (!s.gexec_group[g]) {
+            p->stream = s.gstream;
+            try {
+                // this iteration eagerly (sets kernel attributes outside capture), then capture
+                S.iteration(s.cg_iters, g);
+                cudaGraph_t gr = nullptr;
+                PURIFY_CUDA(cudaStreamBeginCapture(s.gstream, cudaStreamCaptureModeThreadLocal));
+                try {
+                    S.iteration(s.cg_iters, g);
+                } catch (...) {
+                    cudaStreamEndCapture(s.gstream, &gr);
+                    if (gr) cudaGraphDestroy(gr);
+                    throw;
+                }
+                PURIFY_CUDA(cudaStreamEndCapture(s.gstream, &gr));
+                size_t nn = 0;
+                PURIFY_CUDA(cudaGraphGetNodes(gr, nullptr, &nn));
+                std::vector<cudaGraphNode_t> nodes(nn);
+                PURIFY_CUDA(cudaGraphGetNodes(gr, nodes.data(), &nn));
+                int64_t kn = 0;
+                for (auto nd : nodes) {
+                    cudaGraphNodeType t;
+                    PURIFY_CUDA(cudaGraphNodeGetType(nd, &t));
+                    if (t == cudaGraphNodeTypeKernel) ++kn;
+                }
+                cudaError_t ie = cudaGraphInstantiate(&s.gexec_group[g], gr, 0);
+                cudaGraphDestroy(gr);
+                if (ie != cudaSuccess) { s.gexec_group[g] = nullptr; PURIFY_CUDA(ie); }
+                s.kernels_group[g] = kn;
+                add_launches(-kn);
+            } catch (...) {
+                p->stream = user;
+                throw;
+            }
+            p->stream = user;
+            continue;   // this iteration ran eagerly
+        }
+        PURIFY_CUDA(cudaGraphLaunch(s.gexec_group[g], s.gstream));
+        add_launches(s.kernels_group[g]);
+    }
+    PURIFY_CUDA(cudaEventRecord(s.ev_out, s.gstream));
+    PURIFY_CUDA(cudaStreamWaitEvent(user, s.ev_out, 0));
+}
+
 // --------------------------------------------------------- batched plans
 void batch_destroy(BatchState* b) {
     if (!b) return;
@@ -963,8 +1078,13 @@ void batch_iterate(BatchState* b, int iters) {
     for (auto* p : b->plans) p->sd.iters_done += iters;
 }
 
-void sdmm_iterate(purify_plan* p, int iters) {
-    if (p->dtype == PURIFY_F32) run_iterations<float>(p, iters); else run_iterations<double>(p, iters);
+void sdmm_iterate(purify_plan* p, int iters, const int32_t* groups) {
+    if (p->sd.groups > 0) {
+        if (p->dtype == PURIFY_F32) run_group_iterations<float>(p, iters, groups);
+        else run_group_iterations<double>(p, iters, groups);
+    } else {
+        if (p->dtype == PURIFY_F32) run_iterations<float>(p, iters); else run_iterations<double>(p, iters);
+    }
     p->sd.iters_done += iters;
 }
 
@@ -1016,6 +1136,11 @@ static void sdmm_solve_t(purify_plan* p, const void* y, const double* eps, const
         }
         s.toeplitz = prm.toeplitz != 0;
         if (s.toeplitz) S.setup_toeplitz();
+        s.groups = prm.block_groups > 0 ? prm.block_groups : 0;
+        if (s.groups > 0) {
+            PURIFY_REQUIRE(!s.toeplitz, "block groups and the circulant normal operator cannot be combined");
+            build_group_lanes(p, s.groups);
+        }
         PURIFY_CUDA(cudaMemcpyAsync(s.x.p, x_io, sizeof(T) * p->N, cudaMemcpyDefault, p->stream));
         PURIFY_CUDA(cudaMemsetAsync(s.z1.p, 0, s.z1.bytes, p->stream));
         PURIFY_CUDA(cudaMemsetAsync(s.z2.p, 0, s.z2.bytes, p->stream));
@@ -1035,31 +1160,53 @@ static void sdmm_solve_t(purify_plan* p, const void* y, const double* eps, const
         PURIFY_CUDA(cudaMemcpyAsync(S.scal() + S_TOL2, &tol2, sizeof(double), cudaMemcpyHostToDevice, p->stream));
     }
     s.cg_iters = prm.cg_iters > 0 ? prm.cg_iters : 10;
+    if (prm.resume && prm.block_groups != (s.groups > 0 ? s.groups : 0))
+        throw Error{PURIFY_EINVAL, "a resumed solve keeps the block groups of its start"};
     const int check = prm.check_every > 0 ? prm.check_every : 10;
     const bool tol_mode = prm.rel_obj_tol > 0;
     int done = 0;
     purify_status status = PURIFY_OK;
     bool converged = false;
+    // n iterations from iteration `at` of this call (block groups from the
+    // caller's sequence)
+    auto run = [&](int n, int at) {
+        if (s.groups > 0) {
+            run_group_iterations<T>(p, n, prm.group_seq ? prm.group_seq + at : nullptr);
+            s.iters_done += n;
+        } else {
+            run_iterations<T>(p, n);
+            s.iters_done += n;
+        }
+    };
+    const int64_t iters0 = s.iters_done;
+    double prev_check_obj = -1.0;
     if (!tol_mode) {
-        run_iterations<T>(p, prm.max_iter);
+        run(prm.max_iter, 0);
         done = prm.max_iter;
     }
     for (int it = 0; tol_mode && it < prm.max_iter; it += check) {
         const int n = std::min(check, prm.max_iter - it);
-        run_iterations<T>(p, n);
+        run(n, it);
         done += n;
         {
+            // block groups: objective and residuals of every block at x, the
+            // change measured against the previous check
+            if (s.groups > 0) S.evaluate(s.x.template as<T>());
             std::vector<double> sc(S_BLOCKS + 2 * p->R);
             PURIFY_CUDA(cudaMemcpyAsync(sc.data(), S.scal(), sizeof(double) * sc.size(), cudaMemcpyDeviceToHost, p->stream));
             PURIFY_CUDA(cudaStreamSynchronize(p->stream));
             double obj = sc[S_OBJ], prev = sc[S_OBJ_PREV];
-            double rel = obj > 0 ? std::fabs(obj - prev) / obj : 0.0;
+            if (s.groups > 0) {
+                prev = prev_check_obj;
+                prev_check_obj = obj;
+            }
+            double rel = (obj > 0 && prev >= 0) ? std::fabs(obj - prev) / obj : (prev < 0 ? 1.0 : 0.0);
             double worst = 0.0;
             for (int r = 0; r < p->R; ++r) worst = std::max(worst, std::sqrt(sc[S_BLOCKS + p->R + r]) * s.nu / s.eps_host[r]);
             if (rel < prm.rel_obj_tol && worst <= 1.0 + prm.eps_tol) { converged = true; break; }
         }
     }
-    s.iters_done += done;
+    (void)iters0;
     // statistics at the returned x
     int fl[F_COUNT];
     PURIFY_CUDA(cudaMemcpyAsync(fl, S.flags(), sizeof(fl), cudaMemcpyDeviceToHost, p->stream));

@@ -20,6 +20,7 @@ generators stand in for the telescope data it motivates. Recipes:
 * block sizes: lognormal(sigma) draws normalised to M by largest-remainder
   rounding, each at least 1 (the contiguous partition of Eq. 2).
 * noise: complex samples (a + i b) / sqrt(2), a, b ~ N(0, 1).
+* block-group sequences: uniform draws from {0, ..., G-1}, one per iteration.
 
 Seeds follow one PCG64 stream per role: sky 1000 + c, uv 2000 + c,
 noise 3000 + c, blocks 4000 + c for workload index c.
@@ -134,6 +135,12 @@ def unit_noise(M: int, seed: int) -> np.ndarray:
     a = g.standard_normal(M)
     b = g.standard_normal(M)
     return (a + 1j * b) / np.sqrt(2.0)
+
+
+def group_sequence(n: int, G: int, seed: int) -> np.ndarray:
+    """n block-group indices drawn uniformly from {0, ..., G-1} (the group of
+    each iteration of a stochastic block-subset solve), int32."""
+    return rng(seed).integers(0, G, size=n).astype(np.int32)
 
 
 @dataclass

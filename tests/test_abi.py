@@ -61,6 +61,7 @@ int main(void) {
   P(purify_pd_params, tau) P(purify_pd_params, nu)
   P(purify_plan_desc, tile) P(purify_plan_desc, stream) P(purify_plan_desc, dtype) P(purify_plan_desc, block_offsets)
   P(purify_sdmm_params, resume) P(purify_sdmm_params, check_every) P(purify_sdmm_params, toeplitz) P(purify_sdmm_stats, status)
+  P(purify_sdmm_params, block_groups) P(purify_sdmm_params, group_seq)
   P(purify_plan_info, workspace_bytes) P(purify_plan_info, beta) P(purify_plan_info, grid_mode)
   P(purify_plan_info, lane_tile)
   P(purify_plan_desc, grid_mode)
@@ -77,6 +78,8 @@ int main(void) {
     assert int(got["desc"]) == ctypes.sizeof(_lib.purify_plan_desc)
     assert int(got["info"]) == ctypes.sizeof(_lib.purify_plan_info)
     assert int(got["params"]) == ctypes.sizeof(_lib.purify_sdmm_params)
+    assert int(got["purify_sdmm_params.block_groups"]) == _lib.purify_sdmm_params.block_groups.offset
+    assert int(got["purify_sdmm_params.group_seq"]) == _lib.purify_sdmm_params.group_seq.offset
     assert int(got["stats"]) == ctypes.sizeof(_lib.purify_sdmm_stats)
     assert int(got["ktime"]) == ctypes.sizeof(_lib.purify_kernel_time)
     assert int(got["pd"]) == ctypes.sizeof(_lib.purify_pd_params)
