@@ -224,6 +224,35 @@ purify_status purify_sdmm_iterate(purify_plan *plan, int32_t iters);
  * Errors: EINVAL (no started solve, group out of range). */
 purify_status purify_sdmm_iterate_groups(purify_plan *plan, int32_t iters, const int32_t *groups);
 
+/* Block-sharded SDMM (Sec. 1: the block split of Eqs. 2-3 and SDMM's parallel
+ * structure): each shard (a process, a GPU, or several plans of one process)
+ * holds a plan over its own blocks of the data, y_k, eps_k, and the shards run
+ * the same iteration on replicated x, wavelet and positivity state. The only
+ * data exchanged are N-pixel images, summed over the shards by the caller
+ * (for example an NCCL all-reduce) at two points:
+ *   per iteration:  purify_shard_iterate_local(r_out)  -> sum r over shards ->
+ *                   purify_shard_cg_begin(r_sum);
+ *   per CG step k:  purify_shard_cg_apply(k, u_out)     -> sum u over shards ->
+ *                   purify_shard_cg_combine(k, u_sum);
+ *   then            purify_shard_iterate_end(cg_steps).
+ * r_out = Re Phi_k^H (s2_k - z2_k - Phi_k x / nu) / nu (this shard's blocks, after
+ * their projections and multiplier updates); u_out = Re Phi_k^H Phi_k r / nu^2 for
+ * the current CG residual r (after step k - 1's update); cg_combine forms
+ * u = 2 r + u_sum, the dot products and the step's scalars, identically on every
+ * shard. With one shard the sequence is one iteration of purify_sdmm_solve.
+ * Start every shard with purify_sdmm_solve(max_iter = 0) on its own y_k and eps_k
+ * with the SAME gamma, nu (> 0) and x, w on all shards; read statistics with
+ * purify_sdmm_solve(resume = 1, max_iter = 0) (objective: any shard; residual
+ * ratio: max over shards). All images are DEVICE [ny][nx] real (dtype), owned by
+ * the caller; calls are asynchronous on the plan's stream. Not with
+ * block_groups or toeplitz. Errors: EINVAL (no started solve, host pointer,
+ * negative step), ECUDA. */
+purify_status purify_shard_iterate_local(purify_plan *plan, void *r_out);
+purify_status purify_shard_cg_begin(purify_plan *plan, const void *r_sum);
+purify_status purify_shard_cg_apply(purify_plan *plan, int32_t step, void *u_out);
+purify_status purify_shard_cg_combine(purify_plan *plan, int32_t step, const void *u_sum);
+purify_status purify_shard_iterate_end(purify_plan *plan, int32_t cg_steps);
+
 /* Primal-dual solver for problem (3) without an inner CG (the paper's SDMM
  * family; Chambolle & Pock 2011, Algorithm 1 with theta = 1) on
  *   min_x  i_{R_+^N}(x) + ||W v||_1 + sum_i i_{B(y_i/nu, eps_i/nu)}(s_i),

@@ -111,6 +111,11 @@ _SIGS = {
                                     C.POINTER(purify_sdmm_params), C.POINTER(purify_sdmm_stats)]),
     "purify_sdmm_iterate": (C.c_int, [_P, C.c_int32]),
     "purify_sdmm_iterate_groups": (C.c_int, [_P, C.c_int32, C.POINTER(C.c_int32)]),
+    "purify_shard_iterate_local": (C.c_int, [_P, _P]),
+    "purify_shard_cg_begin": (C.c_int, [_P, _P]),
+    "purify_shard_cg_apply": (C.c_int, [_P, C.c_int32, _P]),
+    "purify_shard_cg_combine": (C.c_int, [_P, C.c_int32, _P]),
+    "purify_shard_iterate_end": (C.c_int, [_P, C.c_int32]),
     "purify_pd_solve": (C.c_int, [_P, _P, C.POINTER(C.c_double), _P, _P,
                                   C.POINTER(purify_pd_params), C.POINTER(purify_sdmm_stats)]),
     "purify_batch_create": (C.c_int, [C.POINTER(_P), C.c_int32, _P, C.POINTER(_P)]),

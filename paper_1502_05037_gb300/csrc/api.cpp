@@ -296,6 +296,41 @@ purify_status purify_sdmm_iterate_groups(purify_plan* p, int32_t iters, const in
     });
 }
 
+purify_status purify_shard_iterate_local(purify_plan* p, void* r_out) {
+    return guarded([&] {
+        PURIFY_REQUIRE(p != nullptr, "null plan");
+        shard_step(p, 0, 0, r_out);
+    });
+}
+
+purify_status purify_shard_cg_begin(purify_plan* p, const void* r_sum) {
+    return guarded([&] {
+        PURIFY_REQUIRE(p != nullptr, "null plan");
+        shard_step(p, 1, 0, const_cast<void*>(r_sum));
+    });
+}
+
+purify_status purify_shard_cg_apply(purify_plan* p, int32_t step, void* u_out) {
+    return guarded([&] {
+        PURIFY_REQUIRE(p != nullptr, "null plan");
+        shard_step(p, 2, step, u_out);
+    });
+}
+
+purify_status purify_shard_cg_combine(purify_plan* p, int32_t step, const void* u_sum) {
+    return guarded([&] {
+        PURIFY_REQUIRE(p != nullptr, "null plan");
+        shard_step(p, 3, step, const_cast<void*>(u_sum));
+    });
+}
+
+purify_status purify_shard_iterate_end(purify_plan* p, int32_t cg_steps) {
+    return guarded([&] {
+        PURIFY_REQUIRE(p != nullptr, "null plan");
+        shard_step(p, 4, cg_steps, nullptr);
+    });
+}
+
 struct purify_batch {
     purify::BatchState* st;
 };

@@ -346,6 +346,10 @@ struct BatchState {
 void batch_iterate(BatchState* b, int iters);
 void batch_destroy(BatchState* b);
 void sdmm_iterate(purify_plan* p, int iters, const int32_t* groups = nullptr);
+// block-sharded SDMM steps: op 0 local terms (adjoint term out), 1 summed
+// adjoint term in, 2 CG apply (this shard's normal operator out), 3 CG
+// combine (summed normal operator in), 4 end of iteration (step = CG steps)
+void shard_step(purify_plan* p, int op, int step, void* ptr);
 void pd_solve(purify_plan* p, const void* y, const double* eps, const void* w, void* x,
               const purify_pd_params& prm, purify_sdmm_stats* st);
 void add_launches(int64_t n);

@@ -346,6 +346,37 @@ __global__ void k_fill_one(typename cplx_of<T>::type* __restrict__ y, int64_t n)
         y[t] = cmake<typename cplx_of<T>::type>(T(1), T(0));
 }
 
+// Block-sharded CG: u = 2 r + u_sum (u_sum the sum over the shards of
+// Re Phi_k^H Phi_k r / nu^2), per-block partials of r.r and r.u, and the
+// step's scalars decided by the last block (cg_decide). Returns at once when
+// the solve already stopped.
+template <typename T>
+__global__ void k_cg_combine(const T* __restrict__ u_sum, int64_t N, CgFold fold) {
+    pdl_wait();
+    if (block_flag(fold.flags + F_CGDONE)) return;
+    const T* r = static_cast<const T*>(fold.r);
+    T* u = static_cast<T*>(const_cast<void*>(fold.u));
+    T g = 0, d = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const T rv = r[i];
+        const T uv = T(2) * rv + u_sum[i];
+        u[i] = uv;
+        g += rv * rv;
+        d += rv * uv;
+    }
+    const double b0 = block_sum_t(g);
+    const double b1 = block_sum_t(d);
+    if (threadIdx.x == 0) {
+        fold.part[2 * blockIdx.x] = b0;
+        fold.part[2 * blockIdx.x + 1] = b1;
+    }
+    if (arrive_last(fold.counter)) {
+        cg_decide(fold, fold.step, gridDim.x);
+        if (threadIdx.x == 0) *fold.counter = 0;
+    }
+    pdl_trigger();
+}
+
 // -------------------------------------------------------------- host side
 static int ew_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 16)); }
 
@@ -546,6 +577,15 @@ template <typename T> struct Solver {
     // groups (see sdmm_iteration_groups of the reading: the group's
     // visibilities only, its data term scaled by the group count)
     void iteration(int cg_iters, int group = -1) {
+        local_terms(group);
+        cg_solve(cg_iters, group);
+    }
+
+    // The x-update's terms of one iteration: f1, f2 (all blocks, or the
+    // group's) and f3 with their multiplier updates, leaving the adjoint term
+    // Re Phi^H (s2 - z2 - Phi x / nu) / nu in r and the image-space terms
+    // Psi (s1 - z1) + (s3 - z3) - 2 x in addend.
+    void local_terms(int group) {
         T* x = s.x.template as<T>();
         const double inv_nu = 1.0 / s.nu;
         // The visibility branch (f2: Phi x, block projections, then the
@@ -622,14 +662,11 @@ template <typename T> struct Solver {
             L.done();
         }
         if (fork) PURIFY_CUDA(cudaStreamWaitEvent(p->stream, s.ev_join, 0));
-        const int* skip = flags() + F_CGDONE;
-        // CG (Chronopoulos-Gear arrangement, see CgFold): the forward row pass
-        // of step 0 adds the image-space terms to r and starts the solve; step
-        // k applies the operator to r; the update of step k is applied by the
-        // forward row pass of step k + 1 or, after the last step, by the
-        // relative-change kernel
+    }
+
+    CgFold make_fold() {
         CgFold fold;
-        fold.x = x;
+        fold.x = s.x.p;
         fold.r = s.r.p;
         fold.p = s.p.p;
         fold.s = s.Ap.p;
@@ -639,6 +676,20 @@ template <typename T> struct Solver {
         fold.counter = ctr() + C_CGI;
         fold.scal = scal();
         fold.flags = flags();
+        return fold;
+    }
+
+    // The CG x-update from the terms local_terms left, then the relative change.
+    void cg_solve(int cg_iters, int group) {
+        T* x = s.x.template as<T>();
+        const double inv_nu = 1.0 / s.nu;
+        const int* skip = flags() + F_CGDONE;
+        // CG (Chronopoulos-Gear arrangement, see CgFold): the forward row pass
+        // of step 0 adds the image-space terms to r and starts the solve; step
+        // k applies the operator to r; the update of step k is applied by the
+        // forward row pass of step k + 1 or, after the last step, by the
+        // relative-change kernel
+        CgFold fold = make_fold();
         for (int k = 0; k < cg_iters; ++k) {
             fold.step = k;
             if (s.toeplitz) {
@@ -662,14 +713,44 @@ template <typename T> struct Solver {
             }
         }
         // the last step's pending update is applied by the relative-change kernel
+        finish(cg_iters);
+    }
+
+    // The last CG step's pending update and the relative change of x.
+    void finish(int cg_iters) {
+        CgFold fold = make_fold();
         fold.step = cg_iters - 1;
         if (cg_iters == 0) fold = CgFold();   // no CG step ran: nothing pending
-        {
-            Launch L(p, "relchange");
-            launch_dependent(k_relchange<T>, red_blocks(p->N), RB, 0, p->stream, x, s.xprev.template as<T>(), p->N,
-                             part(), ctr(), scal(), fold);
-            L.done();
-        }
+        Launch L(p, "relchange");
+        launch_dependent(k_relchange<T>, red_blocks(p->N), RB, 0, p->stream, s.x.template as<T>(),
+                         s.xprev.template as<T>(), p->N, part(), ctr(), scal(), fold);
+        L.done();
+    }
+
+    // Block-sharded CG step k (see purify_shard_cg_apply): the pending update
+    // and the transform of the new r, then this shard's Re Phi^H Phi r / nu^2
+    // alone into u_out (no 2 r, no dot products).
+    void shard_cg_apply(int k, void* u_out) {
+        const double inv_nu = 1.0 / s.nu;
+        const int* skip = flags() + F_CGDONE;
+        CgFold fold = make_fold();
+        fold.step = k;
+        launch_scale_pad_rows(p, nullptr, inv_nu, skip, true, true, &fold);
+        launch_cols_fwd(p, skip);
+        launch_normal_gg(p, skip, true);
+        launch_cols_inv(p, skip);
+        launch_rows_inv_crop(p, u_out, inv_nu, 1, nullptr, 0.0, skip, nullptr, true);
+    }
+
+    // Block-sharded CG step k, after the exchange: u = 2 r + u_sum, the dot
+    // products r.r and r.u, and the step's scalars (cg_decide).
+    void shard_cg_combine(int k, const void* u_sum) {
+        CgFold fold = make_fold();
+        fold.step = k;
+        const int nb = red_blocks(p->N);
+        Launch L(p, "cg_combine");
+        launch_dependent(k_cg_combine<T>, nb, RB, 0, p->stream, (const T*)u_sum, p->N, fold);
+        L.done();
     }
 };
 
@@ -959,6 +1040,39 @@ template <typename T> static void run_group_iterations(purify_plan* p, int n, co
     }
     PURIFY_CUDA(cudaEventRecord(s.ev_out, s.gstream));
     PURIFY_CUDA(cudaStreamWaitEvent(user, s.ev_out, 0));
+}
+
+// ------------------------------------------------- block-sharded steps
+template <typename T> static void shard_step_t(purify_plan* p, int op, int step, void* ptr) {
+    Solver<T> S(p);
+    SdmmState& s = p->sd;
+    const size_t bytes = sizeof(T) * (size_t)p->N;
+    switch (op) {
+        case 0:   // this shard's x-update terms; its adjoint term out
+            S.local_terms(-1);
+            PURIFY_CUDA(cudaMemcpyAsync(ptr, s.r.p, bytes, cudaMemcpyDeviceToDevice, p->stream));
+            break;
+        case 1:   // the summed adjoint term in
+            PURIFY_CUDA(cudaMemcpyAsync(s.r.p, ptr, bytes, cudaMemcpyDeviceToDevice, p->stream));
+            break;
+        case 2: S.shard_cg_apply(step, ptr); break;
+        case 3: S.shard_cg_combine(step, ptr); break;
+        default:  // 4: the last pending update and the relative change
+            S.finish(step);
+            s.iters_done += 1;
+            break;
+    }
+}
+
+void shard_step(purify_plan* p, int op, int step, void* ptr) {
+    SdmmState& s = p->sd;
+    if (!s.started) throw Error{PURIFY_EINVAL, "no SDMM solve started on this plan"};
+    if (s.groups > 0 || s.toeplitz)
+        throw Error{PURIFY_EINVAL, "block-sharded steps need a solve without block groups or toeplitz"};
+    if (op != 4 && (ptr == nullptr || is_host_pointer(ptr))) throw Error{PURIFY_EINVAL, "a device image is required"};
+    if ((op == 2 || op == 3) && step < 0) throw Error{PURIFY_EINVAL, "negative CG step"};
+    if (op == 4 && step < 0) throw Error{PURIFY_EINVAL, "negative CG step count"};
+    if (p->dtype == PURIFY_F32) shard_step_t<float>(p, op, step, ptr); else shard_step_t<double>(p, op, step, ptr);
 }
 
 // --------------------------------------------------------- batched plans

@@ -112,3 +112,58 @@ def test_block_sharded_iterations_equal_the_unsharded_ones():
         assert np.allclose(z2_own, ref.z2[idx], rtol=0, atol=1e-12 * np.abs(ref.z2).max())
     # the two ranks' blocks partition the visibilities
     assert sorted(np.concatenate([out[0][2], out[1][2]]).tolist()) == list(range(prob.plan.M))
+
+
+# ------------------------------------------- the library's shard driver
+def _driver_rank_main(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_1502_05037_gb300 import sharded
+        from shard_oracle import OracleShard
+        prob = _problem()
+        shard = OracleShard(prob, sharded.shard_blocks(prob.R, world, rank))
+        drv = sharded.ShardedSdmm([shard], sharded.all_reduce_images, cg_iters=6)
+        drv.iterate(2)
+        out[rank] = (shard.x, shard.z2[shard.own], np.flatnonzero(shard.own), drv.exchanges)
+        dist.barrier()
+    finally:
+        dist.destroy_process_group()
+
+
+def test_shard_driver_on_two_gloo_ranks_equals_the_unsharded_solve():
+    # the host orchestration of purify_shard_* (the exchange points, their
+    # order and the round-robin block assignment), each rank's steps computed
+    # by the oracle, against the unsharded oracle SDMM
+    from oracle import sdmm
+    world = 2
+    mgr = mp.Manager()
+    out = mgr.dict()
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    mp.spawn(_driver_rank_main, args=(world, _free_port(), out), nprocs=world, join=True)
+    prob = _problem()
+    ref = sdmm.sdmm_solve(prob, np.zeros((prob.plan.ny, prob.plan.nx)), 2, 6)
+    scale = np.linalg.norm(ref.x)
+    for r in range(world):
+        x, z2_own, idx, nex = out[r]
+        assert np.linalg.norm(x - ref.x) <= 1e-9 * scale
+        assert np.allclose(z2_own, ref.z2[idx], rtol=0, atol=1e-11 * np.abs(ref.z2).max())
+        assert nex == 2 * (1 + 6)     # one adjoint and one normal-operator exchange per CG step
+    assert sorted(np.concatenate([out[0][2], out[1][2]]).tolist()) == list(range(prob.plan.M))
+
+
+def test_shard_driver_in_one_process_equals_the_unsharded_solve():
+    # three shards driven by one process (sum_in_place as the all-reduce)
+    from oracle import sdmm
+    from paper_1502_05037_gb300 import sharded
+    sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
+    from shard_oracle import OracleShard
+    prob = _problem()
+    shards = [OracleShard(prob, sharded.shard_blocks(prob.R, 3, k)) for k in range(3)]
+    sharded.ShardedSdmm(shards, sharded.sum_in_place, cg_iters=6).iterate(2)
+    ref = sdmm.sdmm_solve(prob, np.zeros((prob.plan.ny, prob.plan.nx)), 2, 6)
+    for sh in shards:
+        assert np.linalg.norm(sh.x - ref.x) <= 1e-9 * np.linalg.norm(ref.x)
+    idx, offs = sharded.shard_visibilities(prob.offsets, [1, 3])
+    assert offs[-1] == idx.size and np.array_equal(idx[:3], np.arange(prob.offsets[1], prob.offsets[1] + 3))
