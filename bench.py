@@ -922,6 +922,103 @@ def run_channels(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sharded(args):
+    """Block-sharded SDMM (strong scaling): under torchrun each rank holds the
+    blocks i = rank mod N of the workload on its GPU; x and the wavelet state
+    are replicated; the two N-pixel exchanges per iteration and per CG step
+    are NCCL all-reduces. Timed like the headline: W warm-up then K
+    iterations bracketed by CUDA events, the max over ranks."""
+    import torch
+
+    import paper_1502_05037_gb300 as pk
+    from paper_1502_05037_gb300 import build as pbuild
+    from paper_1502_05037_gb300 import sharded, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    pbuild.build()
+    wl = synth.WORKLOADS[args.workload]
+    x_true, u, v, offs, nz = wl.draw()
+    stream = torch.cuda.current_stream(dev)
+    # the unsharded constants: nu by power iteration over all shards, gamma
+    # from the summed dirty image (both through the exchange)
+    blocks = sharded.shard_blocks(wl.R, world, rank)
+    idx, loffs = sharded.shard_visibilities(offs, blocks)
+    plan = pk.Plan(wl.nx, wl.ny, torch.from_numpy(u[idx]).to(dev), torch.from_numpy(v[idx]).to(dev), kb_width=wl.J,
+                   levels=wl.levels, block_offsets=loffs, stream=stream)
+    allreduce = sharded.all_reduce_images if dist is not None else sharded.sum_in_place
+    xt = torch.from_numpy(x_true.astype(np.float32)).to(dev)
+    y0 = torch.empty(idx.size, dtype=torch.complex64, device=dev)
+    pk.purify_phi(plan, xt, y0)
+    ysq = torch.tensor([float(torch.linalg.vector_norm(y0.to(torch.complex128)) ** 2)], dtype=torch.float64,
+                       device=dev)
+    if dist is not None:
+        dist.all_reduce(ysq)
+    from paper_1502_05037_gb300 import problem
+    sigma = problem.noise_sigma_from_norm(float(ysq.sqrt().item()), wl.M, wl.snr_db)
+    y = y0 + torch.from_numpy((sigma * nz[idx]).astype(np.complex64)).to(dev)
+    eps = problem.chi2_epsilon(sigma, np.diff(offs))[blocks]
+    # nu: power iteration on the summed normal operator
+    g = torch.Generator(device="cpu").manual_seed(7)
+    w = torch.randn((wl.ny, wl.nx), generator=g, dtype=torch.float32).to(dev)
+    w /= torch.linalg.vector_norm(w)
+    out = torch.empty_like(w)
+    lam = 0.0
+    for _ in range(30):
+        pk.purify_phi_normal(plan, w, out)
+        allreduce([out])
+        lam = float(torch.linalg.vector_norm(out.double()).item())
+        w = out / lam
+    nu = float(np.sqrt(lam))
+    dirty = torch.empty((wl.ny, wl.nx), dtype=torch.complex64, device=dev)
+    pk.purify_phi_adj(plan, y, dirty)
+    dr = dirty.real.contiguous()
+    allreduce([dr])
+    c = torch.empty((plan.info.q, wl.ny, wl.nx), dtype=torch.float32, device=dev)
+    pk.purify_psi_adj(plan, dr, c)
+    gamma = 1e-3 * float(c.abs().max().item()) / nu ** 2
+    x0 = torch.zeros((wl.ny, wl.nx), dtype=torch.float32, device=dev)
+    pk.purify_sdmm_solve(plan, y, eps, x0, max_iter=0, cg_iters=args.cg_iters, gamma=gamma, nu=nu)
+    drv = sharded.ShardedSdmm([sharded.LibraryShard(plan, dev, torch.float32)], allreduce, args.cg_iters)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for i in range(args.warmup):
+        drv.iterate(1)
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    evs = []
+    with ClockSampler(dev.index or 0) as clk:
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            drv.iterate(1)
+            b.record(stream)
+            evs.append((a, b))
+        torch.cuda.synchronize(dev)
+    total = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dist, dev)
+    if rank == 0:
+        line = {"metric": "SDMM iters/s (block-sharded)", "value": args.steps / (total / 1e3), "unit": "iters/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
+                "higher_is_better": True, "scaling": "strong", "dtype": "f32", "data": "synthetic",
+                "config": {"workload": describe(wl), "cg_iters": args.cg_iters,
+                           "parallelism": f"blocks round-robin over {world} shards, NCCL all-reduce of N-pixel "
+                                          f"images ({1 + args.cg_iters} per iteration)"},
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def run_groups(args):
     """Time to tolerance of the stochastic block-subset SDMM (G groups, one
     drawn per iteration) against plain SDMM on the same problem: wall time
@@ -1101,6 +1198,8 @@ def main():
     ap.add_argument("--channels32", action="store_true",
                     help="batched independent 512x512 channel problems (one graph per iteration)")
     ap.add_argument("--channels", type=int, default=32)
+    ap.add_argument("--shard-blocks", action="store_true",
+                    help="block-sharded SDMM over the ranks (strong scaling; NCCL all-reduce of images)")
     ap.add_argument("--groups", action="store_true",
                     help="time-to-tolerance of the stochastic block-subset SDMM versus plain SDMM")
     ap.add_argument("--groups-list", type=int, nargs="*", default=[2, 4, 8])
@@ -1123,6 +1222,8 @@ def main():
         run_channels(args)
     elif args.groups:
         run_groups(args)
+    elif args.shard_blocks:
+        run_sharded(args)
     elif args.warmstart:
         run_warmstart(args)
     elif args.profile_op:

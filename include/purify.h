@@ -325,16 +325,17 @@ purify_status purify_coef_std(purify_plan *plan, const void *x, double *std_out)
  *   nx, ny, levels, basis_mask  as in purify_plan_desc (mask 0 => 0x1FF)
  *   stream  cudaStream_t (NULL = legacy default stream)
  * No plan is needed and nothing is allocated: the wavelet low-pass scratch
- * is a 4 MiB file-scope device array that every GPU loading the library
- * keeps until the process exits. Sizes whose scratch exceeds it are rejected
- * with EINVAL: it needs 256 + 2 * (number of wavelet bases) * (nx*ny/4) *
- * sizeof(dtype) bytes, e.g. up to 512 x 512 in FP64 or 512 x 1024 in FP32
- * with all eight wavelets. The first call on each device looks up the
- * array's device address and uploads the constant filter tables (both
- * synchronous), so make that first call before any stream capture. All
- * calls share the one array and it keeps the previous call's contents;
- * calls that may overlap on the GPU (different streams, or different host
- * threads) race on it and must be ordered by the caller.
+ * is a 4 MiB file-scope device array, and the basis table a 64-byte one,
+ * that every GPU loading the library keeps until the process exits. Sizes
+ * whose scratch exceeds the array are rejected with EINVAL: it needs
+ * (number of wavelet bases) * (nx*ny/4 + nx*ny/16) * sizeof(dtype) bytes,
+ * e.g. up to 512 x 512 in FP32 or 512 x 256 in FP64 with all eight
+ * wavelets. The first call on each device looks up the arrays' device
+ * addresses and uploads the constant filter tables (both synchronous), so
+ * make that first call before any stream capture. All calls share the one
+ * array and it keeps the previous call's contents; calls that may overlap on
+ * the GPU (different streams, or different host threads) race on it and must
+ * be ordered by the caller.
  * Errors: EINVAL (sizes, host pointers), ECUDA. */
 purify_status purify_psi_adj_static(const void *x, void *c, int32_t nx, int32_t ny, int32_t levels,
                                     uint32_t basis_mask, purify_dtype dtype, void *stream);

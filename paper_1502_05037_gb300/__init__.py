@@ -236,7 +236,21 @@ def purify_coef_std(plan: Plan, x) -> float:
 def purify_psi_adj_static(x, c, nx: int, ny: int, levels: int, basis_mask: int = 0, dtype: int = PURIFY_F32,
                           stream=None):
     """Psi^dagger without a plan and without any device allocation (device
-    pointers only; see include/purify.h for the size limit and sharing)."""
+    pointers only; see include/purify.h for the size limit and sharing).
+    The C side cannot see buffer sizes, so they are checked here: x holds
+    nx * ny and c q * nx * ny values of `dtype`, q the number of bases."""
+    mask = basis_mask if basis_mask else 0x1FF
+    q = bin(mask & 0x1FF).count("1")
+    itemsize = 4 if dtype == PURIFY_F32 else 8
+    for name, a, n in (("x", x, nx * ny), ("c", c, q * nx * ny)):
+        if hasattr(a, "numel"):
+            size, isz = a.numel(), a.element_size()
+            floating = a.is_floating_point()
+        else:
+            arr = np.asarray(a)
+            size, isz, floating = arr.size, arr.itemsize, arr.dtype.kind == "f"
+        if size != n or isz != itemsize or not floating:
+            raise ValueError(f"{name} must hold {n} {'float32' if itemsize == 4 else 'float64'} values")
     check(load().purify_psi_adj_static(_ptr(x), _ptr(c), nx, ny, levels, basis_mask, dtype, _stream_ptr(stream)))
 
 

@@ -345,11 +345,14 @@ static const int* pid_array(const purify_plan* p) { return p->wmeta.as<int>(); }
 static const int* plane_array(const purify_plan* p) { return p->wmeta.as<int>() + 8; }
 
 static bool g_bank_ready[64];
+static std::mutex g_bank_mutex;
 
 void init_filter_banks() {
     int dev = 0;
     PURIFY_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) throw Error{PURIFY_ECUDA, "device index out of range"};
+    // one upload per device, also when several host threads make their first call at once
+    std::lock_guard<std::mutex> lock(g_bank_mutex);
     if (g_bank_ready[dev]) return;
     FilterBank<float> bf;
     FilterBank<double> bd;
@@ -479,29 +482,40 @@ void launch_psi(purify_plan* p, const void* c, void* x) {
 namespace purify {
 
 static const size_t kStaticScratchBytes = size_t(4) << 20;  // 4 MiB
+// The two low-pass buffers: level 0 writes nw N / 4 values into the first,
+// level 1 nw N / 16 into the second, deeper levels alternate and need less.
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+// the basis table of the current mask (pids, then coefficient planes)
+static __device__ __align__(16) int g_static_meta[16];
 
-// Host code cannot use g_static_scratch's name as a device address: its
-// device address is looked up once per device (with that device current).
+// Host code cannot use the arrays' names as device addresses: their device
+// addresses are looked up once per device (with that device current).
 static std::mutex g_static_mutex;
 static void* g_static_addr[64];
+static void* g_static_meta_addr[64];
 
-static void* static_scratch_address() {
+static void* symbol_address(const void* symbol, const char* what) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, symbol);
+    if (e != cudaSuccess || ptr == nullptr) {
+        cudaGetLastError();
+        throw Error{PURIFY_ECUDA, std::string("cudaGetSymbolAddress of the ") + what + " failed: " +
+                                      cudaGetErrorString(e)};
+    }
+    return ptr;
+}
+
+static void static_addresses(void** scratch, int** meta) {
     int dev = 0;
     PURIFY_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) throw Error{PURIFY_ECUDA, "device index out of range"};
     std::lock_guard<std::mutex> lock(g_static_mutex);
     if (!g_static_addr[dev]) {
-        void* ptr = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
-        if (e != cudaSuccess || ptr == nullptr) {
-            cudaGetLastError();
-            throw Error{PURIFY_ECUDA, std::string("cudaGetSymbolAddress of the static scratch failed: ") +
-                                          cudaGetErrorString(e)};
-        }
-        g_static_addr[dev] = ptr;
+        g_static_meta_addr[dev] = symbol_address(g_static_meta, "static basis table");
+        g_static_addr[dev] = symbol_address(g_static_scratch, "static scratch");
     }
-    return g_static_addr[dev];
+    *scratch = g_static_addr[dev];
+    *meta = static_cast<int*>(g_static_meta_addr[dev]);
 }
 
 // Basis table of a mask: pids[z] = db index of wavelet z, planes[z] = its
@@ -522,15 +536,16 @@ size_t psi_adj_static_bytes(int nx, int ny, unsigned mask, int dtype) {
     for (int b = 1; b < 9; ++b) nw += (mask >> b & 1);
     size_t rb = dtype == PURIFY_F32 ? 4 : 8;
     size_t N = (size_t)nx * ny;
-    return 256 + 2 * (size_t)nw * (N / 4) * rb;
+    return (size_t)nw * (N / 4 + N / 16) * rb;
 }
 
 size_t psi_adj_static_capacity() { return kStaticScratchBytes; }
 
 template <typename T>
 static void psi_adj_static_t(const T* x, T* c, int nx, int ny, int levels, unsigned mask, cudaStream_t st) {
-    unsigned char* base = static_cast<unsigned char*>(static_scratch_address());
-    int* meta = reinterpret_cast<int*>(base);
+    void* scratch = nullptr;
+    int* meta = nullptr;
+    static_addresses(&scratch, &meta);
     const size_t N = (size_t)nx * ny;
     int nw = 0, q = 0, dirac_plane = -1;
     for (int b = 0; b < 9; ++b) {
@@ -538,7 +553,9 @@ static void psi_adj_static_t(const T* x, T* c, int nx, int ny, int levels, unsig
         if (b == 0) dirac_plane = q; else ++nw;
         ++q;
     }
-    T* bufs[2] = {reinterpret_cast<T*>(base + 256), reinterpret_cast<T*>(base + 256) + (size_t)nw * (N / 4)};
+    // per-basis strides: N / 4 in the first buffer, N / 16 in the second
+    T* bufs[2] = {static_cast<T*>(scratch), static_cast<T*>(scratch) + (size_t)nw * (N / 4)};
+    const int strides[2] = {(int)(N / 4), (int)(N / 16)};
     int maxL = 2;
     for (int b = 1; b < 9; ++b) if (mask >> b & 1) maxL = std::max(maxL, 2 * b);
     const T inv_sqrt_q = (T)(1.0 / std::sqrt((double)q));
@@ -558,7 +575,6 @@ static void psi_adj_static_t(const T* x, T* c, int nx, int ny, int levels, unsig
     int h = ny, w = nx;
     const T* src = x;
     int src_stride = 0, src_ld = nx;
-    const int llstride = (int)(N / 4);
     for (int lev = 0; lev < levels; ++lev) {
         const bool last = lev == levels - 1;
         const int hs = h / 2, wsub = w / 2;
@@ -567,6 +583,7 @@ static void psi_adj_static_t(const T* x, T* c, int nx, int ny, int levels, unsig
         int zdim = nw + ((lev == 0 && dirac_plane >= 0) ? 1 : 0);
         dim3 g((wsub + TW - 1) / TW, (hs + TH - 1) / TH, zdim);
         T* llo = last ? nullptr : bufs[lev & 1];
+        const int llstride = strides[lev & 1];
         launch_dependent(k_dwt_level<T>, g, 256, sm, st, src, src_stride, src_ld, c, planes, (int)N, nx, llo, llstride, h, w, TH,
                                            TW, pids, nw, dirac_plane, inv_sqrt_q);
         PURIFY_CUDA(cudaGetLastError());
