@@ -458,7 +458,8 @@ def run_ours(args):
     kernel_table = kernel_rates(ktimes, plan.info, args.steps, dtb, wl.levels)
     inf = plan.info
     decomposition = {"grid": inf.grid_mode, "degrid": inf.degrid_mode, "normal": inf.normal_mode,
-                     "lane_tile": inf.lane_tile, "legend": "1 tile subproblems, 2 run sets, 3 lanes, 4 lanes by tiles"}
+                     "lane_tile": inf.lane_tile, "legend": "1 tile subproblems, 2 run sets, 3 a lane per run, 4 a lane pair per run, "
+                               "5 a lane pair per run with runs grouped by grid tile"}
 
     # ---- pass C: end to end through the public API with pinned host buffers
     y_host = torch.empty(wl.M, dtype=cdt, pin_memory=True)
