@@ -233,7 +233,7 @@ def job_rate(world: int, steps: int, total_ms: float) -> float:
 
 
 # -------------------------------------------------------- problem set-up
-def setup_problem(wl_name: str, replica: int, dev):
+def setup_problem(wl_name: str, replica: int, dev, grid_mode: int = 0):
     import torch
 
     import paper_1502_05037_gb300 as pk
@@ -246,7 +246,7 @@ def setup_problem(wl_name: str, replica: int, dev):
     rt, ct = (torch.float64, torch.complex128) if f64 else (torch.float32, torch.complex64)
     plan = pk.Plan(wl.nx, wl.ny, torch.from_numpy(u).to(dev), torch.from_numpy(v).to(dev), kb_width=wl.J,
                    levels=wl.levels, block_offsets=offs, stream=torch.cuda.current_stream(dev),
-                   dtype=pk.PURIFY_F64 if f64 else pk.PURIFY_F32)
+                   dtype=pk.PURIFY_F64 if f64 else pk.PURIFY_F32, grid_mode=grid_mode)
     xt = torch.from_numpy(x_true).to(rt).to(dev)
     y0 = torch.empty(wl.M, dtype=ct, device=dev)
     pk.purify_phi(plan, xt, y0)
@@ -374,7 +374,7 @@ def run_ours(args):
     pbuild.build()
     pk.load()
 
-    wl, plan, y, eps, x_true = setup_problem(args.workload, rank, dev)
+    wl, plan, y, eps, x_true = setup_problem(args.workload, rank, dev, args.grid_mode)
     stream = torch.cuda.current_stream(dev)
     rdt = torch.float64 if wl.dtype == "f64" else torch.float32
     cdt = torch.complex128 if wl.dtype == "f64" else torch.complex64
@@ -459,7 +459,8 @@ def run_ours(args):
     inf = plan.info
     decomposition = {"grid": inf.grid_mode, "degrid": inf.degrid_mode, "normal": inf.normal_mode,
                      "lane_tile": inf.lane_tile, "legend": "1 tile subproblems, 2 run sets, 3 a lane per run, 4 a lane pair per run, "
-                               "5 a lane pair per run with runs grouped by grid tile"}
+                               "5 a lane pair per run with runs grouped by grid tile, 6 a lane pair per run with "
+                               "stored patches summed per cell in a fixed order (deterministic)"}
 
     # ---- pass C: end to end through the public API with pinned host buffers
     y_host = torch.empty(wl.M, dtype=cdt, pin_memory=True)
@@ -824,7 +825,7 @@ def run_profile_op(args):
     from paper_1502_05037_gb300 import build as pbuild
     pbuild.build()
     dev = torch.device("cuda", 0)
-    wl, plan, y, eps, x_true = setup_problem(args.workload, 0, dev)
+    wl, plan, y, eps, x_true = setup_problem(args.workload, 0, dev, args.grid_mode)
     x = torch.from_numpy(x_true.astype(np.float32)).to(dev)
     yv = torch.empty(wl.M, dtype=torch.complex64, device=dev)
     xa = torch.empty((wl.ny, wl.nx), dtype=torch.complex64, device=dev)
@@ -1223,6 +1224,9 @@ def main():
     ap.add_argument("--epochs", type=int, default=30)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--grid-mode", type=int, default=0,
+                    help="gridding decomposition of the timed plan (0 autotuned; 6 deterministic: stored run "
+                         "patches summed per cell in a fixed order)")
     ap.add_argument("--profile-op", choices=["phi", "phi_adj", "psi", "psi_adj", "normal", "iteration"], default=None,
                     help="only launch this operator W + K times (for ncu captures); prints no bench line")
     args = ap.parse_args()

@@ -80,7 +80,13 @@ typedef struct {
                                       by lanes: each run of visibilities sharing a first-tap cell
                                       owned by one lane (3) or a lane pair (4; 5: runs grouped by
                                       grid tile), its patch and accumulator in registers (FP32,
-                                      J <= 6 only) */
+                                      J <= 6 only); 6 => deterministic: as 4, but each run's
+                                      J x J patch is stored and every grid cell sums the patches
+                                      covering it in a fixed order, so G^H, the normal operator
+                                      and an SDMM solve give the same bits on every run of the
+                                      same plan and inputs (FP32, J <= 6; no floating-point
+                                      atomics; J^2 * 8 bytes per run of extra memory). Not a
+                                      passage of the paper: an execution choice. */
 } purify_plan_desc;
 
 /* Build a plan: validates the description, computes the correction, kernel,
@@ -103,9 +109,11 @@ typedef struct {
     double beta;
     int64_t workspace_bytes;
     int32_t grid_mode;             /* the G^H decomposition in use: 1 tile subproblems, 2 runs,
-                                      3..5 lanes (as grid_mode of the description) */
+                                      3..5 lanes, 6 deterministic lanes (as grid_mode of the
+                                      description) */
     int32_t degrid_mode;           /* the G decomposition in use: 1 tile subproblems, 3..5 lanes */
-    int32_t normal_mode;           /* the fused G^H G of the CG normal operator: 2 runs, 3..5 lanes */
+    int32_t normal_mode;           /* the fused G^H G of the CG normal operator: 2 runs, 3..5 lanes,
+                                      6 deterministic lanes */
     int32_t lane_tile;             /* grid tile edge grouping the runs of normal_mode 5 (else 0) */
 } purify_plan_info;
 purify_status purify_plan_get_info(const purify_plan *plan, purify_plan_info *info);

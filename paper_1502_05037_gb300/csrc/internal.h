@@ -94,6 +94,12 @@ struct RunWork {
 // internal / caller order. Set order: runs sorted by length (longest
 // first), or with tile > 0 grouped by grid tile of that edge (tiles in
 // raster order, runs by length within a tile).
+// Deterministic form (cstart non-empty): the kernels store each run's J x J
+// patch at patch[(b J + a) * nsets * width + run] instead of adding it to
+// the grid, and a gather sums, for every grid cell, the patches of the runs
+// whose footprint covers it in a fixed order (taps b, a, then the cell's
+// runs in run order): cstart[c] .. cstart[c + 1] index clist, the runs with
+// first-tap cell c (c = cy Kx + cx) in increasing run order.
 static constexpr int kLaneMaxJ = 6;
 struct LaneWork {
     int nsets = 0, width = 32, tile = 0;
@@ -102,6 +108,8 @@ struct LaneWork {
     DevBuf run_cl;                // int2 (cell, len) per run
     DevBuf rec;                   // float2 (phx, phy) per record
     DevBuf idx, idx_caller;       // int per record
+    DevBuf cstart, clist;         // deterministic form: int [Kx Ky + 1], int per real run
+    bool deterministic() const { return cstart.p != nullptr; }
     void release() {
         nsets = 0;
         rows = 0;
@@ -110,6 +118,8 @@ struct LaneWork {
         rec.release();
         idx.release();
         idx_caller.release();
+        cstart.release();
+        clist.release();
     }
 };
 
@@ -220,11 +230,13 @@ struct purify_plan {
     purify::RunWork runs;             // run-ordered work of the fused normal operator
     purify::LaneWork lanes[3];        // lane-per-run forms of the same runs (FP32, J <= 6): one lane
                                       // per run; two lanes per run; two, sets grouped by tile
-    int normal_kind = 2;              // G^H G: 2 run sets, 3..5 lanes (as lanes[kind - 3]); autotuned
+    purify::DevBuf det_patch;         // run patches of the deterministic lane form (float2)
+    int normal_kind = 2;              // G^H G: 2 run sets, 3..5 lanes (as lanes[kind - 3]), 6 the
+                                      // deterministic lane pairs (lanes[1]); autotuned or forced
     int group_count = 0;              // G of group_lanes / group_chunks (0: not built)
     std::vector<purify::LaneWork> group_lanes;
     std::vector<purify::GroupChunks> group_chunks;
-    int grid_kind = 1;                // G^H: 1 tile subproblems, 2 run sets, 3..5 lanes; autotuned
+    int grid_kind = 1;                // G^H: 1 tile subproblems, 2 run sets, 3..5 lanes, 6 deterministic
     int degrid_kind = 1;              // G: 1 tile subproblems, 3..5 lanes; autotuned
     int fft_rb = 0, fft_cb = 0;       // FFT rows / columns per block (0: heuristic)
     // workspaces

@@ -909,12 +909,15 @@ __device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-template <int J, int MODE, int H>
-__global__ void __launch_bounds__(128, H == 2 ? 4 : 1)
+// With DET the accumulators are not added to the grid: run q's J x J patch
+// is stored at out[(b J + a) * dstride + q] (q = set * (32 / H) + its lane
+// in the set), for k_lane_gather to sum in a fixed order.
+template <int J, int MODE, int H, bool DET = false>
+__global__ void __launch_bounds__(128, H == 2 ? (DET ? 3 : 4) : 1)
 k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __restrict__ yout,
        const int2* __restrict__ set_info, const int2* __restrict__ run_cl, const float2* __restrict__ recs,
        const int* __restrict__ idx, int nsets, KbPoly kp, int Kx, int Ky, float2* __restrict__ out,
-       const int* __restrict__ skip) {
+       const int* __restrict__ skip, int64_t dstride) {
     constexpr bool HAS_X = MODE != LANE_GRID, HAS_ACC = MODE != LANE_DEGRID;
     constexpr int WID = 32 / H, RH = LaneStage<J, H>::RH, LS = LaneStage<J, H>::LS;
     pdl_wait();
@@ -1102,10 +1105,26 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
         }
         if constexpr (HAS_ACC) {
             if (len > 0) {
+                if constexpr (DET) {
+                    // this lane's rows, tap by tap (consecutive runs of the
+                    // set write consecutive slots of each tap plane)
+                    float2* P = out + (size_t)set * WID + r + (size_t)(h * RH * J) * dstride;
 #pragma unroll
-                for (int i = 0; i < RH; ++i) {
-                    const int b = h * RH + i;
-                    if (b < J) red_row<J>(out + (size_t)((cy + b) & (Ky - 1)) * Kx, cx, Kx, ar[i], ai[i]);
+                    for (int i = 0; i < RH; ++i) {
+                        if (h * RH + i < J) {
+#pragma unroll
+                            for (int a = 0; a < J; ++a) {
+                                *P = make_float2(ar[i][a], ai[i][a]);
+                                P += dstride;
+                            }
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < RH; ++i) {
+                        const int b = h * RH + i;
+                        if (b < J) red_row<J>(out + (size_t)((cy + b) & (Ky - 1)) * Kx, cx, Kx, ar[i], ai[i]);
+                    }
                 }
             }
         }
@@ -1118,6 +1137,39 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
         i1 = ni1;
     }
     cp_async_wait_all();
+    pdl_trigger();
+}
+
+// Deterministic gridding sum: every grid cell g = (gx, gy) is the sum of the
+// stored run patches covering it, taken in a fixed order (tap row b, tap
+// column a, then the runs with first-tap cell (gx - a, gy - b) (periodic) in
+// increasing run order), written over the previous contents.
+template <int J>
+__global__ void __launch_bounds__(256)
+k_lane_gather(const float2* __restrict__ P, int64_t dstride, const int* __restrict__ cstart,
+              const int* __restrict__ clist, int Kx, int Ky, float2* __restrict__ out, const int* __restrict__ skip) {
+    pdl_wait();
+    if (skip && *skip) return;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g < (int64_t)Kx * Ky) {
+        const int gx = (int)(g & (Kx - 1)), gy = (int)(g / Kx);
+        float sr = 0.f, si = 0.f;
+        const float2* Pt = P;   // tap plane b J + a
+        for (int b = 0; b < J; ++b) {
+            const int* rowc = cstart + (size_t)((gy - b) & (Ky - 1)) * Kx;
+            for (int a = 0; a < J; ++a) {
+                const int c = (gx - a) & (Kx - 1);
+                const int e = rowc[c + 1];
+                for (int q = rowc[c]; q < e; ++q) {
+                    const float2 v = Pt[clist[q]];
+                    sr += v.x;
+                    si += v.y;
+                }
+                Pt += dstride;
+            }
+        }
+        out[g] = make_float2(sr, si);
+    }
     pdl_trigger();
 }
 
@@ -1397,17 +1449,15 @@ static void grid_sets_tj(purify_plan* p, const void* y, bool caller_order, const
 // 5: two lanes per run with the sets grouped by grid tile): a persistent
 // grid of 4-warp blocks (as many as are resident at once, or fewer when
 // there is less work).
-static const LaneWork& lane_work(const purify_plan* p, int kind) { return p->lanes[kind - 3]; }
-template <int J, int MODE, int H>
-static void lane_tw(purify_plan* p, const LaneWork& lw, const void* yin, void* yout, bool caller_order,
-                    const int* skip, bool zeroed) {
-    if (MODE != LANE_DEGRID && !zeroed) PURIFY_CUDA(cudaMemsetAsync(p->gacc.p, 0, p->gacc.bytes, p->stream));
-    if (lw.nsets == 0) return;
+static const LaneWork& lane_work(const purify_plan* p, int kind) { return p->lanes[kind == 6 ? 1 : kind - 3]; }
+template <int J, int MODE, int H, bool DET>
+static void lane_launch(purify_plan* p, const LaneWork& lw, const void* yin, void* yout, bool caller_order,
+                        const int* skip, float2* out, int64_t dstride) {
     const size_t lane_smem = 4 * LaneStage<J, H>::bytes_per_warp;
     static int per_sm = 0;   // resident blocks per SM of this instantiation
     if (per_sm == 0) {
-        set_smem(k_lane<J, MODE, H>, lane_smem);
-        PURIFY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lane<J, MODE, H>, 128, lane_smem));
+        set_smem(k_lane<J, MODE, H, DET>, lane_smem);
+        PURIFY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lane<J, MODE, H, DET>, 128, lane_smem));
         per_sm = std::max(1, per_sm);
     }
     int sms = 0, dev = 0;
@@ -1415,11 +1465,35 @@ static void lane_tw(purify_plan* p, const LaneWork& lw, const void* yin, void* y
     PURIFY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int blocks = std::max(1, std::min(sms * per_sm, (lw.nsets + 3) / 4));
     Launch L(p, MODE == LANE_GG ? "normal_gg" : (MODE == LANE_GRID ? "grid" : "degrid"));
-    launch_dependent(k_lane<J, MODE, H>, blocks, 128, lane_smem, p->stream, p->grid.as<float2>(), (const float2*)yin,
-                     (float2*)yout, lw.set_info.as<int2>(), lw.run_cl.as<int2>(), lw.rec.as<float2>(),
-                     caller_order ? lw.idx_caller.as<int>() : lw.idx.as<int>(), lw.nsets, p->kbp, p->Kx, p->Ky,
-                     p->gacc.as<float2>(), skip);
+    launch_dependent(k_lane<J, MODE, H, DET>, blocks, 128, lane_smem, p->stream, p->grid.as<float2>(),
+                     (const float2*)yin, (float2*)yout, lw.set_info.as<int2>(), lw.run_cl.as<int2>(),
+                     lw.rec.as<float2>(), caller_order ? lw.idx_caller.as<int>() : lw.idx.as<int>(), lw.nsets,
+                     p->kbp, p->Kx, p->Ky, out, skip, dstride);
     L.done();
+}
+template <int J, int MODE, int H>
+static void lane_tw(purify_plan* p, const LaneWork& lw, const void* yin, void* yout, bool caller_order,
+                    const int* skip, bool zeroed) {
+    if constexpr (H == 2 && MODE != LANE_DEGRID) {
+        if (lw.deterministic() && lw.nsets > 0) {
+            // run patches stored, then summed per cell in a fixed order
+            // (the sum overwrites the accumulator: no clearing needed)
+            const int64_t stride = (int64_t)lw.nsets * lw.width;
+            PURIFY_REQUIRE(p->det_patch.bytes >= sizeof(float2) * (size_t)J * J * (size_t)stride,
+                           "deterministic patch buffer too small");
+            lane_launch<J, MODE, H, true>(p, lw, yin, yout, caller_order, skip, p->det_patch.as<float2>(), stride);
+            const int64_t cells = (int64_t)p->Kx * p->Ky;
+            Launch L(p, "det_gather");
+            launch_dependent(k_lane_gather<J>, (unsigned)((cells + 255) / 256), 256, 0, p->stream,
+                             (const float2*)p->det_patch.as<float2>(), stride, lw.cstart.as<int>(),
+                             lw.clist.as<int>(), p->Kx, p->Ky, p->gacc.as<float2>(), skip);
+            L.done();
+            return;
+        }
+    }
+    if (MODE != LANE_DEGRID && !zeroed) PURIFY_CUDA(cudaMemsetAsync(p->gacc.p, 0, p->gacc.bytes, p->stream));
+    if (lw.nsets == 0) return;
+    lane_launch<J, MODE, H, false>(p, lw, yin, yout, caller_order, skip, p->gacc.as<float2>(), 0);
 }
 template <int J, int MODE>
 static void lane_on(purify_plan* p, const LaneWork& lw, const void* yin, void* yout, bool c, const int* s, bool z) {
@@ -1456,7 +1530,8 @@ template <int J> static void gsets_d(purify_plan* p, const void* y, bool c, cons
 
 bool lane_work_ok(const purify_plan* p) { return p->dtype == PURIFY_F32 && p->J <= kLaneMaxJ; }
 static void require_lane_work(const purify_plan* p, int kind) {
-    if (!lane_work_ok(p) || kind < 3 || kind > 5 || lane_work(p, kind).nsets == 0)
+    if (!lane_work_ok(p) || kind < 3 || kind > 6 || lane_work(p, kind).nsets == 0 ||
+        (kind == 6 && !lane_work(p, kind).deterministic()))
         throw Error{PURIFY_EINVAL, "lane-per-run kernels need an FP32 plan with J <= 6 built for that form"};
 }
 

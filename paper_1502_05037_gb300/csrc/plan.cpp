@@ -321,10 +321,11 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
     p->fft_rb = val.rb;
     p->fft_cb = val.cb;
     // a forced decomposition: grid_mode 1 and 2 degrid by tiles and apply
-    // G^H G by run sets, 3..5 do all three by that lane form
+    // G^H G by run sets, 3..5 do all three by that lane form, 6 grids by
+    // the deterministic lane pairs and degrids by the lane pairs
     const int gm = p->desc.grid_mode;
     p->grid_kind = gm == 0 ? val.gkind : gm;
-    p->degrid_kind = gm == 0 ? val.dkind : (gm >= 3 ? gm : 1);
+    p->degrid_kind = gm == 0 ? val.dkind : (gm == 6 ? 4 : (gm >= 3 ? gm : 1));
     p->normal_kind = gm == 0 ? val.nkind : (gm >= 3 ? gm : 2);
     build_gridlist(p, bins_for(val.tile), cell_order, val.tile, val.units, p->work);
     build_gridlist(p, bins_for(val.dtile), cell_order, val.dtile, val.dunits, p->dwork);
@@ -337,7 +338,7 @@ struct HostRun { int cell; int64_t first; int len; };
 template <typename Rec>
 static void build_lanework(purify_plan* p, const std::vector<HostRun>& runs, const std::vector<Rec>& rec,
                            const std::vector<int>& start, const std::vector<int>& perm, int width, int tile,
-                           LaneWork& w) {
+                           LaneWork& w, bool det = false) {
     const size_t nr = runs.size();
     std::vector<int> order(nr);
     std::iota(order.begin(), order.end(), 0);
@@ -390,6 +391,33 @@ static void build_lanework(purify_plan* p, const std::vector<HostRun>& runs, con
     upload(w.rec, lrec);
     upload(w.idx, lidx);
     upload(w.idx_caller, lcal);
+    w.cstart.release();
+    w.clist.release();
+    if (det) {
+        // the runs of every first-tap cell in increasing run order (a
+        // counting sort over the Kx Ky cells, stable in the run index)
+        const int64_t ncell = (int64_t)p->Kx * p->Ky;
+        std::vector<int> cstart(ncell + 1, 0), clist;
+        auto cell_of = [&](const int2& rc) {
+            return (int64_t)(((unsigned)rc.x >> 16) & (p->Ky - 1)) * p->Kx + ((rc.x & 0xFFFF) & (p->Kx - 1));
+        };
+        int64_t nreal = 0;
+        for (size_t q = 0; q < run_cl.size(); ++q)
+            if (run_cl[q].y > 0) { cstart[cell_of(run_cl[q]) + 1]++; ++nreal; }
+        for (int64_t c = 0; c < ncell; ++c) cstart[c + 1] += cstart[c];
+        clist.assign((size_t)std::max<int64_t>(1, nreal), 0);
+        std::vector<int> fill(cstart.begin(), cstart.end() - 1);
+        for (size_t q = 0; q < run_cl.size(); ++q)
+            if (run_cl[q].y > 0) clist[fill[cell_of(run_cl[q])]++] = (int)q;
+        upload(w.cstart, cstart);
+        upload(w.clist, clist);
+        // one patch slot per run of the lane work, J x J taps each; sized by
+        // the plan's own lane work (a block group has no more runs than the
+        // whole plan), never reallocated under captured graphs
+        const size_t need = sizeof(float2) * (size_t)p->J * p->J * run_cl.size();
+        if (p->det_patch.bytes == 0) p->det_patch.alloc(need);
+        PURIFY_REQUIRE(need <= p->det_patch.bytes, "deterministic lane work larger than the plan's patch buffer");
+    }
 }
 
 // Run-ordered work (see RunWork): runs of equal first-tap cell in the cell
@@ -434,7 +462,7 @@ static void build_runwork(purify_plan* p, const std::vector<T>& us, const std::v
     }
     if (sizeof(T) == 4 && p->J <= kLaneMaxJ) {
         build_lanework(p, runs, rec, start, perm, 32, 0, p->lanes[0]);
-        build_lanework(p, runs, rec, start, perm, 16, 0, p->lanes[1]);
+        build_lanework(p, runs, rec, start, perm, 16, 0, p->lanes[1], p->desc.grid_mode == 6);
         build_lanework(p, runs, rec, start, perm, 16, std::min(32, std::min(p->Kx, p->Ky)), p->lanes[2]);
     }
     p->runs.G = G;
@@ -503,7 +531,7 @@ void build_group_lanes(purify_plan* p, int G) {
             start[r] = (int)q;
             for (int k = 0; k < runs[r].len; ++k) rec[q++] = rec_of[idx[runs[r].first + k]];
         }
-        build_lanework(p, runs, rec, start, perm, 16, 0, p->group_lanes[g]);
+        build_lanework(p, runs, rec, start, perm, 16, 0, p->group_lanes[g], p->desc.grid_mode == 6);
         // the group's visibility chunks (the plan's chunking, blocks of the group only)
         const int64_t CH = 4096;
         std::vector<int> cb, cs, ce, cf(p->R + 1, 0);
@@ -528,7 +556,8 @@ void build_group_lanes(purify_plan* p, int G) {
 }
 
 static int64_t lane_bytes(const LaneWork& w) {
-    return (int64_t)(w.set_info.bytes + w.run_cl.bytes + w.rec.bytes + w.idx.bytes + w.idx_caller.bytes);
+    return (int64_t)(w.set_info.bytes + w.run_cl.bytes + w.rec.bytes + w.idx.bytes + w.idx_caller.bytes +
+                     w.cstart.bytes + w.clist.bytes);
 }
 
 template <typename T> static void finish_plan(purify_plan* p) {
@@ -622,10 +651,15 @@ template <typename T> static void finish_plan(purify_plan* p) {
     }
     build_runwork<T>(p, us, vs, scx, scy, cell_order, perm);
     autotune<T>(p, cand, bins_for, cell_order, d.tile == 0);
-    // keep only the lane work in use
+    // keep only the lane work in use (kind 6 runs on the lane pairs of kind 4)
+    auto uses = [&](int k) {
+        auto is = [&](int kind) { return kind == k || (k == 4 && kind == 6); };
+        return is(p->grid_kind) || is(p->degrid_kind) || is(p->normal_kind);
+    };
     for (int k = 3; k <= 5; ++k)
-        if (p->grid_kind != k && p->degrid_kind != k && p->normal_kind != k) p->lanes[k - 3].release();
+        if (!uses(k)) p->lanes[k - 3].release();
     for (int k = 0; k < 3; ++k) p->workspace_bytes += lane_bytes(p->lanes[k]);
+    p->workspace_bytes += (int64_t)p->det_patch.bytes;
 }
 
 purify_plan* create_plan(const purify_plan_desc* d) {
@@ -649,9 +683,9 @@ purify_plan* create_plan(const purify_plan_desc* d) {
                        Ky <= 8192 && Kx > d->nx && Ky > d->ny,
                    "oversample must make K = alpha n a power of two above n (at most 8192)");
     PURIFY_REQUIRE(d->tile == 0 || (is_pow2(d->tile) && d->tile >= 8 && d->tile <= 64), "tile must be 0 or a power of two in [8, 64]");
-    PURIFY_REQUIRE(d->grid_mode >= 0 && d->grid_mode <= 5, "grid_mode must be in 0..5");
+    PURIFY_REQUIRE(d->grid_mode >= 0 && d->grid_mode <= 6, "grid_mode must be in 0..6");
     PURIFY_REQUIRE(d->grid_mode < 3 || (d->dtype == PURIFY_F32 && d->kb_width <= kLaneMaxJ),
-                   "grid_mode 3..5 (lanes) needs an FP32 plan with kb_width <= 6");
+                   "grid_mode 3..6 (lanes) needs an FP32 plan with kb_width <= 6");
     std::vector<int64_t> offs;
     if (d->block_offsets) {
         offs.assign(d->block_offsets, d->block_offsets + d->R + 1);

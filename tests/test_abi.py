@@ -118,10 +118,13 @@ def test_invalid_description_is_rejected_before_any_launch(lib):
     ({"kb_width": 1}, b"kb_width"),
     ({"levels": 6, "nx": 16, "ny": 16}, b"too small"),            # deeper than the image allows
     ({"tile": 12}, b"tile"),
-    ({"grid_mode": 6}, b"grid_mode"),
-    ({"grid_mode": 4, "dtype": 1}, b"grid_mode 3..5"),
-    ({"grid_mode": 3, "dtype": 1}, b"grid_mode 3..5"),               # lanes are FP32 only
-    ({"grid_mode": 3, "kb_width": 7}, b"grid_mode 3..5"),
+    ({"grid_mode": 7}, b"grid_mode"),
+    ({"grid_mode": -1}, b"grid_mode"),
+    ({"grid_mode": 4, "dtype": 1}, b"grid_mode 3..6"),
+    ({"grid_mode": 3, "dtype": 1}, b"grid_mode 3..6"),               # lanes are FP32 only
+    ({"grid_mode": 3, "kb_width": 7}, b"grid_mode 3..6"),
+    ({"grid_mode": 6, "dtype": 1}, b"grid_mode 3..6"),               # deterministic lanes too
+    ({"grid_mode": 6, "kb_width": 8}, b"grid_mode 3..6"),
     ({"oversample": 1.5}, b"oversample"),
     ({"dtype": 7}, b"dtype"),
     ({"basis_mask": 0x200}, b"basis_mask"),

@@ -151,7 +151,7 @@ def test_full_size_sampled_outputs():
     assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
 
 
-@pytest.mark.parametrize("grid_mode", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("grid_mode", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("nx,M,J,R,dtype,tile", [
     (64, 30011, 6, 3, pk.PURIFY_F32, 0),
     (64, 30011, 6, 3, pk.PURIFY_F32, 16),
@@ -161,7 +161,8 @@ def test_full_size_sampled_outputs():
 ])
 def test_phi_adj_both_decompositions(nx, M, J, R, dtype, tile, grid_mode):
     # G^H by tile subproblems, by first-tap-cell runs and by lanes (3: a run
-    # per lane, 4: per lane pair, 5: per lane pair, runs grouped by tile), each against the
+    # per lane, 4: per lane pair, 5: per lane pair, runs grouped by tile, 6:
+    # per lane pair with stored patches summed in a fixed order), each against the
     # oracle in caller order: several tiles, runs cut at their length cap, a
     # ragged last run set, an odd J and a handful of visibilities; also G
     # (Phi) and the normal operator of each decomposition
@@ -187,7 +188,7 @@ def test_phi_adj_both_decompositions(nx, M, J, R, dtype, tile, grid_mode):
     assert rel(out.cpu().numpy(), want_n) <= TOL[dtype]
 
 
-@pytest.mark.parametrize("grid_mode", [1, 2, 3, 4, 5])
+@pytest.mark.parametrize("grid_mode", [1, 2, 3, 4, 5, 6])
 def test_phi_adj_single_cell_runs(grid_mode):
     # every visibility in a handful of cells: runs longer than the cap are
     # cut and flushed into the same cells
