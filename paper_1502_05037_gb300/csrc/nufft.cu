@@ -960,13 +960,20 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
         if constexpr (HAS_X) patch_async(rc, buf(0));
     }
     cp_async_commit();
+    // the next set's descriptors, loaded a set ahead of their use
+    int nset = set_of(1);
+    int2 nsi = make_int2(0, 0), nrc = make_int2(0, 0);
+    if (nset < nsets) {
+        nsi = set_info[nset];
+        nrc = run_cl[(size_t)nset * WID + r];
+    }
     for (int it = 0; set < nsets; ++it) {
-        const int nset = set_of(it + 1);
         const bool has_next = nset < nsets;
-        int2 nsi = make_int2(0, 0), nrc = make_int2(0, 0);
-        if (has_next) {
-            nsi = set_info[nset];
-            nrc = run_cl[(size_t)nset * WID + r];
+        const int n2set = set_of(it + 2);
+        int2 n2si = make_int2(0, 0), n2rc = make_int2(0, 0);
+        if (n2set < nsets) {
+            n2si = set_info[n2set];
+            n2rc = run_cl[(size_t)n2set * WID + r];
         }
         const int cx = rc.x & 0xFFFF, cy = (int)((unsigned)rc.x >> 16), len = rc.y;
         float xr[HAS_X ? RH : 1][HAS_X ? J : 1], xi[HAS_X ? RH : 1][HAS_X ? J : 1];
@@ -991,15 +998,27 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
 #pragma unroll
                 for (int a = 0; a < J; ++a) ar[i][a] = ai[i][a] = 0.f;
         }
+        // the next set's patch (into the buffer read at the start of the
+        // previous set) and first records, a whole set ahead of their use
+        float2 nf0 = make_float2(0.f, 0.f), nf1 = make_float2(0.f, 0.f);
+        int ni0 = -1, ni1 = -1;
+        if (has_next) {
+            if constexpr (HAS_X) patch_async(nrc, buf(it + 1));
+            const size_t nb = (size_t)nsi.x * WID + r;
+            nf0 = recs[nb];
+            if (nsi.y > 1) nf1 = recs[nb + WID];
+            if (MODE != LANE_GG) {
+                ni0 = idx[nb];
+                if (nsi.y > 1) ni1 = idx[nb + WID];
+            }
+        }
+        cp_async_commit();
         const size_t base = (size_t)si.x * WID + r;
         const int lmax = si.y;
         float2 rc0 = f0, rc1 = f1;
         int ic0 = i0, ic1 = i1;
         float2 yv0 = make_float2(0.f, 0.f);   // gridding: this step's value, one step ahead
         if (MODE == LANE_GRID && ic0 >= 0) yv0 = yin[ic0];
-        float2 nf0 = make_float2(0.f, 0.f), nf1 = make_float2(0.f, 0.f);
-        int ni0 = -1, ni1 = -1;
-        bool issued = false;
         for (int k = 0; k < lmax; ++k) {
             // records two steps ahead, the gridding value one step ahead
             float2 rc2 = make_float2(0.f, 0.f);
@@ -1073,35 +1092,11 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
                     }
                 }
             }
-            if (k == 0 && has_next) {
-                // the next set's patch and first records, behind this set's work
-                if constexpr (HAS_X) patch_async(nrc, buf(it + 1));
-                cp_async_commit();
-                const size_t nb = (size_t)nsi.x * WID + r;
-                nf0 = recs[nb];
-                if (nsi.y > 1) nf1 = recs[nb + WID];
-                if (MODE != LANE_GG) {
-                    ni0 = idx[nb];
-                    if (nsi.y > 1) ni1 = idx[nb + WID];
-                }
-                issued = true;
-            }
             rc0 = rc1;
             rc1 = rc2;
             ic0 = ic1;
             ic1 = ic2;
             yv0 = yv1;
-        }
-        if (has_next && !issued) {
-            if constexpr (HAS_X) patch_async(nrc, buf(it + 1));
-            cp_async_commit();
-            const size_t nb = (size_t)nsi.x * WID + r;
-            nf0 = recs[nb];
-            if (nsi.y > 1) nf1 = recs[nb + WID];
-            if (MODE != LANE_GG) {
-                ni0 = idx[nb];
-                if (nsi.y > 1) ni1 = idx[nb + WID];
-            }
         }
         if constexpr (HAS_ACC) {
             if (len > 0) {
@@ -1131,6 +1126,9 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
         set = nset;
         si = nsi;
         rc = nrc;
+        nset = n2set;
+        nsi = n2si;
+        nrc = n2rc;
         f0 = nf0;
         f1 = nf1;
         i0 = ni0;
@@ -1141,9 +1139,11 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
 }
 
 // Deterministic gridding sum: every grid cell g = (gx, gy) is the sum of the
-// stored run patches covering it, taken in a fixed order (tap row b, tap
-// column a, then the runs with first-tap cell (gx - a, gy - b) (periodic) in
-// increasing run order), written over the previous contents.
+// stored run patches covering it (the runs with first-tap cell
+// (gx - a, gy - b), periodic, at tap (b, a)), written over the previous
+// contents, in a fixed order: per tap row b, the first run of each tap
+// column a = 0..J-1 (their index and patch loads all in flight at once),
+// then the further runs of each column in increasing run order.
 template <int J>
 __global__ void __launch_bounds__(256)
 k_lane_gather(const float2* __restrict__ P, int64_t dstride, const int* __restrict__ cstart,
@@ -1154,18 +1154,36 @@ k_lane_gather(const float2* __restrict__ P, int64_t dstride, const int* __restri
     if (g < (int64_t)Kx * Ky) {
         const int gx = (int)(g & (Kx - 1)), gy = (int)(g / Kx);
         float sr = 0.f, si = 0.f;
-        const float2* Pt = P;   // tap plane b J + a
+#pragma unroll
         for (int b = 0; b < J; ++b) {
             const int* rowc = cstart + (size_t)((gy - b) & (Ky - 1)) * Kx;
+            const float2* Pb = P + (size_t)(b * J) * dstride;
+            int s[J], e[J];
+#pragma unroll
             for (int a = 0; a < J; ++a) {
                 const int c = (gx - a) & (Kx - 1);
-                const int e = rowc[c + 1];
-                for (int q = rowc[c]; q < e; ++q) {
-                    const float2 v = Pt[clist[q]];
-                    sr += v.x;
-                    si += v.y;
+                s[a] = __ldg(rowc + c);
+                e[a] = __ldg(rowc + c + 1);
+            }
+            int q0[J];
+#pragma unroll
+            for (int a = 0; a < J; ++a) q0[a] = s[a] < e[a] ? __ldg(clist + s[a]) : -1;
+            float2 v[J];
+#pragma unroll
+            for (int a = 0; a < J; ++a)
+                v[a] = q0[a] >= 0 ? __ldg(Pb + (size_t)a * dstride + q0[a]) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int a = 0; a < J; ++a) {
+                sr += v[a].x;
+                si += v[a].y;
+            }
+#pragma unroll
+            for (int a = 0; a < J; ++a) {
+                for (int q = s[a] + 1; q < e[a]; ++q) {
+                    const float2 w = __ldg(Pb + (size_t)a * dstride + __ldg(clist + q));
+                    sr += w.x;
+                    si += w.y;
                 }
-                Pt += dstride;
             }
         }
         out[g] = make_float2(sr, si);
