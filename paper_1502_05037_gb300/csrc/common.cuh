@@ -99,16 +99,31 @@ PURIFY_HD void split_coord(double coord, const AxisConst& ax, int J, int& k0, do
 PURIFY_HD constexpr int kb_poly_deg(int J) { return J <= 3 ? 10 : (J == 4 ? 9 : 8); }
 
 // Float weights of one axis from the per-tap polynomials (Horner in z).
+// The kernel is even in the tap offset, so tap J-1-a at z is tap a at -z
+// (the host table holds p_{J-1-a}(z) = p_a(-z) exactly): each mirrored pair
+// comes from the even and odd parts of p_a, p_a(+-z) = E(z^2) +- z O(z^2),
+// Horner in z^2 (the middle tap of an odd J is even).
 template <int J>
 __device__ __forceinline__ void kb_weights(const KbPoly& kp, float phi, float (&w)[J]) {
     constexpr int DEG = kb_poly_deg(J);
-    float z = fmaf(2.0f, phi, -1.0f);
+    constexpr int DE = DEG & ~1, DO = (DEG & 1) ? DEG : DEG - 1;   // top even / odd degree
+    const float z = fmaf(2.0f, phi, -1.0f);
+    const float z2 = z * z;
 #pragma unroll
-    for (int a = 0; a < J; ++a) {
-        float acc = kp.coef[a][DEG];
+    for (int a = 0; a < (J + 1) / 2; ++a) {
+        float e = kp.coef[a][DE];
 #pragma unroll
-        for (int i = DEG - 1; i >= 0; --i) acc = fmaf(acc, z, kp.coef[a][i]);
-        w[a] = acc;
+        for (int i = DE - 2; i >= 0; i -= 2) e = fmaf(e, z2, kp.coef[a][i]);
+        if (2 * a + 1 == J) {
+            w[a] = e;
+        } else {
+            float o = kp.coef[a][DO];
+#pragma unroll
+            for (int i = DO - 2; i >= 1; i -= 2) o = fmaf(o, z2, kp.coef[a][i]);
+            const float oz = o * z;
+            w[a] = e + oz;
+            w[J - 1 - a] = e - oz;
+        }
     }
 }
 

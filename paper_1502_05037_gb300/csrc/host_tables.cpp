@@ -85,6 +85,18 @@ KbPoly fit_kb_poly(int J, double beta, int deg) {
             kp.coef[a][i] = (float)m;
         }
     }
+    // the kernel is even in the offset: tap J-1-a at z equals tap a at -z;
+    // store the mirrored taps as exact reflections (the middle tap of an odd
+    // J as an even polynomial), so that the weights can be evaluated from
+    // even and odd parts
+    for (int a = 0; a < (J + 1) / 2; ++a)
+        for (int i = 0; i < n; ++i) {
+            if (2 * a + 1 == J) {
+                if (i & 1) kp.coef[a][i] = 0.0f;
+            } else {
+                kp.coef[J - 1 - a][i] = (i & 1) ? -kp.coef[a][i] : kp.coef[a][i];
+            }
+        }
     return kp;
 }
 

@@ -976,8 +976,11 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
             n2rc = run_cl[(size_t)n2set * WID + r];
         }
         const int cx = rc.x & 0xFFFF, cy = (int)((unsigned)rc.x >> 16), len = rc.y;
-        float xr[HAS_X ? RH : 1][HAS_X ? J : 1], xi[HAS_X ? RH : 1][HAS_X ? J : 1];
-        float ar[HAS_ACC ? RH : 1][HAS_ACC ? J : 1], ai[HAS_ACC ? RH : 1][HAS_ACC ? J : 1];
+        // complex patch values and accumulators as (re, im) pairs: the
+        // interpolation and spreading below are packed two-lane FP32
+        // multiply-adds (per component the same roundings as scalar ones)
+        float2 xv[HAS_X ? RH : 1][HAS_X ? J : 1];
+        float2 av[HAS_ACC ? RH : 1][HAS_ACC ? J : 1];
         if constexpr (HAS_X) {
             cp_async_wait_all();
             const float2* cur = buf(it);
@@ -987,8 +990,7 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
 #pragma unroll
                 for (int a = 0; a < J; ++a) {
                     const float2 v = rowok ? cur[i * J + a] : make_float2(0.f, 0.f);
-                    xr[i][a] = v.x;
-                    xi[i][a] = v.y;
+                    xv[i][a] = v;
                 }
             }
         }
@@ -996,7 +998,7 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
 #pragma unroll
             for (int i = 0; i < RH; ++i)
 #pragma unroll
-                for (int a = 0; a < J; ++a) ar[i][a] = ai[i][a] = 0.f;
+                for (int a = 0; a < J; ++a) av[i][a] = make_float2(0.f, 0.f);
         }
         // the next set's patch (into the buffer read at the start of the
         // previous set) and first records, a whole set ahead of their use
@@ -1055,17 +1057,16 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
             }
             float yr = 0.f, yi = 0.f;
             if constexpr (HAS_X) {
+                float2 y2 = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int i = 0; i < RH; ++i) {
-                    float tr = 0.f, ti = 0.f;
+                    float2 t = make_float2(0.f, 0.f);
 #pragma unroll
-                    for (int a = 0; a < J; ++a) {
-                        tr = fmaf(wx[a], xr[i][a], tr);
-                        ti = fmaf(wx[a], xi[i][a], ti);
-                    }
-                    yr = fmaf(wy[i], tr, yr);
-                    yi = fmaf(wy[i], ti, yi);
+                    for (int a = 0; a < J; ++a) t = __ffma2_rn(make_float2(wx[a], wx[a]), xv[i][a], t);
+                    y2 = __ffma2_rn(make_float2(wy[i], wy[i]), t, y2);
                 }
+                yr = y2.x;
+                yi = y2.y;
                 if constexpr (H == 2) {
                     // rows of the pair in order: the h = 0 half first
                     const float pr = __shfl_xor_sync(0xffffffffu, yr, WID);
@@ -1084,12 +1085,9 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
             if constexpr (HAS_ACC) {
 #pragma unroll
                 for (int i = 0; i < RH; ++i) {
-                    const float ur = wy[i] * yr, ui = wy[i] * yi;
+                    const float2 u = __fmul2_rn(make_float2(wy[i], wy[i]), make_float2(yr, yi));
 #pragma unroll
-                    for (int a = 0; a < J; ++a) {
-                        ar[i][a] = fmaf(wx[a], ur, ar[i][a]);
-                        ai[i][a] = fmaf(wx[a], ui, ai[i][a]);
-                    }
+                    for (int a = 0; a < J; ++a) av[i][a] = __ffma2_rn(make_float2(wx[a], wx[a]), u, av[i][a]);
                 }
             }
             rc0 = rc1;
@@ -1109,7 +1107,7 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
                         if (h * RH + i < J) {
 #pragma unroll
                             for (int a = 0; a < J; ++a) {
-                                *P = make_float2(ar[i][a], ai[i][a]);
+                                *P = av[i][a];
                                 P += dstride;
                             }
                         }
@@ -1118,7 +1116,15 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
 #pragma unroll
                     for (int i = 0; i < RH; ++i) {
                         const int b = h * RH + i;
-                        if (b < J) red_row<J>(out + (size_t)((cy + b) & (Ky - 1)) * Kx, cx, Kx, ar[i], ai[i]);
+                        if (b < J) {
+                            float ar[J], ai[J];
+#pragma unroll
+                            for (int a = 0; a < J; ++a) {
+                                ar[a] = av[i][a].x;
+                                ai[a] = av[i][a].y;
+                            }
+                            red_row<J>(out + (size_t)((cy + b) & (Ky - 1)) * Kx, cx, Kx, ar, ai);
+                        }
                     }
                 }
             }
