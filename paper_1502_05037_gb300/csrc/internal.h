@@ -86,9 +86,12 @@ struct RunWork {
 
 // Lane-per-run work (FP32 plans, J <= 6): the same runs, `width` per warp
 // set (32 / lanes per run). Set s holds record rows [row0, row0 + lmax) with
-// lmax its longest run; the record of run width s + r at step k is
-// rec[(row0 + k) * width + r], so one step of a warp reads `width`
-// consecutive records. Records past a run's end are padding (zero offsets,
+// lmax its longest run; the record of run width s + r at step k is in
+// record row row0 + k: with width 32 the float2 (phx, phy) at
+// rec[(row0 + k) * 32 + r], with width 16 (a lane pair per run) phx at
+// float (row0 + k) * 32 + r and phy at float (row0 + k) * 32 + 16 + r, so
+// one step of a warp reads one record row (8 bytes per run), each lane of a
+// pair its own axis. Records past a run's end are padding (zero offsets,
 // index -1). run_cl[width s + r] = (cell, len), the cell packed as
 // (cy << 16) | cx; idx / idx_caller give each record's visibility in
 // internal / caller order. Set order: runs sorted by length (longest
@@ -106,7 +109,7 @@ struct LaneWork {
     int64_t rows = 0;
     DevBuf set_info;              // int2 (row0, lmax) per set
     DevBuf run_cl;                // int2 (cell, len) per run
-    DevBuf rec;                   // float2 (phx, phy) per record
+    DevBuf rec;                   // 8 bytes per record (layout above)
     DevBuf idx, idx_caller;       // int per record
     DevBuf cstart, clist;         // deterministic form: int [Kx Ky + 1], int per real run
     bool deterministic() const { return cstart.p != nullptr; }

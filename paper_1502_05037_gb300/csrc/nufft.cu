@@ -12,6 +12,7 @@
 //   rows_inv  : row pass of F^H fused with Z^T (crop) and S.
 // FFTs are radix-4 Stockham passes (one radix-2 pass first for odd log2 K)
 // in shared memory on several rows or columns per thread block.
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -943,19 +944,32 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
             }
         }
     };
+    // records: with H = 2 each lane reads its own axis offset (the work
+    // stores a record row as the 16 runs' x offsets, then their y offsets),
+    // with H = 1 both offsets; PD steps ahead of their use
+    using Rec = typename std::conditional<H == 2, float, float2>::type;
+    constexpr int PD = 3;
+    const Rec* __restrict__ rl = reinterpret_cast<const Rec*>(recs);
+    auto rec_at = [&](int row0, int k) -> Rec { return rl[(size_t)(row0 + k) * 32 + lane]; };
+    auto idx_at = [&](int row0, int k) -> int { return idx[(size_t)(row0 + k) * WID + r]; };
     int set = set_of(0);
     int2 si = make_int2(0, 0), rc = make_int2(0, 0);
-    float2 f0 = make_float2(0.f, 0.f), f1 = make_float2(0.f, 0.f);
-    int i0 = -1, i1 = -1;
+    Rec fq[PD];
+    int fi[PD];
+#pragma unroll
+    for (int j = 0; j < PD; ++j) {
+        fq[j] = Rec{};
+        fi[j] = -1;
+    }
     if (set < nsets) {
         si = set_info[set];
         rc = run_cl[(size_t)set * WID + r];
-        const size_t b0 = (size_t)si.x * WID + r;
-        f0 = recs[b0];
-        if (si.y > 1) f1 = recs[b0 + WID];
-        if (MODE != LANE_GG) {
-            i0 = idx[b0];
-            if (si.y > 1) i1 = idx[b0 + WID];
+#pragma unroll
+        for (int j = 0; j < PD; ++j) {
+            if (si.y > j) {
+                fq[j] = rec_at(si.x, j);
+                if (MODE != LANE_GG) fi[j] = idx_at(si.x, j);
+            }
         }
         if constexpr (HAS_X) patch_async(rc, buf(0));
     }
@@ -1002,44 +1016,53 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
         }
         // the next set's patch (into the buffer read at the start of the
         // previous set) and first records, a whole set ahead of their use
-        float2 nf0 = make_float2(0.f, 0.f), nf1 = make_float2(0.f, 0.f);
-        int ni0 = -1, ni1 = -1;
+        Rec nq[PD];
+        int ni[PD];
+#pragma unroll
+        for (int j = 0; j < PD; ++j) {
+            nq[j] = Rec{};
+            ni[j] = -1;
+        }
         if (has_next) {
             if constexpr (HAS_X) patch_async(nrc, buf(it + 1));
-            const size_t nb = (size_t)nsi.x * WID + r;
-            nf0 = recs[nb];
-            if (nsi.y > 1) nf1 = recs[nb + WID];
-            if (MODE != LANE_GG) {
-                ni0 = idx[nb];
-                if (nsi.y > 1) ni1 = idx[nb + WID];
+#pragma unroll
+            for (int j = 0; j < PD; ++j) {
+                if (nsi.y > j) {
+                    nq[j] = rec_at(nsi.x, j);
+                    if (MODE != LANE_GG) ni[j] = idx_at(nsi.x, j);
+                }
             }
         }
         cp_async_commit();
-        const size_t base = (size_t)si.x * WID + r;
-        const int lmax = si.y;
-        float2 rc0 = f0, rc1 = f1;
-        int ic0 = i0, ic1 = i1;
+        const int row0 = si.x, lmax = si.y;
+        Rec rq[PD];
+        int iq[PD];
+#pragma unroll
+        for (int j = 0; j < PD; ++j) {
+            rq[j] = fq[j];
+            iq[j] = fi[j];
+        }
         float2 yv0 = make_float2(0.f, 0.f);   // gridding: this step's value, one step ahead
-        if (MODE == LANE_GRID && ic0 >= 0) yv0 = yin[ic0];
+        if (MODE == LANE_GRID && iq[0] >= 0) yv0 = yin[iq[0]];
         for (int k = 0; k < lmax; ++k) {
-            // records two steps ahead, the gridding value one step ahead
-            float2 rc2 = make_float2(0.f, 0.f);
-            int ic2 = -1;
-            if (k + 2 < lmax) {
-                rc2 = recs[base + (size_t)(k + 2) * WID];
-                if (MODE != LANE_GG) ic2 = idx[base + (size_t)(k + 2) * WID];
+            // records PD steps ahead, the gridding value one step ahead
+            Rec rn = Rec{};
+            int in = -1;
+            if (k + PD < lmax) {
+                rn = rec_at(row0, k + PD);
+                if (MODE != LANE_GG) in = idx_at(row0, k + PD);
             }
             float2 yv1 = make_float2(0.f, 0.f);
-            if (MODE == LANE_GRID && ic1 >= 0) yv1 = yin[ic1];
+            if (MODE == LANE_GRID && iq[1] >= 0) yv1 = yin[iq[1]];
             const bool valid = k < len;
             float wx[J], wy[RH];
             if constexpr (H == 1) {
-                kb_weights<J>(kp, rc0.x, wx);
-                kb_weights<J>(kp, rc0.y, wy);
+                kb_weights<J>(kp, rq[0].x, wx);
+                kb_weights<J>(kp, rq[0].y, wy);
             } else {
                 // this lane's axis, then the partner's by shuffle
                 float own[J], oth[J];
-                kb_weights<J>(kp, h ? rc0.y : rc0.x, own);
+                kb_weights<J>(kp, rq[0], own);
 #pragma unroll
                 for (int a = 0; a < J; ++a) oth[a] = __shfl_xor_sync(0xffffffffu, own[a], WID);
 #pragma unroll
@@ -1050,10 +1073,6 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
                     const float w1 = RH + i < J ? own[RH + i < J ? RH + i : 0] : 0.f;   // row RH + i (h = 1)
                     wy[i] = h ? w1 : w0;
                 }
-            }
-            if (!valid) {
-#pragma unroll
-                for (int a = 0; a < J; ++a) wx[a] = 0.f;
             }
             float yr = 0.f, yi = 0.f;
             if constexpr (HAS_X) {
@@ -1068,19 +1087,20 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
                 yr = y2.x;
                 yi = y2.y;
                 if constexpr (H == 2) {
-                    // rows of the pair in order: the h = 0 half first
-                    const float pr = __shfl_xor_sync(0xffffffffu, yr, WID);
-                    const float pi = __shfl_xor_sync(0xffffffffu, yi, WID);
-                    yr = h ? pr + yr : yr + pr;
-                    yi = h ? pi + yi : yi + pi;
+                    // the pair's two halves (addition commutes exactly, so
+                    // both lanes hold the same sum)
+                    yr += __shfl_xor_sync(0xffffffffu, yr, WID);
+                    yi += __shfl_xor_sync(0xffffffffu, yi, WID);
                 }
+                // a step past the run's end contributes nothing
+                if (!valid) yr = yi = 0.f;
             }
             if constexpr (MODE == LANE_GRID) {
                 yr = yv0.x;
                 yi = yv0.y;
             }
             if constexpr (MODE == LANE_DEGRID) {
-                if (valid && ic0 >= 0 && h == 0) yout[ic0] = make_float2(yr, yi);
+                if (valid && iq[0] >= 0 && h == 0) yout[iq[0]] = make_float2(yr, yi);
             }
             if constexpr (HAS_ACC) {
 #pragma unroll
@@ -1090,10 +1110,13 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
                     for (int a = 0; a < J; ++a) av[i][a] = __ffma2_rn(make_float2(wx[a], wx[a]), u, av[i][a]);
                 }
             }
-            rc0 = rc1;
-            rc1 = rc2;
-            ic0 = ic1;
-            ic1 = ic2;
+#pragma unroll
+            for (int j = 0; j + 1 < PD; ++j) {
+                rq[j] = rq[j + 1];
+                iq[j] = iq[j + 1];
+            }
+            rq[PD - 1] = rn;
+            iq[PD - 1] = in;
             yv0 = yv1;
         }
         if constexpr (HAS_ACC) {
@@ -1135,10 +1158,11 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
         nset = n2set;
         nsi = n2si;
         nrc = n2rc;
-        f0 = nf0;
-        f1 = nf1;
-        i0 = ni0;
-        i1 = ni1;
+#pragma unroll
+        for (int j = 0; j < PD; ++j) {
+            fq[j] = nq[j];
+            fi[j] = ni[j];
+        }
     }
     cp_async_wait_all();
     pdl_trigger();

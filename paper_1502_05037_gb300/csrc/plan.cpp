@@ -367,7 +367,10 @@ static void build_lanework(purify_plan* p, const std::vector<HostRun>& runs, con
         rows += lmax;
     }
     PURIFY_REQUIRE(rows * width < ((int64_t)1 << 31), "too many visibility records for the lane work");
-    std::vector<float2> lrec((size_t)rows * width, make_float2(0.f, 0.f));
+    PURIFY_REQUIRE(width == 32 || width == 16, "lane work width must be 32 or 16");
+    // record row layout: width 32, (phx, phy) per run; width 16, the 16
+    // runs' phx then their phy (each lane of a pair reads its own axis)
+    std::vector<float> lrec((size_t)rows * 2 * width, 0.f);   // 8 bytes per record
     std::vector<int> lidx((size_t)rows * width, -1), lcal((size_t)rows * width, -1);
     for (int s = 0; s < nsets; ++s)
         for (int l = 0; l < width; ++l) {
@@ -376,8 +379,14 @@ static void build_lanework(purify_plan* p, const std::vector<HostRun>& runs, con
             const int r = order[q0];
             for (int k = 0; k < runs[r].len; ++k) {
                 const Rec& e = rec[start[r] + k];
-                const size_t q = ((size_t)set_info[s].x + k) * width + l;
-                lrec[q] = make_float2((float)e.phx, (float)e.phy);
+                const size_t row = (size_t)set_info[s].x + k, q = row * width + l;
+                if (width == 32) {
+                    lrec[2 * q] = (float)e.phx;
+                    lrec[2 * q + 1] = (float)e.phy;
+                } else {
+                    lrec[row * 2 * width + l] = (float)e.phx;
+                    lrec[row * 2 * width + width + l] = (float)e.phy;
+                }
                 lidx[q] = e.m;
                 lcal[q] = perm[e.m];
             }
