@@ -1042,18 +1042,26 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
             rq[j] = fq[j];
             iq[j] = fi[j];
         }
-        float2 yv0 = make_float2(0.f, 0.f);   // gridding: this step's value, one step ahead
-        if (MODE == LANE_GRID && iq[0] >= 0) yv0 = yin[iq[0]];
+        // gridding: the values of the next YD steps (indices are PD > YD
+        // steps ahead)
+        constexpr int YD = MODE == LANE_GRID ? 2 : 1;
+        static_assert(YD < PD, "value prefetch needs the index further ahead");
+        float2 yq[YD];
+#pragma unroll
+        for (int j = 0; j < YD; ++j) {
+            yq[j] = make_float2(0.f, 0.f);
+            if (MODE == LANE_GRID && iq[j] >= 0) yq[j] = yin[iq[j]];
+        }
         for (int k = 0; k < lmax; ++k) {
-            // records PD steps ahead, the gridding value one step ahead
+            // records PD steps ahead, gridding values YD steps ahead
             Rec rn = Rec{};
             int in = -1;
             if (k + PD < lmax) {
                 rn = rec_at(row0, k + PD);
                 if (MODE != LANE_GG) in = idx_at(row0, k + PD);
             }
-            float2 yv1 = make_float2(0.f, 0.f);
-            if (MODE == LANE_GRID && iq[1] >= 0) yv1 = yin[iq[1]];
+            float2 ynew = make_float2(0.f, 0.f);
+            if (MODE == LANE_GRID && iq[YD] >= 0) ynew = yin[iq[YD]];
             const bool valid = k < len;
             float wx[J], wy[RH];
             if constexpr (H == 1) {
@@ -1096,8 +1104,8 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
                 if (!valid) yr = yi = 0.f;
             }
             if constexpr (MODE == LANE_GRID) {
-                yr = yv0.x;
-                yi = yv0.y;
+                yr = yq[0].x;
+                yi = yq[0].y;
             }
             if constexpr (MODE == LANE_DEGRID) {
                 if (valid && iq[0] >= 0 && h == 0) yout[iq[0]] = make_float2(yr, yi);
@@ -1117,7 +1125,9 @@ k_lane(const float2* __restrict__ X, const float2* __restrict__ yin, float2* __r
             }
             rq[PD - 1] = rn;
             iq[PD - 1] = in;
-            yv0 = yv1;
+#pragma unroll
+            for (int j = 0; j + 1 < YD; ++j) yq[j] = yq[j + 1];
+            yq[YD - 1] = ynew;
         }
         if constexpr (HAS_ACC) {
             if (len > 0) {
