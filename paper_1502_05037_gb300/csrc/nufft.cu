@@ -1,4 +1,5 @@
-// Measurement operator Phi = G F Z S and its adjoint S Z^T F^H G^H.
+// Measurement operator Phi = G F Z S and its adjoint S Z^T F^H G^H: the
+// gridding steps and the operator-level launchers.
 //
 // The paper (Sec. 1) writes the measurement equation as y = Phi x + n and
 // leaves the discretisation open; the plan realises Phi with Kaiser-Bessel
@@ -7,11 +8,11 @@
 //               other K - ny grid rows are zero and never stored);
 //   cols_fwd  : column pass of F, treating the missing rows as zeros;
 //   degrid    : G, J x J separable Kaiser-Bessel interpolation per visibility;
-//   grid      : G^H, per-tile shared-memory accumulation of the footprints;
+//   grid      : G^H, accumulation of the J x J footprints;
 //   cols_inv  : column pass of F^H producing only the ny rows kept by Z^T;
 //   rows_inv  : row pass of F^H fused with Z^T (crop) and S.
-// FFTs are radix-4 Stockham passes (one radix-2 pass first for odd log2 K)
-// in shared memory on several rows or columns per thread block.
+// The four FFT passes (radix-8 Stockham transforms in shared memory) are in
+// fft.cu; this file holds G, G^H, the fused G^H G and the launchers.
 #include <type_traits>
 #include <cuda_runtime.h>
 
@@ -23,382 +24,6 @@
 #include "reduce.cuh"
 
 namespace purify {
-
-// --------------------------------------------------------------- FFT core
-// Length-N transforms (N = 2^logN >= 16) by Stockham autosort stages, N / 8
-// threads per transform, eight values per thread in registers. A stage of
-// radix r over span Ns (the product of the earlier radices) takes butterfly
-// j's inputs v_k = x[j + k N / r], multiplies v_k by W_{r Ns}^{(j mod Ns) k},
-// forms the r-point DFT V_q = sum_k v_k W_r^{k q} and writes V_q to
-// ((j - j mod Ns) r + j mod Ns + q Ns). The first stage (Ns = 1, radix 2, 4
-// or 8 so that the rest are radix 8) needs no twiddles and reads the input
-// through `load`; the last (Ns = N / 8) writes element j + q N / 8 through
-// `store`; the stages in between exchange through shared memory (`slot`).
-// Forward uses W_n = exp(-2 pi i / n), inverse its conjugate (unnormalised).
-template <typename C, bool INV> __device__ __forceinline__ C mul_neg_i(C a) {
-    // forward: -i a; inverse: +i a
-    return INV ? cmake<C>(-a.y, a.x) : cmake<C>(a.y, -a.x);
-}
-
-template <typename C, bool INV> __device__ __forceinline__ void dft2(C& a0, C& a1) {
-    C t = a0;
-    a0 = cadd(t, a1);
-    a1 = csub(t, a1);
-}
-
-// 4-point DFT, natural order in and out
-template <typename C, bool INV> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
-    C t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = mul_neg_i<C, INV>(csub(a1, a3));
-    a0 = cadd(t0, t2);
-    a1 = cadd(t1, t3);
-    a2 = csub(t0, t2);
-    a3 = csub(t1, t3);
-}
-
-// 8-point DFT, natural order in and out: two 4-point DFTs of the even and odd
-// samples combined with W_8^q.
-template <typename C, bool INV> __device__ __forceinline__ void dft8(C (&v)[8]) {
-    using T = decltype(C::x);
-    const T h = T(0.70710678118654752440084436210484904);   // 1 / sqrt(2)
-    dft4<C, INV>(v[0], v[2], v[4], v[6]);
-    dft4<C, INV>(v[1], v[3], v[5], v[7]);
-    // odd part times W_8^q, q = 1, 2, 3
-    C o1 = v[3], o2 = v[5], o3 = v[7];
-    // W_8 = (1 -+ i) / sqrt(2), W_8^3 = (-1 -+ i) / sqrt(2)
-    if (INV) {
-        o1 = cmake<C>(h * (o1.x - o1.y), h * (o1.x + o1.y));
-        o3 = cmake<C>(-h * (o3.x + o3.y), h * (o3.x - o3.y));
-    } else {
-        o1 = cmake<C>(h * (o1.x + o1.y), h * (o1.y - o1.x));
-        o3 = cmake<C>(h * (o3.y - o3.x), -h * (o3.x + o3.y));
-    }
-    o2 = mul_neg_i<C, INV>(o2);
-    const C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
-    v[0] = cadd(e0, o0);
-    v[4] = csub(e0, o0);
-    v[1] = cadd(e1, o1);
-    v[5] = csub(e1, o1);
-    v[2] = cadd(e2, o2);
-    v[6] = csub(e2, o2);
-    v[3] = cadd(e3, o3);
-    v[7] = csub(e3, o3);
-}
-
-// shared-memory index of element n with one pad slot per 8 (keeps the
-// stride-8 writes of the early stages off a single bank)
-__device__ __forceinline__ int fft_pad(int n) { return n + (n >> 3); }
-__host__ __device__ inline int fft_padded(int n) { return n + (n >> 3); }
-
-template <typename C, bool INV, typename Load, typename Store, typename Slot>
-__device__ __forceinline__ void fft_reg(int N, int logN, int t, const C* __restrict__ tw, Load load, Store store,
-                                        Slot slot) {
-    const int N8 = N >> 3;
-    const int r0 = (logN % 3 == 0) ? 8 : (logN % 3 == 1 ? 2 : 4);
-    C v[8];
-    if (r0 == 8) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = load(t + k * N8);
-        dft8<C, INV>(v);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) slot(t * 8 + q) = v[q];
-    } else if (r0 == 4) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = load(t + k * N8);
-        // butterflies j = t (inputs k = 0, 2, 4, 6) and j = t + N/8 (1, 3, 5, 7)
-        dft4<C, INV>(v[0], v[2], v[4], v[6]);
-        dft4<C, INV>(v[1], v[3], v[5], v[7]);
-        const int j1 = t + N8;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            slot(t * 4 + q) = v[2 * q];
-            slot(j1 * 4 + q) = v[2 * q + 1];
-        }
-    } else {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = load(t + k * N8);
-        // butterflies j = t + m N/8, m < 4, inputs m and m + 4
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            dft2<C, INV>(v[m], v[m + 4]);
-            slot((t + m * N8) * 2) = v[m];
-            slot((t + m * N8) * 2 + 1) = v[m + 4];
-        }
-    }
-    for (int Ns = r0; Ns < N; Ns <<= 3) {
-        __syncthreads();
-        const int kk = t & (Ns - 1);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = slot(t + k * N8);
-        // W^{k ts} for k = 1..7 from three table entries (k = 1, 2, 4) and
-        // four products
-        const int ts = kk * (N8 / Ns);
-        C w[8];
-        w[1] = tw[ts];
-        w[2] = tw[2 * ts];
-        w[4] = tw[4 * ts];
-        w[3] = cmul(w[1], w[2]);
-        w[5] = cmul(w[1], w[4]);
-        w[6] = cmul(w[2], w[4]);
-        w[7] = cmul(w[3], w[4]);
-#pragma unroll
-        for (int k = 1; k < 8; ++k) v[k] = INV ? cmulconj(v[k], w[k]) : cmul(v[k], w[k]);
-        dft8<C, INV>(v);
-        if (Ns == N8) {
-#pragma unroll
-            for (int q = 0; q < 8; ++q) store(t + q * N8, v[q]);
-        } else {
-            __syncthreads();
-            const int base = (t - kk) * 8 + kk;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) slot(base + q * Ns) = v[q];
-        }
-    }
-}
-
-__host__ __device__ inline int ilog2(int n) { int l = 0; while ((1 << l) < n) ++l; return l; }
-
-// ------------------------------------------------------------ row passes
-// Row kernels: a block holds rb transforms of length Kx, thread
-// (f, t) = (tid / (Kx/8), tid mod (Kx/8)); row f's shared slots are
-// [f * pad(Kx), (f + 1) * pad(Kx)).
-//
-// S Z and the forward row FFT: rows [i0, i0+rb) of the image to rows[i][0..Kx).
-// With a CG fold (fold.x set) the input is the residual r after the step's
-// update (see CgFold), not x. When zero_grid != null block b also clears rows
-// [b Ky/gridDim, (b+1) Ky/gridDim) of that Ky x Kx complex grid (the gridding
-// accumulator of the same CG step, or of the adjoint that follows Phi).
-template <typename T>
-__global__ void __launch_bounds__(1024) k_rows_fwd(const T* __restrict__ x, typename cplx_of<T>::type* __restrict__ rows,
-                           const T* __restrict__ sx, const T* __restrict__ sy,
-                           const typename cplx_of<T>::type* __restrict__ tw, int nx, int ny, int Kx,
-                           int rb, T scale, const int* __restrict__ skip,
-                           typename cplx_of<T>::type* __restrict__ zero_grid, int Ky, CgFold fold) {
-    using C = typename cplx_of<T>::type;
-    pdl_wait();
-    // step 0 starts the solve; later steps first apply the previous step's
-    // update unless it met the stop test (see CgFold)
-    const bool first = fold.x && fold.step == 0;
-    T* const fx = static_cast<T*>(fold.x);
-    T* const fr = static_cast<T*>(fold.r);
-    T* const fs = static_cast<T*>(fold.s);
-    T* const pdir = static_cast<T*>(fold.p);
-    const T* const fu = static_cast<const T*>(fold.u);
-    const T* const fadd = static_cast<const T*>(fold.add);
-    // stopped at an earlier step (block 0 of this pass may set the flag
-    // meanwhile: each block reads it once)
-    if (block_flag(first ? nullptr : skip)) return;
-    bool pending = false;
-    T alpha = T(0), cbeta = T(0);
-    if (fold.x && !first) {
-        // the previous step's update (it did not stop the solve: checked above)
-        double al, be;
-        if (!cg_pending(fold, al, be)) return;
-        pending = true;
-        alpha = (T)al;
-        cbeta = (T)be;
-    }
-    if (first && blockIdx.x == 0 && threadIdx.x == 0) fold.flags[F_CGDONE] = 0;   // the next kernels read it
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (zero_grid) {
-        const int per = Ky / gridDim.x;   // whole rows per block (Ky is a multiple of the block count)
-        C* g = zero_grid + (size_t)blockIdx.x * per * Kx;
-        for (int t = threadIdx.x; t < per * Kx; t += blockDim.x) g[t] = cmake<C>(T(0), T(0));
-    }
-    const int N8 = Kx >> 3;
-    const int f = threadIdx.x / N8, t = threadIdx.x - f * N8;
-    C* buf = reinterpret_cast<C*>(smem_raw) + f * fft_padded(Kx);
-    const int i = blockIdx.x * rb + f;
-    const T rs = sy[i] * scale;
-    auto load = [&](int p1) -> C {
-        // pixel column j with (j - nx/2) mod Kx == p1
-        const int j = (p1 < Kx / 2 ? p1 : p1 - Kx) + nx / 2;
-        T val = T(0);
-        if (j >= 0 && j < nx) {
-            const size_t idx = (size_t)i * nx + j;
-            T xv;
-            if (fold.x) {
-                // Chronopoulos-Gear update, then the transform of the new r
-                T rv = fr[idx];
-                if (first) {
-                    if (fadd) {
-                        rv += fadd[idx];
-                        fr[idx] = rv;
-                    }
-                    pdir[idx] = T(0);
-                    fs[idx] = T(0);
-                } else if (pending) {
-                    const T pv = rv + cbeta * pdir[idx];
-                    const T sv = fu[idx] + cbeta * fs[idx];
-                    pdir[idx] = pv;
-                    fs[idx] = sv;
-                    fx[idx] += alpha * pv;
-                    rv = rv - alpha * sv;
-                    fr[idx] = rv;
-                }
-                xv = rv;
-            } else {
-                xv = x[idx];
-            }
-            val = xv * sx[j] * rs;
-        }
-        return cmake<C>(val, T(0));
-    };
-    auto store = [&](int k, C v) { rows[(size_t)i * Kx + k] = v; };
-    auto slot = [&](int n) -> C& { return buf[fft_pad(n)]; };
-    fft_reg<C, false>(Kx, ilog2(Kx), t, tw, load, store, slot);
-    pdl_trigger();
-}
-
-// Column kernels: a block holds cb adjacent columns, thread
-// (t, f) = (tid / cb, tid mod cb) so that a warp's global accesses cover cb
-// consecutive cells of each row; element n of column f sits in shared slot
-// pad(n) * cb + f.
-//
-// Forward column FFT over columns [c0, c0+cb): the only non-zero grid rows
-// are p2 = (i - ny/2) mod Ky for image rows i.
-template <typename T>
-__global__ void __launch_bounds__(1024) k_cols_fwd(const typename cplx_of<T>::type* __restrict__ rows,
-                           typename cplx_of<T>::type* __restrict__ grid,
-                           const typename cplx_of<T>::type* __restrict__ tw, int ny, int Kx, int Ky,
-                           int cb, const int* __restrict__ skip) {
-    using C = typename cplx_of<T>::type;
-    pdl_wait();
-    if (skip && *skip) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
-    const int t = threadIdx.x / cb, f = threadIdx.x - t * cb;
-    const int c = blockIdx.x * cb + f;
-    auto load = [&](int k) -> C {
-        const int i = (k < Ky / 2 ? k : k - Ky) + ny / 2;
-        return (i >= 0 && i < ny) ? rows[(size_t)i * Kx + c] : cmake<C>(T(0), T(0));
-    };
-    auto store = [&](int k, C v) { grid[(size_t)k * Kx + c] = v; };
-    auto slot = [&](int n) -> C& { return buf[fft_pad(n) * cb + f]; };
-    fft_reg<C, false>(Ky, ilog2(Ky), t, tw, load, store, slot);
-    pdl_trigger();
-}
-
-// Inverse column FFT over columns [c0, c0+cb) (grid optionally multiplied
-// elementwise by `mult` first), keeping only the image rows.
-template <typename T>
-__global__ void __launch_bounds__(1024) k_cols_inv(const typename cplx_of<T>::type* __restrict__ grid,
-                           typename cplx_of<T>::type* __restrict__ rows,
-                           const typename cplx_of<T>::type* __restrict__ tw, int ny, int Kx, int Ky,
-                           int cb, const int* __restrict__ skip, const T* __restrict__ mult) {
-    using C = typename cplx_of<T>::type;
-    pdl_wait();
-    if (skip && *skip) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
-    const int t = threadIdx.x / cb, f = threadIdx.x - t * cb;
-    const int c = blockIdx.x * cb + f;
-    auto load = [&](int k) -> C {
-        const size_t g = (size_t)k * Kx + c;
-        C v = grid[g];
-        if (mult) v = cscale(v, mult[g]);
-        return v;
-    };
-    auto store = [&](int p2, C v) {
-        const int i = (p2 + ny / 2) & (Ky - 1);
-        if (i < ny) rows[(size_t)i * Kx + c] = v;
-    };
-    auto slot = [&](int n) -> C& { return buf[fft_pad(n) * cb + f]; };
-    fft_reg<C, true>(Ky, ilog2(Ky), t, tw, load, store, slot);
-    pdl_trigger();
-}
-
-// Inverse row FFT of image rows [i0, i0+rb), then Z^T and S:
-//   out_mode 0: complex out[i][j] = scale * s * v
-//   out_mode 1: real    out[i][j] = scale * s * Re v + add_coef * (add ? add[i][j] : 0)
-// With cg.part set (a CG step: out = A r, add = r, see CgFold) the kernel
-// also writes per-block partials of r . r and r . A r, and its last block
-// reduces them and decides the step (cg_decide).
-template <typename T, int MAXT>
-__global__ void __launch_bounds__(MAXT) k_rows_inv(const typename cplx_of<T>::type* __restrict__ rows, void* out,
-                           const T* __restrict__ sx, const T* __restrict__ sy,
-                           const typename cplx_of<T>::type* __restrict__ tw, int nx, int ny, int Kx,
-                           int rb, T scale, int out_mode, const T* __restrict__ add, T add_coef,
-                           const int* __restrict__ skip, CgFold cgf) {
-    using C = typename cplx_of<T>::type;
-    pdl_wait();
-    if (skip && *skip) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N8 = Kx >> 3;
-    const int f = threadIdx.x / N8, t = threadIdx.x - f * N8;
-    C* buf = reinterpret_cast<C*>(smem_raw) + f * fft_padded(Kx);
-    const int i = blockIdx.x * rb + f;
-    const T rs = sy[i] * scale;
-    T dacc = 0, gacc2 = 0;   // add.out, and with the folded CG add.add (add = r, out = A r)
-    const bool cg = cgf.part != nullptr;
-    auto load = [&](int k) -> C { return rows[(size_t)i * Kx + k]; };
-    auto store = [&](int p1, C v) {
-        const int j = (p1 + nx / 2) & (Kx - 1);
-        if (j >= nx) return;
-        const T s = sx[j] * rs;
-        const size_t idx = (size_t)i * nx + j;
-        if (out_mode == 0) {
-            reinterpret_cast<C*>(out)[idx] = cscale(v, s);
-        } else {
-            T r = v.x * s;
-            if (add) {
-                const T a = add[idx];
-                r += add_coef * a;
-                dacc += a * r;
-                if (cg) gacc2 += a * a;
-            }
-            reinterpret_cast<T*>(out)[idx] = r;
-        }
-    };
-    auto slot = [&](int n) -> C& { return buf[fft_pad(n)]; };
-    fft_reg<C, true>(Kx, ilog2(Kx), t, tw, load, store, slot);
-    if (cg) {
-        // Chronopoulos-Gear partials (see CgFold): gamma = r.r, delta = r.A r;
-        // the consumer of this step's scalars reduces them
-        const double b0 = block_sum_t(gacc2);
-        const double b1 = block_sum_t(dacc);
-        if (threadIdx.x == 0) {
-            cgf.part[2 * blockIdx.x] = b0;
-            cgf.part[2 * blockIdx.x + 1] = b1;
-        }
-        if (arrive_last(cgf.counter)) {
-            cg_decide(cgf, cgf.step, gridDim.x);
-            if (threadIdx.x == 0) *cgf.counter = 0;
-        }
-    }
-    pdl_trigger();
-}
-
-// Plain in-place 2-D FFT pieces (purify_fft2): full row pass / column pass.
-// In place is safe: every input element is read in the first stage, before
-// the first barrier, and every output is written in the last.
-template <typename T, bool INV>
-__global__ void __launch_bounds__(1024) k_rows_full(typename cplx_of<T>::type* grid, const typename cplx_of<T>::type* __restrict__ tw,
-                            int Kx, int rb) {
-    using C = typename cplx_of<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int N8 = Kx >> 3;
-    const int f = threadIdx.x / N8, t = threadIdx.x - f * N8;
-    C* buf = reinterpret_cast<C*>(smem_raw) + f * fft_padded(Kx);
-    C* row = grid + ((size_t)blockIdx.x * rb + f) * Kx;
-    auto load = [&](int k) -> C { return row[k]; };
-    auto store = [&](int k, C v) { row[k] = v; };
-    auto slot = [&](int n) -> C& { return buf[fft_pad(n)]; };
-    fft_reg<C, INV>(Kx, ilog2(Kx), t, tw, load, store, slot);
-}
-
-template <typename T, bool INV>
-__global__ void __launch_bounds__(1024) k_cols_full(typename cplx_of<T>::type* grid, const typename cplx_of<T>::type* __restrict__ tw,
-                            int Kx, int Ky, int cb) {
-    using C = typename cplx_of<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
-    const int t = threadIdx.x / cb, f = threadIdx.x - t * cb;
-    const int c = blockIdx.x * cb + f;
-    auto load = [&](int k) -> C { return grid[(size_t)k * Kx + c]; };
-    auto store = [&](int k, C v) { grid[(size_t)k * Kx + c] = v; };
-    auto slot = [&](int n) -> C& { return buf[fft_pad(n) * cb + f]; };
-    fft_reg<C, INV>(Ky, ilog2(Ky), t, tw, load, store, slot);
-}
 
 // ------------------------------------------------------ gridding helpers
 __device__ __forceinline__ void atomic_add_c(float2* a, float2 v) { atomicAdd(a, v); }
@@ -1307,102 +932,10 @@ k_degrid_tile(const typename cplx_of<T>::type* __restrict__ grid, const T* __res
 }
 
 // ------------------------------------------------------------- launchers
-// FFT launch shapes: K / 8 threads per transform; transforms per block
-// (rows rb, columns cb) chosen so that a block has at most 512 threads and
-// the grid covers the 152 SMs about twice; the autotuner may override.
-static int fft_block_limit(int K, size_t cbytes) {
-    int nb = 1;
-    while (nb < 8 && 2 * nb * (K / 8) <= 512 && 2 * (size_t)nb * fft_padded(K) * cbytes <= 160 * 1024) nb *= 2;
-    return nb;
-}
-template <typename T> static int rows_per_block(int nrows, int K) {
-    int rb = std::min(fft_block_limit(K, sizeof(typename cplx_of<T>::type)), std::max(1, nrows / 256));
-    while (rb > 1 && nrows % rb) rb >>= 1;
-    return rb;
-}
-template <typename T> static int cols_per_block(int Ky, int Kx) {
-    int cb = std::min(fft_block_limit(Ky, sizeof(typename cplx_of<T>::type)), std::max(1, Kx / 256));
-    while (cb > 1 && Kx % cb) cb >>= 1;
-    return cb;
-}
-bool fft_shape_ok(int nb, int K, int dtype) {
-    const size_t cbytes = dtype == PURIFY_F32 ? 8 : 16;
-    return nb * (K / 8) <= 1024 && (size_t)nb * fft_padded(K) * cbytes <= 160 * 1024;
-}
-
 template <typename K> static void set_smem(K kernel, size_t bytes) {
     if (bytes > 48 * 1024) PURIFY_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
 }
 
-template <typename T>
-static void rows_fwd_t(purify_plan* p, const void* x, double scale, const int* skip, bool corr, bool zero_acc,
-                       const CgFold* fold) {
-    using C = typename cplx_of<T>::type;
-    int rb = p->fft_rb > 0 ? p->fft_rb : rows_per_block<T>(p->ny, p->Kx);
-    while (p->ny % rb) rb >>= 1;
-    size_t sm = (size_t)rb * fft_padded(p->Kx) * sizeof(C);
-    set_smem(k_rows_fwd<T>, sm);
-    Launch L(p, "fft_rows_fwd");
-    launch_dependent(k_rows_fwd<T>, p->ny / rb, rb * (p->Kx / 8), sm, p->stream,
-        (const T*)x, p->rows.as<C>(), corr ? p->sx.as<T>() : p->onesx.as<T>(),
-        corr ? p->sy.as<T>() : p->onesy.as<T>(), p->twx.as<C>(), p->nx, p->ny, p->Kx,
-        rb, (T)scale, skip, zero_acc ? p->gacc.as<C>() : nullptr, p->Ky,
-        fold ? *fold : CgFold());
-    L.done();
-}
-
-template <typename T> static void cols_fwd_t(purify_plan* p, const int* skip) {
-    using C = typename cplx_of<T>::type;
-    int cb = p->fft_cb > 0 ? p->fft_cb : cols_per_block<T>(p->Ky, p->Kx);
-    size_t sm = (size_t)cb * fft_padded(p->Ky) * sizeof(C);
-    set_smem(k_cols_fwd<T>, sm);
-    Launch L(p, "fft_cols_fwd");
-    launch_dependent(k_cols_fwd<T>, p->Kx / cb, cb * (p->Ky / 8), sm, p->stream, p->rows.as<C>(), p->grid.as<C>(),
-                     p->twy.as<C>(), p->ny, p->Kx, p->Ky, cb, skip);
-    L.done();
-}
-
-template <typename T> static void cols_inv_t(purify_plan* p, const int* skip, const void* mult) {
-    using C = typename cplx_of<T>::type;
-    int cb = p->fft_cb > 0 ? p->fft_cb : cols_per_block<T>(p->Ky, p->Kx);
-    size_t sm = (size_t)cb * fft_padded(p->Ky) * sizeof(C);
-    set_smem(k_cols_inv<T>, sm);
-    Launch L(p, "fft_cols_inv");
-    // the adjoint reads the gridding output; the circulant path the forward grid
-    const C* src = mult ? p->grid.as<C>() : p->gacc.as<C>();
-    launch_dependent(k_cols_inv<T>, p->Kx / cb, cb * (p->Ky / 8), sm, p->stream, src, p->rows.as<C>(),
-                     p->twy.as<C>(), p->ny, p->Kx, p->Ky, cb, skip, (const T*)mult);
-    L.done();
-}
-
-template <typename T>
-static void rows_inv_t(purify_plan* p, void* out, double scale, int out_mode, const void* add, double add_coef,
-                       const int* skip, const CgFold* cg, bool corr) {
-    using C = typename cplx_of<T>::type;
-    int rb = p->fft_rb > 0 ? p->fft_rb : rows_per_block<T>(p->ny, p->Kx);
-    while (p->ny % rb) rb >>= 1;
-    size_t sm = (size_t)rb * fft_padded(p->Kx) * sizeof(C);
-    const int nt = rb * (p->Kx / 8);
-    // the fused epilogue needs more than 64 registers: blocks of at most 512
-    // threads get them, 1024-thread blocks (8192-point rows) take spills
-    auto kern = nt <= 512 ? k_rows_inv<T, 512> : k_rows_inv<T, 1024>;
-    set_smem(kern, sm);
-    Launch L(p, "fft_rows_inv");
-    launch_dependent(kern, p->ny / rb, nt, sm, p->stream, p->rows.as<C>(), out, corr ? p->sx.as<T>() : p->onesx.as<T>(),
-                                            corr ? p->sy.as<T>() : p->onesy.as<T>(), p->twx.as<C>(), p->nx, p->ny,
-                                            p->Kx, rb, (T)scale, out_mode, (const T*)add, (T)add_coef, skip,
-                                            cg ? *cg : CgFold());
-    L.done();
-}
-
-
-int rows_inv_blocks(purify_plan* p) {
-    int rb = p->fft_rb > 0 ? p->fft_rb
-                           : (p->dtype == PURIFY_F32 ? rows_per_block<float>(p->ny, p->Kx)
-                                                     : rows_per_block<double>(p->ny, p->Kx));
-    while (p->ny % rb) rb >>= 1;
-    return p->ny / rb;
-}
 
 template <typename T, int J> static void degrid_tj(purify_plan* p, void* y, bool caller_order, const int* skip) {
     using C = typename cplx_of<T>::type;
@@ -1645,23 +1178,6 @@ int max_grid_tile(int dtype, int J) {
     return t;
 }
 
-void launch_scale_pad_rows(purify_plan* p, const void* x, double scale, const int* skip, bool corr, bool zero_acc,
-                           const CgFold* fold) {
-    if (p->dtype == PURIFY_F32) rows_fwd_t<float>(p, x, scale, skip, corr, zero_acc, fold);
-    else rows_fwd_t<double>(p, x, scale, skip, corr, zero_acc, fold);
-}
-
-void launch_cols_fwd(purify_plan* p, const int* skip) {
-    if (p->dtype == PURIFY_F32) cols_fwd_t<float>(p, skip); else cols_fwd_t<double>(p, skip);
-}
-void launch_cols_inv(purify_plan* p, const int* skip, const void* mult) {
-    if (p->dtype == PURIFY_F32) cols_inv_t<float>(p, skip, mult); else cols_inv_t<double>(p, skip, mult);
-}
-void launch_rows_inv_crop(purify_plan* p, void* out, double scale, int out_mode, const void* add, double add_coef,
-                          const int* skip, const CgFold* cg, bool corr) {
-    if (p->dtype == PURIFY_F32) rows_inv_t<float>(p, out, scale, out_mode, add, add_coef, skip, cg, corr);
-    else rows_inv_t<double>(p, out, scale, out_mode, add, add_coef, skip, cg, corr);
-}
 void launch_degrid(purify_plan* p, void* y, bool caller_order, const int* skip) {
     if (p->degrid_kind >= 3) {
         launch_degrid_lanes(p, p->degrid_kind, y, caller_order, skip);
@@ -1694,30 +1210,6 @@ void launch_phi_adj(purify_plan* p, const void* y, void* out, bool caller_order,
     launch_grid(p, y, caller_order, nullptr, acc_zeroed);
     launch_cols_inv(p, nullptr);
     launch_rows_inv_crop(p, out, scale, out_mode, add, 1.0, nullptr);
-}
-
-template <typename T> static void fft2_t(purify_plan* p, void* grid, bool inverse) {
-    using C = typename cplx_of<T>::type;
-    int rb = rows_per_block<T>(p->Ky, p->Kx);
-    size_t smr = (size_t)rb * fft_padded(p->Kx) * sizeof(C);
-    int cb = cols_per_block<T>(p->Ky, p->Kx);
-    size_t smc = (size_t)cb * fft_padded(p->Ky) * sizeof(C);
-    const int tr = rb * (p->Kx / 8), tc = cb * (p->Ky / 8);
-    if (inverse) {
-        set_smem(k_rows_full<T, true>, smr);
-        set_smem(k_cols_full<T, true>, smc);
-        { Launch L(p, "fft_full_rows"); k_rows_full<T, true><<<p->Ky / rb, tr, smr, p->stream>>>((C*)grid, p->twx.as<C>(), p->Kx, rb); L.done(); }
-        { Launch L(p, "fft_full_cols"); k_cols_full<T, true><<<p->Kx / cb, tc, smc, p->stream>>>((C*)grid, p->twy.as<C>(), p->Kx, p->Ky, cb); L.done(); }
-    } else {
-        set_smem(k_rows_full<T, false>, smr);
-        set_smem(k_cols_full<T, false>, smc);
-        { Launch L(p, "fft_full_rows"); k_rows_full<T, false><<<p->Ky / rb, tr, smr, p->stream>>>((C*)grid, p->twx.as<C>(), p->Kx, rb); L.done(); }
-        { Launch L(p, "fft_full_cols"); k_cols_full<T, false><<<p->Kx / cb, tc, smc, p->stream>>>((C*)grid, p->twy.as<C>(), p->Kx, p->Ky, cb); L.done(); }
-    }
-}
-
-void launch_fft2(purify_plan* p, void* grid, bool inverse) {
-    if (p->dtype == PURIFY_F32) fft2_t<float>(p, grid, inverse); else fft2_t<double>(p, grid, inverse);
 }
 
 }  // namespace purify
