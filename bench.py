@@ -460,7 +460,9 @@ def run_ours(args):
     decomposition = {"grid": inf.grid_mode, "degrid": inf.degrid_mode, "normal": inf.normal_mode,
                      "lane_tile": inf.lane_tile, "legend": "1 tile subproblems, 2 run sets, 3 a lane per run, 4 a lane pair per run, "
                                "5 a lane pair per run with runs grouped by grid tile, 6 a lane pair per run with "
-                               "stored patches summed per cell in a fixed order (deterministic)"}
+                               "stored patches summed per cell in a fixed order (deterministic)",
+                     "fft": {"rows_per_block": inf.fft_rows_per_block, "cols_per_block": inf.fft_cols_per_block,
+                             "cols_per_thread": inf.fft_cols_per_thread}}
 
     # ---- pass C: end to end through the public API with pinned host buffers
     y_host = torch.empty(wl.M, dtype=cdt, pin_memory=True)

@@ -115,6 +115,9 @@ typedef struct {
     int32_t normal_mode;           /* the fused G^H G of the CG normal operator: 2 runs, 3..5 lanes,
                                       6 deterministic lanes */
     int32_t lane_tile;             /* grid tile edge grouping the runs of normal_mode 5 (else 0) */
+    int32_t fft_rows_per_block;    /* FFT launch shape in use: row transforms per block, */
+    int32_t fft_cols_per_block;    /* column transforms per block, */
+    int32_t fft_cols_per_thread;   /* and column transforms per thread (2: packed FP32 pairs) */
 } purify_plan_info;
 purify_status purify_plan_get_info(const purify_plan *plan, purify_plan_info *info);
 

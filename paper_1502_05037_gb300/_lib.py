@@ -48,6 +48,9 @@ class purify_plan_info(C.Structure):
         ("degrid_mode", C.c_int32),
         ("normal_mode", C.c_int32),
         ("lane_tile", C.c_int32),
+        ("fft_rows_per_block", C.c_int32),
+        ("fft_cols_per_block", C.c_int32),
+        ("fft_cols_per_thread", C.c_int32),
     ]
 
 

@@ -171,6 +171,7 @@ purify_status purify_plan_get_info(const purify_plan* plan, purify_plan_info* in
         info->degrid_mode = plan->degrid_kind;
         info->normal_mode = plan->normal_kind;
         info->lane_tile = plan->normal_kind == 5 ? plan->lanes[2].tile : 0;
+        fft_launch_shape(plan, info->fft_rows_per_block, info->fft_cols_per_block, info->fft_cols_per_thread);
     });
 }
 

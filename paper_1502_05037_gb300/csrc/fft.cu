@@ -192,11 +192,189 @@ __device__ __forceinline__ void fft_core(int t, const C* __restrict__ tw, Load l
     }
 }
 
+// ------------------------------------------- two FP32 transforms per thread
+// The same Stockham stages on element n of two transforms at once (two rows
+// of a block, or two adjacent columns): a P2 holds their values as packed
+// pairs (re = (re_0, re_1), im = (im_0, im_1)), so that every butterfly and
+// twiddle product is one packed two-lane FP32 instruction for both
+// transforms and a shared-memory exchange moves 16 bytes. Each lane computes
+// what the one-transform core computes, operation for operation.
+struct P2 {
+    float2 re, im;
+};
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b, rounded once like a subtraction
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ P2 padd(P2 a, P2 b) { return P2{add2(a.re, b.re), add2(a.im, b.im)}; }
+__device__ __forceinline__ P2 psub(P2 a, P2 b) { return P2{sub2(a.re, b.re), sub2(a.im, b.im)}; }
+// v times w (forward) or conj(w) (inverse); w = (wr, wi) broadcast to both lanes
+template <bool INV> __device__ __forceinline__ P2 pmul(P2 v, float2 wr, float2 wi) {
+    if (INV) return P2{__ffma2_rn(v.re, wr, __fmul2_rn(v.im, wi)), __ffma2_rn(v.im, wr, __fmul2_rn(v.re, make_float2(-wi.x, -wi.y)))};
+    return P2{__ffma2_rn(v.re, wr, __fmul2_rn(v.im, make_float2(-wi.x, -wi.y))), __ffma2_rn(v.im, wr, __fmul2_rn(v.re, wi))};
+}
+
+// 4-point DFT of both lanes; the -i (forward) or +i (inverse) factor is
+// folded into the last additions
+template <bool INV> __device__ __forceinline__ void pdft4(P2& a0, P2& a1, P2& a2, P2& a3) {
+    const P2 t0 = padd(a0, a2), t1 = psub(a0, a2), t2 = padd(a1, a3), d = psub(a1, a3);
+    a0 = padd(t0, t2);
+    a2 = psub(t0, t2);
+    if (INV) {   // t3 = i d = (-d.im, d.re)
+        a1 = P2{sub2(t1.re, d.im), add2(t1.im, d.re)};
+        a3 = P2{add2(t1.re, d.im), sub2(t1.im, d.re)};
+    } else {     // t3 = -i d = (d.im, -d.re)
+        a1 = P2{add2(t1.re, d.im), sub2(t1.im, d.re)};
+        a3 = P2{sub2(t1.re, d.im), add2(t1.im, d.re)};
+    }
+}
+
+template <bool INV> __device__ __forceinline__ void pdft8(P2 (&v)[8]) {
+    const float h = 0.70710678118654752440084436210484904f;   // 1 / sqrt(2)
+    pdft4<INV>(v[0], v[2], v[4], v[6]);
+    pdft4<INV>(v[1], v[3], v[5], v[7]);
+    P2 o1 = v[3], o3 = v[7];
+    const P2 o2 = v[5];
+    // o1 W_8, o3 W_8^3; W_8 = (1 -+ i) / sqrt(2), W_8^3 = (-1 -+ i) / sqrt(2)
+    if (INV) {
+        o1 = P2{__fmul2_rn(bc2(h), sub2(o1.re, o1.im)), __fmul2_rn(bc2(h), add2(o1.re, o1.im))};
+        o3 = P2{__fmul2_rn(bc2(-h), add2(o3.re, o3.im)), __fmul2_rn(bc2(h), sub2(o3.re, o3.im))};
+    } else {
+        o1 = P2{__fmul2_rn(bc2(h), add2(o1.re, o1.im)), __fmul2_rn(bc2(h), sub2(o1.im, o1.re))};
+        o3 = P2{__fmul2_rn(bc2(h), sub2(o3.im, o3.re)), __fmul2_rn(bc2(-h), add2(o3.re, o3.im))};
+    }
+    const P2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1];
+    v[0] = padd(e0, o0);
+    v[4] = psub(e0, o0);
+    v[1] = padd(e1, o1);
+    v[5] = psub(e1, o1);
+    // e2 -+ i o2
+    if (INV) {
+        v[2] = P2{sub2(e2.re, o2.im), add2(e2.im, o2.re)};
+        v[6] = P2{add2(e2.re, o2.im), sub2(e2.im, o2.re)};
+    } else {
+        v[2] = P2{add2(e2.re, o2.im), sub2(e2.im, o2.re)};
+        v[6] = P2{sub2(e2.re, o2.im), add2(e2.im, o2.re)};
+    }
+    v[3] = padd(e3, o3);
+    v[7] = psub(e3, o3);
+}
+
+// Shared slots of a pair of transforms: element n at a[fft_pad(n) * cs] as
+// one float4 (re_0, re_1, im_0, im_1), the second buffer `alt` float4 further.
+struct FftSlots2 {
+    float4* a;
+    int cs, alt;
+};
+__device__ __forceinline__ float4 p2_pack(P2 v) { return make_float4(v.re.x, v.re.y, v.im.x, v.im.y); }
+__device__ __forceinline__ P2 p2_unpack(float4 q) { return P2{make_float2(q.x, q.y), make_float2(q.z, q.w)}; }
+
+// fft_core for two FP32 transforms: load(k, n) returns their input element
+// n = t + k N / 8 as a P2, store(q, n, v) receives output element n.
+template <bool INV, int LOGN, typename Load, typename Store>
+__device__ __forceinline__ void fft_core2(int t, const float2* __restrict__ tw, Load load, Store store, FftSlots2 s) {
+    constexpr int N = 1 << LOGN, N8 = N >> 3;
+    constexpr int R0 = (LOGN % 3 == 0) ? 8 : (LOGN % 3 == 1 ? 2 : 4);
+    constexpr int LR0 = R0 == 8 ? 3 : (R0 == 4 ? 2 : 1);
+    constexpr int NST = (LOGN - LR0) / 3;
+    static_assert(LOGN >= 4 && LOGN <= 13, "FFT length out of range");
+    const int cs = s.cs;
+    const bool pp = s.alt != 0;
+    P2 v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = load(k, t + k * N8);
+    float4* const b0 = s.a;
+    if constexpr (R0 == 8) {
+        pdft8<INV>(v);
+        float4* const o = b0 + 9 * t * cs;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) o[q * cs] = p2_pack(v[q]);
+    } else if constexpr (R0 == 4) {
+        pdft4<INV>(v[0], v[2], v[4], v[6]);
+        pdft4<INV>(v[1], v[3], v[5], v[7]);
+        float4* const o = b0 + (4 * t + (t >> 1)) * cs;
+        constexpr int J1 = fft_pad(4 * N8);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            o[q * cs] = p2_pack(v[2 * q]);
+            o[(J1 + q) * cs] = p2_pack(v[2 * q + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const P2 a = v[m], b = v[m + 4];
+            const int n0 = (t + m * N8) * 2;
+            b0[fft_pad(n0) * cs] = p2_pack(padd(a, b));
+            b0[fft_pad(n0 + 1) * cs] = p2_pack(psub(a, b));
+        }
+    }
+#pragma unroll
+    for (int st = 0; st < NST; ++st) {
+        const int Ns = R0 << (3 * st);
+        const float4* const src = (pp && (st & 1)) ? b0 + s.alt : b0;
+        float4* const dst = (pp && !(st & 1)) ? b0 + s.alt : b0;
+        __syncthreads();
+        const int kk = t & (Ns - 1);
+        if constexpr (N8 % 8 == 0) {
+            const float4* const i0 = src + fft_pad(t) * cs;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = p2_unpack(i0[k * fft_pad(N8) * cs]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = p2_unpack(src[fft_pad(t + k * N8) * cs]);
+        }
+        // W^{k ts}, k = 1..7, from three table entries and four products
+        // (the same products as the one-transform core), broadcast to both lanes
+        const int ts = kk * (N8 / Ns);
+        float2 wr[8], wi[8];
+        {
+            const float2 a = tw[ts], b = tw[2 * ts], c = tw[4 * ts];
+            wr[1] = bc2(a.x); wi[1] = bc2(a.y);
+            wr[2] = bc2(b.x); wi[2] = bc2(b.y);
+            wr[4] = bc2(c.x); wi[4] = bc2(c.y);
+        }
+        auto wmul = [&](int a, int b, int o) {
+            // (wr[a] + i wi[a]) (wr[b] + i wi[b])
+            wr[o] = __ffma2_rn(wr[a], wr[b], __fmul2_rn(wi[a], make_float2(-wi[b].x, -wi[b].y)));
+            wi[o] = __ffma2_rn(wr[a], wi[b], __fmul2_rn(wi[a], wr[b]));
+        };
+        wmul(1, 2, 3);
+        wmul(1, 4, 5);
+        wmul(2, 4, 6);
+        wmul(3, 4, 7);
+#pragma unroll
+        for (int k = 1; k < 8; ++k) v[k] = pmul<INV>(v[k], wr[k], wi[k]);
+        pdft8<INV>(v);
+        if (st == NST - 1) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) store(q, t + q * N8, v[q]);
+        } else {
+            if (!pp) __syncthreads();
+            const int base = (t - kk) * 8 + kk;
+            if (Ns % 8 == 0) {
+                float4* const o = dst + fft_pad(base) * cs;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) o[q * fft_pad(Ns) * cs] = p2_pack(v[q]);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 8; ++q) dst[fft_pad(base + q * Ns) * cs] = p2_pack(v[q]);
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------ row passes
 // Row kernels: a block holds rb transforms of length Kx = 2^LX, thread
-// (f, t) = (tid / (Kx/8), tid mod (Kx/8)); row f's slots start at
-// f * pad(Kx), its second buffer (alt > 0) rb * pad(Kx) further.
-//
+// (f, t) = (tid / (Kx/8), tid mod (Kx/8)) runs row f, whose slots start at
+// f * pad(Kx); the second buffer (alt > 0) follows the first. (Rows keep one
+// transform per thread: the forward pass carries the CG vector updates and
+// the inverse pass the dot products, per-pixel work that wants the threads.)
+template <int N8> __device__ __forceinline__ void row_thread(int rb, int& i, int& t, int& f) {
+    f = threadIdx.x / N8;
+    t = threadIdx.x - f * N8;
+    i = blockIdx.x * rb + f;
+}
+
 // S Z and the forward row FFT: rows [i0, i0+rb) of the image to rows[i][0..Kx).
 // With a CG fold (fold.x set) the input is the residual r after the step's
 // update (see CgFold), not x. When zero_grid != null block b also clears rows
@@ -236,64 +414,72 @@ __global__ void __launch_bounds__(1024) k_rows_fwd(const T* __restrict__ x, type
     if (first && blockIdx.x == 0 && threadIdx.x == 0) fold.flags[F_CGDONE] = 0;   // the next kernels read it
     extern __shared__ __align__(16) unsigned char smem_raw[];
     if (zero_grid) {
-        const int per = Ky / gridDim.x;   // whole rows per block (Ky is a multiple of the block count)
-        C* g = zero_grid + (size_t)blockIdx.x * per * Kx;
-        for (int t = threadIdx.x; t < per * Kx; t += blockDim.x) g[t] = cmake<C>(T(0), T(0));
+        // whole rows per block (Ky is a multiple of the block count), in
+        // 16-byte stores
+        const int per = Ky / gridDim.x;
+        float4* g = reinterpret_cast<float4*>(zero_grid + (size_t)blockIdx.x * per * Kx);
+        const int n16 = per * Kx * (int)sizeof(C) / 16;
+        for (int t = threadIdx.x; t < n16; t += blockDim.x) g[t] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
-    const int f = threadIdx.x / N8, t = threadIdx.x - f * N8;
-    C* buf = reinterpret_cast<C*>(smem_raw) + f * fft_padded(Kx);
-    const int i = blockIdx.x * rb + f;
-    const T rs = sy[i] * scale;
-    const size_t row0 = (size_t)i * nx;
-    auto load = [&](int k, int p1) -> C {
-        // pixel column j with (j - nx/2) mod Kx == p1 (p1 < Kx/2 exactly when k < 4)
+    int i0, t, f;
+    row_thread<N8>(rb, i0, t, f);
+    // S Z of pixel p1 of image row i (p1 < Kx/2 exactly when k < 4)
+    auto pix = [&](int i, int k, int p1) -> T {
+        // pixel column j with (j - nx/2) mod Kx == p1
         const int j = (k < 4 ? p1 : p1 - Kx) + nx / 2;
-        T val = T(0);
-        if (j >= 0 && j < nx) {
-            const size_t idx = row0 + j;
-            T xv;
-            if (fold.x) {
-                // Chronopoulos-Gear update, then the transform of the new r
-                T rv = fr[idx];
-                if (first) {
-                    if (fadd) {
-                        rv += fadd[idx];
-                        fr[idx] = rv;
-                    }
-                    pdir[idx] = T(0);
-                    fs[idx] = T(0);
-                } else if (pending) {
-                    const T pv = rv + cbeta * pdir[idx];
-                    const T sv = fu[idx] + cbeta * fs[idx];
-                    pdir[idx] = pv;
-                    fs[idx] = sv;
-                    fx[idx] += alpha * pv;
-                    rv = rv - alpha * sv;
+        if (j < 0 || j >= nx) return T(0);
+        const size_t idx = (size_t)i * nx + j;
+        T xv;
+        if (fold.x) {
+            // Chronopoulos-Gear update, then the transform of the new r
+            T rv = fr[idx];
+            if (first) {
+                if (fadd) {
+                    rv += fadd[idx];
                     fr[idx] = rv;
                 }
-                xv = rv;
-            } else {
-                xv = x[idx];
+                pdir[idx] = T(0);
+                fs[idx] = T(0);
+            } else if (pending) {
+                const T pv = rv + cbeta * pdir[idx];
+                const T sv = fu[idx] + cbeta * fs[idx];
+                pdir[idx] = pv;
+                fs[idx] = sv;
+                fx[idx] += alpha * pv;
+                rv = rv - alpha * sv;
+                fr[idx] = rv;
             }
-            val = xv * sx[j] * rs;
+            xv = rv;
+        } else {
+            xv = x[idx];
         }
-        return cmake<C>(val, T(0));
+        return xv * sx[j] * (sy[i] * scale);
     };
-    C* const out = rows + (size_t)i * Kx;
+    C* buf = reinterpret_cast<C*>(smem_raw) + f * fft_padded(Kx);
+    C* const out = rows + (size_t)i0 * Kx;
+    auto load = [&](int k, int p1) -> C { return cmake<C>(pix(i0, k, p1), T(0)); };
     auto store = [&](int, int k, C v) { out[k] = v; };
     fft_core<C, false, LX>(t, tw, load, store, FftSlots<C>{buf, 1, alt});
     pdl_trigger();
 }
 
-// Column kernels: a block holds cb adjacent columns of length Ky = 2^LY,
-// thread (t, f) = (tid / cb, tid mod cb) so that a warp's global accesses
-// cover cb consecutive cells of each row; element n of column f sits in
-// shared slot pad(n) * cb + f, its second buffer (alt > 0) cb * pad(Ky)
-// further.
-//
+// Column kernels: a block holds cb adjacent columns of length Ky = 2^LY.
+// With W = 1 thread (t, f) = (tid / cb, tid mod cb) runs column f, element
+// n in shared slot pad(n) * cb + f; with W = 2 (FP32) thread
+// (t, f) = (tid / (cb/2), tid mod (cb/2)) runs columns 2f and 2f + 1 as one
+// pair with 16-byte global accesses, element n in float4 slot
+// pad(n) * (cb/2) + f. A warp's global accesses cover consecutive cells of
+// each row. The second buffer (alt > 0) follows the first.
+template <int W> __device__ __forceinline__ void col_thread(int cb, int& c0, int& t, int& f) {
+    const int cp = cb / W;
+    t = threadIdx.x / cp;
+    f = threadIdx.x - t * cp;
+    c0 = blockIdx.x * cb + W * f;
+}
+
 // Forward column FFT over columns [c0, c0+cb): the only non-zero grid rows
 // are p2 = (i - ny/2) mod Ky for image rows i.
-template <typename T, int LY>
+template <typename T, int LY, int W>
 __global__ void __launch_bounds__(1024) k_cols_fwd(const typename cplx_of<T>::type* __restrict__ rows,
                            typename cplx_of<T>::type* __restrict__ grid,
                            const typename cplx_of<T>::type* __restrict__ tw, int ny, int Kx,
@@ -303,22 +489,40 @@ __global__ void __launch_bounds__(1024) k_cols_fwd(const typename cplx_of<T>::ty
     pdl_wait();
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
-    const int t = threadIdx.x / cb, f = threadIdx.x - t * cb;
-    const int c = blockIdx.x * cb + f;
-    auto load = [&](int k, int n) -> C {
-        // grid row n < Ky/2 exactly when k < 4
+    int c, t, f;
+    col_thread<W>(cb, c, t, f);
+    // image row of grid row n (n < Ky/2 exactly when k < 4), or -1
+    auto src_row = [&](int k, int n) -> int {
         const int i = (k < 4 ? n : n - Ky) + ny / 2;
-        return (i >= 0 && i < ny) ? rows[(size_t)i * Kx + c] : cmake<C>(T(0), T(0));
+        return (i >= 0 && i < ny) ? i : -1;
     };
-    auto store = [&](int, int k, C v) { grid[(size_t)k * Kx + c] = v; };
-    fft_core<C, false, LY>(t, tw, load, store, FftSlots<C>{buf + f, cb, alt});
+    if constexpr (W == 1) {
+        C* buf = reinterpret_cast<C*>(smem_raw);
+        auto load = [&](int k, int n) -> C {
+            const int i = src_row(k, n);
+            return i >= 0 ? rows[(size_t)i * Kx + c] : cmake<C>(T(0), T(0));
+        };
+        auto store = [&](int, int k, C v) { grid[(size_t)k * Kx + c] = v; };
+        fft_core<C, false, LY>(t, tw, load, store, FftSlots<C>{buf + f, cb, alt});
+    } else {
+        float4* buf = reinterpret_cast<float4*>(smem_raw);
+        auto load = [&](int k, int n) -> P2 {
+            const int i = src_row(k, n);
+            if (i < 0) return P2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+            const float4 q = *reinterpret_cast<const float4*>(rows + (size_t)i * Kx + c);
+            return P2{make_float2(q.x, q.z), make_float2(q.y, q.w)};
+        };
+        auto store = [&](int, int k, P2 v) {
+            *reinterpret_cast<float4*>(grid + (size_t)k * Kx + c) = make_float4(v.re.x, v.im.x, v.re.y, v.im.y);
+        };
+        fft_core2<false, LY>(t, tw, load, store, FftSlots2{buf + f, cb / 2, alt / 2});
+    }
     pdl_trigger();
 }
 
 // Inverse column FFT over columns [c0, c0+cb) (grid optionally multiplied
 // elementwise by `mult` first), keeping only the image rows.
-template <typename T, int LY>
+template <typename T, int LY, int W>
 __global__ void __launch_bounds__(1024) k_cols_inv(const typename cplx_of<T>::type* __restrict__ grid,
                            typename cplx_of<T>::type* __restrict__ rows,
                            const typename cplx_of<T>::type* __restrict__ tw, int ny, int Kx,
@@ -328,20 +532,44 @@ __global__ void __launch_bounds__(1024) k_cols_inv(const typename cplx_of<T>::ty
     pdl_wait();
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
-    const int t = threadIdx.x / cb, f = threadIdx.x - t * cb;
-    const int c = blockIdx.x * cb + f;
-    auto load = [&](int, int k) -> C {
-        const size_t g = (size_t)k * Kx + c;
-        C v = grid[g];
-        if (mult) v = cscale(v, mult[g]);
-        return v;
-    };
-    auto store = [&](int, int p2, C v) {
+    int c, t, f;
+    col_thread<W>(cb, c, t, f);
+    // image row kept for grid row p2, or -1
+    auto dst_row = [&](int p2) -> int {
         const int i = (p2 + ny / 2) & (Ky - 1);
-        if (i < ny) rows[(size_t)i * Kx + c] = v;
+        return i < ny ? i : -1;
     };
-    fft_core<C, true, LY>(t, tw, load, store, FftSlots<C>{buf + f, cb, alt});
+    if constexpr (W == 1) {
+        C* buf = reinterpret_cast<C*>(smem_raw);
+        auto load = [&](int, int k) -> C {
+            const size_t g = (size_t)k * Kx + c;
+            C v = grid[g];
+            if (mult) v = cscale(v, mult[g]);
+            return v;
+        };
+        auto store = [&](int, int p2, C v) {
+            const int i = dst_row(p2);
+            if (i >= 0) rows[(size_t)i * Kx + c] = v;
+        };
+        fft_core<C, true, LY>(t, tw, load, store, FftSlots<C>{buf + f, cb, alt});
+    } else {
+        float4* buf = reinterpret_cast<float4*>(smem_raw);
+        auto load = [&](int, int k) -> P2 {
+            const size_t g = (size_t)k * Kx + c;
+            float4 q = *reinterpret_cast<const float4*>(grid + g);
+            if (mult) {
+                const float2 m = *reinterpret_cast<const float2*>(mult + g);
+                q = make_float4(q.x * m.x, q.y * m.x, q.z * m.y, q.w * m.y);
+            }
+            return P2{make_float2(q.x, q.z), make_float2(q.y, q.w)};
+        };
+        auto store = [&](int, int p2, P2 v) {
+            const int i = dst_row(p2);
+            if (i >= 0)
+                *reinterpret_cast<float4*>(rows + (size_t)i * Kx + c) = make_float4(v.re.x, v.im.x, v.re.y, v.im.y);
+        };
+        fft_core2<true, LY>(t, tw, load, store, FftSlots2{buf + f, cb / 2, alt / 2});
+    }
     pdl_trigger();
 }
 
@@ -362,24 +590,20 @@ __global__ void __launch_bounds__(MAXT) k_rows_inv(const typename cplx_of<T>::ty
     pdl_wait();
     if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int f = threadIdx.x / N8, t = threadIdx.x - f * N8;
-    C* buf = reinterpret_cast<C*>(smem_raw) + f * fft_padded(Kx);
-    const int i = blockIdx.x * rb + f;
-    const T rs = sy[i] * scale;
+    int i0, t, f;
+    row_thread<N8>(rb, i0, t, f);
     T dacc = 0, gacc2 = 0;   // add.out, and with the folded CG add.add (add = r, out = A r)
     const bool cg = cgf.part != nullptr;
-    const C* const in = rows + (size_t)i * Kx;
-    const size_t row0 = (size_t)i * nx;
-    auto load = [&](int, int k) -> C { return in[k]; };
-    auto store = [&](int, int p1, C v) {
+    // Z^T, S and the epilogue for element p1 of row i's transform
+    auto emit = [&](int i, int p1, T vr, T vi) {
         const int j = (p1 + nx / 2) & (Kx - 1);
         if (j >= nx) return;
-        const T s = sx[j] * rs;
-        const size_t idx = row0 + j;
+        const T s = sx[j] * (sy[i] * scale);
+        const size_t idx = (size_t)i * nx + j;
         if (out_mode == 0) {
-            reinterpret_cast<C*>(out)[idx] = cscale(v, s);
+            reinterpret_cast<C*>(out)[idx] = cmake<C>(vr * s, vi * s);
         } else {
-            T r = v.x * s;
+            T r = vr * s;
             if (add) {
                 const T a = add[idx];
                 r += add_coef * a;
@@ -389,6 +613,10 @@ __global__ void __launch_bounds__(MAXT) k_rows_inv(const typename cplx_of<T>::ty
             reinterpret_cast<T*>(out)[idx] = r;
         }
     };
+    C* buf = reinterpret_cast<C*>(smem_raw) + f * fft_padded(Kx);
+    const C* const in = rows + (size_t)i0 * Kx;
+    auto load = [&](int, int k) -> C { return in[k]; };
+    auto store = [&](int, int p1, C v) { emit(i0, p1, v.x, v.y); };
     fft_core<C, true, LX>(t, tw, load, store, FftSlots<C>{buf, 1, alt});
     if (cg) {
         // Chronopoulos-Gear partials (see CgFold): gamma = r.r, delta = r.A r;
@@ -416,25 +644,38 @@ __global__ void __launch_bounds__(1024) k_rows_full(typename cplx_of<T>::type* g
     using C = typename cplx_of<T>::type;
     constexpr int Kx = 1 << LX, N8 = Kx >> 3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int f = threadIdx.x / N8, t = threadIdx.x - f * N8;
+    int i0, t, f;
+    row_thread<N8>(rb, i0, t, f);
     C* buf = reinterpret_cast<C*>(smem_raw) + f * fft_padded(Kx);
-    C* row = grid + ((size_t)blockIdx.x * rb + f) * Kx;
+    C* row = grid + (size_t)i0 * Kx;
     auto load = [&](int, int k) -> C { return row[k]; };
     auto store = [&](int, int k, C v) { row[k] = v; };
     fft_core<C, INV, LX>(t, tw, load, store, FftSlots<C>{buf, 1, alt});
 }
 
-template <typename T, int LY, bool INV>
+template <typename T, int LY, bool INV, int W>
 __global__ void __launch_bounds__(1024) k_cols_full(typename cplx_of<T>::type* grid, const typename cplx_of<T>::type* __restrict__ tw,
                             int Kx, int cb, int alt) {
     using C = typename cplx_of<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C* buf = reinterpret_cast<C*>(smem_raw);
-    const int t = threadIdx.x / cb, f = threadIdx.x - t * cb;
-    const int c = blockIdx.x * cb + f;
-    auto load = [&](int, int k) -> C { return grid[(size_t)k * Kx + c]; };
-    auto store = [&](int, int k, C v) { grid[(size_t)k * Kx + c] = v; };
-    fft_core<C, INV, LY>(t, tw, load, store, FftSlots<C>{buf + f, cb, alt});
+    int c, t, f;
+    col_thread<W>(cb, c, t, f);
+    if constexpr (W == 1) {
+        C* buf = reinterpret_cast<C*>(smem_raw);
+        auto load = [&](int, int k) -> C { return grid[(size_t)k * Kx + c]; };
+        auto store = [&](int, int k, C v) { grid[(size_t)k * Kx + c] = v; };
+        fft_core<C, INV, LY>(t, tw, load, store, FftSlots<C>{buf + f, cb, alt});
+    } else {
+        float4* buf = reinterpret_cast<float4*>(smem_raw);
+        auto load = [&](int, int k) -> P2 {
+            const float4 q = *reinterpret_cast<const float4*>(grid + (size_t)k * Kx + c);
+            return P2{make_float2(q.x, q.z), make_float2(q.y, q.w)};
+        };
+        auto store = [&](int, int k, P2 v) {
+            *reinterpret_cast<float4*>(grid + (size_t)k * Kx + c) = make_float4(v.re.x, v.im.x, v.re.y, v.im.y);
+        };
+        fft_core2<INV, LY>(t, tw, load, store, FftSlots2{buf + f, cb / 2, alt / 2});
+    }
 }
 
 // ------------------------------------------------------------- launchers
@@ -490,18 +731,27 @@ template <typename T> static int cols_per_block(int Ky, int Kx) {
     while (cb > 1 && Kx % cb) cb >>= 1;
     return cb;
 }
-bool fft_shape_ok(int nb, int K, int dtype) {
+// nb transforms of length K per block, `lanes` of them per thread (2: the
+// packed FP32 column form, for an even nb)
+bool fft_shape_ok(int nb, int K, int dtype, int lanes) {
     const size_t cbytes = dtype == PURIFY_F32 ? 8 : 16;
-    return nb * (K / 8) <= 1024 && (size_t)nb * fft_padded(K) * cbytes <= 160 * 1024;
+    if (lanes != 1 && (lanes != 2 || dtype != PURIFY_F32 || nb % 2)) return false;
+    return nb / lanes * (K / 8) <= 1024 && (size_t)nb * fft_padded(K) * cbytes <= 160 * 1024;
 }
 
-template <typename T> static int plan_rows_per_block(purify_plan* p) {
+template <typename T> static int plan_rows_per_block(const purify_plan* p) {
     int rb = p->fft_rb > 0 ? p->fft_rb : rows_per_block<T>(p->ny, p->Kx);
     while (p->ny % rb) rb >>= 1;
     return rb;
 }
-template <typename T> static int plan_cols_per_block(purify_plan* p) {
+template <typename T> static int plan_cols_per_block(const purify_plan* p) {
     return p->fft_cb > 0 ? p->fft_cb : cols_per_block<T>(p->Ky, p->Kx);
+}
+// columns per thread: the tuned choice, else two (packed) for FP32 blocks of
+// an even number of columns
+template <typename T> static int col_lanes(int cb, int tuned) {
+    if (sizeof(T) != 4 || cb % 2) return 1;
+    return tuned > 0 ? tuned : 2;
 }
 
 template <typename T>
@@ -529,11 +779,14 @@ template <typename T> static void cols_fwd_t(purify_plan* p, const int* skip) {
     const int cb = plan_cols_per_block<T>(p);
     const int alt = fft_alt(cb, p->Ky, sizeof(C));
     const size_t sm = fft_smem(cb, p->Ky, sizeof(C), alt);
+    const int w = col_lanes<T>(cb, p->fft_cw);
     with_log2(p->Ky, [&](auto lg) {
-        auto kern = k_cols_fwd<T, decltype(lg)::value>;
+        constexpr int LY = decltype(lg)::value;
+        auto kern = k_cols_fwd<T, LY, 1>;
+        if constexpr (sizeof(T) == 4) { if (w == 2) kern = k_cols_fwd<T, LY, 2>; }
         set_fft_smem(kern, sm);
         Launch L(p, "fft_cols_fwd");
-        launch_dependent(kern, p->Kx / cb, cb * (p->Ky / 8), sm, p->stream, p->rows.as<C>(), p->grid.as<C>(),
+        launch_dependent(kern, p->Kx / cb, cb / w * (p->Ky / 8), sm, p->stream, p->rows.as<C>(), p->grid.as<C>(),
                          p->twy.as<C>(), p->ny, p->Kx, cb, alt, skip);
         L.done();
     });
@@ -546,11 +799,14 @@ template <typename T> static void cols_inv_t(purify_plan* p, const int* skip, co
     const size_t sm = fft_smem(cb, p->Ky, sizeof(C), alt);
     // the adjoint reads the gridding output; the circulant path the forward grid
     const C* src = mult ? p->grid.as<C>() : p->gacc.as<C>();
+    const int w = col_lanes<T>(cb, p->fft_cw);
     with_log2(p->Ky, [&](auto lg) {
-        auto kern = k_cols_inv<T, decltype(lg)::value>;
+        constexpr int LY = decltype(lg)::value;
+        auto kern = k_cols_inv<T, LY, 1>;
+        if constexpr (sizeof(T) == 4) { if (w == 2) kern = k_cols_inv<T, LY, 2>; }
         set_fft_smem(kern, sm);
         Launch L(p, "fft_cols_inv");
-        launch_dependent(kern, p->Kx / cb, cb * (p->Ky / 8), sm, p->stream, src, p->rows.as<C>(),
+        launch_dependent(kern, p->Kx / cb, cb / w * (p->Ky / 8), sm, p->stream, src, p->rows.as<C>(),
                          p->twy.as<C>(), p->ny, p->Kx, cb, alt, skip, (const T*)mult);
         L.done();
     });
@@ -566,8 +822,7 @@ static void rows_inv_t(purify_plan* p, void* out, double scale, int out_mode, co
     const int nt = rb * (p->Kx / 8);
     with_log2(p->Kx, [&](auto lg) {
         constexpr int LX = decltype(lg)::value;
-        // the fused epilogue needs more than 64 registers: blocks of at most
-        // 512 threads get them, 1024-thread blocks take spills
+        // blocks of at most 512 threads may take more than 64 registers
         auto kern = nt <= 512 ? k_rows_inv<T, LX, 512> : k_rows_inv<T, LX, 1024>;
         set_fft_smem(kern, sm);
         Launch L(p, "fft_rows_inv");
@@ -577,6 +832,18 @@ static void rows_inv_t(purify_plan* p, void* out, double scale, int out_mode, co
                          (T)add_coef, skip, cg ? *cg : CgFold());
         L.done();
     });
+}
+
+void fft_launch_shape(const purify_plan* p, int& rb, int& cb, int& cw) {
+    if (p->dtype == PURIFY_F32) {
+        rb = plan_rows_per_block<float>(p);
+        cb = plan_cols_per_block<float>(p);
+        cw = col_lanes<float>(cb, p->fft_cw);
+    } else {
+        rb = plan_rows_per_block<double>(p);
+        cb = plan_cols_per_block<double>(p);
+        cw = col_lanes<double>(cb, p->fft_cw);
+    }
 }
 
 int rows_inv_blocks(purify_plan* p) {
@@ -607,6 +874,7 @@ template <typename T, bool INV> static void fft2_dir(purify_plan* p, void* grid)
     const int cb = cols_per_block<T>(p->Ky, p->Kx);
     const int ar = fft_alt(rb, p->Kx, sizeof(C)), ac = fft_alt(cb, p->Ky, sizeof(C));
     const size_t smr = fft_smem(rb, p->Kx, sizeof(C), ar), smc = fft_smem(cb, p->Ky, sizeof(C), ac);
+    const int wc = col_lanes<T>(cb, 0);
     with_log2(p->Kx, [&](auto lg) {
         auto kern = k_rows_full<T, decltype(lg)::value, INV>;
         set_fft_smem(kern, smr);
@@ -615,10 +883,12 @@ template <typename T, bool INV> static void fft2_dir(purify_plan* p, void* grid)
         L.done();
     });
     with_log2(p->Ky, [&](auto lg) {
-        auto kern = k_cols_full<T, decltype(lg)::value, INV>;
+        constexpr int LY = decltype(lg)::value;
+        auto kern = k_cols_full<T, LY, INV, 1>;
+        if constexpr (sizeof(T) == 4) { if (wc == 2) kern = k_cols_full<T, LY, INV, 2>; }
         set_fft_smem(kern, smc);
         Launch L(p, "fft_full_cols");
-        kern<<<p->Kx / cb, cb * (p->Ky / 8), smc, p->stream>>>((C*)grid, p->twy.as<C>(), p->Kx, cb, ac);
+        kern<<<p->Kx / cb, cb / wc * (p->Ky / 8), smc, p->stream>>>((C*)grid, p->twy.as<C>(), p->Kx, cb, ac);
         L.done();
     });
 }

@@ -242,6 +242,7 @@ struct purify_plan {
     int grid_kind = 1;                // G^H: 1 tile subproblems, 2 run sets, 3..5 lanes, 6 deterministic
     int degrid_kind = 1;              // G: 1 tile subproblems, 3..5 lanes; autotuned
     int fft_rb = 0, fft_cb = 0;       // FFT rows / columns per block (0: heuristic)
+    int fft_cw = 0;                   // FFT columns per thread, 1 or 2 (0: 2 where the shape allows)
     // workspaces
     purify::DevBuf grid;              // Ky * Kx complex (forward transform output)
     purify::DevBuf gacc;              // Ky * Kx complex gridding output, then a 256-byte work counter
@@ -389,7 +390,9 @@ void launch_lanes_on(purify_plan* p, const LaneWork& lw, int mode, const void* y
 // lane work and chunk lists of G block groups (FP32 plans with J <= kLaneMaxJ)
 void build_group_lanes(purify_plan* p, int G);
 int grid_list_unit(int dtype, int J);
-bool fft_shape_ok(int nb, int K, int dtype);
+bool fft_shape_ok(int nb, int K, int dtype, int lanes = 1);
+// the FFT launch shape the plan's passes use
+void fft_launch_shape(const purify_plan* p, int& rows_per_block, int& cols_per_block, int& cols_per_thread);
 
 // plan-side helpers
 void build_gridlist(purify_plan* p, const std::vector<int>& bins, const std::vector<int>& cell_order, int tile,

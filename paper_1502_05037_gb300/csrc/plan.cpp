@@ -176,7 +176,7 @@ struct TuneKey {
         return std::tie(nx, ny, J, dtype, mlog, R, gm) < std::tie(o.nx, o.ny, o.J, o.dtype, o.mlog, o.R, o.gm);
     }
 };
-struct TuneVal { int tile, dtile, rb, cb, units, dunits, gkind, dkind, nkind; };
+struct TuneVal { int tile, dtile, rb, cb, cw, units, dunits, gkind, dkind, nkind; };
 static std::mutex g_tune_mutex;
 static std::map<TuneKey, TuneVal> g_tune_cache;
 
@@ -244,7 +244,7 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
     // visibilities, in batch units
     const int64_t unit = grid_list_unit(p->dtype, p->J);
     const int u0 = (int)std::max<int64_t>(1, std::min<int64_t>(16, (p->M / (152 * 4) + unit / 2) / unit));
-    TuneVal val{p->work.tile, p->work.tile, 0, 0, u0, u0, 1, 1, 2};
+    TuneVal val{p->work.tile, p->work.tile, 0, 0, 0, u0, u0, 1, 1, 2};
     bool cached = false;
     if (tune) {
         std::lock_guard<std::mutex> lk(g_tune_mutex);
@@ -274,14 +274,19 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
             if (ms < best) { best = ms; val.rb = rb; }
         }
         best = 1e30f;
+        // columns per block, and one or two (packed FP32) columns per thread
         for (int cb = 1; cb <= 8; cb *= 2) {
-            if (p->Kx % cb || !fft_shape_ok(cb, p->Ky, p->dtype)) continue;
-            p->fft_cb = cb;
-            float ms = time_ms(p, [&] { launch_cols_fwd(p, nullptr); }, 10);
-            if (ms < best) { best = ms; val.cb = cb; }
+            for (int cw = 1; cw <= 2; ++cw) {
+                if (p->Kx % cb || !fft_shape_ok(cb, p->Ky, p->dtype, cw)) continue;
+                p->fft_cb = cb;
+                p->fft_cw = cw;
+                float ms = time_ms(p, [&] { launch_cols_fwd(p, nullptr); }, 10);
+                if (ms < best) { best = ms; val.cb = cb; val.cw = cw; }
+            }
         }
         p->fft_rb = val.rb;
         p->fft_cb = val.cb;
+        p->fft_cw = val.cw;
         // gridding and degridding tiles, each timed on its own kernel
         if (cand.size() > 1 && p->M >= 32768) {
             float bg = 1e30f, bd = 1e30f;
@@ -320,6 +325,7 @@ static void autotune(purify_plan* p, const std::vector<int>& cand, BinsFor bins_
     }
     p->fft_rb = val.rb;
     p->fft_cb = val.cb;
+    p->fft_cw = val.cw;
     // a forced decomposition: grid_mode 1 and 2 degrid by tiles and apply
     // G^H G by run sets, 3..5 do all three by that lane form, 6 grids by
     // the deterministic lane pairs and degrids by the lane pairs

@@ -63,7 +63,7 @@ int main(void) {
   P(purify_sdmm_params, resume) P(purify_sdmm_params, check_every) P(purify_sdmm_params, toeplitz) P(purify_sdmm_stats, status)
   P(purify_sdmm_params, block_groups) P(purify_sdmm_params, group_seq)
   P(purify_plan_info, workspace_bytes) P(purify_plan_info, beta) P(purify_plan_info, grid_mode)
-  P(purify_plan_info, lane_tile)
+  P(purify_plan_info, lane_tile) P(purify_plan_info, fft_cols_per_thread)
   P(purify_plan_desc, grid_mode)
   return 0;
 }
@@ -91,6 +91,7 @@ int main(void) {
     assert int(got["purify_plan_desc.grid_mode"]) == _lib.purify_plan_desc.grid_mode.offset
     assert int(got["purify_plan_info.grid_mode"]) == _lib.purify_plan_info.grid_mode.offset
     assert int(got["purify_plan_info.lane_tile"]) == _lib.purify_plan_info.lane_tile.offset
+    assert int(got["purify_plan_info.fft_cols_per_thread"]) == _lib.purify_plan_info.fft_cols_per_thread.offset
     assert int(got["purify_plan_desc.block_offsets"]) == _lib.purify_plan_desc.block_offsets.offset
     assert int(got["purify_sdmm_params.resume"]) == _lib.purify_sdmm_params.resume.offset
     assert int(got["purify_sdmm_params.check_every"]) == _lib.purify_sdmm_params.check_every.offset
