@@ -11,6 +11,10 @@ table or constant generator with it.
 Modules:
   nufft       - measurement operator Phi = G F Z S, its adjoint, exact DFT model
   wavelets    - Daubechies filters, periodic 2-D DWT, SARA dictionary Psi
-  sdmm        - prox, projections, CG, SDMM iteration, reweighting, epsilon
-  primal_dual - an independent Chambolle-Pock solver used only to pin SDMM
+  sdmm        - prox, projections, CG, SDMM iteration (all blocks, or one
+                group of blocks per iteration), reweighting, epsilon
+  primal_dual - a Chambolle-Pock solver of problem (3): pins SDMM's fixed
+                point and is the oracle of the library's primal-dual solver
+  unet        - the learned warm start's network (not in the paper): forward,
+                backward and Adam in FP64
 """

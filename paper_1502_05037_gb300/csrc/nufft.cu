@@ -514,9 +514,10 @@ k_grid_sets(const typename cplx_of<T>::type* __restrict__ yin, const typename cp
 //   G^H G: y = sum_b wy[b] sum_a wx[a] X[b][a];  acc[b][a] += wx[a] wy[b] y
 //   G^H  : y = yin[idx];                          acc[b][a] += wx[a] wy[b] y
 //   G    : yout[idx] = sum_b wy[b] sum_a wx[a] X[b][a]
-// One step of the warp reads 32 / H consecutive records, two steps ahead;
-// padding records (past a run's end) get zero weights. The accumulators are
-// flushed with vector reductions after the set.
+// One step of the warp reads 32 / H consecutive records, three steps ahead
+// (with H = 2 each lane only its own axis offset); padding records (past a
+// run's end) get zero weights. The accumulators are flushed with vector
+// reductions after the set.
 enum { LANE_GG = 0, LANE_GRID = 1, LANE_DEGRID = 2 };
 
 // Shared staging of the lane kernels: per warp two buffers (current and next
