@@ -98,7 +98,7 @@ def _rank_main(rank, world, port, out):
 def test_block_sharded_iterations_equal_the_unsharded_ones():
     from oracle import sdmm
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     mp.spawn(_rank_main, args=(world, _free_port(), out), nprocs=world, join=True)
     prob = _problem()
@@ -138,7 +138,7 @@ def test_shard_driver_on_two_gloo_ranks_equals_the_unsharded_solve():
     # by the oracle, against the unsharded oracle SDMM
     from oracle import sdmm
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()
     out = mgr.dict()
     sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
     mp.spawn(_driver_rank_main, args=(world, _free_port(), out), nprocs=world, join=True)

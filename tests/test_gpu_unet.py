@@ -87,6 +87,22 @@ def test_unet_forward_matches_oracle(small_net):
     assert rel(y.cpu().numpy() - x, pred[..., 0] - x) <= 3e-2
 
 
+def test_unet_forward_matches_bf16_rounded_oracle(small_net):
+    # The oracle rounds to BF16 exactly where the CUDA path stores tensor-core
+    # operands (the input, the weights, every ReLU output; pooling, upsampling
+    # and concatenation move rounded values unchanged). What is left is FP32
+    # against FP64 accumulation, and the few BF16 roundings and ReLU or
+    # pooling choices that difference flips: each moves one activation by at
+    # most one BF16 unit (2^-8 relative), far below this bound, while a wrong
+    # tap, channel or skip connection changes the correction by O(1).
+    net, params, x, t, levels, base = small_net
+    xd = torch.from_numpy(x).to(DEV)
+    y = torch.empty_like(xd)
+    net.forward(xd, y)
+    pred, _ = un.forward(params, x[..., None].astype(np.float64), levels, base, q=bf16_round)
+    assert rel(y.cpu().numpy() - x, pred[..., 0] - x) <= 5e-3
+
+
 @pytest.mark.parametrize("rounding,tol_layer,tol_all", [("bf16", 3e-2, 1.5e-2), ("fp64", 2e-1, 5e-2)])
 def test_unet_gradients_match_oracle(small_net, rounding, tol_layer, tol_all):
     # "bf16": the oracle rounds where the CUDA path stores BF16 tensor-core
