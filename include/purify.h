@@ -25,6 +25,10 @@
  *    No exception crosses the ABI: every call returns a purify_status and, on
  *    failure, leaves a message for purify_last_error() (thread-local).
  *  - A plan is not thread-safe; use one plan per host thread and stream.
+ *  - A plan belongs to the CUDA device that is current when it is created
+ *    (its tables, workspaces and captured graphs live there): make that
+ *    device current before every call on the plan. Plans on different
+ *    devices of one process are independent.
  */
 #ifndef PURIFY_H
 #define PURIFY_H

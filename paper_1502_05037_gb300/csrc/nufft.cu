@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "cg.cuh"
 #include "internal.h"
@@ -937,6 +938,26 @@ template <typename K> static void set_smem(K kernel, size_t bytes) {
     if (bytes > 48 * 1024) PURIFY_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
 }
 
+// Resident blocks per SM of a persistent kernel on the current device,
+// worked out (with its shared-memory limit raised) on the first launch on
+// each device; `cache` is the caller's per-instantiation table, indexed by
+// device, 0 while unknown. Threads racing on a first launch store the same
+// value.
+template <typename K>
+static int blocks_per_sm(std::atomic<int> (&cache)[64], K kernel, int threads, size_t smem) {
+    int dev = 0;
+    PURIFY_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) throw Error{PURIFY_ECUDA, "device index out of range"};
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v == 0) {
+        set_smem(kernel, smem);
+        PURIFY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, threads, smem));
+        v = std::max(1, v);
+        cache[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
+}
+
 
 template <typename T, int J> static void degrid_tj(purify_plan* p, void* y, bool caller_order, const int* skip) {
     using C = typename cplx_of<T>::type;
@@ -1021,11 +1042,8 @@ static void grid_sets_tj(purify_plan* p, const void* y, bool caller_order, const
     if (!zeroed) PURIFY_CUDA(cudaMemsetAsync(p->gacc.p, 0, p->gacc.bytes, p->stream));
     const RunWork& rw = p->runs;
     if (rw.nsets == 0) return;
-    static int per_sm = 0;   // resident blocks per SM of this instantiation
-    if (per_sm == 0) {
-        PURIFY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_grid_sets<T, J, W, FUSED>, W * 32, 0));
-        per_sm = std::max(1, per_sm);
-    }
+    static std::atomic<int> occ[64];   // resident blocks per SM of this instantiation, per device
+    const int per_sm = blocks_per_sm(occ, k_grid_sets<T, J, W, FUSED>, W * 32, 0);
     int sms = 0, dev = 0;
     PURIFY_CUDA(cudaGetDevice(&dev));
     PURIFY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1046,12 +1064,8 @@ template <int J, int MODE, int H, bool DET>
 static void lane_launch(purify_plan* p, const LaneWork& lw, const void* yin, void* yout, bool caller_order,
                         const int* skip, float2* out, int64_t dstride) {
     const size_t lane_smem = 4 * LaneStage<J, H>::bytes_per_warp;
-    static int per_sm = 0;   // resident blocks per SM of this instantiation
-    if (per_sm == 0) {
-        set_smem(k_lane<J, MODE, H, DET>, lane_smem);
-        PURIFY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lane<J, MODE, H, DET>, 128, lane_smem));
-        per_sm = std::max(1, per_sm);
-    }
+    static std::atomic<int> occ[64];   // resident blocks per SM of this instantiation, per device
+    const int per_sm = blocks_per_sm(occ, k_lane<J, MODE, H, DET>, 128, lane_smem);
     int sms = 0, dev = 0;
     PURIFY_CUDA(cudaGetDevice(&dev));
     PURIFY_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -162,11 +163,16 @@ static size_t conv_smem_bytes() { return sizeof(bf16) * (128 + 256) * CONV_KC + 
 void conv_tc_launch(const ConvArgs& a, cudaStream_t st) {
     if (a.Npad < 16 || a.Npad > 256 || a.Npad % 16 || a.Cinp % 16 || (a.k != 1 && a.k != 3))
         throw Error{PURIFY_EINVAL, "conv: unsupported shape"};
-    static bool attr = false;
+    // the shared-memory limit is a per-device setting: raised on the first
+    // launch on each device (threads racing on it set the same value)
+    static std::atomic<bool> attr[64];
     const size_t sm = conv_smem_bytes();
-    if (!attr) {
+    int dev = 0;
+    PURIFY_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) throw Error{PURIFY_ECUDA, "device index out of range"};
+    if (!attr[dev].load(std::memory_order_relaxed)) {
         PURIFY_CUDA(cudaFuncSetAttribute(k_conv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        attr = true;
+        attr[dev].store(true, std::memory_order_relaxed);
     }
     const int npix = a.B * a.H * a.W;
     k_conv_tc<<<(npix + 127) / 128, 128, sm, st>>>(a);
