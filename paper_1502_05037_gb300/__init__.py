@@ -39,6 +39,32 @@ def _ptr(a) -> int | None:
     raise TypeError(f"unsupported array type {type(a)}")
 
 
+def _nbytes(a) -> int | None:
+    if isinstance(a, np.ndarray):
+        return a.nbytes
+    if hasattr(a, "numel") and hasattr(a, "element_size"):
+        return a.numel() * a.element_size()
+    return None
+
+
+def _need(plan, a, values, name: str, cplx: bool = False):
+    """The C calls take raw pointers and cannot see the caller's buffer
+    sizes: refuse a buffer smaller than the `values` real (or complex)
+    elements of the plan's precision that the call reads or writes, instead
+    of letting the device touch memory past its end."""
+    if a is None:
+        return
+    have = _nbytes(a)
+    need = int(values) * (4 if plan.dtype == PURIFY_F32 else 8) * (2 if cplx else 1)
+    if have is not None and have < need:
+        raise ValueError(f"{name} holds {have} bytes; this plan's call needs {need}")
+
+
+def _need_eps(plan, eps):
+    if eps is not None and np.asarray(eps).size < plan.info.R:
+        raise ValueError(f"eps needs one bound per block ({plan.info.R})")
+
+
 def _stream_ptr(stream) -> int | None:
     if stream is None:
         return None
@@ -100,27 +126,38 @@ def purify_plan_destroy(plan: Plan):
 
 
 def purify_phi(plan: Plan, x, y):
+    _need(plan, x, plan.info.N, "x")
+    _need(plan, y, plan.info.M, "y", cplx=True)
     check(load().purify_phi(plan.handle, _ptr(x), _ptr(y)))
 
 
 def purify_phi_adj(plan: Plan, y, x):
+    _need(plan, y, plan.info.M, "y", cplx=True)
+    _need(plan, x, plan.info.N, "x", cplx=True)
     check(load().purify_phi_adj(plan.handle, _ptr(y), _ptr(x)))
 
 
 def purify_phi_normal(plan: Plan, x, out):
     """out = Re Phi^H Phi x (real images), the solver's normal operator."""
+    _need(plan, x, plan.info.N, "x")
+    _need(plan, out, plan.info.N, "out")
     check(load().purify_phi_normal(plan.handle, _ptr(x), _ptr(out)))
 
 
 def purify_fft2(plan: Plan, grid, inverse: bool = False):
+    _need(plan, grid, plan.info.Kx * plan.info.Ky, "grid", cplx=True)
     check(load().purify_fft2(plan.handle, _ptr(grid), int(bool(inverse))))
 
 
 def purify_psi(plan: Plan, c, x):
+    _need(plan, c, plan.info.D, "c")
+    _need(plan, x, plan.info.N, "x")
     check(load().purify_psi(plan.handle, _ptr(c), _ptr(x)))
 
 
 def purify_psi_adj(plan: Plan, x, c):
+    _need(plan, x, plan.info.N, "x")
+    _need(plan, c, plan.info.D, "c")
     check(load().purify_psi_adj(plan.handle, _ptr(x), _ptr(c)))
 
 
@@ -143,6 +180,10 @@ def purify_sdmm_solve(plan: Plan, y, eps, x, w=None, max_iter=200, cg_iters=10, 
     """Solve problem (3); x is updated in place. Returns purify_sdmm_stats.
     block_groups / group_seq: stochastic block-subset iterations (group_seq
     holds max_iter group indices)."""
+    _need(plan, y, plan.info.M, "y", cplx=True)
+    _need(plan, w, plan.info.D, "w")
+    _need(plan, x, plan.info.N, "x")
+    _need_eps(plan, eps)
     eps_np = None
     eps_ptr = None
     if eps is not None:
@@ -165,6 +206,10 @@ def purify_sdmm_solve(plan: Plan, y, eps, x, w=None, max_iter=200, cg_iters=10, 
 def purify_pd_solve(plan: Plan, y, eps, x, w=None, iters=200, tau=0.0, sigma=0.0, nu=0.0):
     """Primal-dual (Chambolle-Pock) iterations for problem (3); x is updated
     in place. Returns purify_sdmm_stats."""
+    _need(plan, y, plan.info.M, "y", cplx=True)
+    _need(plan, w, plan.info.D, "w")
+    _need(plan, x, plan.info.N, "x")
+    _need_eps(plan, eps)
     eps_np = np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
     prm = purify_pd_params(iters=iters, tau=tau, sigma=sigma, nu=nu)
     st = purify_sdmm_stats()
@@ -224,10 +269,13 @@ def purify_batch_destroy(batch: Batch):
 
 
 def purify_reweight(plan: Plan, x, rho: float, w):
+    _need(plan, x, plan.info.N, "x")
+    _need(plan, w, plan.info.D, "w")
     check(load().purify_reweight(plan.handle, _ptr(x), float(rho), _ptr(w)))
 
 
 def purify_coef_std(plan: Plan, x) -> float:
+    _need(plan, x, plan.info.N, "x")
     out = C.c_double()
     check(load().purify_coef_std(plan.handle, _ptr(x), C.byref(out)))
     return out.value
